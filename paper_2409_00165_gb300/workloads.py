@@ -1,0 +1,148 @@
+"""Seeded synthetic workloads for FOS (arxiv 2409.00165): inputs only.
+
+This module builds the inputs of the five standard workloads as NumPy arrays in
+the layouts of the C-ABI (include/fos.h).  It holds none of the method's
+arithmetic (no Mie theory, no effective medium, no photon transport): only
+wavelength grids, synthetic material indices and seeded design draws.  Both the
+CUDA path and the CPU oracle take their inputs from here.
+
+The paper's own material files (BaSO4, TiO2, acrylic, ...) are not available, so
+the materials are closed-form stand-ins:
+  * particle: Cauchy n = 2.5 + 0.05/lambda^2 (lambda in um), k = 0.5 below
+    0.4 um and 1e-4 from 0.4 um on (a TiO2-like absorption edge);
+  * matrix: n = 1.48, k = 1e-5 * lambda (an acrylic-like weakly absorbing binder).
+Layer index arrays are laid out per group g = stack * max_layers + layer.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Photon budgets and sizes of the standard workloads.
+PAINT_N_WL = 400          # full-spectrum paint layer
+STACK_N_DESIGNS = 64      # uneven multilayer batch
+STACK_N_WL = 200
+SWEEP_N_WL = 300          # surrogate design sweep
+
+
+def wavelengths(n: int, lo: float = 0.3, hi: float = 2.5) -> np.ndarray:
+    """Uniform vacuum-wavelength grid in um, both ends included."""
+    return np.linspace(lo, hi, n)
+
+
+def particle_index(wl: np.ndarray) -> np.ndarray:
+    wl = np.asarray(wl, dtype=np.float64)
+    n = 2.5 + 0.05 / (wl * wl)
+    k = np.where(wl < 0.4, 0.5, 1e-4)
+    return n + 1j * k
+
+
+def matrix_index(wl: np.ndarray) -> np.ndarray:
+    wl = np.asarray(wl, dtype=np.float64)
+    return 1.48 + 1j * (1e-5 * wl)
+
+
+# --------------------------------------------------------------------------------
+# Single slab with given optical properties (no Mie): 0.5 mm, mu_s = 10/mm,
+# mu_a = 0.1/mm, g = 0.7, n = 1.5 in air, 1e5 photons, seed 1.
+# --------------------------------------------------------------------------------
+def single_slab(n_photons: int = 100000, seed: int = 1, mu_s: float = 10.0,
+                mu_a: float = 0.1, g: float = 0.7, n: float = 1.5, d: float = 0.5,
+                n_above: float = 1.0, n_below: float = 1.0) -> dict:
+    return dict(n_stacks=1, n_wl=1, max_layers=1,
+                n_layers=np.array([1], np.int32),
+                mu_s=np.array([mu_s]), mu_a=np.array([mu_a]), g=np.array([g]),
+                n_layer=np.array([n]), thickness=np.array([d]),
+                n_above=np.array([n_above]), n_below=np.array([n_below]),
+                substrate_R=None, n_photons=None, photons_per_item=int(n_photons),
+                photon_first=None, item_list=None, seed=int(seed), item_id_base=0,
+                max_events=0)
+
+
+# --------------------------------------------------------------------------------
+# Particle media described for Mie + effective medium, then photon transport.
+# --------------------------------------------------------------------------------
+def _media(wl, radius, vol_frac, thickness, n_layers, max_layers):
+    """Species/group tables for stacks whose layers hold one particle species each.
+
+    radius, vol_frac, thickness: [n_stacks, max_layers]; n_layers: [n_stacks].
+    """
+    n_stacks = len(n_layers)
+    n_wl = len(wl)
+    n_groups = n_stacks * max_layers
+    nm = np.broadcast_to(matrix_index(wl), (n_groups, n_wl)).copy()
+    sg, rad, vf = [], [], []
+    for s in range(n_stacks):
+        for j in range(int(n_layers[s])):
+            sg.append(s * max_layers + j)
+            rad.append(radius[s, j])
+            vf.append(vol_frac[s, j])
+    n_species = len(sg)
+    n_p = np.broadcast_to(particle_index(wl), (n_species, n_wl)).copy()
+    return dict(wl=np.asarray(wl, np.float64), n_groups=n_groups, nm=nm,
+                species_group=np.array(sg, np.int32), n_p=n_p,
+                radius=np.array(rad, np.float64), vol_frac=np.array(vf, np.float64),
+                thickness=np.asarray(thickness, np.float64).reshape(-1),
+                n_layers=np.asarray(n_layers, np.int32), n_stacks=n_stacks,
+                max_layers=max_layers, n_wl=n_wl)
+
+
+def paint_layer(n_wl: int = PAINT_N_WL, photons: int = 1000000, seed: int = 1,
+                radius: float = 0.2, vol_frac: float = 0.10,
+                thickness: float = 300.0) -> dict:
+    """Full-spectrum paint layer: one 300 um layer, r = 0.2 um, f = 0.10, air both sides."""
+    wl = wavelengths(n_wl)
+    m = _media(wl, np.array([[radius]]), np.array([[vol_frac]]), np.array([[thickness]]),
+               np.array([1]), 1)
+    m.update(photons_per_item=int(photons), n_photons=None, substrate_R=None,
+             seed=int(seed))
+    return m
+
+
+def layer_stacks(n_designs: int = STACK_N_DESIGNS, n_wl: int = STACK_N_WL, seed: int = 3,
+                 substrate_R: float = 0.05, photons_lo: float = 1e4,
+                 photons_hi: float = 1e6) -> dict:
+    """Uneven batch of 1-3 layer stacks on an opaque reflector.
+
+    Per layer r ~ U(0.05, 1) um, f ~ U(0.01, 0.3), d ~ U(10, 500) um; photon budgets
+    round(10^U(log10 lo, log10 hi)) per (design, wavelength); numpy default_rng(seed).
+    """
+    rng = np.random.default_rng(seed)
+    max_layers = 3
+    n_layers = rng.integers(1, 4, size=n_designs)
+    radius = rng.uniform(0.05, 1.0, size=(n_designs, max_layers))
+    vol_frac = rng.uniform(0.01, 0.3, size=(n_designs, max_layers))
+    thickness = rng.uniform(10.0, 500.0, size=(n_designs, max_layers))
+    wl = wavelengths(n_wl)
+    m = _media(wl, radius, vol_frac, thickness, n_layers, max_layers)
+    budgets = np.round(10.0 ** rng.uniform(np.log10(photons_lo), np.log10(photons_hi),
+                                           size=n_designs * n_wl)).astype(np.int64)
+    m.update(n_photons=budgets, photons_per_item=0,
+             substrate_R=np.full(n_designs * n_wl, float(substrate_R)), seed=int(seed))
+    return m
+
+
+def single_layer_designs(n_designs: int, seed: int, n_wl: int | None = SWEEP_N_WL,
+                         random_wl: bool = False) -> dict:
+    """Single-layer designs in the ranges of the multilayer batch (r, f, d).
+
+    With random_wl, each design gets one wavelength drawn from U(0.3, 2.5) um (the
+    surrogate training set); otherwise every design uses the n_wl-point grid.
+    """
+    rng = np.random.default_rng(seed)
+    radius = rng.uniform(0.05, 1.0, size=n_designs)
+    vol_frac = rng.uniform(0.01, 0.3, size=n_designs)
+    thickness = rng.uniform(10.0, 500.0, size=n_designs)
+    if random_wl:
+        wl = rng.uniform(0.3, 2.5, size=n_designs)
+    else:
+        wl = wavelengths(n_wl)
+    return dict(radius=radius, vol_frac=vol_frac, thickness=thickness, wl=wl,
+                random_wl=bool(random_wl))
+
+
+def media_arrays(m: dict) -> dict:
+    """Matrix and particle indices split into real and imaginary parts."""
+    return dict(nm_re=np.ascontiguousarray(m["nm"].real.reshape(-1)),
+                nm_im=np.ascontiguousarray(m["nm"].imag.reshape(-1)),
+                np_re=np.ascontiguousarray(m["n_p"].real.reshape(-1)),
+                np_im=np.ascontiguousarray(m["n_p"].imag.reshape(-1)))
