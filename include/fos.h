@@ -1,0 +1,200 @@
+/*
+ * fos.h - C ABI of libfos: the GB300 hot path of FOS (arxiv 2409.00165, "FOS: Fast
+ * Optical Spectrum calculations of nanoparticle media").
+ *
+ * The library computes the spectral reflectance, absorptance and transmittance of
+ * particle-filled layers:
+ *   fos_mie_properties  Mie theory + effective medium -> mu_s, mu_a, g per layer and
+ *                       wavelength (section "Scattering properties", Eqs. 1-20).
+ *   fos_mc_spectrum     Monte Carlo photon transport through layer stacks -> integer
+ *                       photon counts R, A, T per (stack, wavelength) (section
+ *                       "Photon transport").
+ *   fos_surrogate_*     a learned MLP that predicts R, A, T from (wavelength, n, k,
+ *                       radius, volume fraction, thickness, g, mu_s, mu_a), trained on
+ *                       spectra from fos_mc_spectrum (the paper's "machine learning
+ *                       method" of section "Photon transport").
+ *
+ * Conventions for every entry point:
+ *   - Plain C types only.  Pointers documented "device" point to CUDA device memory
+ *     of the current device; pointers documented "host" to host memory.
+ *   - The caller owns every buffer it passes.  The library owns only a per-device
+ *     workspace (work queue, status word, packed item tables, Mie scratch) that it
+ *     allocates on first use, grows when needed and frees at unload.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All device work
+ *     is ordered on it.
+ *   - Every argument is validated before results are produced.  Host-visible problems
+ *     (NULL pointers, bad sizes) return FOS_ERR_INVALID_ARG before any launch.
+ *     Values that live in device memory (NaN, negative coefficients, ...) are checked
+ *     by the first kernel of the call, which sets a device status word; the later
+ *     kernels then do no work and the call returns FOS_ERR_INVALID_ARG.
+ *   - Calls are synchronous (they wait for their stream and return the device
+ *     status) unless FOS_ASYNC is given; then the status of the work is returned by
+ *     the next fos_sync_status(stream) call.
+ *   - No call traps, asserts on the device or waits without a bound.
+ */
+#ifndef FOS_H
+#define FOS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FOS_API_VERSION 1
+
+typedef int fos_status;
+enum {
+    FOS_OK = 0,
+    FOS_ERR_INVALID_ARG = 1,   /* bad argument (host check or device validation)     */
+    FOS_ERR_CUDA = 2,          /* a CUDA runtime call failed                          */
+    FOS_ERR_NOMEM = 3,         /* workspace allocation failed                          */
+    FOS_ERR_STEP_LIMIT = 4,    /* some photon hit max_events; counted as "runaway"    */
+    FOS_ERR_TIMEOUT = 5,       /* the bounded wait for the stream ran out             */
+    FOS_ERR_OUT_OF_RANGE = 6,  /* input outside what a kernel supports (e.g. Mie order) */
+    FOS_ERR_INJECTED = 7,      /* test-only failure injected by FOS_TEST_INJECT       */
+    FOS_ERR_UNSUPPORTED = 8    /* device is not sm_103 / feature not built            */
+};
+
+/* Flags (bitwise OR). */
+#define FOS_ASYNC        0x1u  /* return after enqueueing; status via fos_sync_status  */
+#define FOS_NO_GRAPH     0x2u  /* launch kernels directly instead of a cached CUDA graph */
+#define FOS_AUTOTUNE     0x4u  /* re-run the launch autotuner for this batch shape     */
+#define FOS_TEST_INJECT  0x10000u /* test only: the first kernel reports a failure      */
+
+#define FOS_MAX_LAYERS   8     /* layers per stack                                     */
+#define FOS_NCOUNT       6     /* counts per item: R, A, T, runaway, collisions, interface events */
+#define FOS_MIE_MAX_TERMS 512  /* Mie: highest order n_max + 16 the kernel supports    */
+
+const char* fos_status_string(fos_status s);
+int fos_api_version(void);
+
+/* Waits (bounded by timeout_ms; <= 0 -> 600000) for `stream` and returns the status of
+ * the library work enqueued on the current device since the last check (FOS_ASYNC
+ * calls), then clears it. */
+fos_status fos_sync_status(void* stream, int timeout_ms);
+
+/* --------------------------------------------------------------------------------
+ * fos_mie_properties: scattering properties of particle-filled media.
+ *
+ * Follows section "Scattering properties" of arxiv 2409.00165:
+ *   size parameters x = 2 pi r n_m / lambda, y = 2 pi r n_p / lambda (Eq. 1); Mie
+ *   coefficients a_n, b_n (Eqs. 2-5) with the logarithmic derivative of psi_n(z) =
+ *   z j_n(z) from a downward recurrence in FP64; the absorbing-host geometric term
+ *   (Eq. 10, read with alpha = 4 pi r k_m / lambda); Q_ext, Q_sca (Eqs. 11-12 with
+ *   n_max = ceil(2 + |y| + 4.3 |y|^(1/3))); g_i (Eq. 15); then per group (a layer
+ *   matrix with its particles) the effective medium mu_s, mu_a (Eqs. 13-14), g (Eq.
+ *   16), negative coefficients set to 0, the dependent-scattering factor C = 1 + 1.5F
+ *   - 0.75F^2 when F = sum f > 0.08 (Eqs. 17-19) and the matrix absorption 4 pi k_m
+ *   (1 - F)/lambda (Eq. 20).
+ *
+ * Units: wavelength and radius in one length unit (um in the paper); outputs in the
+ * inverse of that unit.  All arrays are device, FP64, row-major:
+ *   wl            [n_wl]                 vacuum wavelengths, > 0
+ *   nm_re, nm_im  [n_groups*n_wl]        matrix n + ik per group (k >= 0)
+ *   species_group [n_species]            group of each particle species, non-decreasing
+ *   np_re, np_im  [n_species*n_wl]       particle n + ik (k >= 0)
+ *   radius        [n_species]            sphere radius, > 0
+ *   vol_frac      [n_species]            volume fraction in [0,1); per-group sum < 1
+ *   mu_s, mu_a, g [n_groups*n_wl]        outputs (overwritten)
+ *   q_ext, q_sca, g_species [n_species*n_wl]  optional outputs (NULL to skip)
+ * Errors: FOS_ERR_INVALID_ARG (sizes, NULL, bad values), FOS_ERR_OUT_OF_RANGE (some
+ * n_max + 16 > FOS_MIE_MAX_TERMS; outputs then undefined), FOS_ERR_CUDA.
+ * ------------------------------------------------------------------------------ */
+fos_status fos_mie_properties(int n_wl, const double* wl,
+                              int n_groups, const double* nm_re, const double* nm_im,
+                              int n_species, const int* species_group,
+                              const double* np_re, const double* np_im,
+                              const double* radius, const double* vol_frac,
+                              double* mu_s, double* mu_a, double* g,
+                              double* q_ext, double* q_sca, double* g_species,
+                              unsigned flags, void* stream);
+
+/* --------------------------------------------------------------------------------
+ * fos_mc_spectrum: Monte Carlo photon transport (section "Photon transport").
+ *
+ * An item is one (stack, wavelength) pair, item = stack * n_wl + w.  A stack is
+ * 1..max_layers homogeneous layers (layer 0 on top) between a medium above and a
+ * medium below (refractive index; default air n = 1) or an opaque specular
+ * reflector below.  Photons arrive at normal incidence on the top surface.  Only
+ * the depth z and the direction cosine mu_z are tracked.  Each photon:
+ *   1. meets the top surface: reflected with the unpolarised Fresnel reflectance
+ *      (drawn) -> R; otherwise enters layer 0 with mu_z = 1;
+ *   2. flies an optical depth tau = -ln u; inside layer j it collides after tau /
+ *      mu_t; a boundary reached first is crossed with the rest of tau carried on;
+ *   3. at a collision is absorbed with probability mu_a/mu_t -> A, else is deflected
+ *      by a Henyey-Greenstein angle (g) and a uniform azimuth;
+ *   4. at a boundary between different indices is reflected (total internal
+ *      reflection, or Fresnel draw) or refracted (Snell); leaving the top -> R,
+ *      leaving the bottom or absorbed by the reflector -> T;
+ *   5. after max_events collisions + boundary arrivals is stopped -> runaway.
+ * The walk is FP32 with a fixed operation order; random numbers come from
+ * Philox4x32-10 with key = seed and counter = (photon id, item id, event, stream),
+ * so results depend only on (seed, item id, photon id), not on launch shape, and
+ * agree bit for bit with any implementation of the same operation order.
+ *
+ * Property layout (device, FP64): layer j of stack s at wavelength w is element
+ * (s*max_layers + j)*n_wl + w of mu_s, mu_a, g, n_layer (the layout of the
+ * fos_mie_properties outputs with group = s*max_layers + j).
+ * ------------------------------------------------------------------------------ */
+typedef struct fos_mc_batch {
+    int n_stacks;                 /* >= 1                                              */
+    int n_wl;                     /* >= 1                                              */
+    int max_layers;               /* 1..FOS_MAX_LAYERS, row stride of the layer tables */
+    const int* n_layers;          /* device [n_stacks] in 1..max_layers, or NULL (= max_layers) */
+    const double* mu_s;           /* device, scattering coefficient >= 0, 1/length     */
+    const double* mu_a;           /* device, absorption coefficient >= 0, 1/length     */
+    const double* g;              /* device, HG asymmetry in (-1, 1)                   */
+    const double* n_layer;        /* device, real refractive index of the layer, > 0   */
+    const double* thickness;      /* device [n_stacks*max_layers], > 0, length         */
+    const double* n_above;        /* device [n_items] index above the stack, or NULL (= 1) */
+    const double* n_below;        /* device [n_items] index below the stack, or NULL (= 1) */
+    const double* substrate_R;    /* device [n_items] in [0,1]: opaque reflector below
+                                     (replaces n_below), or NULL (none)               */
+    const long long* n_photons;   /* device [n_items] >= 0, or NULL (= photons_per_item) */
+    long long photons_per_item;   /* used when n_photons is NULL                       */
+    const long long* photon_first;/* device [n_items] first photon id, or NULL (= 0);
+                                     first + count <= 2^32                            */
+    const int* item_list;         /* device [n_list] items to run, or NULL (all, in order) */
+    int n_list;
+    unsigned long long seed;      /* Philox key                                       */
+    unsigned int item_id_base;    /* added to the item index in the Philox counter    */
+    long long max_events;         /* per-photon cap, 1..2^32-1; 0 -> 100000000        */
+} fos_mc_batch;
+
+/* counts: device int64 [n_run * FOS_NCOUNT], n_run = n_list (item_list given) or
+ *   n_stacks*n_wl; row r holds R, A, T, runaway, collisions, interface events of the
+ *   r-th item run.  R + A + T + runaway = photons of that item exactly.  Overwritten.
+ * photon_log: optional device int32 [n_run * log_stride]: photon i of row r writes
+ *   min(collisions << 2 | outcome, 2^31-1) at r*log_stride + i (outcome 0 R, 1 A,
+ *   2 T, 3 runaway).  NULL to skip.  Requires every count <= log_stride.
+ * Returns FOS_OK, FOS_ERR_STEP_LIMIT (counts valid; some photons hit max_events),
+ * FOS_ERR_INVALID_ARG, FOS_ERR_CUDA, FOS_ERR_NOMEM, FOS_ERR_TIMEOUT, FOS_ERR_INJECTED. */
+fos_status fos_mc_spectrum(const fos_mc_batch* batch, long long* counts, int* photon_log,
+                           long long log_stride, unsigned flags, void* stream);
+
+/* Launch shape of the walk kernel: threads per block (multiple of 32, 64..1024) and
+ * photons per thread per work unit (a warp claims 32*ppt photons at a time).
+ * fos_mc_set_tuning(0, 0) returns to autotuned/default shapes. */
+fos_status fos_mc_set_tuning(int block, int photons_per_thread);
+fos_status fos_mc_get_tuning(const fos_mc_batch* batch, int* block, int* photons_per_thread);
+
+/* Times the candidate launch shapes on a capped-photon copy of `batch` and caches
+ * the fastest for batches of this shape (writes it to *block, *ppt if non-NULL). */
+fos_status fos_mc_autotune(const fos_mc_batch* batch, void* stream, int* block,
+                           int* photons_per_thread);
+
+/* --------------------------------------------------------------------------------
+ * Diagnostics of the walk's building blocks (used by the parity tests).
+ * fos_philox4x32_10: out[4i..4i+3] = Philox4x32-10(counter = ctr[4i..4i+3],
+ *   key = (k0, k1)); device uint32 arrays of 4n words (Salmon et al., SC'11).
+ * fos_walk_math_f32: for u[i] in (0,1): neg_log[i] = -ln u, cos2pi[i] = cos(2 pi u),
+ *   as the walk evaluates them (device float arrays [n]; either output may be NULL).
+ * ------------------------------------------------------------------------------ */
+fos_status fos_philox4x32_10(const unsigned* ctr, unsigned k0, unsigned k1, unsigned* out,
+                             long long n, void* stream);
+fos_status fos_walk_math_f32(const float* u, float* neg_log, float* cos2pi, long long n,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FOS_H */

@@ -1,0 +1,66 @@
+// Internal definitions shared by the libfos translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/fos.h"
+
+namespace fos {
+
+// Bits of the per-device status word written by kernels (atomicOr).
+enum : unsigned {
+    DEV_INVALID = 1u,     // a value failed validation
+    DEV_STEP_LIMIT = 2u,  // some photon reached max_events
+    DEV_INJECTED = 4u,    // FOS_TEST_INJECT
+    DEV_RANGE = 8u,       // input outside the kernel's supported range
+};
+
+// status words on the device: [0] the current call, [1] accumulated FOS_ASYNC work,
+// [2] first offending index of the current call (for diagnostics).
+enum { ST_CALL = 0, ST_ASYNC = 1, ST_INDEX = 2, ST_WORDS = 4 };
+
+struct Workspace {
+    int device = -1;
+    int num_sms = 0;
+    int cc_major = 0, cc_minor = 0;
+    unsigned* status = nullptr;             // device [ST_WORDS]
+    unsigned long long* cursor = nullptr;   // device work-queue counter(s) [4]
+    void* mc_tables = nullptr;              // packed item tables + unit prefix
+    size_t mc_bytes = 0;
+    void* mie_scratch = nullptr;            // Mie recurrence scratch + per-species Q's
+    size_t mie_bytes = 0;
+    long long* tune_counts = nullptr;       // autotuner output
+    size_t tune_bytes = 0;
+    cudaStream_t side = nullptr;            // private stream for graph capture
+    unsigned long long generation = 0;      // bumps when a table is reallocated
+};
+
+// Per-device workspace of the current device (created on first use).
+fos_status get_workspace(Workspace** ws);
+// Grows a workspace buffer to at least `bytes` (synchronous cudaMalloc).
+fos_status ensure_buffer(Workspace* ws, void** buf, size_t* cur, size_t bytes);
+
+fos_status from_cuda(cudaError_t e);
+fos_status status_from_bits(unsigned bits);
+
+// Bounded wait: polls the stream until it is idle or timeout_ms passes.
+fos_status wait_stream(cudaStream_t s, int timeout_ms);
+
+// Enqueues work that moves the call status into the accumulated async status.
+fos_status accumulate_async_status(Workspace* ws, cudaStream_t s);
+
+// Ends a call: for synchronous calls waits (bounded) and converts the status word.
+fos_status finish_call(Workspace* ws, cudaStream_t s, unsigned flags);
+
+inline int default_timeout_ms() { return 600000; }
+
+}  // namespace fos
+
+#define FOS_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) return ::fos::from_cuda(_e);  \
+    } while (0)

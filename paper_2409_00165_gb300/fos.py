@@ -1,0 +1,222 @@
+"""Thin Python binding of libfos (include/fos.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls and takes CUDA torch tensors
+(PyTorch supplies device memory and streams).  Nothing here computes: every step runs
+in the library's kernels.  If libfos.so cannot be loaded the calls raise, there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+FOS_OK = 0
+FOS_ERR_INVALID_ARG = 1
+FOS_ERR_CUDA = 2
+FOS_ERR_NOMEM = 3
+FOS_ERR_STEP_LIMIT = 4
+FOS_ERR_TIMEOUT = 5
+FOS_ERR_OUT_OF_RANGE = 6
+FOS_ERR_INJECTED = 7
+FOS_ERR_UNSUPPORTED = 8
+
+FOS_ASYNC = 0x1
+FOS_NO_GRAPH = 0x2
+FOS_AUTOTUNE = 0x4
+FOS_TEST_INJECT = 0x10000
+
+FOS_MAX_LAYERS = 8
+FOS_NCOUNT = 6
+FOS_MIE_MAX_TERMS = 512
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FosError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {fos_status_string(status)} (status {status})")
+
+
+class FosBatch(ctypes.Structure):
+    _fields_ = [
+        ("n_stacks", ctypes.c_int), ("n_wl", ctypes.c_int), ("max_layers", ctypes.c_int),
+        ("n_layers", ctypes.c_void_p),
+        ("mu_s", ctypes.c_void_p), ("mu_a", ctypes.c_void_p), ("g", ctypes.c_void_p),
+        ("n_layer", ctypes.c_void_p), ("thickness", ctypes.c_void_p),
+        ("n_above", ctypes.c_void_p), ("n_below", ctypes.c_void_p),
+        ("substrate_R", ctypes.c_void_p),
+        ("n_photons", ctypes.c_void_p), ("photons_per_item", ctypes.c_longlong),
+        ("photon_first", ctypes.c_void_p),
+        ("item_list", ctypes.c_void_p), ("n_list", ctypes.c_int),
+        ("seed", ctypes.c_ulonglong), ("item_id_base", ctypes.c_uint),
+        ("max_events", ctypes.c_longlong),
+    ]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads libfos.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError("libfos.so is missing: the CUDA path cannot run")
+            L = ctypes.CDLL(path)
+            vp, i32, i64, u32, u64 = (ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong,
+                                      ctypes.c_uint, ctypes.c_ulonglong)
+            L.fos_status_string.argtypes = [i32]
+            L.fos_status_string.restype = ctypes.c_char_p
+            L.fos_api_version.restype = i32
+            L.fos_sync_status.argtypes = [vp, i32]
+            L.fos_mie_properties.argtypes = ([i32, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp]
+                                             + [vp] * 6 + [u32, vp])
+            L.fos_mc_spectrum.argtypes = [ctypes.POINTER(FosBatch), vp, vp, i64, u32, vp]
+            L.fos_mc_set_tuning.argtypes = [i32, i32]
+            L.fos_mc_get_tuning.argtypes = [ctypes.POINTER(FosBatch), ctypes.POINTER(i32),
+                                            ctypes.POINTER(i32)]
+            L.fos_mc_autotune.argtypes = [ctypes.POINTER(FosBatch), vp, ctypes.POINTER(i32),
+                                          ctypes.POINTER(i32)]
+            L.fos_philox4x32_10.argtypes = [vp, u32, u32, vp, i64, vp]
+            L.fos_walk_math_f32.argtypes = [vp, vp, vp, i64, vp]
+            for name in ("fos_sync_status", "fos_mie_properties", "fos_mc_spectrum",
+                         "fos_mc_set_tuning", "fos_mc_get_tuning", "fos_mc_autotune",
+                         "fos_philox4x32_10", "fos_walk_math_f32"):
+                getattr(L, name).restype = i32
+            _lib = L
+    return _lib
+
+
+def fos_status_string(status: int) -> str:
+    return lib().fos_status_string(int(status)).decode()
+
+
+def check(status: int, where: str, allow=(FOS_OK,)) -> int:
+    if status not in allow:
+        raise FosError(status, where)
+    return status
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev(t, dtype, name, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+# --------------------------------------------------------------------------- Mie
+def fos_mie_properties(wl, nm_re, nm_im, species_group, np_re, np_im, radius, vol_frac,
+                       mu_s, mu_a, g, q_ext=None, q_sca=None, g_species=None, flags=0,
+                       stream=None) -> int:
+    n_wl = wl.numel()
+    n_groups = nm_re.numel() // max(n_wl, 1)
+    n_species = radius.numel() if radius is not None else 0
+    f64, i32 = torch.float64, torch.int32
+    args = [n_wl, _dev(wl, f64, "wl"), n_groups, _dev(nm_re, f64, "nm_re"),
+            _dev(nm_im, f64, "nm_im"), n_species,
+            _dev(species_group, i32, "species_group", n_species == 0),
+            _dev(np_re, f64, "np_re", n_species == 0), _dev(np_im, f64, "np_im", n_species == 0),
+            _dev(radius, f64, "radius", n_species == 0),
+            _dev(vol_frac, f64, "vol_frac", n_species == 0),
+            _dev(mu_s, f64, "mu_s"), _dev(mu_a, f64, "mu_a"), _dev(g, f64, "g"),
+            _dev(q_ext, f64, "q_ext", True), _dev(q_sca, f64, "q_sca", True),
+            _dev(g_species, f64, "g_species", True), int(flags), _stream(stream)]
+    return lib().fos_mie_properties(*args)
+
+
+# --------------------------------------------------------------------------- MC
+def make_batch(n_stacks, n_wl, max_layers, mu_s, mu_a, g, n_layer, thickness,
+               n_layers=None, n_above=None, n_below=None, substrate_R=None, n_photons=None,
+               photons_per_item=0, photon_first=None, item_list=None, seed=0,
+               item_id_base=0, max_events=0) -> FosBatch:
+    """Fills the C struct from CUDA tensors (the tensors must outlive the call)."""
+    f64, i32, i64 = torch.float64, torch.int32, torch.int64
+    b = FosBatch()
+    b.n_stacks, b.n_wl, b.max_layers = int(n_stacks), int(n_wl), int(max_layers)
+    b.n_layers = _dev(n_layers, i32, "n_layers", True)
+    b.mu_s = _dev(mu_s, f64, "mu_s")
+    b.mu_a = _dev(mu_a, f64, "mu_a")
+    b.g = _dev(g, f64, "g")
+    b.n_layer = _dev(n_layer, f64, "n_layer")
+    b.thickness = _dev(thickness, f64, "thickness")
+    b.n_above = _dev(n_above, f64, "n_above", True)
+    b.n_below = _dev(n_below, f64, "n_below", True)
+    b.substrate_R = _dev(substrate_R, f64, "substrate_R", True)
+    b.n_photons = _dev(n_photons, i64, "n_photons", True)
+    b.photons_per_item = int(photons_per_item)
+    b.photon_first = _dev(photon_first, i64, "photon_first", True)
+    b.item_list = _dev(item_list, i32, "item_list", True)
+    b.n_list = int(item_list.numel()) if item_list is not None else 0
+    b.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    b.item_id_base = int(item_id_base) & 0xFFFFFFFF
+    b.max_events = int(max_events)
+    return b
+
+
+def fos_mc_spectrum(batch: FosBatch, counts, photon_log=None, log_stride=0, flags=0,
+                    stream=None) -> int:
+    return lib().fos_mc_spectrum(ctypes.byref(batch), _dev(counts, torch.int64, "counts"),
+                                 _dev(photon_log, torch.int32, "photon_log", True),
+                                 int(log_stride), int(flags), _stream(stream))
+
+
+def fos_mc_set_tuning(block: int, photons_per_thread: int) -> int:
+    return lib().fos_mc_set_tuning(int(block), int(photons_per_thread))
+
+
+def fos_mc_get_tuning(batch: FosBatch):
+    b, p = ctypes.c_int(), ctypes.c_int()
+    check(lib().fos_mc_get_tuning(ctypes.byref(batch), ctypes.byref(b), ctypes.byref(p)),
+          "fos_mc_get_tuning")
+    return b.value, p.value
+
+
+def fos_mc_autotune(batch: FosBatch, stream=None):
+    b, p = ctypes.c_int(), ctypes.c_int()
+    check(lib().fos_mc_autotune(ctypes.byref(batch), _stream(stream), ctypes.byref(b),
+                                ctypes.byref(p)), "fos_mc_autotune")
+    return b.value, p.value
+
+
+def fos_sync_status(stream=None, timeout_ms: int = 0) -> int:
+    return lib().fos_sync_status(_stream(stream), int(timeout_ms))
+
+
+# --------------------------------------------------------------------------- diagnostics
+def fos_philox4x32_10(ctr, k0: int, k1: int, out, stream=None) -> int:
+    n = ctr.numel() // 4
+    return lib().fos_philox4x32_10(_dev(ctr, torch.int32, "ctr"), int(k0) & 0xFFFFFFFF,
+                                   int(k1) & 0xFFFFFFFF, _dev(out, torch.int32, "out"), n,
+                                   _stream(stream))
+
+
+def fos_walk_math_f32(u, neg_log=None, cos2pi=None, stream=None) -> int:
+    f32 = torch.float32
+    return lib().fos_walk_math_f32(_dev(u, f32, "u"), _dev(neg_log, f32, "neg_log", True),
+                                   _dev(cos2pi, f32, "cos2pi", True), u.numel(),
+                                   _stream(stream))

@@ -1,0 +1,82 @@
+"""Parity of the FP64 CUDA Mie + effective-medium kernels with the CPU oracle."""
+import numpy as np
+import pytest
+
+from gpu_helpers import gpu_mie
+from paper_2409_00165_gb300 import fos
+from paper_2409_00165_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+RTOL = 1e-10   # FP64 kernel vs FP64 oracle (different recurrences, same equations)
+
+
+def _oracle(orc, m):
+    return orc.mie_properties(m["wl"], m["nm"], m["species_group"], m["n_p"], m["radius"],
+                              m["vol_frac"], n_groups=m["n_groups"])
+
+
+def _close(a, b, rtol=RTOL, atol=0.0):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.all(np.abs(a - b) <= rtol * np.abs(b) + atol)
+
+
+def test_paint_layer_400_wavelengths(orc):
+    m = W.paint_layer()
+    g, o = gpu_mie(m), _oracle(orc, m)
+    for k in ("mu_s", "mu_a", "g", "q_ext", "q_sca"):
+        assert _close(g[k], o[k]), k
+    assert _close(g["g_species"], o["g_sp"])
+
+
+def test_layer_stacks_all_species(orc):
+    m = W.layer_stacks()
+    g, o = gpu_mie(m), _oracle(orc, m)
+    # groups without particles (unused layer slots) hold matrix absorption only
+    for k in ("mu_s", "mu_a", "g"):
+        assert _close(g[k], o[k], atol=1e-300), k
+    for k in ("q_ext", "q_sca"):
+        assert _close(g[k], o[k]), k
+
+
+def test_edge_sizes_and_indices(orc):
+    rng = np.random.default_rng(11)
+    wl = np.array([0.3, 0.31, 0.5, 1.0, 2.5])
+    radius = np.array([1e-3, 0.05, 0.37, 1.0, 2.5, 4.0])
+    n_sp = radius.size
+    n_p = (rng.uniform(1.05, 3.5, size=(n_sp, wl.size))
+           + 1j * rng.choice([0.0, 1e-6, 1e-2, 0.5, 2.0], size=(n_sp, wl.size)))
+    nm = np.array([[1.0 + 0j] * wl.size, [1.33 + 1e-7j] * wl.size, [1.48 + 1e-3j] * wl.size])
+    m = dict(wl=wl, nm=nm, n_groups=3, species_group=np.array([0, 0, 1, 1, 2, 2], np.int32),
+             n_p=n_p, radius=radius, vol_frac=np.array([0.01, 0.02, 0.05, 0.05, 0.1, 0.2]))
+    g, o = gpu_mie(m), _oracle(orc, m)
+    for k in ("q_ext", "q_sca", "g_species"):
+        ok = "g_sp" if k == "g_species" else k
+        assert _close(g[k], o[ok], rtol=1e-9, atol=1e-300), k
+    for k in ("mu_s", "mu_a", "g"):
+        assert _close(g[k], o[k], rtol=1e-9), k
+
+
+def test_host_at_zero_of_psi0(orc):
+    """x = 240 pi (r = 60, lambda = 0.5, n_m = 1): psi_0(x) = sin x = 0."""
+    m = dict(wl=np.array([0.5]), nm=np.array([[1.0 + 0j]]), n_groups=1,
+             species_group=np.array([0], np.int32), n_p=np.array([[1.5 + 0.01j]]),
+             radius=np.array([60.0]), vol_frac=np.array([0.1]))
+    with pytest.raises(fos.FosError):
+        gpu_mie(m)   # n_max + 16 > FOS_MIE_MAX_TERMS: reported, not computed
+    m["radius"] = np.array([10.0])  # x = 40 pi: sin x = 0 again, n_max = 215 in range
+    g, o = gpu_mie(m), _oracle(orc, m)
+    assert _close(g["q_ext"], o["q_ext"], rtol=1e-9)
+
+
+def test_invalid_and_injected():
+    m = W.paint_layer(n_wl=8)
+    m["vol_frac"] = np.array([1.2])
+    r = gpu_mie(m, allow=(fos.FOS_ERR_INVALID_ARG,))
+    assert r["status"] == fos.FOS_ERR_INVALID_ARG
+    m = W.paint_layer(n_wl=8)
+    r = gpu_mie(m, allow=(fos.FOS_ERR_INJECTED,), flags=fos.FOS_TEST_INJECT)
+    assert r["status"] == fos.FOS_ERR_INJECTED
+    r = gpu_mie(m)
+    assert r["status"] == fos.FOS_OK
