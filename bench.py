@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -215,7 +216,7 @@ def run_fos(args):
         return b
 
     # first call tunes the launch shape for this batch (synchronous, untimed)
-    b0 = step(1000, flags=fos.FOS_AUTOTUNE)
+    b0 = step(1000, flags=0 if args.no_autotune else fos.FOS_AUTOTUNE)
     tuning = fos.fos_mc_get_tuning(b0)
     for w in range(args.warmup):
         step(1001 + w)
