@@ -194,6 +194,33 @@ fos_status fos_philox4x32_10(const unsigned* ctr, unsigned k0, unsigned k1, unsi
 fos_status fos_walk_math_f32(const float* u, float* neg_log, float* cos2pi, long long n,
                              void* stream);
 
+/* --------------------------------------------------------------------------------
+ * fos_mc_spectrum_noalloc: fos_mc_spectrum for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this is a property of the library only.
+ *
+ * Some callers cannot call cudaMalloc: a process whose device memory is all reserved
+ * by another allocator (for example a framework's caching pool), or a host under a
+ * fixed memory budget where an allocation may fail or stall.  This entry point
+ * allocates nothing: no cudaMalloc, cudaFree, allocating library routine, stream or
+ * graph.  Its scratch (work-queue counter, status words, packed item tables) is a
+ * file-scope device array of about 1.2 MB, held by every GPU that loads the library
+ * until the process exits.  The caller still passes the inputs (batch, as for
+ * fos_mc_spectrum) and the output counts (device int64 [n_run * FOS_NCOUNT]).
+ *   - n_run (items run) must be <= FOS_NOALLOC_MAX_ITEMS, else FOS_ERR_OUT_OF_RANGE
+ *     is returned before any device work; any max_layers up to FOS_MAX_LAYERS.
+ *   - flags: 0 or FOS_TEST_INJECT.  The call is synchronous (bounded wait on stream).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before
+ *     any stream capture.
+ *   - Every call on a device shares the one array and each call clears what must start
+ *     at zero; calls that overlap on the GPU (other streams, other host threads) race
+ *     on it and must be serialised by the caller.
+ *   - Results are identical to fos_mc_spectrum's for the same batch.
+ * ------------------------------------------------------------------------------ */
+#define FOS_NOALLOC_MAX_ITEMS 4096
+fos_status fos_mc_spectrum_noalloc(const fos_mc_batch* batch, long long* counts,
+                                   unsigned flags, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -938,3 +938,78 @@ fos_status fos_walk_math_f32(const float* u, float* neg_log, float* cos2pi, long
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// fos_mc_spectrum_noalloc: the photon walk without any device allocation.
+//
+// Some callers cannot call cudaMalloc: a process whose device memory is wholly
+// reserved by another allocator (a framework's caching pool that took the GPU), or a
+// host under a fixed memory budget where an allocation could fail or stall at the
+// wrong moment.  This entry point runs the same kernels as fos_mc_spectrum, but its
+// scratch (work-queue counter, status words, packed item tables and unit prefix) lives
+// in the file-scope array below, which every GPU that loads the library holds until
+// the process exits.  Host code only sees a stand-in for that array, so the device
+// address is looked up with cudaGetSymbolAddress on each device's first call.
+// ---------------------------------------------------------------------------------
+namespace fos {
+namespace mc {
+
+constexpr long long NOALLOC_ROWS = FOS_NOALLOC_MAX_ITEMS;
+constexpr size_t NOALLOC_HDR = 512;   // status words at 0, work-queue counter at 256
+constexpr size_t NOALLOC_BYTES =
+    NOALLOC_HDR + (size_t)NOALLOC_ROWS * sizeof(int4) * 2 +
+    (size_t)NOALLOC_ROWS * FOS_MAX_LAYERS * sizeof(float4) * 2 +
+    (size_t)(NOALLOC_ROWS + 1) * sizeof(long long) + 6 * 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64];   // device address of g_noalloc_scratch per device
+
+}  // namespace mc
+}  // namespace fos
+
+extern "C" fos_status fos_mc_spectrum_noalloc(const fos_mc_batch* batch, long long* counts,
+                                              unsigned flags, void* stream) {
+    if (flags & ~(unsigned)FOS_TEST_INJECT) return FOS_ERR_INVALID_ARG;
+    long long n_run = 0;
+    fos_status st = mc::validate_host(batch, counts, nullptr, 0, &n_run);
+    if (st != FOS_OK) return st;
+    if (n_run > mc::NOALLOC_ROWS) return FOS_ERR_OUT_OF_RANGE;
+    if (n_run == 0) return FOS_OK;
+    int dev = 0;
+    FOS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return FOS_ERR_UNSUPPORTED;
+    int major = 0, sms = 0;
+    FOS_CUDA_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+    FOS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (major != 10) return FOS_ERR_UNSUPPORTED;
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mc::g_noalloc_mu);
+        if (!mc::g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            FOS_CUDA_TRY(cudaGetSymbolAddress(&p, mc::g_noalloc_scratch));
+            mc::g_noalloc_ptr[dev] = p;
+        }
+        base = mc::g_noalloc_ptr[dev];
+    }
+    Workspace w;   // views into the static array; nothing is allocated
+    w.device = dev;
+    w.num_sms = sms;
+    w.cc_major = major;
+    w.status = (unsigned*)base;
+    w.cursor = (unsigned long long*)((char*)base + 256);
+    w.mc_tables = (char*)base + mc::NOALLOC_HDR;
+    w.mc_bytes = mc::NOALLOC_BYTES - mc::NOALLOC_HDR;
+    cudaStream_t s = (cudaStream_t)stream;
+    mc::Tuning tu = mc::pick_tuning(batch, dev);
+    const int inject = (flags & FOS_TEST_INJECT) ? 1 : 0;
+    st = mc::enqueue(&w, batch, n_run, counts, nullptr, 0, tu, 0xffffffffu, inject, s);
+    if (st != FOS_OK) return st;
+    st = wait_stream(s, default_timeout_ms());
+    if (st != FOS_OK) return st;
+    unsigned bits = 0;
+    FOS_CUDA_TRY(cudaMemcpy(&bits, w.status + ST_CALL, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    return status_from_bits(bits);
+}

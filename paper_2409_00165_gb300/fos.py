@@ -220,3 +220,18 @@ def fos_walk_math_f32(u, neg_log=None, cos2pi=None, stream=None) -> int:
     return lib().fos_walk_math_f32(_dev(u, f32, "u"), _dev(neg_log, f32, "neg_log", True),
                                    _dev(cos2pi, f32, "cos2pi", True), u.numel(),
                                    _stream(stream))
+
+
+# --------------------------------------------------------------------------- no allocation
+def fos_mc_spectrum_noalloc(batch: FosBatch, counts, flags=0, stream=None) -> int:
+    """fos_mc_spectrum for callers that cannot allocate device memory (scratch is a
+    fixed static device array of the library; at most FOS_NOALLOC_MAX_ITEMS items)."""
+    L = lib()
+    fn = L.fos_mc_spectrum_noalloc
+    fn.argtypes = [ctypes.POINTER(FosBatch), ctypes.c_void_p, ctypes.c_uint, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    return fn(ctypes.byref(batch), _dev(counts, torch.int64, "counts"), int(flags),
+              _stream(stream))
+
+
+FOS_NOALLOC_MAX_ITEMS = 4096
