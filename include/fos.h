@@ -195,6 +195,81 @@ fos_status fos_walk_math_f32(const float* u, float* neg_log, float* cos2pi, long
                              void* stream);
 
 /* --------------------------------------------------------------------------------
+ * Surrogate of the photon walk (section "Photon transport": a network trained on Monte
+ * Carlo simulations predicts R, A, T; Table 1 lists the ranges it was trained on).
+ *
+ * Network: 9 raw features -> standardised -> [Linear 256, GELU] x 4 -> Linear 3 ->
+ * softmax = (R, A, T), summing to 1.  Products run on the tensor cores (tcgen05.mma,
+ * BF16 operands, FP32 accumulation in tensor memory); master weights and Adam state are
+ * FP32.  Features of a row (stack of one layer, wavelength): lambda, n_p, log10 k_p,
+ * radius, volume fraction, log10 thickness, g, log10(mu_s d + 1e-6), log10(mu_a d + 1e-6).
+ *
+ * Model storage: a caller-owned device buffer of n_members * fos_surrogate_model_bytes()
+ * bytes.  Member k starts at k * fos_surrogate_model_bytes(); its first
+ * fos_surrogate_param_count() floats are the FP32 parameters theta, with weight l
+ * (row-major [out][in], padded to [256][64], [256][256] x 3, [64][256]; padding is zero)
+ * at w_off[l] and bias l at b_off[l] (fos_surrogate_param_offsets).  The rest holds Adam
+ * state, BF16 copies and the feature statistics.
+ * ------------------------------------------------------------------------------ */
+size_t fos_surrogate_model_bytes(void);
+long long fos_surrogate_param_count(void);
+fos_status fos_surrogate_param_offsets(long long* w_off, long long* b_off);   /* host [5] each */
+
+/* Initialises n_members members: He-uniform weights from a hash of (seed, member,
+ * index), zero biases and Adam state.  feat_stats: host float[64] = mean[16] | std[16] |
+ * lo[16] | hi[16] of the 9 raw features (first 9 of each used; std > 0, lo <= hi);
+ * rows outside [lo, hi] are flagged for Monte Carlo by fos_surrogate_predict.
+ * Synchronous. */
+fos_status fos_surrogate_init(void* model, int n_members, unsigned long long seed,
+                              const float* feat_stats, void* stream);
+
+/* Raw features of the n_designs x n_wl rows (row = design * n_wl + w) of single-layer
+ * designs: wl [n_wl]; np_re, np_im, g, mu_s, mu_a [n_designs*n_wl] (the layout of
+ * fos_mie_properties outputs with one group per design); radius, vol_frac, thickness
+ * [n_designs].  features: device float [rows * 9].  All inputs device FP64. */
+fos_status fos_surrogate_features(int n_designs, int n_wl, const double* wl,
+                                  const double* np_re, const double* np_im,
+                                  const double* radius, const double* vol_frac,
+                                  const double* thickness, const double* g,
+                                  const double* mu_s, const double* mu_a, float* features,
+                                  unsigned flags, void* stream);
+
+/* fractions[r] = (R, A, T) / (R + A + T) of counts row r (device int64 [n*FOS_NCOUNT]
+ * -> device float [n*3]); asynchronous on stream. */
+fos_status fos_counts_to_fractions(const long long* counts, long long n_rows,
+                                   float* fractions, void* stream);
+
+/* One Adam step (lr, beta 0.9/0.999, eps 1e-8, bias-corrected with t = step + 1) of
+ * member `member` on a batch of `batch` rows (multiple of 256, <= 65536) of features
+ * [n_rows*9] / targets [n_rows*3] (device float; target rows sum to 1).  Rows are
+ * batch_rows [batch] (device int32) if given, else drawn uniformly with replacement
+ * from a hash of (seed, member, step, slot).  Loss: mean soft-label cross-entropy,
+ * written to loss_out (device float) if non-NULL.  If grad_out (device float
+ * [fos_surrogate_param_count()]) is non-NULL the gradient is written there and the
+ * parameters are NOT updated (diagnostic).  Synchronous unless FOS_ASYNC. */
+fos_status fos_surrogate_train_step(void* model, int member, const float* features,
+                                    const float* targets, long long n_rows, int batch,
+                                    const int* batch_rows, unsigned long long seed, int step,
+                                    float lr, float* loss_out, float* grad_out,
+                                    unsigned flags, void* stream);
+
+/* Ensemble prediction with members 0..n_members-1 (1..16): rat [n_rows*3] = mean of the
+ * members' (R, A, T); spread [n_rows] (or NULL) = max over R, A, T of (max - min across
+ * members); needs_mc [n_rows] (or NULL) = 1 where spread > threshold or a raw feature is
+ * outside the training range [lo, hi], else 0.  Device buffers.  Synchronous unless
+ * FOS_ASYNC. */
+fos_status fos_surrogate_predict(void* model, int n_members, const float* features,
+                                 long long n_rows, float* rat, float* spread,
+                                 unsigned char* needs_mc, float threshold, unsigned flags,
+                                 void* stream);
+
+/* Diagnostic: the surrogate's tensor-core product on its own.  C[s][M][N] (device fp32,
+ * s = 0..splits-1 partial sums over K ranges of K/splits) = A[M][K] * B[N][K]^T with A, B
+ * device BF16 row-major; K a multiple of 64*splits, N a multiple of 64.  Synchronous. */
+fos_status fos_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K,
+                         int splits, void* stream);
+
+/* --------------------------------------------------------------------------------
  * fos_mc_spectrum_noalloc: fos_mc_spectrum for callers that cannot allocate device
  * memory.  The paper has no counterpart; this is a property of the library only.
  *

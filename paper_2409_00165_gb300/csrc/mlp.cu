@@ -1,0 +1,1049 @@
+// Learned surrogate of the photon walk on GB300 (arxiv 2409.00165, section "Photon
+// transport": a network trained on Monte Carlo spectra replaces the walk).
+//
+// Network: 9 features -> standardise -> [Linear 256, GELU] x 4 -> Linear 3 -> softmax
+// (R, A, T).  BF16 weights and activations on the tensor cores, FP32 accumulation,
+// FP32 master weights and Adam state.
+//
+// Every matrix product of training and inference runs in gemm_kernel: a 128 x NT output
+// tile per CTA; K-major BF16 operands are staged by TMA (128-byte swizzle) through a
+// 4-stage mbarrier ring; one thread issues tcgen05.mma (M=128, N=NT, K=16) into FP32
+// accumulators in tensor memory; the 4 warps read the accumulators back with tcgen05.ld
+// and apply the fused epilogue of the layer (bias + GELU, softmax + cross-entropy
+// gradient, GELU derivative, or a split-K weight-gradient partial).  Transposed copies of
+// activations and gradients written by the epilogues make every product "A times B^T"
+// with both operands K-major.
+//
+// Padded shapes (zero padding, never updated): layer 0 is 256 x 64 (9 real inputs),
+// layers 1-3 are 256 x 256, layer 4 is 64 x 256 (3 real outputs).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "fos_internal.h"
+#include "sm100_ptx.cuh"
+
+namespace fos {
+namespace mlp {
+
+using namespace fos::sm100;
+typedef __nv_bfloat16 bf16;
+
+constexpr int N_LAYERS = 5;
+constexpr int HID = 256;
+constexpr int IN_PAD = 64;
+constexpr int OUT_PAD = 64;
+constexpr int N_FEAT = 9;
+constexpr int N_OUT = 3;
+constexpr int STAGES = 4;
+constexpr int BM = 128;
+constexpr int BK = 64;
+
+__host__ __device__ constexpr int lay_out(int l) { return l == 4 ? OUT_PAD : HID; }
+__host__ __device__ constexpr int lay_in(int l) { return l == 0 ? IN_PAD : HID; }
+__host__ __device__ constexpr int real_out(int l) { return l == 4 ? N_OUT : HID; }
+__host__ __device__ constexpr int real_in(int l) { return l == 0 ? N_FEAT : HID; }
+
+// ----------------------------------------------------------------------- model layout
+// Per member (all offsets in elements of the named type, from the member base):
+//   theta  fp32 [P]  : W_0 | b_0 | W_1 | b_1 | ... | W_4 | b_4  (W_l row-major [out][in])
+//   adam_m fp32 [P], adam_v fp32 [P]
+//   wb     bf16      : W_l in bf16, [out][in] per layer (forward B operands)
+//   wt     bf16      : W_l^T in bf16, [in][out] for l = 1..4 (backward B operands)
+//   stats  fp32 [64] : mean[16] | std[16] | lo[16] | hi[16] of the raw features
+//   step   int32 [4]
+struct Layout {
+    long long w_off[N_LAYERS], b_off[N_LAYERS], P;
+    long long wb_off[N_LAYERS], wt_off[N_LAYERS], n_wb, n_wt;
+    size_t theta_b, m_b, v_b, wb_b, wt_b, stats_b, step_b, bytes;
+};
+
+static Layout make_layout() {
+    Layout L;
+    long long p = 0, q = 0, t = 0;
+    for (int l = 0; l < N_LAYERS; ++l) {
+        L.w_off[l] = p;
+        p += (long long)lay_out(l) * lay_in(l);
+        L.b_off[l] = p;
+        p += lay_out(l);
+        L.wb_off[l] = q;
+        q += (long long)lay_out(l) * lay_in(l);
+        L.wt_off[l] = t;
+        if (l > 0) t += (long long)lay_out(l) * lay_in(l);
+    }
+    L.P = p;
+    L.n_wb = q;
+    L.n_wt = t;
+    auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+    size_t o = 0;
+    L.theta_b = o; o = al(o + (size_t)p * 4);
+    L.m_b = o;     o = al(o + (size_t)p * 4);
+    L.v_b = o;     o = al(o + (size_t)p * 4);
+    L.wb_b = o;    o = al(o + (size_t)q * 2);
+    L.wt_b = o;    o = al(o + (size_t)t * 2);
+    L.stats_b = o; o = al(o + 64 * 4);
+    L.step_b = o;  o = al(o + 16);
+    L.bytes = o;
+    return L;
+}
+static const Layout LAY = make_layout();
+
+struct MemberPtrs {
+    float *theta, *m, *v, *stats;
+    bf16 *wb, *wt;
+    int* step;
+};
+static MemberPtrs member(void* model, int k) {
+    char* base = (char*)model + (size_t)k * LAY.bytes;
+    MemberPtrs p;
+    p.theta = (float*)(base + LAY.theta_b);
+    p.m = (float*)(base + LAY.m_b);
+    p.v = (float*)(base + LAY.v_b);
+    p.wb = (bf16*)(base + LAY.wb_b);
+    p.wt = (bf16*)(base + LAY.wt_b);
+    p.stats = (float*)(base + LAY.stats_b);
+    p.step = (int*)(base + LAY.step_b);
+    return p;
+}
+
+// ----------------------------------------------------------------------- GEMM kernel
+enum Mode {
+    FWD_HIDDEN = 0,    // Z = acc + b (fp32), H = GELU(Z) (bf16) and H^T
+    INFER_HIDDEN = 1,  // H = GELU(acc + b) (bf16)
+    FWD_OUT = 2,       // softmax(acc + b) over 3 columns -> P; CE gradient G, G^T; loss
+    INFER_OUT = 3,     // softmax(acc + b) -> P
+    BWD_HIDDEN = 4,    // dZ = acc * GELU'(Z_prev) -> dZ (bf16), dZ^T
+    DW_PARTIAL = 5,    // partial[split] = acc (fp32)
+};
+
+struct GemmArgs {
+    int M, N;              // output rows / columns (unpadded extents to store)
+    int k_per_split;       // multiple of BK
+    const float* bias;     // [N]
+    float* out_f;          // Z [M][ldf] | P [M][4] | partial [split][M][ldf]
+    int ldf;
+    bf16* out_h;           // H | G | dZ  [M][ldh]
+    int ldh;
+    bf16* out_t;           // H^T | G^T | dZ^T  [N][ldt]
+    int ldt;
+    const float* aux;      // Z_prev [M][ld_aux] (BWD_HIDDEN) | targets [M][3] (FWD_OUT)
+    int ld_aux;
+    float* loss_sum;
+    float inv_batch;
+    unsigned* status;
+    int a_rows_box;        // rows of the A box (128, or fewer when A has fewer rows)
+    unsigned tx_bytes;     // bytes one stage receives from the two TMA loads
+};
+
+__device__ __forceinline__ float gelu_f(float z) {
+    return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+}
+__device__ __forceinline__ float gelu_grad_f(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
+           z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+template <int NT>
+struct Smem {
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = NT * BK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int BAR_OFF = STAGES * STAGE;
+    static constexpr int TOTAL = BAR_OFF + (2 * STAGES + 1) * 8 + 16;
+    static constexpr int ALLOC = TOTAL + 1024;   // slack for 1024-byte alignment
+};
+
+template <int NT, int MODE>
+__global__ void __launch_bounds__(128, 1)
+    gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                GemmArgs args) {
+    using S = Smem<NT>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - raw);
+    const uint32_t bar_full = base + S::BAR_OFF;
+    const uint32_t bar_empty = bar_full + STAGES * 8;
+    const uint32_t bar_done = bar_empty + STAGES * 8;
+    const uint32_t tslot = bar_done + 8;
+    uint32_t* tslot_ptr = (uint32_t*)(gbase + S::BAR_OFF + (2 * STAGES + 1) * 8);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * NT;
+    const int k0 = blockIdx.z * args.k_per_split;
+    const int n_k = args.k_per_split / BK;
+    constexpr uint32_t NCOLS = NT < 32 ? 32 : NT;
+    constexpr uint32_t IDESC = idesc_bf16(BM, NT);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(bar_full + 8 * s, 1);
+            mbar_init(bar_empty + 8 * s, 1);
+        }
+        mbar_init(bar_done, 1);
+        fence_barrier_init();
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    __syncwarp();
+    if (warp == 0) tmem_alloc(tslot, NCOLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot_ptr;
+
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        int issued = 0, consumed = 0;
+        auto load = [&](int j) {
+            const int s = j % STAGES;
+            const uint32_t a_s = base + s * S::STAGE, b_s = a_s + S::A_BYTES;
+            mbar_arrive_expect_tx(bar_full + 8 * s, args.tx_bytes);
+            tma_load_2d(a_s, &tmA, bar_full + 8 * s, k0 + j * BK, m0);
+            tma_load_2d(b_s, &tmB, bar_full + 8 * s, k0 + j * BK, n0);
+            issued++;
+        };
+        for (int j = 0; j < n_k && j < STAGES; ++j) load(j);
+        for (int j = 0; j < n_k; ++j) {
+            const int s = j % STAGES;
+            const uint32_t ph = (uint32_t)(j / STAGES) & 1u;
+            if (!mbar_wait(bar_full + 8 * s, ph)) {
+                ok = false;
+                break;
+            }
+            consumed++;
+            tc_fence_after();
+            const uint32_t a_s = base + s * S::STAGE, b_s = a_s + S::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                mma_bf16(tmem, desc_sw128(a_s + kk * 32), desc_sw128(b_s + kk * 32), IDESC,
+                         (j > 0 || kk > 0) ? 1u : 0u);
+            }
+            mma_commit(bar_empty + 8 * s);
+            if (j + STAGES < n_k) {
+                if (!mbar_wait(bar_empty + 8 * s, ph)) {
+                    ok = false;
+                    break;
+                }
+                load(j + STAGES);
+            }
+        }
+        mma_commit(bar_done);
+        if (!ok) {
+            // let every load already issued land before the CTA can exit
+            for (int j = consumed; j < issued; ++j)
+                mbar_wait(bar_full + 8 * (j % STAGES), (uint32_t)(j / STAGES) & 1u, 1000000000LL);
+            atomicOr(&args.status[ST_CALL], DEV_RANGE);
+        }
+    }
+    __syncwarp();
+    const bool done_ok = mbar_wait(bar_done, 0);
+    __syncwarp();
+    tc_fence_after();
+    if (!done_ok && threadIdx.x == 0) atomicOr(&args.status[ST_CALL], DEV_RANGE);
+
+    // ------------------------------------------------------------------ epilogue
+    const int r = warp * 32 + lane;           // tile row held by this thread
+    const int m = m0 + r;
+    const bool row_ok = m < args.M && done_ok;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    float v[16];
+    if (MODE == FWD_OUT || MODE == INFER_OUT) {
+        tmem_ld16(trow, v);
+        float li = 0.f;
+        if (row_ok) {
+            float lg[N_OUT], p[N_OUT];
+            float mx = -3.0e38f;
+#pragma unroll
+            for (int c = 0; c < N_OUT; ++c) {
+                lg[c] = v[c] + args.bias[c];
+                mx = fmaxf(mx, lg[c]);
+            }
+            float sum = 0.f;
+#pragma unroll
+            for (int c = 0; c < N_OUT; ++c) {
+                p[c] = expf(lg[c] - mx);
+                sum += p[c];
+            }
+            const float inv = 1.0f / sum;
+#pragma unroll
+            for (int c = 0; c < N_OUT; ++c) p[c] *= inv;
+            *reinterpret_cast<float4*>(args.out_f + (long long)m * 4) =
+                make_float4(p[0], p[1], p[2], 0.f);
+            if (MODE == FWD_OUT) {
+#pragma unroll
+                for (int c = 0; c < N_OUT; ++c) {
+                    const float y = args.aux[(long long)m * 3 + c];
+                    li -= y * logf(fmaxf(p[c], 1e-30f));
+                    const bf16 gb = __float2bfloat16((p[c] - y) * args.inv_batch);
+                    args.out_h[(long long)m * args.ldh + c] = gb;
+                    args.out_t[(long long)c * args.ldt + m] = gb;
+                }
+            }
+        }
+        if (MODE == FWD_OUT) {   // batch-mean loss: warp sum, one atomic per warp
+            li *= args.inv_batch;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) li += __shfl_xor_sync(0xffffffffu, li, off);
+            if (lane == 0 && li != 0.f) atomicAdd(args.loss_sum, li);
+        }
+    } else {
+#pragma unroll 1
+        for (int c0 = 0; c0 < NT; c0 += 16) {
+            __syncwarp();
+            tmem_ld16(trow + c0, v);
+            const int n = n0 + c0;
+            if (!row_ok || n >= args.N) continue;
+            if (MODE == DW_PARTIAL) {
+                float* dst = args.out_f + (long long)blockIdx.z * args.M * args.ldf +
+                             (long long)m * args.ldf + n;
+#pragma unroll
+                for (int i = 0; i < 16; i += 4)
+                    *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                continue;
+            }
+            __align__(16) bf16 hb[16];
+            if (MODE == BWD_HIDDEN) {
+                const float* zp = args.aux + (long long)m * args.ld_aux + n;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) hb[i] = __float2bfloat16(v[i] * gelu_grad_f(zp[i]));
+            } else {
+                float z[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) z[i] = v[i] + args.bias[n + i];
+                if (MODE == FWD_HIDDEN) {
+                    float* zd = args.out_f + (long long)m * args.ldf + n;
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4)
+                        *reinterpret_cast<float4*>(zd + i) = make_float4(z[i], z[i + 1], z[i + 2], z[i + 3]);
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) hb[i] = __float2bfloat16(gelu_f(z[i]));
+            }
+            uint4* hd = reinterpret_cast<uint4*>(args.out_h + (long long)m * args.ldh + n);
+            hd[0] = reinterpret_cast<const uint4*>(hb)[0];
+            hd[1] = reinterpret_cast<const uint4*>(hb)[1];
+            if (MODE != INFER_HIDDEN) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) args.out_t[(long long)(n + i) * args.ldt + m] = hb[i];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, NCOLS);
+}
+
+// ----------------------------------------------------------------------- small kernels
+// Raw features of row (d, w): wavelength, n_p, log10 k_p, radius, volume fraction,
+// log10 thickness, g, log10(mu_s d + 1e-6), log10(mu_a d + 1e-6).
+__global__ void features_kernel(int n_designs, int n_wl, const double* wl, const double* np_re,
+                                const double* np_im, const double* radius, const double* vf,
+                                const double* thick, const double* g, const double* mu_s,
+                                const double* mu_a, float* out, unsigned* status) {
+    const long long n = (long long)n_designs * n_wl;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int d = (int)(i / n_wl), w = (int)(i % n_wl);
+        const double t = thick[d];
+        float* o = out + i * N_FEAT;
+        o[0] = (float)wl[w];
+        o[1] = (float)np_re[i];
+        o[2] = (float)log10(fmax(np_im[i], 1e-12));
+        o[3] = (float)radius[d];
+        o[4] = (float)vf[d];
+        o[5] = (float)log10(t);
+        o[6] = (float)g[i];
+        o[7] = (float)log10(mu_s[i] * t + 1e-6);
+        o[8] = (float)log10(mu_a[i] * t + 1e-6);
+        if (!(t > 0.0) || !isfinite(mu_s[i]) || !isfinite(mu_a[i]))
+            atomicOr(&status[ST_CALL], DEV_INVALID);
+    }
+}
+
+__global__ void fractions_kernel(const long long* counts, long long n, float* out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long* c = counts + i * FOS_NCOUNT;
+        const double tot = (double)(c[0] + c[1] + c[2]);
+        const double inv = tot > 0 ? 1.0 / tot : 0.0;
+        out[i * 3 + 0] = (float)(c[0] * inv);
+        out[i * 3 + 1] = (float)(c[1] * inv);
+        out[i * 3 + 2] = (float)(c[2] * inv);
+    }
+}
+
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {   // a 32-bit integer hash (murmur3 finaliser)
+    x ^= x >> 16; x *= 0x85ebca6bu; x ^= x >> 13; x *= 0xc2b2ae35u; x ^= x >> 16;
+    return x;
+}
+
+// Training batch: rows given, or drawn uniformly (with replacement) by hashing (seed,
+// step, slot);
+// standardised features -> X0 [B][64] and X0^T [64][B] (pads stay 0); targets -> Y.
+__global__ void gather_kernel(const float* feat, const float* targets, long long n_rows, int B,
+                              unsigned seed, unsigned step, const int* rows, const float* stats,
+                              bf16* X0, bf16* X0T, float* Y) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    long long src;
+    if (rows) {
+        src = rows[b];
+    } else {
+        const uint32_t h = mix32(mix32(seed ^ 0x9E3779B9u) ^ mix32(step * 0x85ebca6bu + (uint32_t)b));
+        src = (long long)(((unsigned long long)h * (unsigned long long)n_rows) >> 32);
+    }
+    for (int f = 0; f < N_FEAT; ++f) {
+        const float x = (feat[src * N_FEAT + f] - stats[f]) / stats[16 + f];
+        const bf16 xb = __float2bfloat16(x);
+        X0[(long long)b * IN_PAD + f] = xb;
+        X0T[(long long)f * B + b] = xb;
+    }
+    for (int c = 0; c < N_OUT; ++c) Y[(long long)b * 3 + c] = targets[src * 3 + c];
+}
+
+// Inference input: standardised features of rows [r0, r0+n) -> X0 [n][64].
+__global__ void normalize_kernel(const float* feat, long long r0, long long n, const float* stats,
+                                 bf16* X0) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        for (int f = 0; f < N_FEAT; ++f)
+            X0[i * IN_PAD + f] = __float2bfloat16((feat[(r0 + i) * N_FEAT + f] - stats[f]) / stats[16 + f]);
+    }
+}
+
+// Column sums of a bf16 [rows][ld] matrix (bias gradients): one block per 64 columns.
+__global__ void colsum_kernel(const bf16* G, int rows, int ld, int ncols, float* out) {
+    __shared__ float part[4][64];
+    const int c = blockIdx.x * 64 + (threadIdx.x & 63);
+    const int q = threadIdx.x >> 6;   // 4 row phases
+    float acc = 0.f;
+    if (c < ncols)
+        for (int r = q; r < rows; r += 4) acc += __bfloat162float(G[(long long)r * ld + c]);
+    part[q][threadIdx.x & 63] = acc;
+    __syncthreads();
+    if (q == 0 && c < ncols)
+        out[c] = part[0][threadIdx.x] + part[1][threadIdx.x] + part[2][threadIdx.x] + part[3][threadIdx.x];
+}
+
+struct AdamArgs {
+    float *theta, *m, *v;
+    bf16 *wb, *wt;
+    long long w_off[N_LAYERS], b_off[N_LAYERS], wb_off[N_LAYERS], wt_off[N_LAYERS];
+    const float* part[N_LAYERS];   // split-K partials of dW_l [splits][out][in]
+    const float* db[N_LAYERS];     // bias gradients [out]
+    int splits;
+    float lr, b1, b2, eps, c1, c2;  // c1 = 1 - b1^t, c2 = 1 - b2^t
+};
+
+// Adam (Kingma & Ba) on every real parameter, then the bf16 copies W (and W^T for
+// layers >= 1).  Padding stays zero.
+__global__ void adam_kernel(AdamArgs A, long long P) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int l = 0;
+        while (l + 1 < N_LAYERS && idx >= A.w_off[l + 1]) ++l;
+        const int in_p = lay_in(l), out_p = lay_out(l);
+        float g;
+        long long e = -1;
+        int o, i = 0;
+        if (idx < A.b_off[l]) {
+            e = idx - A.w_off[l];
+            o = (int)(e / in_p);
+            i = (int)(e % in_p);
+            if (o >= real_out(l) || i >= real_in(l)) continue;
+            const long long stride = (long long)out_p * in_p;
+            g = 0.f;
+            for (int s = 0; s < A.splits; ++s) g += A.part[l][s * stride + e];
+        } else {
+            o = (int)(idx - A.b_off[l]);
+            if (o >= real_out(l)) continue;
+            g = A.db[l][o];
+        }
+        const float mm = A.b1 * A.m[idx] + (1.f - A.b1) * g;
+        const float vv = A.b2 * A.v[idx] + (1.f - A.b2) * g * g;
+        A.m[idx] = mm;
+        A.v[idx] = vv;
+        const float th = A.theta[idx] - A.lr * (mm / A.c1) / (sqrtf(vv / A.c2) + A.eps);
+        A.theta[idx] = th;
+        if (e >= 0) {
+            A.wb[A.wb_off[l] + e] = __float2bfloat16(th);
+            if (l > 0) A.wt[A.wt_off[l] + (long long)i * out_p + o] = __float2bfloat16(th);
+        }
+    }
+}
+
+// The gradient vector in the layout of theta (padding 0): what adam_kernel consumes.
+__global__ void grad_kernel(AdamArgs A, long long P, float* grad) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int l = 0;
+        while (l + 1 < N_LAYERS && idx >= A.w_off[l + 1]) ++l;
+        const int in_p = lay_in(l), out_p = lay_out(l);
+        float g = 0.f;
+        if (idx < A.b_off[l]) {
+            const long long e = idx - A.w_off[l];
+            const int o = (int)(e / in_p), i = (int)(e % in_p);
+            if (o < real_out(l) && i < real_in(l)) {
+                const long long stride = (long long)out_p * in_p;
+                for (int s = 0; s < A.splits; ++s) g += A.part[l][s * stride + e];
+            }
+        } else {
+            const int o = (int)(idx - A.b_off[l]);
+            if (o < real_out(l)) g = A.db[l][o];
+        }
+        grad[idx] = g;
+    }
+}
+
+// He-uniform initial weights (hash of seed, member, index -> uniform), zero biases,
+// zero Adam state, bf16 copies, step 0.
+__global__ void init_kernel(float* theta, float* m, float* v, bf16* wb, bf16* wt, int* step,
+                            unsigned seed, unsigned member, AdamArgs lay, long long P) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int l = 0;
+        while (l + 1 < N_LAYERS && idx >= lay.w_off[l + 1]) ++l;
+        const int in_p = lay_in(l), out_p = lay_out(l);
+        float th = 0.f;
+        long long e = -1;
+        int o = 0, i = 0;
+        if (idx < lay.b_off[l]) {
+            e = idx - lay.w_off[l];
+            o = (int)(e / in_p);
+            i = (int)(e % in_p);
+            if (o < real_out(l) && i < real_in(l)) {
+                const uint32_t h = mix32(mix32(seed) ^ mix32(member * 0x27d4eb2du + 0x165667b1u) ^
+                                         mix32((uint32_t)idx));
+                const float u = ((float)(h >> 8) + 0.5f) * 0x1p-24f;   // (0,1)
+                const float lim = sqrtf(6.0f / (float)real_in(l));
+                th = (2.f * u - 1.f) * lim;
+            }
+        }
+        theta[idx] = th;
+        m[idx] = 0.f;
+        v[idx] = 0.f;
+        if (e >= 0) {
+            wb[lay.wb_off[l] + e] = __float2bfloat16(th);
+            if (l > 0) wt[lay.wt_off[l] + (long long)i * out_p + o] = __float2bfloat16(th);
+        }
+        if (idx == 0) step[0] = 0;
+    }
+}
+
+// Mean over members, spread = max over R, A, T of (max - min across members), and the
+// fallback flag: spread > threshold or any raw feature outside the training range.
+__global__ void ensemble_kernel(const float* probs, int n_members, long long n, long long r0,
+                                const float* feat, const float* stats, float* rat, float* spread,
+                                unsigned char* needs, float thr) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float mean[3] = {0.f, 0.f, 0.f}, lo[3] = {3.f, 3.f, 3.f}, hi[3] = {-3.f, -3.f, -3.f};
+        for (int k = 0; k < n_members; ++k) {
+            const float4 p = *reinterpret_cast<const float4*>(probs + ((long long)k * n + i) * 4);
+            const float q[3] = {p.x, p.y, p.z};
+            for (int c = 0; c < 3; ++c) {
+                mean[c] += q[c];
+                lo[c] = fminf(lo[c], q[c]);
+                hi[c] = fmaxf(hi[c], q[c]);
+            }
+        }
+        float spr = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            rat[(r0 + i) * 3 + c] = mean[c] / (float)n_members;
+            spr = fmaxf(spr, hi[c] - lo[c]);
+        }
+        if (spread) spread[r0 + i] = spr;
+        if (needs) {
+            bool out = spr > thr;
+            for (int f = 0; f < N_FEAT; ++f) {
+                const float x = feat[(r0 + i) * N_FEAT + f];
+                out = out || !(x >= stats[32 + f] && x <= stats[48 + f]);
+            }
+            needs[r0 + i] = out ? 1 : 0;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::mutex g_mu;
+
+static fos_status get_encoder() {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_encode) return FOS_OK;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return FOS_ERR_CUDA;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    return FOS_OK;
+}
+
+// 2-D BF16 row-major matrix [rows][ld] (K = cols used), box of box_rows x 64, 128B swizzle.
+static fos_status make_map(CUtensorMap* map, const void* ptr, long long rows, long long cols,
+                           long long ld, int box_rows) {
+    if (((uintptr_t)ptr & 15u) != 0 || (ld * 2) % 16 != 0 || cols % BK != 0) return FOS_ERR_INVALID_ARG;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? FOS_OK : FOS_ERR_CUDA;
+}
+
+struct Operand {
+    const bf16* ptr;
+    long long rows, cols, ld;   // cols = K extent (multiple of 64)
+};
+
+template <int NT, int MODE>
+static fos_status gemm(const Operand& A, const Operand& B, int splits, GemmArgs g,
+                       cudaStream_t s) {
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    FOS_CUDA_TRY(cudaGetDevice(&dev));
+    if (!attr_set[dev]) {
+        FOS_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel<NT, MODE>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          Smem<NT>::ALLOC));
+        attr_set[dev] = true;
+    }
+    if (A.cols != B.cols || A.cols % ((long long)splits * BK) != 0) return FOS_ERR_INVALID_ARG;
+    if (B.rows < NT) return FOS_ERR_INVALID_ARG;
+    const int a_box = A.rows < BM ? (int)A.rows : BM;
+    CUtensorMap ta, tb;
+    fos_status st = make_map(&ta, A.ptr, A.rows, A.cols, A.ld, a_box);
+    if (st != FOS_OK) return st;
+    st = make_map(&tb, B.ptr, B.rows, B.cols, B.ld, NT);
+    if (st != FOS_OK) return st;
+    g.k_per_split = (int)(A.cols / splits);
+    g.a_rows_box = a_box;
+    g.tx_bytes = (unsigned)(a_box * BK * 2 + NT * BK * 2);
+    dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + NT - 1) / NT), (unsigned)splits);
+    gemm_kernel<NT, MODE><<<grid, 128, Smem<NT>::ALLOC, s>>>(ta, tb, g);
+    return from_cuda(cudaGetLastError());
+}
+
+// Training workspace for batch B (library-owned, per device).
+struct TrainWs {
+    int B = 0;
+    int splits = 0;
+    void* mem = nullptr;
+    size_t bytes = 0;
+    bf16 *X0, *X0T, *H[4], *HT[4], *G4, *G4T, *dZ[2], *dZT[2];
+    float *Z[4], *P, *Y, *part[N_LAYERS], *db[N_LAYERS], *loss;
+};
+static TrainWs g_tws[64];
+
+static fos_status ensure_train_ws(int dev, int B) {
+    TrainWs& w = g_tws[dev];
+    if (w.mem && w.B == B) return FOS_OK;
+    if (w.mem) {
+        FOS_CUDA_TRY(cudaDeviceSynchronize());
+        cudaFree(w.mem);
+        w.mem = nullptr;
+    }
+    const int splits = B / 256 > 0 ? (B / 256 < 32 ? B / 256 : 32) : 1;
+    size_t o = 0;
+    auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+    struct Item { void** p; size_t bytes; };
+    std::vector<Item> items;
+    auto add = [&](void** p, size_t bytes) { items.push_back({p, bytes}); };
+    add((void**)&w.X0, (size_t)B * IN_PAD * 2);
+    add((void**)&w.X0T, (size_t)IN_PAD * B * 2);
+    for (int l = 0; l < 4; ++l) {
+        add((void**)&w.Z[l], (size_t)B * HID * 4);
+        add((void**)&w.H[l], (size_t)B * HID * 2);
+        add((void**)&w.HT[l], (size_t)HID * B * 2);
+    }
+    add((void**)&w.P, (size_t)B * 4 * 4);
+    add((void**)&w.Y, (size_t)B * 3 * 4);
+    add((void**)&w.G4, (size_t)B * OUT_PAD * 2);
+    add((void**)&w.G4T, (size_t)OUT_PAD * B * 2);
+    for (int k = 0; k < 2; ++k) {
+        add((void**)&w.dZ[k], (size_t)B * HID * 2);
+        add((void**)&w.dZT[k], (size_t)HID * B * 2);
+    }
+    for (int l = 0; l < N_LAYERS; ++l) {
+        add((void**)&w.part[l], (size_t)splits * lay_out(l) * lay_in(l) * 4);
+        add((void**)&w.db[l], (size_t)lay_out(l) * 4);
+    }
+    add((void**)&w.loss, 16);
+    for (auto& it : items) o = al(o + it.bytes);
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, o);
+    if (e != cudaSuccess) return from_cuda(e);
+    FOS_CUDA_TRY(cudaMemset(mem, 0, o));   // padding columns stay zero for good
+    size_t q = 0;
+    for (auto& it : items) {
+        *it.p = (char*)mem + q;
+        q = al(q + it.bytes);
+    }
+    w.mem = mem;
+    w.bytes = o;
+    w.B = B;
+    w.splits = splits;
+    return FOS_OK;
+}
+
+static AdamArgs layout_args(const MemberPtrs& mp) {
+    AdamArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.theta = mp.theta;
+    a.m = mp.m;
+    a.v = mp.v;
+    a.wb = mp.wb;
+    a.wt = mp.wt;
+    for (int l = 0; l < N_LAYERS; ++l) {
+        a.w_off[l] = LAY.w_off[l];
+        a.b_off[l] = LAY.b_off[l];
+        a.wb_off[l] = LAY.wb_off[l];
+        a.wt_off[l] = LAY.wt_off[l];
+    }
+    return a;
+}
+
+static GemmArgs gargs(unsigned* status) {
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.status = status;
+    return g;
+}
+
+// Forward + backward + Adam for one member on one batch (all on stream s).
+static fos_status train_step(Workspace* ws, const MemberPtrs& mp, const float* feat,
+                             const float* targets, long long n_rows, int B, unsigned seed,
+                             unsigned step, const int* rows, float lr, float* grad_out,
+                             cudaStream_t s) {
+    TrainWs& w = g_tws[ws->device];
+    const int splits = w.splits;
+    FOS_CUDA_TRY(cudaMemsetAsync(w.loss, 0, 4, s));
+    gather_kernel<<<(B + 255) / 256, 256, 0, s>>>(feat, targets, n_rows, B, seed, step, rows,
+                                                  mp.stats, w.X0, w.X0T, w.Y);
+    FOS_CUDA_TRY(cudaGetLastError());
+    const float* bias[N_LAYERS];
+    const bf16* wb[N_LAYERS];
+    const bf16* wt[N_LAYERS];
+    for (int l = 0; l < N_LAYERS; ++l) {
+        bias[l] = mp.theta + LAY.b_off[l];
+        wb[l] = mp.wb + LAY.wb_off[l];
+        wt[l] = mp.wt + LAY.wt_off[l];
+    }
+    fos_status st;
+    // forward
+    for (int l = 0; l < 4; ++l) {
+        Operand A = (l == 0) ? Operand{w.X0, B, IN_PAD, IN_PAD} : Operand{w.H[l - 1], B, HID, HID};
+        Operand Bm{wb[l], HID, lay_in(l), lay_in(l)};
+        GemmArgs g = gargs(ws->status);
+        g.M = B; g.N = HID; g.bias = bias[l];
+        g.out_f = w.Z[l]; g.ldf = HID; g.out_h = w.H[l]; g.ldh = HID; g.out_t = w.HT[l]; g.ldt = B;
+        st = gemm<128, FWD_HIDDEN>(A, Bm, 1, g, s);
+        if (st != FOS_OK) return st;
+    }
+    {
+        GemmArgs g = gargs(ws->status);
+        g.M = B; g.N = OUT_PAD; g.bias = bias[4];
+        g.out_f = w.P; g.out_h = w.G4; g.ldh = OUT_PAD; g.out_t = w.G4T; g.ldt = B;
+        g.aux = w.Y; g.loss_sum = w.loss; g.inv_batch = 1.0f / (float)B;
+        st = gemm<64, FWD_OUT>(Operand{w.H[3], B, HID, HID}, Operand{wb[4], OUT_PAD, HID, HID}, 1, g, s);
+        if (st != FOS_OK) return st;
+    }
+    // backward: layer 4 gradients, then down through the hidden layers
+    const bf16* Gcur = w.G4;
+    const bf16* GcurT = w.G4T;
+    int gcols = OUT_PAD;
+    for (int l = 4; l >= 0; --l) {
+        // bias gradient
+        colsum_kernel<<<(real_out(l) + 63) / 64, 256, 0, s>>>(Gcur, B, gcols, real_out(l), w.db[l]);
+        FOS_CUDA_TRY(cudaGetLastError());
+        // weight gradient dW_l = G^T · H_{l-1}  (A = G^T [out][B], B = H_{l-1}^T [in][B])
+        {
+            Operand A{GcurT, lay_out(l), B, B};
+            Operand Bm = (l == 0) ? Operand{w.X0T, IN_PAD, B, B} : Operand{w.HT[l - 1], HID, B, B};
+            GemmArgs g = gargs(ws->status);
+            g.M = lay_out(l); g.N = lay_in(l); g.out_f = w.part[l]; g.ldf = lay_in(l);
+            if (l == 0) st = gemm<64, DW_PARTIAL>(A, Bm, splits, g, s);
+            else st = gemm<256, DW_PARTIAL>(A, Bm, splits, g, s);
+            if (st != FOS_OK) return st;
+        }
+        if (l == 0) break;
+        // dZ_{l-1} = (G · W_l) * GELU'(Z_{l-1})  (A = G [B][out], B = W_l^T [in][out])
+        {
+            bf16* dz = w.dZ[l & 1];
+            bf16* dzt = w.dZT[l & 1];
+            Operand A{Gcur, B, lay_out(l), gcols};
+            Operand Bm{wt[l], HID, lay_out(l), lay_out(l)};
+            GemmArgs g = gargs(ws->status);
+            g.M = B; g.N = HID; g.aux = w.Z[l - 1]; g.ld_aux = HID;
+            g.out_h = dz; g.ldh = HID; g.out_t = dzt; g.ldt = B;
+            st = gemm<128, BWD_HIDDEN>(A, Bm, 1, g, s);
+            if (st != FOS_OK) return st;
+            Gcur = dz;
+            GcurT = dzt;
+            gcols = HID;
+        }
+    }
+    // Adam
+    AdamArgs a = layout_args(mp);
+    for (int l = 0; l < N_LAYERS; ++l) {
+        a.part[l] = w.part[l];
+        a.db[l] = w.db[l];
+    }
+    a.splits = splits;
+    if (grad_out) {   // diagnostic: export the gradient instead of updating
+        grad_kernel<<<(unsigned)((LAY.P + 255) / 256), 256, 0, s>>>(a, LAY.P, grad_out);
+        return from_cuda(cudaGetLastError());
+    }
+    a.lr = lr;
+    a.b1 = 0.9f;
+    a.b2 = 0.999f;
+    a.eps = 1e-8f;
+    const double t = (double)step + 1.0;
+    a.c1 = (float)(1.0 - pow(0.9, t));
+    a.c2 = (float)(1.0 - pow(0.999, t));
+    adam_kernel<<<(unsigned)((LAY.P + 255) / 256), 256, 0, s>>>(a, LAY.P);
+    return from_cuda(cudaGetLastError());
+}
+
+// Inference workspace: rows per chunk.
+struct InferWs {
+    long long rows = 0;
+    int members = 0;
+    void* mem = nullptr;
+    bf16 *X0, *H[2];
+    float* P;
+};
+static InferWs g_iws[64];
+constexpr long long INFER_CHUNK = 1 << 19;
+
+static fos_status ensure_infer_ws(int dev, int members) {
+    InferWs& w = g_iws[dev];
+    if (w.mem && w.members >= members) return FOS_OK;
+    if (w.mem) {
+        FOS_CUDA_TRY(cudaDeviceSynchronize());
+        cudaFree(w.mem);
+        w.mem = nullptr;
+    }
+    const long long R = INFER_CHUNK;
+    const size_t bx = (size_t)R * IN_PAD * 2, bh = (size_t)R * HID * 2,
+                 bp = (size_t)members * R * 4 * 4;
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, bx + 2 * bh + bp + 4096);
+    if (e != cudaSuccess) return from_cuda(e);
+    FOS_CUDA_TRY(cudaMemset(mem, 0, bx));
+    w.mem = mem;
+    w.X0 = (bf16*)mem;
+    w.H[0] = (bf16*)((char*)mem + bx);
+    w.H[1] = (bf16*)((char*)mem + bx + bh);
+    w.P = (float*)((char*)mem + bx + 2 * bh);
+    w.rows = R;
+    w.members = members;
+    return FOS_OK;
+}
+
+static fos_status predict(Workspace* ws, void* model, int n_members, const float* feat,
+                          long long n_rows, float* rat, float* spread, unsigned char* needs,
+                          float thr, cudaStream_t s) {
+    InferWs& w = g_iws[ws->device];
+    for (long long r0 = 0; r0 < n_rows; r0 += INFER_CHUNK) {
+        const long long n = (n_rows - r0 < INFER_CHUNK) ? n_rows - r0 : INFER_CHUNK;
+        for (int k = 0; k < n_members; ++k) {
+            MemberPtrs mp = member(model, k);
+            normalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(feat, r0, n, mp.stats, w.X0);
+            FOS_CUDA_TRY(cudaGetLastError());
+            for (int l = 0; l < 4; ++l) {
+                Operand A = (l == 0) ? Operand{w.X0, n, IN_PAD, IN_PAD}
+                                     : Operand{w.H[(l - 1) & 1], n, HID, HID};
+                Operand Bm{mp.wb + LAY.wb_off[l], HID, lay_in(l), lay_in(l)};
+                GemmArgs g = gargs(ws->status);
+                g.M = (int)n; g.N = HID; g.bias = mp.theta + LAY.b_off[l];
+                g.out_h = w.H[l & 1]; g.ldh = HID;
+                fos_status st = gemm<256, INFER_HIDDEN>(A, Bm, 1, g, s);
+                if (st != FOS_OK) return st;
+            }
+            GemmArgs g = gargs(ws->status);
+            g.M = (int)n; g.N = OUT_PAD; g.bias = mp.theta + LAY.b_off[4];
+            g.out_f = w.P + (long long)k * n * 4;
+            fos_status st = gemm<64, INFER_OUT>(Operand{w.H[1], n, HID, HID},
+                                                Operand{mp.wb + LAY.wb_off[4], OUT_PAD, HID, HID},
+                                                1, g, s);
+            if (st != FOS_OK) return st;
+        }
+        MemberPtrs m0 = member(model, 0);
+        ensemble_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+            w.P, n_members, n, r0, feat, m0.stats, rat, spread, needs, thr);
+        FOS_CUDA_TRY(cudaGetLastError());
+    }
+    return FOS_OK;
+}
+
+static fos_status prep(Workspace** ws) {
+    fos_status st = get_workspace(ws);
+    if (st != FOS_OK) return st;
+    if ((*ws)->cc_major != 10) return FOS_ERR_UNSUPPORTED;
+    return get_encoder();
+}
+
+}  // namespace mlp
+}  // namespace fos
+
+using namespace fos;
+
+extern "C" {
+
+size_t fos_surrogate_model_bytes(void) { return mlp::LAY.bytes; }
+
+long long fos_surrogate_param_count(void) { return mlp::LAY.P; }
+
+fos_status fos_surrogate_param_offsets(long long* w_off, long long* b_off) {
+    if (!w_off || !b_off) return FOS_ERR_INVALID_ARG;
+    for (int l = 0; l < mlp::N_LAYERS; ++l) {
+        w_off[l] = mlp::LAY.w_off[l];
+        b_off[l] = mlp::LAY.b_off[l];
+    }
+    return FOS_OK;
+}
+
+fos_status fos_surrogate_init(void* model, int n_members, unsigned long long seed,
+                              const float* feat_stats, void* stream) {
+    if (!model || n_members < 1 || !feat_stats) return FOS_ERR_INVALID_ARG;
+    for (int f = 0; f < mlp::N_FEAT; ++f)
+        if (!(feat_stats[16 + f] > 0.f) || !(feat_stats[32 + f] <= feat_stats[48 + f]))
+            return FOS_ERR_INVALID_ARG;
+    Workspace* ws = nullptr;
+    fos_status st = mlp::prep(&ws);
+    if (st != FOS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < n_members; ++k) {
+        mlp::MemberPtrs mp = mlp::member(model, k);
+        mlp::AdamArgs lay = mlp::layout_args(mp);
+        FOS_CUDA_TRY(cudaMemsetAsync((char*)model + (size_t)k * mlp::LAY.bytes, 0, mlp::LAY.bytes, s));
+        mlp::init_kernel<<<(unsigned)((mlp::LAY.P + 255) / 256), 256, 0, s>>>(
+            mp.theta, mp.m, mp.v, mp.wb, mp.wt, mp.step, (unsigned)(seed ^ (seed >> 32)),
+            (unsigned)k, lay, mlp::LAY.P);
+        FOS_CUDA_TRY(cudaGetLastError());
+        FOS_CUDA_TRY(cudaMemcpyAsync(mp.stats, feat_stats, 64 * sizeof(float),
+                                     cudaMemcpyHostToDevice, s));
+    }
+    FOS_CUDA_TRY(cudaStreamSynchronize(s));
+    return FOS_OK;
+}
+
+fos_status fos_surrogate_features(int n_designs, int n_wl, const double* wl, const double* np_re,
+                                  const double* np_im, const double* radius,
+                                  const double* vol_frac, const double* thickness, const double* g,
+                                  const double* mu_s, const double* mu_a, float* features,
+                                  unsigned flags, void* stream) {
+    if (n_designs < 0 || n_wl < 1) return FOS_ERR_INVALID_ARG;
+    if (!wl || !np_re || !np_im || !radius || !vol_frac || !thickness || !g || !mu_s || !mu_a ||
+        !features)
+        return FOS_ERR_INVALID_ARG;
+    Workspace* ws = nullptr;
+    fos_status st = get_workspace(&ws);
+    if (st != FOS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    FOS_CUDA_TRY(cudaMemsetAsync(ws->status + ST_CALL, 0, sizeof(unsigned), s));
+    const long long n = (long long)n_designs * n_wl;
+    if (n > 0) {
+        long long blocks = (n + 255) / 256;
+        if (blocks > (long long)ws->num_sms * 16) blocks = (long long)ws->num_sms * 16;
+        mlp::features_kernel<<<(unsigned)blocks, 256, 0, s>>>(n_designs, n_wl, wl, np_re, np_im,
+                                                              radius, vol_frac, thickness, g, mu_s,
+                                                              mu_a, features, ws->status);
+        FOS_CUDA_TRY(cudaGetLastError());
+    }
+    return finish_call(ws, s, flags);
+}
+
+fos_status fos_counts_to_fractions(const long long* counts, long long n_rows, float* fractions,
+                                   void* stream) {
+    if (n_rows < 0 || (n_rows > 0 && (!counts || !fractions))) return FOS_ERR_INVALID_ARG;
+    if (n_rows == 0) return FOS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    long long blocks = (n_rows + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    mlp::fractions_kernel<<<(unsigned)blocks, 256, 0, s>>>(counts, n_rows, fractions);
+    return from_cuda(cudaGetLastError());
+}
+
+fos_status fos_surrogate_train_step(void* model, int member, const float* features,
+                                    const float* targets, long long n_rows, int batch,
+                                    const int* batch_rows, unsigned long long seed, int step,
+                                    float lr, float* loss_out, float* grad_out, unsigned flags,
+                                    void* stream) {
+    if (!model || member < 0 || !features || !targets || n_rows < 1 || step < 0) return FOS_ERR_INVALID_ARG;
+    if (batch < 256 || batch % 256 != 0 || batch > 65536) return FOS_ERR_INVALID_ARG;
+    if (!(lr > 0.f)) return FOS_ERR_INVALID_ARG;
+    Workspace* ws = nullptr;
+    fos_status st = mlp::prep(&ws);
+    if (st != FOS_OK) return st;
+    st = mlp::ensure_train_ws(ws->device, batch);
+    if (st != FOS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    FOS_CUDA_TRY(cudaMemsetAsync(ws->status + ST_CALL, 0, sizeof(unsigned), s));
+    mlp::MemberPtrs mp = mlp::member(model, member);
+    st = mlp::train_step(ws, mp, features, targets, n_rows, batch,
+                         (unsigned)(seed ^ (seed >> 32)) ^ (unsigned)(member * 0x9E3779B9u),
+                         (unsigned)step, batch_rows, lr, grad_out, s);
+    if (st != FOS_OK) return st;
+    if (loss_out) {
+        mlp::TrainWs& w = mlp::g_tws[ws->device];
+        FOS_CUDA_TRY(cudaMemcpyAsync(loss_out, w.loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
+    }
+    return finish_call(ws, s, flags);
+}
+
+fos_status fos_surrogate_predict(void* model, int n_members, const float* features,
+                                 long long n_rows, float* rat, float* spread,
+                                 unsigned char* needs_mc, float threshold, unsigned flags,
+                                 void* stream) {
+    if (!model || n_members < 1 || n_members > 16 || n_rows < 0) return FOS_ERR_INVALID_ARG;
+    if (n_rows > 0 && (!features || !rat)) return FOS_ERR_INVALID_ARG;
+    if (n_rows == 0) return FOS_OK;
+    Workspace* ws = nullptr;
+    fos_status st = mlp::prep(&ws);
+    if (st != FOS_OK) return st;
+    st = mlp::ensure_infer_ws(ws->device, n_members);
+    if (st != FOS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    FOS_CUDA_TRY(cudaMemsetAsync(ws->status + ST_CALL, 0, sizeof(unsigned), s));
+    st = mlp::predict(ws, model, n_members, features, n_rows, rat, spread, needs_mc, threshold, s);
+    if (st != FOS_OK) return st;
+    return finish_call(ws, s, flags);
+}
+
+// Plain GEMM through the same kernel (diagnostic): C[M][N] fp32 = A[M][K] * B[N][K]^T,
+// A and B bf16 row-major with K a multiple of 64.
+fos_status fos_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, int splits,
+                         void* stream) {
+    if (!A || !B || !C || M < 1 || N < 1 || K < 64 || K % 64 != 0 || splits < 1 ||
+        K % (64 * splits) != 0 || N % 64 != 0)
+        return FOS_ERR_INVALID_ARG;
+    Workspace* ws = nullptr;
+    fos_status st = mlp::prep(&ws);
+    if (st != FOS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    FOS_CUDA_TRY(cudaMemsetAsync(ws->status + ST_CALL, 0, sizeof(unsigned), s));
+    mlp::GemmArgs g = mlp::gargs(ws->status);
+    g.M = M;
+    g.N = N;
+    g.out_f = C;
+    g.ldf = N;
+    mlp::Operand a{(const mlp::bf16*)A, M, K, K}, b{(const mlp::bf16*)B, N, K, K};
+    if (N % 256 == 0) st = mlp::gemm<256, mlp::DW_PARTIAL>(a, b, splits, g, s);
+    else st = mlp::gemm<64, mlp::DW_PARTIAL>(a, b, splits, g, s);
+    if (st != FOS_OK) return st;
+    return finish_call(ws, s, 0);
+}
+
+}  // extern "C"

@@ -222,6 +222,97 @@ def fos_walk_math_f32(u, neg_log=None, cos2pi=None, stream=None) -> int:
                                    _stream(stream))
 
 
+# --------------------------------------------------------------------------- surrogate
+def _sfn(name, argtypes, restype=ctypes.c_int):
+    fn = getattr(lib(), name)
+    fn.argtypes = argtypes
+    fn.restype = restype
+    return fn
+
+
+def fos_surrogate_model_bytes() -> int:
+    return int(_sfn("fos_surrogate_model_bytes", [], ctypes.c_size_t)())
+
+
+def fos_surrogate_param_count() -> int:
+    return int(_sfn("fos_surrogate_param_count", [], ctypes.c_longlong)())
+
+
+def fos_surrogate_param_offsets():
+    w = (ctypes.c_longlong * 5)()
+    b = (ctypes.c_longlong * 5)()
+    check(_sfn("fos_surrogate_param_offsets", [ctypes.c_void_p, ctypes.c_void_p])(w, b),
+          "fos_surrogate_param_offsets")
+    return list(w), list(b)
+
+
+def fos_surrogate_init(model, n_members, seed, feat_stats, stream=None) -> int:
+    """feat_stats: host sequence of 64 floats (mean[16] | std[16] | lo[16] | hi[16])."""
+    st = (ctypes.c_float * 64)(*[float(v) for v in feat_stats])
+    return _sfn("fos_surrogate_init", [ctypes.c_void_p, ctypes.c_int, ctypes.c_ulonglong,
+                                       ctypes.c_void_p, ctypes.c_void_p])(
+        _dev(model, torch.uint8, "model"), int(n_members), int(seed) & 0xFFFFFFFFFFFFFFFF,
+        st, _stream(stream))
+
+
+def fos_surrogate_features(wl, np_re, np_im, radius, vol_frac, thickness, g, mu_s, mu_a,
+                           features, flags=0, stream=None) -> int:
+    f64 = torch.float64
+    n_designs, n_wl = radius.numel(), wl.numel()
+    return _sfn("fos_surrogate_features", [ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 10
+                + [ctypes.c_uint, ctypes.c_void_p])(
+        n_designs, n_wl, _dev(wl, f64, "wl"), _dev(np_re, f64, "np_re"),
+        _dev(np_im, f64, "np_im"), _dev(radius, f64, "radius"), _dev(vol_frac, f64, "vol_frac"),
+        _dev(thickness, f64, "thickness"), _dev(g, f64, "g"), _dev(mu_s, f64, "mu_s"),
+        _dev(mu_a, f64, "mu_a"), _dev(features, torch.float32, "features"), int(flags),
+        _stream(stream))
+
+
+def fos_counts_to_fractions(counts, fractions, stream=None) -> int:
+    n = counts.numel() // FOS_NCOUNT
+    return _sfn("fos_counts_to_fractions", [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
+                                            ctypes.c_void_p])(
+        _dev(counts, torch.int64, "counts"), n, _dev(fractions, torch.float32, "fractions"),
+        _stream(stream))
+
+
+def fos_surrogate_train_step(model, member, features, targets, batch, seed, step, lr,
+                             batch_rows=None, loss_out=None, grad_out=None, flags=0,
+                             stream=None) -> int:
+    f32 = torch.float32
+    n_rows = features.numel() // 9
+    return _sfn("fos_surrogate_train_step",
+                [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
+                 ctypes.c_int, ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_int, ctypes.c_float,
+                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint, ctypes.c_void_p])(
+        _dev(model, torch.uint8, "model"), int(member), _dev(features, f32, "features"),
+        _dev(targets, f32, "targets"), n_rows, int(batch),
+        _dev(batch_rows, torch.int32, "batch_rows", True), int(seed) & 0xFFFFFFFFFFFFFFFF,
+        int(step), float(lr), _dev(loss_out, f32, "loss_out", True),
+        _dev(grad_out, f32, "grad_out", True), int(flags), _stream(stream))
+
+
+def fos_surrogate_predict(model, n_members, features, rat, spread=None, needs_mc=None,
+                          threshold=0.01, flags=0, stream=None) -> int:
+    f32 = torch.float32
+    n_rows = features.numel() // 9
+    return _sfn("fos_surrogate_predict",
+                [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
+                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_uint, ctypes.c_void_p])(
+        _dev(model, torch.uint8, "model"), int(n_members), _dev(features, f32, "features"), n_rows,
+        _dev(rat, f32, "rat"), _dev(spread, f32, "spread", True),
+        _dev(needs_mc, torch.uint8, "needs_mc", True), float(threshold), int(flags),
+        _stream(stream))
+
+
+def fos_gemm_bf16(A, B, C, splits=1, stream=None) -> int:
+    M, K = A.shape
+    N = B.shape[0]
+    return _sfn("fos_gemm_bf16", [ctypes.c_void_p] * 3 + [ctypes.c_int] * 4 + [ctypes.c_void_p])(
+        _dev(A, torch.bfloat16, "A"), _dev(B, torch.bfloat16, "B"), _dev(C, torch.float32, "C"),
+        int(M), int(N), int(K), int(splits), _stream(stream))
+
+
 # --------------------------------------------------------------------------- no allocation
 def fos_mc_spectrum_noalloc(batch: FosBatch, counts, flags=0, stream=None) -> int:
     """fos_mc_spectrum for callers that cannot allocate device memory (scratch is a

@@ -1,0 +1,245 @@
+"""Parity of the tcgen05 surrogate kernels (GEMM, forward, backward, Adam) with the
+FP64 NumPy oracle (oracle/mlp.py), through the C-ABI."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from paper_2409_00165_gb300 import fos
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+REAL = [(256, 9), (256, 256), (256, 256), (256, 256), (3, 256)]
+
+
+def _bf16(rng, shape, scale=1.0):
+    return torch.as_tensor(rng.normal(0, scale, size=shape), dtype=torch.float32).to(
+        torch.bfloat16).cuda()
+
+
+@pytest.mark.parametrize("Mr,N,K,splits", [(128, 256, 64, 1), (256, 256, 256, 1),
+                                          (300, 64, 512, 1), (64, 256, 8192, 32),
+                                          (1000, 256, 256, 4), (128, 64, 64, 1),
+                                          (8192, 256, 256, 1)])
+def test_gemm_matches_fp64(Mr, N, K, splits):
+    rng = np.random.default_rng(Mr * 7 + N + K)
+    A = _bf16(rng, (Mr, K))
+    B = _bf16(rng, (N, K))
+    C = torch.zeros((splits, Mr, N), dtype=torch.float32, device="cuda")
+    fos.check(fos.fos_gemm_bf16(A, B, C, splits), "fos_gemm_bf16")
+    a = A.float().double().cpu().numpy()
+    b = B.float().double().cpu().numpy()
+    ref = a @ b.T
+    bound = np.abs(a) @ np.abs(b).T
+    got = C.sum(dim=0).double().cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 1e-5 * bound + 1e-6)
+
+
+def _stats(x):
+    mean, std = x.mean(axis=0), x.std(axis=0) + 1e-3
+    lo, hi = x.min(axis=0), x.max(axis=0)
+    st = np.zeros(64, np.float32)
+    st[0:9], st[16:25], st[32:41], st[48:57] = mean, std, lo, hi
+    st[16 + 9:32] = 1.0
+    return st, mean, std
+
+
+def _params(model, member=0):
+    P = fos.fos_surrogate_param_count()
+    w_off, b_off = fos.fos_surrogate_param_offsets()
+    mb = fos.fos_surrogate_model_bytes()
+    theta = model[member * mb: member * mb + 4 * P].view(torch.float32).double().cpu().numpy()
+    out = []
+    shapes = [(256, 64), (256, 256), (256, 256), (256, 256), (64, 256)]
+    for l, ((o, i), (ro, ri)) in enumerate(zip(shapes, REAL)):
+        W = theta[w_off[l]: w_off[l] + o * i].reshape(o, i)
+        b = theta[b_off[l]: b_off[l] + o]
+        out.append((W, b, W[:ro, :ri].copy(), b[:ro].copy()))
+    return out, theta
+
+
+def _model(n_members, stats, seed=1):
+    mb = fos.fos_surrogate_model_bytes()
+    model = torch.zeros(n_members * mb, dtype=torch.uint8, device="cuda")
+    fos.check(fos.fos_surrogate_init(model, n_members, seed, stats), "init")
+    return model
+
+
+def _data(n, seed=0):
+    rng = np.random.default_rng(seed)
+    x = np.column_stack([rng.uniform(0.3, 2.5, n), rng.uniform(2.5, 3.1, n),
+                         rng.uniform(-4, -0.3, n), rng.uniform(0.05, 1, n),
+                         rng.uniform(0.01, 0.3, n), rng.uniform(1, 2.7, n),
+                         rng.uniform(0, 0.9, n), rng.uniform(-1, 3, n), rng.uniform(-4, 2, n)])
+    y = rng.dirichlet(np.ones(3), size=n)
+    return x, y
+
+
+def test_init_layout_and_padding():
+    x, _ = _data(100)
+    st, _, _ = _stats(x)
+    model = _model(2, st)
+    p0, th0 = _params(model, 0)
+    p1, th1 = _params(model, 1)
+    for l, (W, b, Wr, br) in enumerate(p0):
+        ro, ri = REAL[l]
+        lim = math.sqrt(6.0 / ri)
+        assert np.all(np.abs(Wr) <= lim) and np.all(b == 0)
+        assert np.all(W[ro:, :] == 0) and np.all(W[:, ri:] == 0)
+        assert np.std(Wr) > 0.3 * lim
+    assert not np.array_equal(th0, th1)
+
+
+def test_forward_matches_oracle():
+    x, _ = _data(1000, 1)
+    st, mean, std = _stats(x)
+    model = _model(1, st)
+    params, _ = _params(model)
+    feats = torch.as_tensor(x, dtype=torch.float32).cuda().contiguous()
+    rat = torch.zeros((1000, 3), dtype=torch.float32, device="cuda")
+    fos.check(fos.fos_surrogate_predict(model, 1, feats, rat), "predict")
+    got = rat.double().cpu().numpy()
+    assert np.allclose(got.sum(axis=1), 1.0, atol=1e-5)
+    ps = [(Wr, br) for _, _, Wr, br in params]
+    xs = np.asarray(x, np.float32).astype(np.float64)
+    ref = M.forward(ps, xs, mean.astype(np.float32), std.astype(np.float32))
+    mirror = M.forward(ps, xs, mean.astype(np.float32), std.astype(np.float32),
+                       round_fn=M.bf16_round)
+    assert np.max(np.abs(got - mirror)) < 3e-3
+    assert np.max(np.abs(got - ref)) < 2e-2
+
+
+def test_gradients_match_oracle():
+    n, B = 2000, 512
+    x, y = _data(n, 2)
+    st, mean, std = _stats(x)
+    model = _model(1, st, seed=5)
+    params, _ = _params(model)
+    feats = torch.as_tensor(x, dtype=torch.float32).cuda().contiguous()
+    targ = torch.as_tensor(y, dtype=torch.float32).cuda().contiguous()
+    rows = np.random.default_rng(9).integers(0, n, size=B).astype(np.int32)
+    P = fos.fos_surrogate_param_count()
+    grad = torch.zeros(P, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    fos.check(fos.fos_surrogate_train_step(model, 0, feats, targ, B, 1, 0, 1e-3,
+                                           batch_rows=torch.as_tensor(rows).cuda(),
+                                           loss_out=loss, grad_out=grad), "grad")
+    ps = [(Wr, br) for _, _, Wr, br in params]
+    xs = np.asarray(x, np.float32).astype(np.float64)[rows]
+    ys = np.asarray(y, np.float32).astype(np.float64)[rows]
+    L, gref = M.loss_and_grads(ps, xs, ys, mean.astype(np.float32), std.astype(np.float32))
+    assert abs(loss.item() - L) < 2e-3 * abs(L)
+    g = grad.double().cpu().numpy()
+    w_off, b_off = fos.fos_surrogate_param_offsets()
+    shapes = [(256, 64), (256, 256), (256, 256), (256, 256), (64, 256)]
+    for l, ((o, i), (ro, ri)) in enumerate(zip(shapes, REAL)):
+        gw = g[w_off[l]: w_off[l] + o * i].reshape(o, i)
+        gb = g[b_off[l]: b_off[l] + o]
+        assert np.all(gw[ro:, :] == 0) and np.all(gw[:, ri:] == 0) and np.all(gb[ro:] == 0)
+        for got, want in ((gw[:ro, :ri], gref[l][0]), (gb[:ro], gref[l][1])):
+            rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+            cos = np.sum(got * want) / (np.linalg.norm(got) * np.linalg.norm(want))
+            assert rel < 2e-2 and cos > 0.9995, (l, rel, cos)
+
+
+def test_adam_update_arithmetic():
+    n, B = 1024, 256
+    x, y = _data(n, 3)
+    st, _, _ = _stats(x)
+    model = _model(1, st, seed=8)
+    _, th0 = _params(model)
+    feats = torch.as_tensor(x, dtype=torch.float32).cuda().contiguous()
+    targ = torch.as_tensor(y, dtype=torch.float32).cuda().contiguous()
+    rows = torch.arange(B, dtype=torch.int32, device="cuda")
+    P = fos.fos_surrogate_param_count()
+    grad = torch.zeros(P, dtype=torch.float32, device="cuda")
+    fos.check(fos.fos_surrogate_train_step(model, 0, feats, targ, B, 1, 0, 1e-3, batch_rows=rows,
+                                           grad_out=grad), "grad")
+    fos.check(fos.fos_surrogate_train_step(model, 0, feats, targ, B, 1, 0, 1e-3, batch_rows=rows),
+              "step")
+    _, th1 = _params(model)
+    g = grad.double().cpu().numpy()
+    # first Adam step: m_hat = g, v_hat = g^2 -> delta = -lr g / (|g| + eps)
+    want = -1e-3 * g / (np.abs(g) + 1e-8)
+    assert np.allclose(th1 - th0, want, rtol=2e-3, atol=2e-9)
+
+
+def test_training_reduces_loss_and_fits():
+    n = 40000
+    rng = np.random.default_rng(4)
+    x, _ = _data(n, 4)
+    st, mean, std = _stats(x)
+    Wt = rng.normal(size=(3, 9)) * 0.8
+    z = ((x - mean) / std) @ Wt.T
+    y = np.exp(z) / np.exp(z).sum(axis=1, keepdims=True)
+    model = _model(1, st, seed=2)
+    feats = torch.as_tensor(x, dtype=torch.float32).cuda().contiguous()
+    targ = torch.as_tensor(y, dtype=torch.float32).cuda().contiguous()
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    losses = []
+    for step in range(400):
+        fos.check(fos.fos_surrogate_train_step(model, 0, feats, targ, 1024, 11, step, 1e-3,
+                                               loss_out=loss), "train")
+        losses.append(loss.item())
+    H = -np.mean(np.sum(y * np.log(y), axis=1))
+    assert losses[-1] - H < 0.1 * (losses[0] - H)
+    rat = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    fos.check(fos.fos_surrogate_predict(model, 1, feats, rat), "predict")
+    assert np.mean(np.abs(rat.cpu().numpy() - y)) < 0.03
+
+
+def test_ensemble_spread_and_fallback_flags():
+    x, _ = _data(3000, 5)
+    st, _, _ = _stats(x)
+    model = _model(2, st, seed=3)
+    mb = fos.fos_surrogate_model_bytes()
+    model[mb:2 * mb].copy_(model[:mb])          # two identical members
+    xx = x.copy()
+    xx[10, 0] = 9.0                              # wavelength outside the training range
+    xx[11, 5] = -1.0                             # thickness outside the training range
+    feats = torch.as_tensor(xx, dtype=torch.float32).cuda().contiguous()
+    rat = torch.zeros((3000, 3), dtype=torch.float32, device="cuda")
+    spread = torch.full((3000,), -1.0, dtype=torch.float32, device="cuda")
+    needs = torch.full((3000,), 7, dtype=torch.uint8, device="cuda")
+    fos.check(fos.fos_surrogate_predict(model, 2, feats, rat, spread, needs, 0.01), "predict")
+    assert torch.all(spread == 0)
+    nz = set(torch.nonzero(needs).flatten().tolist())
+    assert nz == {10, 11}
+    one = torch.zeros_like(rat)
+    fos.check(fos.fos_surrogate_predict(model, 1, feats, one), "predict1")
+    assert torch.allclose(one, rat, atol=1e-6)
+    # two different members: spread > 0 and flags follow the threshold
+    model2 = _model(2, st, seed=4)
+    fos.check(fos.fos_surrogate_predict(model2, 2, feats, rat, spread, needs, 0.0), "predict2")
+    assert torch.all(spread > 0) and torch.all(needs == 1)
+
+
+def test_features_and_fractions():
+    rng = np.random.default_rng(6)
+    nd, nw = 7, 5
+    f64 = torch.float64
+    wl = rng.uniform(0.3, 2.5, nw)
+    arr = {k: rng.uniform(0.1, 3.0, nd * nw) for k in ("np_re", "np_im", "g", "mu_s", "mu_a")}
+    arr["np_im"] = 10 ** rng.uniform(-4, -0.3, nd * nw)
+    arr["g"] = rng.uniform(0, 0.9, nd * nw)
+    des = {k: rng.uniform(0.05, 1.0, nd) for k in ("radius", "vol_frac")}
+    thick = rng.uniform(10, 500, nd)
+    t = lambda a: torch.as_tensor(a, dtype=f64).cuda()
+    feats = torch.zeros((nd * nw, 9), dtype=torch.float32, device="cuda")
+    fos.check(fos.fos_surrogate_features(t(wl), t(arr["np_re"]), t(arr["np_im"]), t(des["radius"]),
+                                         t(des["vol_frac"]), t(thick), t(arr["g"]), t(arr["mu_s"]),
+                                         t(arr["mu_a"]), feats), "features")
+    d = np.repeat(np.arange(nd), nw)
+    w = np.tile(np.arange(nw), nd)
+    want = np.column_stack([wl[w], arr["np_re"], np.log10(arr["np_im"]), des["radius"][d],
+                            des["vol_frac"][d], np.log10(thick[d]), arr["g"],
+                            np.log10(arr["mu_s"] * thick[d] + 1e-6),
+                            np.log10(arr["mu_a"] * thick[d] + 1e-6)]).astype(np.float32)
+    assert np.allclose(feats.cpu().numpy(), want, rtol=1e-6, atol=1e-6)
+    counts = torch.as_tensor([[3, 5, 2, 0, 77, 1], [0, 0, 0, 0, 0, 0]], dtype=torch.int64).cuda()
+    fr = torch.zeros((2, 3), dtype=torch.float32, device="cuda")
+    fos.check(fos.fos_counts_to_fractions(counts, fr), "fractions")
+    torch.cuda.synchronize()
+    assert np.allclose(fr.cpu().numpy(), [[0.3, 0.5, 0.2], [0, 0, 0]])
