@@ -234,6 +234,12 @@ fos_status fos_surrogate_features(int n_designs, int n_wl, const double* wl,
                                   const double* mu_s, const double* mu_a, float* features,
                                   unsigned flags, void* stream);
 
+/* Statistics of raw feature rows [n_rows*9] (device float) into stats (device float[64]
+ * = mean[16] | std[16] | lo[16] | hi[16], first 9 of each used; std floored at 1e-3),
+ * the layout fos_surrogate_init takes.  Synchronous. */
+fos_status fos_surrogate_feature_stats(const float* features, long long n_rows, float* stats,
+                                       void* stream);
+
 /* fractions[r] = (R, A, T) / (R + A + T) of counts row r (device int64 [n*FOS_NCOUNT]
  * -> device float [n*3]); asynchronous on stream. */
 fos_status fos_counts_to_fractions(const long long* counts, long long n_rows,

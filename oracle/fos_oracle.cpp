@@ -80,7 +80,8 @@ static double uniform_of(uint32_t x) {
 //   [sqrt(1/2), sqrt(2)); ln 2 is split into a short head (exact products e*hi)
 //   and a tail.  cos(2 pi u) uses the symmetries of cosine to reduce u exactly to
 //   [0, 1/8] (cos Taylor series) or (1/8, 1/4] (sin Taylor series of the
-//   complement).  Constants are the float roundings of 1/(2j+1), 1/k!, 2 pi, ln 2.
+//   complement), both evaluated by one Horner chain.  Constants are the float
+//   roundings of 1/(2j+1), 1/k!, 2 pi, ln 2.
 // --------------------------------------------------------------------------------
 static inline uint32_t f2u(float f) { uint32_t u; std::memcpy(&u, &f, 4); return u; }
 static inline float u2f(uint32_t u) { float f; std::memcpy(&f, &u, 4); return f; }
@@ -104,37 +105,31 @@ static float neg_log_f32(float u) {
     return -r;
 }
 
-static float cos_poly_f32(float x) {  // cos x, |x| <= pi/4
-    float w = x * x;
-    float c = std::fmaf(w, -0x1.27e4fcp-22f, 0x1.a01a02p-16f);
-    c = std::fmaf(w, c, -0x1.6c16c2p-10f);
-    c = std::fmaf(w, c, 0x1.555556p-5f);
-    c = std::fmaf(w, c, -0.5f);
-    c = std::fmaf(w, c, 1.0f);
-    return c;
-}
-
-static float sin_poly_f32(float x) {  // sin x, |x| <= pi/4
-    float w = x * x;
-    float s = std::fmaf(w, 0x1.71de3ap-19f, -0x1.a01a02p-13f);
-    s = std::fmaf(w, s, 0x1.111112p-7f);
-    s = std::fmaf(w, s, -0x1.555556p-3f);
-    s = s * w;
-    return std::fmaf(x, s, x);
-}
-
+// cos(2 pi u): after the exact reductions, b in [0, 1/8] and x = 2 pi b; the cosine
+// branch evaluates cos x = 1 + w P_c(w) and the sine branch (complement past 1/8)
+// sin x = x + (x w) P_s(w), with w = x^2 and P_c, P_s degree-4 Taylor polynomials
+// (coefficients 1/k!, with the unused top sine coefficient 0) evaluated by one Horner
+// chain whose coefficients are selected per branch.
 static float cos2pi_f32(float u) {
     float a = (u > 0.5f) ? (1.0f - u) : u;   // cos(2 pi u) = cos(2 pi (1-u)); exact
     float sign = 1.0f;
     if (a > 0.25f) { a = 0.5f - a; sign = -1.0f; }  // cos(2 pi a) = -cos(2 pi (1/2 - a)); exact
-    float r;
-    if (a <= 0.125f) {
-        r = cos_poly_f32(a * 0x1.921fb6p+2f);
-    } else {
-        float b = 0.25f - a;                  // cos(2 pi a) = sin(2 pi (1/4 - a)); exact
-        r = sin_poly_f32(b * 0x1.921fb6p+2f);
-    }
-    return sign * r;
+    const bool use_sin = a > 0.125f;            // cos(2 pi a) = sin(2 pi (1/4 - a))
+    const float b = use_sin ? (0.25f - a) : a;  // exact
+    const float x = b * 0x1.921fb6p+2f;
+    const float w = x * x;
+    const float k4 = use_sin ? 0.0f : -0x1.27e4fcp-22f;           // 0 | -1/10!
+    const float k3 = use_sin ? 0x1.71de3ap-19f : 0x1.a01a02p-16f;  // 1/9! | 1/8!
+    const float k2 = use_sin ? -0x1.a01a02p-13f : -0x1.6c16c2p-10f;  // -1/7! | -1/6!
+    const float k1 = use_sin ? 0x1.111112p-7f : 0x1.555556p-5f;    // 1/5! | 1/4!
+    const float k0 = use_sin ? -0x1.555556p-3f : -0.5f;            // -1/3! | -1/2!
+    float p = std::fmaf(w, k4, k3);
+    p = std::fmaf(w, p, k2);
+    p = std::fmaf(w, p, k1);
+    p = std::fmaf(w, p, k0);
+    const float m = use_sin ? x * w : w;
+    const float base = use_sin ? x : 1.0f;
+    return sign * std::fmaf(m, p, base);
 }
 
 // --------------------------------------------------------------------------------
@@ -176,10 +171,11 @@ static typename M::R hg_cos(typename M::R g, typename M::R u) {
         R one_p_g2 = (R)1 + g * g;
         R one_m_g = (R)1 - g;
         R two_g = g + g;
+        R inv_two_g = (R)1 / two_g;
         R den = M::fma_(two_g, u, one_m_g);
         R t = one_m_g2 / den;
         R num = M::fma_(-t, t, one_p_g2);
-        cost = num / two_g;
+        cost = num * inv_two_g;
     }
     if (cost < (R)-1) cost = (R)-1;
     if (cost > (R)1) cost = (R)1;
@@ -239,7 +235,7 @@ typedef struct orc_batch {
 template <class M>
 struct LayerP {
     typedef typename M::R R;
-    R mu_t, p_abs, g, n, d;
+    R mu_t, inv_mu_t, p_abs, g, n, d;
 };
 
 // Random numbers of one photon.  Collision event e reads the block at counter
@@ -260,7 +256,6 @@ static int walk_photon(const LayerP<M>* L, int nl, typename M::R n_above, typena
                        unsigned long long max_events, unsigned long long* n_coll,
                        unsigned long long* n_iface) {
     typedef typename M::R R;
-    const R INF = std::numeric_limits<R>::infinity();
     uint32_t k_if = 0;          // interface draws so far
     uint32_t e = 0;             // collision events so far
     unsigned long long events = 0, coll = 0, iface = 0;
@@ -288,14 +283,17 @@ static int walk_photon(const LayerP<M>* L, int nl, typename M::R n_above, typena
     for (;;) {
         if (events >= max_events) { outcome = OUT_RUNAWAY; break; }
         const LayerP<M>& Lj = L[j];
-        R tb;
-        if (mu > (R)0) tb = Lj.mu_t * ((Lj.d - z) / mu);
-        else if (mu < (R)0) tb = Lj.mu_t * (z / (-mu));
-        else tb = (Lj.mu_t > (R)0) ? INF : (R)0;
+        // Distance to the boundary ahead along z; the photon collides first iff
+        // tau |mu_z| < mu_t dist (tau < mu_t dist / |mu_z| without the division).
+        const R am = M::abs_(mu);
+        const R dist = (mu > (R)0) ? (Lj.d - z) : z;
+        bool collide;
+        if (mu != (R)0) collide = tau * am < Lj.mu_t * dist;
+        else collide = Lj.mu_t > (R)0;
 
-        if (tau < tb) {
+        if (collide) {
             // Collision inside layer j.
-            R s = tau / Lj.mu_t;
+            R s = tau * Lj.inv_mu_t;
             z = M::fma_(mu, s, z);
             events++; coll++;
             if (u1 < Lj.p_abs) { outcome = OUT_A; break; }
@@ -315,9 +313,13 @@ static int walk_photon(const LayerP<M>* L, int nl, typename M::R n_above, typena
             u1 = M::uni(blk[1]); u2 = M::uni(blk[2]); u3 = M::uni(blk[3]);
             continue;
         }
+        // Optical depth to the boundary (0 when mu_z = 0); the remainder of tau is
+        // carried on, never below 0.
+        const R tb = (mu != (R)0) ? Lj.mu_t * (dist / am) : (R)0;
 
         // The free path reaches the boundary of layer j first.
         tau = tau - tb;
+        if (tau < (R)0) tau = (R)0;
         bool down = mu > (R)0;
         z = down ? Lj.d : (R)0;
         events++; iface++;
@@ -378,6 +380,7 @@ static int run_batch(const orc_batch* b, long long* counts, int* photon_log, lon
             long long pi = ((long long)s * b->max_layers + j) * b->n_wl + w;
             R ms = (R)b->mu_s[pi], ma = (R)b->mu_a[pi];
             L[j].mu_t = ms + ma;
+            L[j].inv_mu_t = (L[j].mu_t > (R)0) ? (R)1 / L[j].mu_t : (R)0;
             L[j].p_abs = (L[j].mu_t > (R)0) ? ma / L[j].mu_t : (R)0;
             L[j].g = (R)b->g[pi];
             L[j].n = (R)b->n_layer[pi];

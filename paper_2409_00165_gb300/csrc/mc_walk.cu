@@ -44,9 +44,25 @@ __device__ __forceinline__ uint4 philox(uint4 c, unsigned k0, unsigned k1) {
     return c;
 }
 
-// Top 23 bits k of a word -> (2k+1) 2^-24, exactly representable, in (0,1).
+// The same generator with the 10 round keys computed on the host (the key is the
+// seed, identical for every photon): key words of round r are k + r * Weyl increment.
+struct RoundKeys {
+    unsigned k0[10], k1[10];
+};
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const RoundKeys& rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ rk.k0[r], lo1, hi0 ^ c.w ^ rk.k1[r], lo0);
+    }
+    return c;
+}
+
+// Top 23 bits k of a word -> (2k+1) 2^-24, exactly representable, in (0,1): the float
+// 1 + k 2^-23 (k as mantissa) minus (1 - 2^-24), an exact subtraction.
 __device__ __forceinline__ float uni(unsigned x) {
-    return (float)(((x >> 9) << 1) | 1u) * 0x1p-24f;
+    return __uint_as_float((x >> 9) | 0x3f800000u) - 0x1.fffffep-1f;
 }
 
 __device__ __forceinline__ unsigned word(uint4 b, unsigned i) {
@@ -79,8 +95,9 @@ __device__ __forceinline__ float neg_log_u(float u) {
 }
 
 // cos(2 pi u), u in (0,1): exact reductions u -> min(u, 1-u) -> [0,1/4] (sign flip
-// past 1/4), then the cos Taylor series on [0, pi/4] or the sin series of the
-// complement on (0, pi/4].
+// past 1/4) -> b in [0, 1/8] (the complement past 1/8 turns cos into sin); then one
+// Horner chain in w = x^2, x = 2 pi b, with per-branch Taylor coefficients:
+// cos x = 1 + w P_c(w), sin x = x + (x w) P_s(w).  No divergent branch.
 __device__ __forceinline__ float cos_2pi_u(float u) {
     float a = (u > 0.5f) ? (1.0f - u) : u;
     float sign = 1.0f;
@@ -88,26 +105,22 @@ __device__ __forceinline__ float cos_2pi_u(float u) {
         a = 0.5f - a;
         sign = -1.0f;
     }
-    float r;
-    if (a <= 0.125f) {
-        const float x = a * 0x1.921fb6p+2f;
-        const float w = x * x;
-        float c = fmaf(w, -0x1.27e4fcp-22f, 0x1.a01a02p-16f);   // -1/10!, 1/8!
-        c = fmaf(w, c, -0x1.6c16c2p-10f);                        // -1/6!
-        c = fmaf(w, c, 0x1.555556p-5f);                          // 1/4!
-        c = fmaf(w, c, -0.5f);
-        r = fmaf(w, c, 1.0f);
-    } else {
-        const float b = 0.25f - a;
-        const float x = b * 0x1.921fb6p+2f;
-        const float w = x * x;
-        float s = fmaf(w, 0x1.71de3ap-19f, -0x1.a01a02p-13f);   // 1/9!, -1/7!
-        s = fmaf(w, s, 0x1.111112p-7f);                          // 1/5!
-        s = fmaf(w, s, -0x1.555556p-3f);                         // -1/3!
-        s = s * w;
-        r = fmaf(x, s, x);
-    }
-    return sign * r;
+    const bool use_sin = a > 0.125f;
+    const float b = use_sin ? (0.25f - a) : a;
+    const float x = b * 0x1.921fb6p+2f;
+    const float w = x * x;
+    const float k4 = use_sin ? 0.0f : -0x1.27e4fcp-22f;            // 0 | -1/10!
+    const float k3 = use_sin ? 0x1.71de3ap-19f : 0x1.a01a02p-16f;   // 1/9! | 1/8!
+    const float k2 = use_sin ? -0x1.a01a02p-13f : -0x1.6c16c2p-10f; // -1/7! | -1/6!
+    const float k1 = use_sin ? 0x1.111112p-7f : 0x1.555556p-5f;     // 1/5! | 1/4!
+    const float k0 = use_sin ? -0x1.555556p-3f : -0.5f;             // -1/3! | -1/2!
+    float p = fmaf(w, k4, k3);
+    p = fmaf(w, p, k2);
+    p = fmaf(w, p, k1);
+    p = fmaf(w, p, k0);
+    const float m = use_sin ? x * w : w;
+    const float base = use_sin ? x : 1.0f;
+    return sign * fmaf(m, p, base);
 }
 
 // Unpolarised Fresnel reflectance (mean of s and p) from index ni into nt at
@@ -131,8 +144,9 @@ __device__ __forceinline__ float fresnel(float ni, float nt, float ci, float& ct
 }
 
 // Henyey-Greenstein deflection cosine by inversion of its distribution function.
-// hg = {1-g^2, 1+g^2, 1-g} precomputed with the same operations as written here.
-__device__ __forceinline__ float hg_cos(float g, float omg2, float opg2, float omg, float u) {
+// {1-g^2, 1+g^2, 1-g, 1/(2g)} are precomputed per layer by pack_kernel.
+__device__ __forceinline__ float hg_cos(float g, float omg2, float opg2, float omg,
+                                        float inv2g, float u) {
     float cost;
     if (fabsf(g) < 0x1.0c6f7ap-20f) {   // |g| < 1e-6: isotropic
         cost = (u + u) - 1.0f;
@@ -141,7 +155,7 @@ __device__ __forceinline__ float hg_cos(float g, float omg2, float opg2, float o
         const float den = fmaf(two_g, u, omg);
         const float t = omg2 / den;
         const float num = fmaf(-t, t, opg2);
-        cost = num / two_g;
+        cost = num * inv2g;
     }
     cost = fminf(fmaxf(cost, -1.0f), 1.0f);
     return cost;
@@ -155,15 +169,16 @@ struct Tables {
     int4* info;       // {rng item id, first photon id, photon count, 0}
     float4* layA;     // [row*max_layers + j] {mu_t, mu_a/mu_t, g, n}
     float4* layB;     // [row*max_layers + j] {d, 1-g^2, 1+g^2, 1-g}
+    float4* layC;     // [row*max_layers + j] {1/mu_t, 1/(2g), 0, 0}
     long long* prefix;  // [n_run + 1] exclusive prefix of work units
 };
 
 static size_t tables_bytes(long long n_run, int max_layers) {
     size_t b = 0;
     b += (size_t)n_run * sizeof(int4) * 2;
-    b += (size_t)n_run * max_layers * sizeof(float4) * 2;
+    b += (size_t)n_run * max_layers * sizeof(float4) * 3;
     b += (size_t)(n_run + 1) * sizeof(long long);
-    return b + 6 * 256;   // each of the 5 regions is rounded up to 256 bytes
+    return b + 7 * 256;   // each of the 6 regions is rounded up to 256 bytes
 }
 
 static Tables carve(void* base, long long n_run, int max_layers) {
@@ -178,6 +193,7 @@ static Tables carve(void* base, long long n_run, int max_layers) {
     t.info = (int4*)take((size_t)n_run * sizeof(int4));
     t.layA = (float4*)take((size_t)n_run * max_layers * sizeof(float4));
     t.layB = (float4*)take((size_t)n_run * max_layers * sizeof(float4));
+    t.layC = (float4*)take((size_t)n_run * max_layers * sizeof(float4));
     t.prefix = (long long*)take((size_t)(n_run + 1) * sizeof(long long));
     return t;
 }
@@ -219,6 +235,7 @@ __global__ void pack_kernel(PackArgs A) {
     }
     for (int j = 0; j < b.max_layers; ++j) {
         float4 la = make_float4(0.f, 0.f, 0.f, 1.f), lb = make_float4(1.f, 1.f, 1.f, 1.f);
+        float4 lc = make_float4(0.f, 0.f, 0.f, 0.f);
         if (j < nl) {
             const long long pi = ((long long)s * b.max_layers + j) * b.n_wl + w;
             const double ms = b.mu_s[pi], ma = b.mu_a[pi], gg = b.g[pi], nn = b.n_layer[pi];
@@ -233,9 +250,12 @@ __global__ void pack_kernel(PackArgs A) {
                 ok = false;
             la = make_float4(mt, pabs, gf, (float)nn);
             lb = make_float4((float)dd, 1.0f - gf * gf, 1.0f + gf * gf, 1.0f - gf);
+            lc = make_float4((mt > 0.0f) ? 1.0f / mt : 0.0f,
+                             (fabsf(gf) < 0x1.0c6f7ap-20f) ? 0.0f : 1.0f / (gf + gf), 0.f, 0.f);
         }
         A.t.layA[(long long)r * b.max_layers + j] = la;
         A.t.layB[(long long)r * b.max_layers + j] = lb;
+        A.t.layC[(long long)r * b.max_layers + j] = lc;
     }
     const double na = b.n_above ? b.n_above[it] : 1.0;
     const double nb = b.n_below ? b.n_below[it] : 1.0;
@@ -292,7 +312,7 @@ struct WalkArgs {
     int n_run, max_layers;
     unsigned unit;        // photons per warp work unit
     unsigned cap;         // photon cap per row (autotuner), 0xffffffff otherwise
-    unsigned key0, key1;
+    RoundKeys rk;
     unsigned max_events;
     unsigned long long* cursor;
     unsigned long long* counts;
@@ -360,7 +380,7 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
     unsigned item_rng = 0, p = 0, p_first = 0, e = 0, kif = 0, ev = 0;
     float z = 0.f, mu = 1.f, tau = 0.f, u1 = 0.f, u2 = 0.f, u3 = 0.f;
     float l_mut = 0.f, l_pabs = 0.f, l_g = 0.f, l_n = 1.f, l_d = 1.f, l_omg2 = 1.f,
-          l_opg2 = 1.f, l_omg = 1.f;
+          l_opg2 = 1.f, l_omg = 1.f, l_imt = 0.f, l_i2g = 0.f;
     float n_above = 1.f, n_below = 1.f, r_sub = -1.f;
 
     // tallies of the current tag (row)
@@ -372,8 +392,10 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
         const long long li = (long long)row * A.max_layers + jj;
         const float4 a = A.t.layA[li];
         const float4 b = A.t.layB[li];
+        const float2 c = *reinterpret_cast<const float2*>(&A.t.layC[li]);
         l_mut = a.x; l_pabs = a.y; l_g = a.z; l_n = a.w;
         l_d = b.x; l_omg2 = b.y; l_opg2 = b.z; l_omg = b.w;
+        l_imt = c.x; l_i2g = c.y;
     };
     auto finish = [&](int out) {
         if (out == O_R) cR++;
@@ -455,7 +477,7 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
                     float ct;
                     bool tir;
                     const float Rf = fresnel(n_above, l_n, 1.0f, ct, tir);
-                    const uint4 blk = philox(make_uint4(p, item_rng, 0u, 1u), A.key0, A.key1);
+                    const uint4 blk = philox_rk(make_uint4(p, item_rng, 0u, 1u), A.rk);
                     const float u = uni(blk.x);
                     kif = 1u;
                     reflected = tir || (u < Rf);
@@ -465,7 +487,7 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
                 } else {
                     z = 0.0f;
                     mu = 1.0f;
-                    const uint4 blk = philox(make_uint4(p, item_rng, 0u, 0u), A.key0, A.key1);
+                    const uint4 blk = philox_rk(make_uint4(p, item_rng, 0u, 0u), A.rk);
                     tau = neg_log_u(uni(blk.x));
                     u1 = uni(blk.y);
                     u2 = uni(blk.z);
@@ -483,13 +505,13 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
                 finish(O_X);
                 continue;
             }
-            float tb;
-            if (mu > 0.0f) tb = l_mut * ((l_d - z) / mu);
-            else if (mu < 0.0f) tb = l_mut * (z / (-mu));
-            else tb = (l_mut > 0.0f) ? __int_as_float(0x7f800000) : 0.0f;
-            if (tau < tb) {
+            // collides first iff tau |mu| < mu_t dist (no division on this path)
+            const float am = fabsf(mu);
+            const float dist = (mu > 0.0f) ? (l_d - z) : z;
+            const bool collide = (mu != 0.0f) ? (tau * am < l_mut * dist) : (l_mut > 0.0f);
+            if (collide) {
                 // collision inside the layer
-                const float s = tau / l_mut;
+                const float s = tau * l_imt;
                 z = fmaf(mu, s, z);
                 ev++;
                 cC++;
@@ -497,8 +519,8 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
                     finish(O_A);
                     continue;
                 }
-                const float cost = hg_cos(l_g, l_omg2, l_opg2, l_omg, u2);
-                if (fabsf(mu) > 0x1.fffeb0p-1f) {
+                const float cost = hg_cos(l_g, l_omg2, l_opg2, l_omg, l_i2g, u2);
+                if (am > 0x1.fffeb0p-1f) {
                     mu = (mu > 0.0f) ? cost : -cost;
                 } else {
                     const float q = sqrtf(fmaf(-mu, mu, 1.0f) * fmaf(-cost, cost, 1.0f));
@@ -507,14 +529,15 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
                     mu = fminf(fmaxf(mu, -1.0f), 1.0f);
                 }
                 e++;
-                const uint4 blk = philox(make_uint4(p, item_rng, e, 0u), A.key0, A.key1);
+                const uint4 blk = philox_rk(make_uint4(p, item_rng, e, 0u), A.rk);
                 tau = neg_log_u(uni(blk.x));
                 u1 = uni(blk.y);
                 u2 = uni(blk.z);
                 u3 = uni(blk.w);
             } else {
-                // boundary of the layer reached first; carry the rest of tau
-                tau = tau - tb;
+                // boundary of the layer reached first; carry the rest of tau (>= 0)
+                const float tb = (mu != 0.0f) ? l_mut * (dist / am) : 0.0f;
+                tau = fmaxf(tau - tb, 0.0f);
                 const bool down = mu > 0.0f;
                 z = down ? l_d : 0.0f;
                 ev++;
@@ -522,7 +545,7 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
                 const int nb = down ? j + 1 : j - 1;
                 const bool outside = (nb < 0) || (nb >= nl);
                 if (down && outside && r_sub >= 0.0f) {
-                    const uint4 blk = philox(make_uint4(p, item_rng, kif >> 2, 1u), A.key0, A.key1);
+                    const uint4 blk = philox_rk(make_uint4(p, item_rng, kif >> 2, 1u), A.rk);
                     const float u = uni(word(blk, kif & 3u));
                     kif++;
                     if (u < r_sub) mu = -mu;
@@ -544,7 +567,7 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
                         transmit = false;
                     } else {
                         const uint4 blk =
-                            philox(make_uint4(p, item_rng, kif >> 2, 1u), A.key0, A.key1);
+                            philox_rk(make_uint4(p, item_rng, kif >> 2, 1u), A.rk);
                         const float u = uni(word(blk, kif & 3u));
                         kif++;
                         transmit = !(u < Rf);
@@ -702,8 +725,15 @@ static fos_status enqueue(Workspace* ws, const fos_mc_batch* b, long long n_run,
     wa.max_layers = b->max_layers;
     wa.unit = unit;
     wa.cap = cap;
-    wa.key0 = (unsigned)(b->seed & 0xffffffffull);
-    wa.key1 = (unsigned)(b->seed >> 32);
+    {
+        unsigned k0 = (unsigned)(b->seed & 0xffffffffull), k1 = (unsigned)(b->seed >> 32);
+        for (int r = 0; r < 10; ++r) {
+            wa.rk.k0[r] = k0;
+            wa.rk.k1[r] = k1;
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+    }
     wa.max_events = b->max_events > 0 ? (unsigned)b->max_events : 100000000u;
     wa.cursor = ws->cursor;
     wa.counts = (unsigned long long*)counts;
@@ -958,8 +988,8 @@ constexpr long long NOALLOC_ROWS = FOS_NOALLOC_MAX_ITEMS;
 constexpr size_t NOALLOC_HDR = 512;   // status words at 0, work-queue counter at 256
 constexpr size_t NOALLOC_BYTES =
     NOALLOC_HDR + (size_t)NOALLOC_ROWS * sizeof(int4) * 2 +
-    (size_t)NOALLOC_ROWS * FOS_MAX_LAYERS * sizeof(float4) * 2 +
-    (size_t)(NOALLOC_ROWS + 1) * sizeof(long long) + 6 * 256;
+    (size_t)NOALLOC_ROWS * FOS_MAX_LAYERS * sizeof(float4) * 3 +
+    (size_t)(NOALLOC_ROWS + 1) * sizeof(long long) + 7 * 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 

@@ -570,6 +570,46 @@ __global__ void ensemble_kernel(const float* probs, int n_members, long long n, 
     }
 }
 
+// Feature statistics: per feature mean, standard deviation (floored at 1e-3 so that a
+// feature constant over the training set cannot blow up), min, max over n rows.
+// One block per feature; FP64 accumulation; writes stats[f], [16+f], [32+f], [48+f].
+__global__ void stats_kernel(const float* feat, long long n, float* stats) {
+    __shared__ double s1[256], s2[256];
+    __shared__ float mn[256], mx[256];
+    const int f = blockIdx.x;
+    double a = 0.0, b = 0.0;
+    float lo = 3.0e38f, hi = -3.0e38f;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        const float x = feat[i * N_FEAT + f];
+        a += x;
+        b += (double)x * x;
+        lo = fminf(lo, x);
+        hi = fmaxf(hi, x);
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    mn[threadIdx.x] = lo;
+    mx[threadIdx.x] = hi;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) {
+            s1[threadIdx.x] += s1[threadIdx.x + off];
+            s2[threadIdx.x] += s2[threadIdx.x + off];
+            mn[threadIdx.x] = fminf(mn[threadIdx.x], mn[threadIdx.x + off]);
+            mx[threadIdx.x] = fmaxf(mx[threadIdx.x], mx[threadIdx.x + off]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mean = s1[0] / (double)n;
+        const double var = s2[0] / (double)n - mean * mean;
+        stats[f] = (float)mean;
+        stats[16 + f] = fmaxf((float)sqrt(var > 0.0 ? var : 0.0), 1e-3f);
+        stats[32 + f] = mn[0];
+        stats[48 + f] = mx[0];
+    }
+}
+
 // ----------------------------------------------------------------------- host side
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 static std::mutex g_mu;
@@ -963,6 +1003,16 @@ fos_status fos_surrogate_features(int n_designs, int n_wl, const double* wl, con
         FOS_CUDA_TRY(cudaGetLastError());
     }
     return finish_call(ws, s, flags);
+}
+
+fos_status fos_surrogate_feature_stats(const float* features, long long n_rows, float* stats,
+                                       void* stream) {
+    if (!features || !stats || n_rows < 1) return FOS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    FOS_CUDA_TRY(cudaMemsetAsync(stats, 0, 64 * sizeof(float), s));
+    mlp::stats_kernel<<<mlp::N_FEAT, 256, 0, s>>>(features, n_rows, stats);
+    FOS_CUDA_TRY(cudaGetLastError());
+    return from_cuda(cudaStreamSynchronize(s));
 }
 
 fos_status fos_counts_to_fractions(const long long* counts, long long n_rows, float* fractions,

@@ -268,6 +268,13 @@ def fos_surrogate_features(wl, np_re, np_im, radius, vol_frac, thickness, g, mu_
         _stream(stream))
 
 
+def fos_surrogate_feature_stats(features, stats, stream=None) -> int:
+    return _sfn("fos_surrogate_feature_stats", [ctypes.c_void_p, ctypes.c_longlong,
+                                                ctypes.c_void_p, ctypes.c_void_p])(
+        _dev(features, torch.float32, "features"), features.numel() // 9,
+        _dev(stats, torch.float32, "stats"), _stream(stream))
+
+
 def fos_counts_to_fractions(counts, fractions, stream=None) -> int:
     n = counts.numel() // FOS_NCOUNT
     return _sfn("fos_counts_to_fractions", [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,

@@ -134,8 +134,10 @@ def single_layer_designs(n_designs: int, seed: int, n_wl: int | None = SWEEP_N_W
     thickness = rng.uniform(10.0, 500.0, size=n_designs)
     if random_wl:
         wl = rng.uniform(0.3, 2.5, size=n_designs)
-    else:
+    elif n_wl:
         wl = wavelengths(n_wl)
+    else:
+        wl = None
     return dict(radius=radius, vol_frac=vol_frac, thickness=thickness, wl=wl,
                 random_wl=bool(random_wl))
 
