@@ -58,6 +58,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--surrogate", choices=["full", "quick", "off"], default="full",
+                    help="surrogate leg (1 GPU only): MC training data, ensemble training, "
+                         "design sweep with MC fallback and audit")
+    ap.add_argument("--stacks", action="store_true",
+                    help="also time the uneven multilayer-stack batch once")
     return ap.parse_args()
 
 
@@ -320,6 +325,15 @@ def run_fos(args):
                            "(maximum SM clock)")
     if clocks:
         roof["frac_at_sampled_clock"] = achieved / (sm_count * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+    surr = None
+    if args.surrogate != "off" and world == 1:
+        try:
+            surr = run_surrogate(args.surrogate)
+        except Exception as exc:  # the surrogate leg must not hide the MC number
+            surr = dict(error=str(exc))
+    stacks = None
+    if args.stacks and world == 1:
+        stacks = run_stacks()
     cpu = None
     if not args.no_cpu and world == 1:
         try:
@@ -336,7 +350,8 @@ def run_fos(args):
                     precision="Mie f64, walk f32, tallies int64", parallelism=f"replicas x{world}"),
         spectra_per_s=spectra_per_s, photons_per_s=phot_all / secs,
         photon_steps_per_photon=coll / max(photons, 1),
-        e2e=e2e, roofline=roof, cpu_baseline=cpu, clocks=clocks,
+        e2e=e2e, roofline=roof, cpu_baseline=cpu, clocks=clocks, surrogate=surr,
+        layer_stacks=stacks,
         gpu_launches=5 * K,
         gpu_launches_detail="per step: mie_kernel, emt_kernel, pack_kernel, unit_scan_kernel, "
                             "walk_kernel",
@@ -344,6 +359,80 @@ def run_fos(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------ surrogate leg
+def run_surrogate(mode: str):
+    """Surrogate spectra/s vs plain GPU Monte Carlo spectra/s on the same designs.
+
+    Training data: single-layer designs (r, f, d in the workload ranges) x 50 random
+    wavelengths per block, Monte Carlo fractions at 1e4 photons; 4 members trained by
+    Adam.  Sweep: 1e5 designs x 300 wavelengths, ensemble spread > 0.01 or out-of-range
+    rows re-run by Monte Carlo at 1e5 photons; 0.1 % of rows audited by Monte Carlo at
+    1e5 photons."""
+    import torch
+
+    from paper_2409_00165_gb300 import surrogate as S
+    cfg = dict(full=dict(designs=20000, blocks=20, wl=50, photons=10000, steps=6000,
+                         sweep=100000),
+               quick=dict(designs=4000, blocks=10, wl=24, photons=10000, steps=2500,
+                          sweep=20000))[mode]
+    t0 = time.perf_counter()
+    f, y, info = S.training_set(cfg["designs"], cfg["wl"], cfg["blocks"], cfg["photons"], seed=4)
+    sur = S.Surrogate(4, S.Surrogate.stats_of(f), seed=7)
+    t1 = time.perf_counter()
+    hist = sur.fit(f, y, steps=cfg["steps"], batch=8192, lr=2e-3, log_every=cfg["steps"] - 1)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    r = S.sweep(sur, n_designs=cfg["sweep"], n_wl=300, seed=5, threshold=0.01,
+                audit_frac=0.001)
+    r["train"] = dict(rows=info["rows"], photons_per_row=info["photons_per_row"],
+                      data_seconds=t1 - t0, train_seconds=t2 - t1, members=4,
+                      steps_per_member=cfg["steps"], batch=8192,
+                      final_loss=[h[-1][1] for h in hist.values()])
+    r["mode"] = mode
+    return r
+
+
+def run_stacks():
+    """The uneven batch of 64 multilayer stacks x 200 wavelengths (log-uniform 1e4-1e6
+    photons each) in one graph-captured launch with an autotuned shape: photon-steps/s."""
+    import torch
+
+    from paper_2409_00165_gb300 import fos
+    from paper_2409_00165_gb300 import workloads as W
+    m = W.layer_stacks()
+    dev = "cuda"
+    f64 = torch.float64
+    d = {k: torch.as_tensor(v, dtype=f64, device=dev) for k, v in W.media_arrays(m).items()}
+    wl = torch.as_tensor(m["wl"], dtype=f64, device=dev)
+    sg = torch.as_tensor(m["species_group"], dtype=torch.int32, device=dev)
+    rad = torch.as_tensor(m["radius"], dtype=f64, device=dev)
+    vf = torch.as_tensor(m["vol_frac"], dtype=f64, device=dev)
+    n = m["n_groups"] * m["n_wl"]
+    mu_s, mu_a, g = (torch.zeros(n, dtype=f64, device=dev) for _ in range(3))
+    fos.check(fos.fos_mie_properties(wl, d["nm_re"], d["nm_im"], sg, d["np_re"], d["np_im"],
+                                     rad, vf, mu_s, mu_a, g), "mie")
+    th = torch.as_tensor(m["thickness"], dtype=f64, device=dev)
+    nl = torch.as_tensor(m["n_layers"], dtype=torch.int32, device=dev)
+    nph = torch.as_tensor(m["n_photons"], dtype=torch.int64, device=dev)
+    sub = torch.as_tensor(m["substrate_R"], dtype=f64, device=dev)
+    b = fos.make_batch(m["n_stacks"], m["n_wl"], m["max_layers"], mu_s, mu_a, g, d["nm_re"], th,
+                       n_layers=nl, substrate_R=sub, n_photons=nph, seed=m["seed"])
+    counts = torch.zeros((m["n_stacks"] * m["n_wl"], fos.FOS_NCOUNT), dtype=torch.int64,
+                         device=dev)
+    fos.check(fos.fos_mc_spectrum(b, counts, None, 0, fos.FOS_AUTOTUNE), "stacks autotune")
+    tun = fos.fos_mc_get_tuning(b)
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    fos.check(fos.fos_mc_spectrum(b, counts, None, 0, 0), "stacks")
+    e.record()
+    torch.cuda.synchronize()
+    s = a.elapsed_time(e) / 1e3
+    c = counts.sum(dim=0).cpu().numpy()
+    return dict(items=int(counts.shape[0]), photons=int(c[:4].sum()), photon_steps=int(c[4]),
+                seconds=s, photon_steps_per_s=float(c[4]) / s,
+                spectra_per_s=m["n_stacks"] / s, tuning=dict(block=tun[0], ppt=tun[1]))
 
 
 # ------------------------------------------------------------------------ reference arm

@@ -235,15 +235,25 @@ fos_status fos_surrogate_features(int n_designs, int n_wl, const double* wl,
                                   unsigned flags, void* stream);
 
 /* Statistics of raw feature rows [n_rows*9] (device float) into stats (device float[64]
- * = mean[16] | std[16] | lo[16] | hi[16], first 9 of each used; std floored at 1e-3),
- * the layout fos_surrogate_init takes.  Synchronous. */
+ * = mean[16] | std[16] | lo[16] | hi[16], first 9 of each used; std floored at 1e-3;
+ * [lo, hi] is the observed range widened by 1 % of its span on each side), the layout
+ * fos_surrogate_init takes.  Synchronous. */
 fos_status fos_surrogate_feature_stats(const float* features, long long n_rows, float* stats,
                                        void* stream);
 
-/* fractions[r] = (R, A, T) / (R + A + T) of counts row r (device int64 [n*FOS_NCOUNT]
- * -> device float [n*3]); asynchronous on stream. */
-fos_status fos_counts_to_fractions(const long long* counts, long long n_rows,
+/* (R, A, T) / (R + A + T) of counts row r (device int64 [n_rows*FOS_NCOUNT]) into row
+ * rows[r] of fractions (device float [*3]; row r when rows is NULL): turns photon counts
+ * into the spectra and scatters Monte Carlo fallback results into a prediction.
+ * Asynchronous on stream. */
+fos_status fos_counts_to_fractions(const long long* counts, long long n_rows, const int* rows,
                                    float* fractions, void* stream);
+
+/* The indices of the nonzero bytes of mask [n] (device) into rows (device int32,
+ * capacity n) and their number into *count (device int64): the work list of the rows
+ * fos_surrogate_predict flagged for Monte Carlo.  Order: ascending within blocks of 1024
+ * rows, blocks in any order.  Asynchronous on stream. */
+fos_status fos_mask_to_rows(const unsigned char* mask, long long n, int* rows, long long* count,
+                            void* stream);
 
 /* One Adam step (lr, beta 0.9/0.999, eps 1e-8, bias-corrected with t = step + 1) of
  * member `member` on a batch of `batch` rows (multiple of 256, <= 65536) of features

@@ -366,16 +366,43 @@ __global__ void features_kernel(int n_designs, int n_wl, const double* wl, const
     }
 }
 
-__global__ void fractions_kernel(const long long* counts, long long n, float* out) {
+__global__ void fractions_kernel(const long long* counts, long long n, const int* rows,
+                                 float* out) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const long long* c = counts + i * FOS_NCOUNT;
         const double tot = (double)(c[0] + c[1] + c[2]);
         const double inv = tot > 0 ? 1.0 / tot : 0.0;
-        out[i * 3 + 0] = (float)(c[0] * inv);
-        out[i * 3 + 1] = (float)(c[1] * inv);
-        out[i * 3 + 2] = (float)(c[2] * inv);
+        const long long o = rows ? (long long)rows[i] : i;
+        out[o * 3 + 0] = (float)(c[0] * inv);
+        out[o * 3 + 1] = (float)(c[1] * inv);
+        out[o * 3 + 2] = (float)(c[2] * inv);
     }
+}
+
+// Indices of the nonzero bytes of mask [n] -> rows (ascending within each block of 1024,
+// blocks in any order) and their number in *count (which must start at 0).
+__global__ void mask_rows_kernel(const unsigned char* mask, long long n, int* rows,
+                                 unsigned long long* count) {
+    __shared__ unsigned wsum[32];
+    __shared__ unsigned long long base;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const bool on = i < n && mask[i] != 0;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, on);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+        for (unsigned w = 0; w < blockDim.x / 32; ++w) {
+            const unsigned v = wsum[w];
+            wsum[w] = tot;
+            tot += v;
+        }
+        base = tot ? atomicAdd(count, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    if (on) rows[base + wsum[warp] + __popc(bal & ((1u << lane) - 1u))] = (int)i;
 }
 
 __device__ __forceinline__ uint32_t mix32(uint32_t x) {   // a 32-bit integer hash (murmur3 finaliser)
@@ -571,7 +598,8 @@ __global__ void ensemble_kernel(const float* probs, int n_members, long long n, 
 }
 
 // Feature statistics: per feature mean, standard deviation (floored at 1e-3 so that a
-// feature constant over the training set cannot blow up), min, max over n rows.
+// feature constant over the training set cannot blow up), and the range [min, max]
+// over n rows widened by 1 % of its span on each side (the trusted input range).
 // One block per feature; FP64 accumulation; writes stats[f], [16+f], [32+f], [48+f].
 __global__ void stats_kernel(const float* feat, long long n, float* stats) {
     __shared__ double s1[256], s2[256];
@@ -605,8 +633,9 @@ __global__ void stats_kernel(const float* feat, long long n, float* stats) {
         const double var = s2[0] / (double)n - mean * mean;
         stats[f] = (float)mean;
         stats[16 + f] = fmaxf((float)sqrt(var > 0.0 ? var : 0.0), 1e-3f);
-        stats[32 + f] = mn[0];
-        stats[48 + f] = mx[0];
+        const float span = fmaxf(mx[0] - mn[0], 1e-3f);
+        stats[32 + f] = mn[0] - 0.01f * span;   // training range, widened by 1 % of its span
+        stats[48 + f] = mx[0] + 0.01f * span;
     }
 }
 
@@ -1015,14 +1044,26 @@ fos_status fos_surrogate_feature_stats(const float* features, long long n_rows, 
     return from_cuda(cudaStreamSynchronize(s));
 }
 
-fos_status fos_counts_to_fractions(const long long* counts, long long n_rows, float* fractions,
-                                   void* stream) {
+fos_status fos_counts_to_fractions(const long long* counts, long long n_rows, const int* rows,
+                                   float* fractions, void* stream) {
     if (n_rows < 0 || (n_rows > 0 && (!counts || !fractions))) return FOS_ERR_INVALID_ARG;
     if (n_rows == 0) return FOS_OK;
     cudaStream_t s = (cudaStream_t)stream;
     long long blocks = (n_rows + 255) / 256;
     if (blocks > 65535) blocks = 65535;
-    mlp::fractions_kernel<<<(unsigned)blocks, 256, 0, s>>>(counts, n_rows, fractions);
+    mlp::fractions_kernel<<<(unsigned)blocks, 256, 0, s>>>(counts, n_rows, rows, fractions);
+    return from_cuda(cudaGetLastError());
+}
+
+fos_status fos_mask_to_rows(const unsigned char* mask, long long n, int* rows, long long* count,
+                            void* stream) {
+    if (n < 0 || n > 0x7fffffffLL || (n > 0 && (!mask || !rows)) || !count)
+        return FOS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    FOS_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(long long), s));
+    if (n == 0) return FOS_OK;
+    mlp::mask_rows_kernel<<<(unsigned)((n + 1023) / 1024), 1024, 0, s>>>(
+        mask, n, rows, (unsigned long long*)count);
     return from_cuda(cudaGetLastError());
 }
 

@@ -275,12 +275,19 @@ def fos_surrogate_feature_stats(features, stats, stream=None) -> int:
         _dev(stats, torch.float32, "stats"), _stream(stream))
 
 
-def fos_counts_to_fractions(counts, fractions, stream=None) -> int:
+def fos_counts_to_fractions(counts, fractions, rows=None, stream=None) -> int:
     n = counts.numel() // FOS_NCOUNT
     return _sfn("fos_counts_to_fractions", [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
-                                            ctypes.c_void_p])(
-        _dev(counts, torch.int64, "counts"), n, _dev(fractions, torch.float32, "fractions"),
-        _stream(stream))
+                                            ctypes.c_void_p, ctypes.c_void_p])(
+        _dev(counts, torch.int64, "counts"), n, _dev(rows, torch.int32, "rows", True),
+        _dev(fractions, torch.float32, "fractions"), _stream(stream))
+
+
+def fos_mask_to_rows(mask, rows, count, stream=None) -> int:
+    return _sfn("fos_mask_to_rows", [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p])(
+        _dev(mask, torch.uint8, "mask"), mask.numel(), _dev(rows, torch.int32, "rows"),
+        _dev(count, torch.int64, "count"), _stream(stream))
 
 
 def fos_surrogate_train_step(model, member, features, targets, batch, seed, step, lr,

@@ -77,10 +77,18 @@ class Media:
         return out
 
 
-def fractions(counts, stream=None):
-    out = torch.zeros((counts.shape[0], 3), dtype=torch.float32, device=counts.device)
-    fos.check(fos.fos_counts_to_fractions(counts, out, stream), "fos_counts_to_fractions")
+def fractions(counts, stream=None, rows=None, out=None):
+    if out is None:
+        out = torch.zeros((counts.shape[0], 3), dtype=torch.float32, device=counts.device)
+    fos.check(fos.fos_counts_to_fractions(counts, out, rows, stream), "fos_counts_to_fractions")
     return out
+
+
+def flagged_rows(needs):
+    rows = torch.empty(needs.numel(), dtype=torch.int32, device=needs.device)
+    count = torch.zeros(1, dtype=torch.int64, device=needs.device)
+    fos.check(fos.fos_mask_to_rows(needs, rows, count), "fos_mask_to_rows")
+    return rows[: int(count.item())]
 
 
 class Surrogate:
@@ -130,3 +138,129 @@ class Surrogate:
                                             spread, needs, threshold, flags=flags, stream=stream),
                   "fos_surrogate_predict")
         return rat, spread, needs
+
+
+def training_set(n_designs: int, wl_per_block: int, blocks: int, photons: int, seed: int,
+                 device="cuda"):
+    """Monte Carlo training rows of single-layer designs (workload ranges of r, f, d).
+
+    The designs are split into `blocks`; each block gets its own sorted random
+    wavelength set drawn from U(0.3, 2.5) um plus both ends of that range, so that the
+    training rows cover the whole spectrum.  Returns (features, fractions, info)."""
+    rng = np.random.default_rng(seed)
+    d = W.single_layer_designs(n_designs, seed=seed, n_wl=None)
+    per = n_designs // blocks
+    feats, targs = [], []
+    coll = phot = 0
+    mc_s = 0.0
+    for k in range(blocks):
+        sl = slice(k * per, (k + 1) * per)
+        wl = np.sort(np.concatenate([[0.3, 2.5], rng.uniform(0.3, 2.5, wl_per_block - 2)]))
+        m = Media(d["radius"][sl], d["vol_frac"][sl], d["thickness"][sl], wl, device)
+        m.mie()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        counts = m.mc(photons, seed=seed * 1000 + k)
+        b.record()
+        torch.cuda.synchronize()
+        mc_s += a.elapsed_time(b) / 1e3
+        tot = counts.sum(dim=0)
+        coll += int(tot[4].item())
+        phot += int(tot[:4].sum().item())
+        feats.append(m.features())
+        targs.append(fractions(counts))
+    info = dict(rows=per * blocks * wl_per_block, designs=per * blocks, photons_per_row=photons,
+                mc_seconds=mc_s, photon_steps=coll, photons=phot)
+    return torch.cat(feats), torch.cat(targs), info
+
+
+def sweep(sur: Surrogate, n_designs: int, n_wl: int, seed: int, threshold: float = 0.01,
+          fallback_photons: int = 100000, audit_frac: float = 0.001, audit_photons: int = 100000,
+          device="cuda"):
+    """Surrogate design sweep: Mie -> features -> ensemble prediction -> Monte Carlo on the
+    rows the ensemble flags; then a random audit of rows by Monte Carlo.  Returns timings,
+    counts and the audit errors (absolute, per R, A, T) of the final spectra."""
+    d = W.single_layer_designs(n_designs, seed=seed, n_wl=n_wl)
+    m = Media(d["radius"], d["vol_frac"], d["thickness"], d["wl"], device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    m.mie(flags=fos.FOS_ASYNC)
+    f = m.features(flags=fos.FOS_ASYNC)
+    ev[1].record()
+    rat, spread, needs = sur.predict(f, threshold, flags=fos.FOS_ASYNC)
+    ev[2].record()
+    flagged = flagged_rows(needs)
+    n_flag = int(flagged.numel())
+    if n_flag:
+        cf = m.mc(fallback_photons, seed=seed + 17, item_list=flagged)
+        fractions(cf, rows=flagged, out=rat)
+    ev[3].record()
+    torch.cuda.synchronize()
+    fos.check(fos.fos_sync_status(), "sweep")
+    t_mie = ev[0].elapsed_time(ev[1]) / 1e3
+    t_pred = ev[1].elapsed_time(ev[2]) / 1e3
+    t_fb = ev[2].elapsed_time(ev[3]) / 1e3
+    total = t_mie + t_pred + t_fb
+    out = dict(designs=n_designs, wavelengths=n_wl, rows=m.rows, flagged=n_flag,
+               mie_features_s=t_mie, predict_s=t_pred, fallback_mc_s=t_fb, total_s=total,
+               spectra_per_s=n_designs / total,
+               spectra_per_s_no_fallback=n_designs / (t_mie + t_pred))
+    if audit_frac > 0:
+        arng = np.random.default_rng(seed + 99)
+        n_aud = max(1, int(m.rows * audit_frac))
+        rows = np.sort(arng.choice(m.rows, size=n_aud, replace=False)).astype(np.int32)
+        rt = torch.as_tensor(rows, device=device)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ca = m.mc(audit_photons, seed=seed + 23, item_list=rt)
+        b.record()
+        torch.cuda.synchronize()
+        t_a = a.elapsed_time(b) / 1e3
+        ya = fractions(ca)
+        err = (rat[rt.long()] - ya).abs()
+        phot = int(ca[:, :4].sum().item())
+        out["audit"] = dict(rows=n_aud, photons=audit_photons,
+                            mae=err.mean(dim=0).cpu().tolist(),
+                            max=err.max(dim=0).values.cpu().tolist())
+        # plain GPU Monte Carlo on the same designs, per spectrum of n_wl wavelengths
+        out["mc_photons_per_s"] = phot / t_a
+        out["mc_spectra_per_s"] = phot / t_a / (n_wl * audit_photons)
+        out["speedup_vs_mc"] = out["spectra_per_s"] / out["mc_spectra_per_s"]
+    return out
+
+
+def _predict_demo(rows: int, members: int, reps: int):
+    """Ensemble prediction on random in-range features (a profiling target)."""
+    rng = np.random.default_rng(0)
+    x = np.column_stack([rng.uniform(0.3, 2.5, rows), rng.uniform(2.5, 3.1, rows),
+                         rng.uniform(-4, -0.3, rows), rng.uniform(0.05, 1, rows),
+                         rng.uniform(0.01, 0.3, rows), rng.uniform(1, 2.7, rows),
+                         rng.uniform(0, 0.9, rows), rng.uniform(-1, 3, rows),
+                         rng.uniform(-4, 2, rows)]).astype(np.float32)
+    f = torch.as_tensor(x, device="cuda").contiguous()
+    sur = Surrogate(members, Surrogate.stats_of(f), seed=1)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        sur.predict(f)
+    a.record()
+    for _ in range(reps):
+        sur.predict(f)
+    b.record()
+    torch.cuda.synchronize()
+    s = a.elapsed_time(b) / 1e3 / reps
+    flops = 2.0 * rows * members * (64 * 256 + 3 * 256 * 256 + 256 * 64)
+    print(f"predict {rows} rows x {members} members: {s * 1e3:.3f} ms, "
+          f"{flops / s / 1e12:.1f} TFLOP/s (padded products)")
+
+
+if __name__ == "__main__":
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--predict-demo", action="store_true")
+    ap.add_argument("--rows", type=int, default=1 << 19)
+    ap.add_argument("--members", type=int, default=4)
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+    if a.predict_demo:
+        _predict_demo(a.rows, a.members, a.reps)

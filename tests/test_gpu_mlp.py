@@ -243,3 +243,25 @@ def test_features_and_fractions():
     fos.check(fos.fos_counts_to_fractions(counts, fr), "fractions")
     torch.cuda.synchronize()
     assert np.allclose(fr.cpu().numpy(), [[0.3, 0.5, 0.2], [0, 0, 0]])
+    # scatter into given rows
+    big = torch.full((5, 3), -1.0, dtype=torch.float32, device="cuda")
+    fos.check(fos.fos_counts_to_fractions(counts, big, torch.tensor([4, 1], dtype=torch.int32,
+                                                                    device="cuda")), "scatter")
+    torch.cuda.synchronize()
+    b = big.cpu().numpy()
+    assert np.allclose(b[4], [0.3, 0.5, 0.2]) and np.allclose(b[1], 0) and np.all(b[0] == -1)
+
+
+def test_mask_to_rows():
+    rng = np.random.default_rng(8)
+    for n in (0, 1, 1023, 1024, 1025, 300000):
+        m = (rng.random(n) < 0.01).astype(np.uint8)
+        if n:
+            m[-1] = 1
+        mask = torch.as_tensor(m, device="cuda")
+        rows = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        fos.check(fos.fos_mask_to_rows(mask, rows, cnt), "mask_to_rows")
+        k = int(cnt.item())
+        got = np.sort(rows[:k].cpu().numpy())
+        assert np.array_equal(got, np.nonzero(m)[0])
