@@ -66,6 +66,9 @@ enum {
 
 const char* fos_status_string(fos_status s);
 int fos_api_version(void);
+/* Name and message of the last CUDA runtime error a library call on this host thread
+ * met (the cause behind FOS_ERR_CUDA / FOS_ERR_NOMEM); "" if none. */
+const char* fos_last_cuda_error(void);
 
 /* Waits (bounded by timeout_ms; <= 0 -> 600000) for `stream` and returns the status of
  * the library work enqueued on the current device since the last check (FOS_ASYNC
@@ -127,9 +130,13 @@ fos_status fos_mie_properties(int n_wl, const double* wl,
  *      leaving the bottom or absorbed by the reflector -> T;
  *   5. after max_events collisions + boundary arrivals is stopped -> runaway.
  * The walk is FP32 with a fixed operation order; random numbers come from
- * Philox4x32-10 with key = seed and counter = (photon id, item id, event, stream),
- * so results depend only on (seed, item id, photon id), not on launch shape, and
- * agree bit for bit with any implementation of the same operation order.
+ * Philox4x32-10 with key = seed and counter = (photon id, item id, event, stream):
+ * collision e uses the 4 words of counter (p, item, e, 0) (free path, absorption,
+ * deflection, azimuth; word 3 of block 0 is the entry Fresnel test, since the first
+ * collision has mu_z = +-1 and needs no azimuth), boundary draw k uses word k mod 4 of
+ * counter (p, item, k/4, 1).  Results depend only on (seed, item id, photon id), not
+ * on launch shape, and agree bit for bit with any implementation of the same
+ * operation order.
  *
  * Property layout (device, FP64): layer j of stack s at wavelength w is element
  * (s*max_layers + j)*n_wl + w of mu_s, mu_a, g, n_layer (the layout of the
@@ -199,7 +206,8 @@ fos_status fos_walk_math_f32(const float* u, float* neg_log, float* cos2pi, long
  * Carlo simulations predicts R, A, T; Table 1 lists the ranges it was trained on).
  *
  * Network: 9 raw features -> standardised -> [Linear 256, GELU] x 4 -> Linear 3 ->
- * softmax = (R, A, T), summing to 1.  Products run on the tensor cores (tcgen05.mma,
+ * softmax = (R, A, T), summing to 1 (GELU in its tanh form z/2 (1 + tanh(sqrt(2/pi)
+ * (z + 0.044715 z^3)))).  Products run on the tensor cores (tcgen05.mma,
  * BF16 operands, FP32 accumulation in tensor memory); master weights and Adam state are
  * FP32.  Features of a row (stack of one layer, wavelength): lambda, n_p, log10 k_p,
  * radius, volume fraction, log10 thickness, g, log10(mu_s d + 1e-6), log10(mu_a d + 1e-6).

@@ -239,8 +239,9 @@ struct LayerP {
 };
 
 // Random numbers of one photon.  Collision event e reads the block at counter
-// (p, item, e, 0): u0 free path, u1 absorb test, u2 HG deflection, u3 azimuth.
-// Interface draw k reads word k mod 4 of the block at counter (p, item, k/4, 1).
+// (p, item, e, 0): u0 free path, u1 absorb test, u2 HG deflection, u3 azimuth (in
+// block 0, u3 is the entry Fresnel test instead).  Interface draw k (boundary
+// crossings after entry) reads word k mod 4 of the block at counter (p, item, k/4, 1).
 struct PhotonRng {
     uint32_t key[2];
     uint32_t p, item;
@@ -262,21 +263,21 @@ static int walk_photon(const LayerP<M>* L, int nl, typename M::R n_above, typena
     uint32_t blk[4];
     int outcome = -1;
 
-    // Launch: normal incidence at the top surface (z = 0), from the medium above.
+    // Launch: normal incidence at the top surface (z = 0), from the medium above.  The
+    // entry Fresnel test reads word 3 of collision block 0: that word is the azimuth
+    // of the first collision, which is never used because mu_z is exactly +-1 until
+    // the first scattering (refraction and reflection at normal incidence keep it).
+    rng.block(e, 0u, blk);
     {
         R ni = n_above, nt = L[0].n;
         if (ni != nt) {
             R ct; bool tir;
             R Rf = fresnel<M>(ni, nt, (R)1, &ct, &tir);
-            rng.block(k_if >> 2, 1u, blk);
-            R u = M::uni(blk[k_if & 3u]);
-            k_if++;
-            if (tir || u < Rf) { *n_coll = 0; *n_iface = 0; return OUT_R; }
+            if (M::uni(blk[3]) < Rf) { *n_coll = 0; *n_iface = 0; return OUT_R; }
         }
     }
     int j = 0;
     R z = (R)0, mu = (R)1;
-    rng.block(e, 0u, blk);
     R tau = M::neg_log(M::uni(blk[0]));
     R u1 = M::uni(blk[1]), u2 = M::uni(blk[2]), u3 = M::uni(blk[3]);
 

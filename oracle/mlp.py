@@ -6,7 +6,8 @@ features to (R, A, T):
 
     x (9) -> standardise -> [Linear 256, GELU] x 4 -> Linear 3 -> softmax
 
-GELU is the exact form x * Phi(x) = x/2 (1 + erf(x / sqrt 2)).  The loss is the
+GELU is its tanh form x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))) (Hendrycks &
+Gimpel 2016), evaluated here with exact tanh.  The loss is the
 softmax cross-entropy against the Monte Carlo fractions (soft labels), averaged over the
 batch.  Adam (Kingma & Ba 2015) updates FP32 master weights.  Everything here is plain
 float64 NumPy, written from those definitions, with no blocking or fusion.
@@ -20,7 +21,6 @@ from __future__ import annotations
 import math
 
 import numpy as np
-from scipy.special import erf
 
 N_IN = 9
 HIDDEN = 256
@@ -33,12 +33,17 @@ def layer_shapes(n_in=N_IN, hidden=HIDDEN, n_hidden=N_HIDDEN_LAYERS, n_out=N_OUT
     return [(dims[i + 1], dims[i]) for i in range(len(dims) - 1)]   # (out, in)
 
 
+GELU_C = math.sqrt(2.0 / math.pi)
+GELU_A = 0.044715
+
+
 def gelu(z):
-    return 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))
+    return 0.5 * z * (1.0 + np.tanh(GELU_C * (z + GELU_A * z ** 3)))
 
 
 def gelu_grad(z):
-    return 0.5 * (1.0 + erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2 * math.pi)
+    t = np.tanh(GELU_C * (z + GELU_A * z ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * GELU_C * (1.0 + 3.0 * GELU_A * z * z)
 
 
 def softmax(z):

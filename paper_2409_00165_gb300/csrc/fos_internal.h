@@ -6,7 +6,7 @@
 #include <cstddef>
 #include <cstdint>
 
-#include "../../include/fos.h"
+#include "fos.h"   // include/ is on the compiler include path
 
 namespace fos {
 

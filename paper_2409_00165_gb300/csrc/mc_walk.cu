@@ -14,6 +14,8 @@
 // cos(2 pi u) are self-contained series (see neg_log_u / cos_2pi_u) so that the walk
 // is a fixed sequence of IEEE operations: the same operation order on any machine
 // gives the same photons bit for bit.
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -166,7 +168,7 @@ __device__ __forceinline__ float hg_cos(float g, float omg2, float opg2, float o
 // ---------------------------------------------------------------------------------
 struct Tables {
     int4* head;       // {n_layers, n_above bits, n_below bits, substrate R bits (<0: none)}
-    int4* info;       // {rng item id, first photon id, photon count, 0}
+    int4* info;       // {rng item id, first photon id, photon count, entry reflectance bits}
     float4* layA;     // [row*max_layers + j] {mu_t, mu_a/mu_t, g, n}
     float4* layB;     // [row*max_layers + j] {d, 1-g^2, 1+g^2, 1-g}
     float4* layC;     // [row*max_layers + j] {1/mu_t, 1/(2g), 0, 0}
@@ -273,8 +275,17 @@ __global__ void pack_kernel(PackArgs A) {
     if (!ok) flag_invalid(A.status, r);
     A.t.head[r] = make_int4(nl, __float_as_int((float)na), __float_as_int((float)nb),
                             __float_as_int(rsub));
+    float r_entry = 0.0f;
+    {
+        const float na_f = (float)na, n0 = A.t.layA[(long long)r * b.max_layers].w;
+        if (na_f != n0) {
+            float ct;
+            bool tir;
+            r_entry = fresnel(na_f, n0, 1.0f, ct, tir);
+        }
+    }
     A.t.info[r] = make_int4((int)(b.item_id_base + (unsigned)it), (int)(unsigned)first,
-                            ok ? (int)(unsigned)N : 0, 0);
+                            ok ? (int)(unsigned)N : 0, __float_as_int(r_entry));
 }
 
 // Exclusive prefix of work units per row, one block: each thread sums a contiguous
@@ -472,26 +483,16 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
                 e = 0u;
                 kif = 0u;
                 ev = 0u;
-                bool reflected = false;
-                if (n_above != l_n) {   // entry: normal incidence from the medium above
-                    float ct;
-                    bool tir;
-                    const float Rf = fresnel(n_above, l_n, 1.0f, ct, tir);
-                    const uint4 blk = philox_rk(make_uint4(p, item_rng, 0u, 1u), A.rk);
-                    const float u = uni(blk.x);
-                    kif = 1u;
-                    reflected = tir || (u < Rf);
-                }
-                if (reflected) {
+                const uint4 blk0 = philox_rk(make_uint4(p, item_rng, 0u, 0u), A.rk);
+                if (uni(blk0.w) < __int_as_float(inf.w)) {
                     finish(O_R);
                 } else {
                     z = 0.0f;
                     mu = 1.0f;
-                    const uint4 blk = philox_rk(make_uint4(p, item_rng, 0u, 0u), A.rk);
-                    tau = neg_log_u(uni(blk.x));
-                    u1 = uni(blk.y);
-                    u2 = uni(blk.z);
-                    u3 = uni(blk.w);
+                    tau = neg_log_u(uni(blk0.x));
+                    u1 = uni(blk0.y);
+                    u2 = uni(blk0.z);
+                    u3 = uni(blk0.w);
                     alive = true;
                 }
             }
@@ -509,6 +510,10 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
             const float am = fabsf(mu);
             const float dist = (mu > 0.0f) ? (l_d - z) : z;
             const bool collide = (mu != 0.0f) ? (tau * am < l_mut * dist) : (l_mut > 0.0f);
+            // one Philox block per event at a common point (no divergence around it):
+            // collision -> next collision block; boundary -> interface block of draw kif
+            const uint4 blk = philox_rk(make_uint4(p, item_rng, collide ? e + 1u : (kif >> 2),
+                                                   collide ? 0u : 1u), A.rk);
             if (collide) {
                 // collision inside the layer
                 const float s = tau * l_imt;
@@ -529,7 +534,6 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
                     mu = fminf(fmaxf(mu, -1.0f), 1.0f);
                 }
                 e++;
-                const uint4 blk = philox_rk(make_uint4(p, item_rng, e, 0u), A.rk);
                 tau = neg_log_u(uni(blk.x));
                 u1 = uni(blk.y);
                 u2 = uni(blk.z);
@@ -545,7 +549,6 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
                 const int nb = down ? j + 1 : j - 1;
                 const bool outside = (nb < 0) || (nb >= nl);
                 if (down && outside && r_sub >= 0.0f) {
-                    const uint4 blk = philox_rk(make_uint4(p, item_rng, kif >> 2, 1u), A.rk);
                     const float u = uni(word(blk, kif & 3u));
                     kif++;
                     if (u < r_sub) mu = -mu;
@@ -566,8 +569,6 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
                     if (tir) {
                         transmit = false;
                     } else {
-                        const uint4 blk =
-                            philox_rk(make_uint4(p, item_rng, kif >> 2, 1u), A.rk);
                         const float u = uni(word(blk, kif & 3u));
                         kif++;
                         transmit = !(u < Rf);
@@ -810,11 +811,15 @@ static fos_status autotune(Workspace* ws, const fos_mc_batch* b, long long n_run
     const size_t cbytes = (size_t)n_run * FOS_NCOUNT * sizeof(long long);
     fos_status st = ensure_buffer(ws, (void**)&ws->tune_counts, &ws->tune_bytes, cbytes);
     if (st != FOS_OK) return st;
-    // cap each row so that the probe runs about 2^21 photons in total
-    long long cap = (1LL << 21) / (n_run > 0 ? n_run : 1);
-    if (cap < 256) cap = 256;
-    const int blocks[] = {128, 256, 512};
-    const int ppts[] = {2, 8, 32};
+    // cap each row so that the probe runs about 2^24 photons in total: enough photons per
+    // warp that the probe measures the steady state, not the tail of the last units
+    long long cap = (1LL << 24) / (n_run > 0 ? n_run : 1);
+    if (cap < 4096) cap = 4096;
+    // Candidate shapes keep 24 warps resident per SM at the kernel's register count
+    // (512-thread blocks fit only once per SM and measured 15 % slower at full size).
+    const int blocks[] = {128, 256};
+    const int ppts[] = {4, 8, 32};
+    const bool verbose = getenv("FOS_AUTOTUNE_VERBOSE") != nullptr;
     cudaEvent_t e0, e1;
     FOS_CUDA_TRY(cudaEventCreate(&e0));
     FOS_CUDA_TRY(cudaEventCreate(&e1));
@@ -838,6 +843,7 @@ static fos_status autotune(Workspace* ws, const fos_mc_batch* b, long long n_run
                 if (rep > 0 && ms < ms_min) ms_min = ms;
             }
             if (st != FOS_OK) break;
+            if (verbose) fprintf(stderr, "fos autotune: block %d ppt %d: %.3f ms\n", bl, pp, ms_min);
             if (ms_min < best_ms) {
                 best_ms = ms_min;
                 bt = tu;

@@ -30,8 +30,9 @@ __device__ __forceinline__ cx operator*(cx a, cx b) {
     return cx{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
 __device__ __forceinline__ cx operator*(double s, cx a) { return cx{s * a.re, s * a.im}; }
-// Smith's algorithm for complex division (no intermediate overflow).
-__device__ __forceinline__ cx operator/(cx a, cx b) {
+// Complex division a/b = a conj(b) / |b|^2 with one real division; Smith's algorithm
+// (no intermediate overflow) when |b| is outside [1e-150, 1e150].
+__device__ __forceinline__ cx div_smith(cx a, cx b) {
     if (fabs(b.re) >= fabs(b.im)) {
         const double r = b.im / b.re, d = b.re + b.im * r;
         return cx{(a.re + a.im * r) / d, (a.im - a.re * r) / d};
@@ -39,6 +40,12 @@ __device__ __forceinline__ cx operator/(cx a, cx b) {
         const double r = b.re / b.im, d = b.re * r + b.im;
         return cx{(a.re * r + a.im) / d, (a.im * r - a.re) / d};
     }
+}
+__device__ __forceinline__ cx operator/(cx a, cx b) {
+    const double m = fmax(fabs(b.re), fabs(b.im));
+    if (m > 1e150 || m < 1e-150) return div_smith(a, b);
+    const double inv = 1.0 / (b.re * b.re + b.im * b.im);
+    return cx{(a.re * b.re + a.im * b.im) * inv, (a.im * b.re - a.re * b.im) * inv};
 }
 __device__ __forceinline__ double norm2(cx a) { return a.re * a.re + a.im * a.im; }
 __device__ __forceinline__ double cabs_(cx a) { return hypot(a.re, a.im); }

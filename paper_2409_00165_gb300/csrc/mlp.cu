@@ -1,7 +1,7 @@
 // Learned surrogate of the photon walk on GB300 (arxiv 2409.00165, section "Photon
 // transport": a network trained on Monte Carlo spectra replaces the walk).
 //
-// Network: 9 features -> standardise -> [Linear 256, GELU] x 4 -> Linear 3 -> softmax
+// Network: 9 features -> standardise -> [Linear 256, GELU (tanh form)] x 4 -> Linear 3 -> softmax
 // (R, A, T).  BF16 weights and activations on the tensor cores, FP32 accumulation,
 // FP32 master weights and Adam state.
 //
@@ -140,12 +140,24 @@ struct GemmArgs {
     unsigned tx_bytes;     // bytes one stage receives from the two TMA loads
 };
 
+// GELU in its tanh form, z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))), with the
+// hardware tanh approximation (relative error ~2^-11, below BF16 rounding).
+__device__ __forceinline__ float tanh_fast(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float gelu_f(float z) {
-    return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+    const float z2 = z * z;
+    const float t = tanh_fast(z * fmaf(0.0356774081f, z2, 0.7978845608f));
+    const float hz = 0.5f * z;
+    return fmaf(hz, t, hz);
 }
 __device__ __forceinline__ float gelu_grad_f(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
-           z * expf(-0.5f * z * z) * 0.39894228040143268f;
+    const float z2 = z * z;
+    const float t = tanh_fast(z * fmaf(0.0356774081f, z2, 0.7978845608f));
+    const float dudz = fmaf(0.1070322243f, z2, 0.7978845608f);   // d/dz of the tanh argument
+    return fmaf(0.5f, 1.0f + t, 0.5f * z * (1.0f - t * t) * dudz);
 }
 
 template <int NT>

@@ -1,5 +1,6 @@
 // libfos runtime: status strings, per-device workspace, bounded waits.
 #include <chrono>
+#include <cstdio>
 #include <mutex>
 #include <thread>
 
@@ -19,8 +20,14 @@ __global__ void accumulate_status_kernel(unsigned* st) {
 }
 }  // namespace
 
+namespace {
+thread_local char t_last_error[256] = "";
+}
+
 fos_status from_cuda(cudaError_t e) {
     if (e == cudaSuccess) return FOS_OK;
+    snprintf(t_last_error, sizeof(t_last_error), "%s: %s", cudaGetErrorName(e),
+             cudaGetErrorString(e));
     if (e == cudaErrorMemoryAllocation) return FOS_ERR_NOMEM;
     return FOS_ERR_CUDA;
 }
@@ -126,6 +133,8 @@ const char* fos_status_string(fos_status s) {
 }
 
 int fos_api_version(void) { return FOS_API_VERSION; }
+
+const char* fos_last_cuda_error(void) { return fos::t_last_error; }
 
 fos_status fos_sync_status(void* stream, int timeout_ms) {
     fos::Workspace* ws = nullptr;

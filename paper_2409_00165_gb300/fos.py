@@ -41,7 +41,10 @@ _lib = None
 class FosError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
-        super().__init__(f"{where}: {fos_status_string(status)} (status {status})")
+        extra = ""
+        if status in (FOS_ERR_CUDA, FOS_ERR_NOMEM):
+            extra = f" [{fos_last_cuda_error()}]"
+        super().__init__(f"{where}: {fos_status_string(status)} (status {status}){extra}")
 
 
 class FosBatch(ctypes.Structure):
@@ -99,6 +102,12 @@ def lib():
 
 def fos_status_string(status: int) -> str:
     return lib().fos_status_string(int(status)).decode()
+
+
+def fos_last_cuda_error() -> str:
+    fn = lib().fos_last_cuda_error
+    fn.restype = ctypes.c_char_p
+    return (fn() or b"").decode()
 
 
 def check(status: int, where: str, allow=(FOS_OK,)) -> int:

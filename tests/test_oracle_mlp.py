@@ -47,7 +47,7 @@ def test_gradients_match_torch_autograd_full_size():
     h = (torch.tensor(x) - torch.tensor(mean)) / torch.tensor(std)
     for i, (W, b) in enumerate(tp):
         z = h @ W.T + b
-        h = torch.nn.functional.gelu(z) if i < len(tp) - 1 else z
+        h = torch.nn.functional.gelu(z, approximate="tanh") if i < len(tp) - 1 else z
     lt = -(torch.tensor(y) * torch.log_softmax(h, dim=1)).sum(dim=1).mean()
     lt.backward()
     assert abs(lt.item() - L) < 1e-12
@@ -73,8 +73,14 @@ def test_gelu_special_values():
     z = np.array([-3.0, -1.0, 0.0, 1.0, 3.0])
     g = M.gelu(z)
     assert g[2] == 0.0
-    assert abs(g[3] - 0.8413447460685429) < 1e-15      # 1 * Phi(1)
     assert abs(g[3] - g[1] - 1.0) < 1e-15              # gelu(x) - gelu(-x) = x
+    # the tanh form stays within 2e-3 of the exact x Phi(x)
+    from scipy.special import erf
+    exact = 0.5 * z * (1 + erf(z / math.sqrt(2)))
+    assert np.max(np.abs(g - exact)) < 2e-3
+    torch = pytest.importorskip("torch")
+    tt = torch.nn.functional.gelu(torch.tensor(z), approximate="tanh").numpy()
+    assert np.allclose(g, tt, rtol=1e-14, atol=1e-15)
     # derivative by finite differences
     h = 1e-6
     fd = (M.gelu(z + h) - M.gelu(z - h)) / (2 * h)
