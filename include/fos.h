@@ -48,7 +48,8 @@ enum {
     FOS_ERR_CUDA = 2,          /* a CUDA runtime call failed                          */
     FOS_ERR_NOMEM = 3,         /* workspace allocation failed                          */
     FOS_ERR_STEP_LIMIT = 4,    /* some photon hit max_events; counted as "runaway"    */
-    FOS_ERR_TIMEOUT = 5,       /* the bounded wait for the stream ran out             */
+    FOS_ERR_TIMEOUT = 5,       /* a bounded wait ran out (host wait for the stream, or
+                                  an in-kernel wait that gave up and returned)         */
     FOS_ERR_OUT_OF_RANGE = 6,  /* input outside what a kernel supports (e.g. Mie order) */
     FOS_ERR_INJECTED = 7,      /* test-only failure injected by FOS_TEST_INJECT       */
     FOS_ERR_UNSUPPORTED = 8    /* device is not sm_103 / feature not built            */
@@ -59,6 +60,8 @@ enum {
 #define FOS_NO_GRAPH     0x2u  /* launch kernels directly instead of a cached CUDA graph */
 #define FOS_AUTOTUNE     0x4u  /* re-run the launch autotuner for this batch shape     */
 #define FOS_TEST_INJECT  0x10000u /* test only: the first kernel reports a failure      */
+#define FOS_TEST_STALL   0x20000u /* test only (fos_gemm_bf16): a pipeline stage is never
+                                     loaded, so its bounded wait runs out -> FOS_ERR_TIMEOUT */
 
 #define FOS_MAX_LAYERS   8     /* layers per stack                                     */
 #define FOS_NCOUNT       6     /* counts per item: R, A, T, runaway, collisions, interface events */
@@ -289,9 +292,12 @@ fos_status fos_surrogate_predict(void* model, int n_members, const float* featur
 
 /* Diagnostic: the surrogate's tensor-core product on its own.  C[s][M][N] (device fp32,
  * s = 0..splits-1 partial sums over K ranges of K/splits) = A[M][K] * B[N][K]^T with A, B
- * device BF16 row-major; K a multiple of 64*splits, N a multiple of 64.  Synchronous. */
+ * device BF16 row-major; K a multiple of 64*splits, N a multiple of 64.  flags: 0,
+ * FOS_ASYNC or FOS_TEST_STALL (every in-kernel wait is bounded: a stage that never fills
+ * makes the kernel give up, drain its copies, free its tensor memory and report
+ * FOS_ERR_TIMEOUT).  Synchronous unless FOS_ASYNC. */
 fos_status fos_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K,
-                         int splits, void* stream);
+                         int splits, unsigned flags, void* stream);
 
 /* --------------------------------------------------------------------------------
  * fos_mc_spectrum_noalloc: fos_mc_spectrum for callers that cannot allocate device

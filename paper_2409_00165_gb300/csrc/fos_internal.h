@@ -16,6 +16,7 @@ enum : unsigned {
     DEV_STEP_LIMIT = 2u,  // some photon reached max_events
     DEV_INJECTED = 4u,    // FOS_TEST_INJECT
     DEV_RANGE = 8u,       // input outside the kernel's supported range
+    DEV_TIMEOUT = 16u,    // a bounded in-kernel wait ran out (the kernel returned early)
 };
 
 // status words on the device: [0] the current call, [1] accumulated FOS_ASYNC work,

@@ -138,6 +138,8 @@ struct GemmArgs {
     unsigned* status;
     int a_rows_box;        // rows of the A box (128, or fewer when A has fewer rows)
     unsigned tx_bytes;     // bytes one stage receives from the two TMA loads
+    long long wait_limit;  // cycles an mbarrier wait may take before the kernel gives up
+    int test_stall;        // test only: the producer never issues the load of chunk 0
 };
 
 // GELU in its tanh form, z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))), with the
@@ -211,20 +213,21 @@ __global__ void __launch_bounds__(128, 1)
 
     bool ok = true;
     if (threadIdx.x == 0) {
-        int issued = 0, consumed = 0;
+        int last_issued = -1, consumed = 0;
         auto load = [&](int j) {
             const int s = j % STAGES;
             const uint32_t a_s = base + s * S::STAGE, b_s = a_s + S::A_BYTES;
+            last_issued = j;
+            if (args.test_stall && j == 0) return;   // test: this stage never fills
             mbar_arrive_expect_tx(bar_full + 8 * s, args.tx_bytes);
             tma_load_2d(a_s, &tmA, bar_full + 8 * s, k0 + j * BK, m0);
             tma_load_2d(b_s, &tmB, bar_full + 8 * s, k0 + j * BK, n0);
-            issued++;
         };
         for (int j = 0; j < n_k && j < STAGES; ++j) load(j);
         for (int j = 0; j < n_k; ++j) {
             const int s = j % STAGES;
             const uint32_t ph = (uint32_t)(j / STAGES) & 1u;
-            if (!mbar_wait(bar_full + 8 * s, ph)) {
+            if (!mbar_wait(bar_full + 8 * s, ph, args.wait_limit)) {
                 ok = false;
                 break;
             }
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(128, 1)
             }
             mma_commit(bar_empty + 8 * s);
             if (j + STAGES < n_k) {
-                if (!mbar_wait(bar_empty + 8 * s, ph)) {
+                if (!mbar_wait(bar_empty + 8 * s, ph, args.wait_limit)) {
                     ok = false;
                     break;
                 }
@@ -247,17 +250,20 @@ __global__ void __launch_bounds__(128, 1)
         }
         mma_commit(bar_done);
         if (!ok) {
-            // let every load already issued land before the CTA can exit
-            for (int j = consumed; j < issued; ++j)
-                mbar_wait(bar_full + 8 * (j % STAGES), (uint32_t)(j / STAGES) & 1u, 1000000000LL);
-            atomicOr(&args.status[ST_CALL], DEV_RANGE);
+            // let every load that was issued land before the CTA can exit
+            for (int j = consumed; j <= last_issued; ++j) {
+                if (args.test_stall && j == 0) continue;
+                mbar_wait(bar_full + 8 * (j % STAGES), (uint32_t)(j / STAGES) & 1u,
+                          1000000000LL);
+            }
+            atomicOr(&args.status[ST_CALL], DEV_TIMEOUT);
         }
     }
     __syncwarp();
-    const bool done_ok = mbar_wait(bar_done, 0);
+    const bool done_ok = mbar_wait(bar_done, 0, args.wait_limit);
     __syncwarp();
     tc_fence_after();
-    if (!done_ok && threadIdx.x == 0) atomicOr(&args.status[ST_CALL], DEV_RANGE);
+    if (!done_ok && threadIdx.x == 0) atomicOr(&args.status[ST_CALL], DEV_TIMEOUT);
 
     // ------------------------------------------------------------------ epilogue
     const int r = warp * 32 + lane;           // tile row held by this thread
@@ -798,6 +804,7 @@ static GemmArgs gargs(unsigned* status) {
     GemmArgs g;
     std::memset(&g, 0, sizeof(g));
     g.status = status;
+    g.wait_limit = 4000000000LL;   // ~2 s at 2 GHz
     return g;
 }
 
@@ -1128,7 +1135,7 @@ fos_status fos_surrogate_predict(void* model, int n_members, const float* featur
 // Plain GEMM through the same kernel (diagnostic): C[M][N] fp32 = A[M][K] * B[N][K]^T,
 // A and B bf16 row-major with K a multiple of 64.
 fos_status fos_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, int splits,
-                         void* stream) {
+                         unsigned flags, void* stream) {
     if (!A || !B || !C || M < 1 || N < 1 || K < 64 || K % 64 != 0 || splits < 1 ||
         K % (64 * splits) != 0 || N % 64 != 0)
         return FOS_ERR_INVALID_ARG;
@@ -1142,11 +1149,15 @@ fos_status fos_gemm_bf16(const void* A, const void* B, float* C, int M, int N, i
     g.N = N;
     g.out_f = C;
     g.ldf = N;
+    if (flags & FOS_TEST_STALL) {   // test: one stage never fills; the wait gives up fast
+        g.test_stall = 1;
+        g.wait_limit = 2000000LL;
+    }
     mlp::Operand a{(const mlp::bf16*)A, M, K, K}, b{(const mlp::bf16*)B, N, K, K};
     if (N % 256 == 0) st = mlp::gemm<256, mlp::DW_PARTIAL>(a, b, splits, g, s);
     else st = mlp::gemm<64, mlp::DW_PARTIAL>(a, b, splits, g, s);
     if (st != FOS_OK) return st;
-    return finish_call(ws, s, 0);
+    return finish_call(ws, s, flags & FOS_ASYNC);
 }
 
 }  // extern "C"

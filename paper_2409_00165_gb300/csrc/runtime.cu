@@ -35,6 +35,7 @@ fos_status from_cuda(cudaError_t e) {
 fos_status status_from_bits(unsigned bits) {
     if (bits & DEV_INJECTED) return FOS_ERR_INJECTED;
     if (bits & DEV_INVALID) return FOS_ERR_INVALID_ARG;
+    if (bits & DEV_TIMEOUT) return FOS_ERR_TIMEOUT;
     if (bits & DEV_RANGE) return FOS_ERR_OUT_OF_RANGE;
     if (bits & DEV_STEP_LIMIT) return FOS_ERR_STEP_LIMIT;
     return FOS_OK;

@@ -29,6 +29,7 @@ FOS_ASYNC = 0x1
 FOS_NO_GRAPH = 0x2
 FOS_AUTOTUNE = 0x4
 FOS_TEST_INJECT = 0x10000
+FOS_TEST_STALL = 0x20000
 
 FOS_MAX_LAYERS = 8
 FOS_NCOUNT = 6
@@ -328,12 +329,13 @@ def fos_surrogate_predict(model, n_members, features, rat, spread=None, needs_mc
         _stream(stream))
 
 
-def fos_gemm_bf16(A, B, C, splits=1, stream=None) -> int:
+def fos_gemm_bf16(A, B, C, splits=1, flags=0, stream=None) -> int:
     M, K = A.shape
     N = B.shape[0]
-    return _sfn("fos_gemm_bf16", [ctypes.c_void_p] * 3 + [ctypes.c_int] * 4 + [ctypes.c_void_p])(
+    return _sfn("fos_gemm_bf16", [ctypes.c_void_p] * 3 + [ctypes.c_int] * 4
+                + [ctypes.c_uint, ctypes.c_void_p])(
         _dev(A, torch.bfloat16, "A"), _dev(B, torch.bfloat16, "B"), _dev(C, torch.float32, "C"),
-        int(M), int(N), int(K), int(splits), _stream(stream))
+        int(M), int(N), int(K), int(splits), int(flags), _stream(stream))
 
 
 # --------------------------------------------------------------------------- no allocation

@@ -246,3 +246,19 @@ def test_paint_layer_full_size_sampled_photons(orc):
         one["photon_first"] = np.full(m["n_wl"], p, np.int64)
         _, lo = orc.mc_run(one, fp32=True, photon_log=True)
         assert log[w, p] == lo[0, 0], (w, p)
+
+
+def test_host_wait_is_bounded():
+    """fos_sync_status with a 1 ms limit on a stream still running a long walk returns
+    FOS_ERR_TIMEOUT at once; a later wait returns the real status."""
+    b = _slab([20.0], [0.01], [0.9], [1.5], [5.0], 20000000)
+    from gpu_helpers import to_dev
+    f64 = torch.float64
+    keep = {k: to_dev(b[k], f64) for k in ("mu_s", "mu_a", "g", "n_layer", "thickness",
+                                            "n_above", "n_below")}
+    bb = fos.make_batch(1, 1, 1, photons_per_item=b["photons_per_item"], seed=3, **keep)
+    counts = torch.zeros((1, fos.FOS_NCOUNT), dtype=torch.int64, device="cuda")
+    assert fos.fos_mc_spectrum(bb, counts, None, 0, fos.FOS_ASYNC) == fos.FOS_OK
+    assert fos.fos_sync_status(None, 1) == fos.FOS_ERR_TIMEOUT
+    assert fos.fos_sync_status(None, 600000) == fos.FOS_OK
+    assert int(counts[0, :4].sum()) == 20000000

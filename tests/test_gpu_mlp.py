@@ -265,3 +265,19 @@ def test_mask_to_rows():
         k = int(cnt.item())
         got = np.sort(rows[:k].cpu().numpy())
         assert np.array_equal(got, np.nonzero(m)[0])
+
+
+def test_in_kernel_wait_gives_up_and_reports_timeout():
+    """A pipeline stage that never fills (test flag): the bounded mbarrier wait runs
+    out, the kernel drains its other copies, frees its tensor memory and returns; the
+    host reads FOS_ERR_TIMEOUT and the context stays usable."""
+    rng = np.random.default_rng(1)
+    A = _bf16(rng, (256, 512))
+    B = _bf16(rng, (256, 512))
+    C = torch.zeros((1, 256, 256), dtype=torch.float32, device="cuda")
+    st = fos.fos_gemm_bf16(A, B, C, 1, flags=fos.FOS_TEST_STALL)
+    assert st == fos.FOS_ERR_TIMEOUT
+    st = fos.fos_gemm_bf16(A, B, C, 1)
+    assert st == fos.FOS_OK
+    ref = A.float().double().cpu().numpy() @ B.float().double().cpu().numpy().T
+    assert np.allclose(C[0].double().cpu().numpy(), ref, rtol=1e-4, atol=1e-3)
