@@ -334,6 +334,16 @@ def run_fos(args):
     stacks = None
     if args.stacks and world == 1:
         stacks = run_stacks()
+    dists = cs = None
+    if world == 1:
+        try:
+            dists = run_distributions()
+        except Exception as exc:
+            dists = dict(error=str(exc))
+        try:
+            cs = run_core_shell()
+        except Exception as exc:
+            cs = dict(error=str(exc))
     cpu = None
     if not args.no_cpu and world == 1:
         try:
@@ -351,7 +361,7 @@ def run_fos(args):
         spectra_per_s=spectra_per_s, photons_per_s=phot_all / secs,
         photon_steps_per_photon=coll / max(photons, 1),
         e2e=e2e, roofline=roof, cpu_baseline=cpu, clocks=clocks, surrogate=surr,
-        layer_stacks=stacks,
+        layer_stacks=stacks, size_distributions=dists, core_shell=cs,
         gpu_launches=5 * K,
         gpu_launches_detail="per step: mie_kernel, emt_kernel, pack_kernel, unit_scan_kernel, "
                             "walk_kernel",
@@ -366,14 +376,14 @@ def run_surrogate(mode: str):
     """Surrogate spectra/s vs plain GPU Monte Carlo spectra/s on the same designs.
 
     Training data: single-layer designs (r, f, d in the workload ranges) x 50 random
-    wavelengths per block, Monte Carlo fractions at 1e4 photons; 4 members trained by
+    wavelengths per block, Monte Carlo fractions at 3e4 photons; 4 members trained by
     Adam.  Sweep: 1e5 designs x 300 wavelengths, ensemble spread > 0.01 or out-of-range
     rows re-run by Monte Carlo at 1e5 photons; 0.1 % of rows audited by Monte Carlo at
     1e5 photons."""
     import torch
 
     from paper_2409_00165_gb300 import surrogate as S
-    cfg = dict(full=dict(designs=20000, blocks=20, wl=50, photons=10000, steps=6000,
+    cfg = dict(full=dict(designs=20000, blocks=20, wl=50, photons=30000, steps=10000,
                          sweep=100000),
                quick=dict(designs=4000, blocks=10, wl=24, photons=10000, steps=2500,
                           sweep=20000))[mode]
@@ -433,6 +443,81 @@ def run_stacks():
     return dict(items=int(counts.shape[0]), photons=int(c[:4].sum()), photon_steps=int(c[4]),
                 seconds=s, photon_steps_per_s=float(c[4]) / s,
                 spectra_per_s=m["n_stacks"] / s, tuning=dict(block=tun[0], ppt=tun[1]))
+
+
+def _mie_mc_leg(m, photons: int, seed: int):
+    """Mie (core-shell where the media hold core radii) + effective medium, then the walk
+    at `photons` per wavelength, for single-layer stacks in the media dict m; each part
+    timed once with CUDA events after a warm-up call."""
+    import numpy as np
+    import torch
+
+    from paper_2409_00165_gb300 import fos
+    from paper_2409_00165_gb300 import workloads as W
+    dev = "cuda"
+    f64 = torch.float64
+    d = {k: torch.as_tensor(v, dtype=f64, device=dev) for k, v in W.media_arrays(m).items()}
+    t = lambda a, dt=f64: torch.as_tensor(a, dtype=dt, device=dev)
+    wl, sg, rad, vf = t(m["wl"]), t(m["species_group"], torch.int32), t(m["radius"]), t(m["vol_frac"])
+    n = m["n_groups"] * m["n_wl"]
+    mu_s, mu_a, g = (torch.zeros(n, dtype=f64, device=dev) for _ in range(3))
+    if "core_radius" in m:
+        nc = np.asarray(m["n_core"])
+        cr, nc_re, nc_im = t(m["core_radius"]), t(nc.real.reshape(-1)), t(nc.imag.reshape(-1))
+        mie = lambda fl: fos.fos_mie_properties_cs(wl, d["nm_re"], d["nm_im"], sg, d["np_re"],
+                                                   d["np_im"], nc_re, nc_im, rad, cr, vf, mu_s,
+                                                   mu_a, g, flags=fl)
+    else:
+        mie = lambda fl: fos.fos_mie_properties(wl, d["nm_re"], d["nm_im"], sg, d["np_re"],
+                                                d["np_im"], rad, vf, mu_s, mu_a, g, flags=fl)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fos.check(mie(0), "mie warm-up")
+    b = fos.make_batch(m["n_stacks"], m["n_wl"], 1, mu_s, mu_a, g, d["nm_re"], t(m["thickness"]),
+                       photons_per_item=photons, seed=seed)
+    counts = torch.zeros((n, fos.FOS_NCOUNT), dtype=torch.int64, device=dev)
+    fos.check(fos.fos_mc_spectrum(b, counts, None, 0, fos.FOS_AUTOTUNE), "mc warm-up")
+    torch.cuda.synchronize()
+    ev[0].record()
+    fos.check(mie(fos.FOS_ASYNC), "mie")
+    ev[1].record()
+    fos.check(fos.fos_mc_spectrum(b, counts, None, 0, fos.FOS_ASYNC), "mc")
+    ev[2].record()
+    torch.cuda.synchronize()
+    fos.check(fos.fos_sync_status(), "mie + mc")
+    t_mie, t_mc = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
+    c = counts.sum(dim=0).cpu().numpy()
+    evals = len(m["radius"]) * m["n_wl"]
+    cn = counts.cpu().numpy().reshape(m["n_stacks"], m["n_wl"], -1)
+    refl = (cn[:, :, 0] + cn[:, :, 1]) / photons
+    return dict(sizes=len(m["radius"]), mie_evals=evals, mie_seconds=t_mie,
+                mie_evals_per_s=evals / t_mie, mc_seconds=t_mc, photons=int(c[:4].sum()),
+                photon_steps=int(c[4]), photon_steps_per_s=float(c[4]) / t_mc,
+                spectra_per_s=m["n_stacks"] / (t_mie + t_mc),
+                mean_reflectance=[float(x) for x in refl.mean(axis=1)])
+
+
+def run_distributions():
+    """Particle-size distributions (each diameter -> 101 Gaussian sizes over D +- 3 sigma):
+    silicon-like spheres D = 0.5 um at 0.1 % in 500 um of a water-like matrix, sigma = 0,
+    0.05, 0.15 um, 400 wavelengths, 1e6 photons per wavelength; Mie over all 203 sizes,
+    the effective medium per distribution, then the walk."""
+    from paper_2409_00165_gb300 import fos
+    from paper_2409_00165_gb300 import workloads as W
+    dists = [fos.fos_size_distribution(0.5, s, 0.001) for s in (0.0, 0.05, 0.15)]
+    r = _mie_mc_leg(W.size_distribution_media(dists), 1000000, 9)
+    r["sigmas_um"] = [0.0, 0.05, 0.15]
+    return r
+
+
+def run_core_shell():
+    """Core-shell spheres: hollow silica-like spheres (air core D = 0.5 um, outer D = 0.7,
+    0.9, 1.1 um) and solid ones of the same outer sizes, f = 0.6 in a 50 um layer in air,
+    400 wavelengths, 1e6 photons per wavelength."""
+    from paper_2409_00165_gb300 import workloads as W
+    r = _mie_mc_leg(W.hollow_silica_media(), 1000000, 11)
+    r["outer_diameters_um"] = [0.7, 0.9, 1.1]
+    r["stacks"] = "3 hollow then 3 solid"
+    return r
 
 
 # ------------------------------------------------------------------------ reference arm

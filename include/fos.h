@@ -114,6 +114,43 @@ fos_status fos_mie_properties(int n_wl, const double* wl,
                               double* q_ext, double* q_sca, double* g_species,
                               unsigned flags, void* stream);
 
+/* fos_mie_properties_cs: as fos_mie_properties, with core-shell particles (supplement
+ * of arxiv 2409.00165, Eqs. S1-S9): a core of radius a and index n_c inside a shell of
+ * outer radius b and index n_s.  With m1 = n_c/n_m, m2 = n_s/n_m, x = 2 pi a n_m /
+ * lambda and y = 2 pi b n_m / lambda, a_n and b_n come from S1-S2, the shell
+ * coefficients A_n, B_n from S3-S4 (evaluated divided by psi_n(m1 x), i.e. with the
+ * log-derivative D_n(m1 x), which keeps them finite for absorbing cores), chi_n = z y_n(z)
+ * (S8) and xi_n = psi_n + i chi_n (S9); n_max uses 2 pi b max(|n_c|,|n_s|)/lambda in
+ * place of |y| of Eq. 4.  The efficiencies (Eqs. 10-12, 15) and the effective medium
+ * (Eqs. 13-20) use the outer radius b, as the paper's hollow-sphere example does.
+ *   ns_re, ns_im  [n_species*n_wl]   shell index (the np_* of fos_mie_properties)
+ *   nc_re, nc_im  [n_species*n_wl]   core index (read only where core_radius > 0)
+ *   radius        [n_species]        outer radius b
+ *   core_radius   [n_species]        a, 0 <= a < b; a = 0 is a homogeneous sphere of n_s
+ * All device FP64.  Errors as fos_mie_properties; core_radius NULL with n_species > 0
+ * is FOS_ERR_INVALID_ARG, a < 0 or a >= b is FOS_ERR_INVALID_ARG (reported by the
+ * kernel). */
+fos_status fos_mie_properties_cs(int n_wl, const double* wl,
+                                 int n_groups, const double* nm_re, const double* nm_im,
+                                 int n_species, const int* species_group,
+                                 const double* ns_re, const double* ns_im,
+                                 const double* nc_re, const double* nc_im,
+                                 const double* radius, const double* core_radius,
+                                 const double* vol_frac,
+                                 double* mu_s, double* mu_a, double* g,
+                                 double* q_ext, double* q_sca, double* g_species,
+                                 unsigned flags, void* stream);
+
+/* Particle-size distribution (section "Scattering properties", last paragraph): one
+ * particle of diameter D with standard deviation sigma becomes n (101 in the paper; odd)
+ * diameters evenly spaced over D +- 3 sigma.  Each size gets the share
+ * w_i / sum(w) of vol_frac, w_i = exp(-(D_i - D)^2 / (2 sigma^2)); diameters <= 0 are
+ * dropped (n_out < n).  sigma = 0 gives one size.  radius, vol_fracs: host double[n]
+ * outputs, to be passed as species of one group to fos_mie_properties, whose effective
+ * medium (Eqs. 13-16) sums over them. */
+fos_status fos_size_distribution(double diameter, double sigma, double vol_frac, int n,
+                                 double* radius, double* vol_fracs, int* n_out);
+
 /* --------------------------------------------------------------------------------
  * fos_mc_spectrum: Monte Carlo photon transport (section "Photon transport").
  *

@@ -25,10 +25,17 @@ Parity status per function (the pins live in ``tests/test_oracle_*.py``):
                           Rayleigh limit; optical theorem; phase-function
                           quadrature for g; large-sphere extinction limit)
   mie_properties ........ pinned (hand arithmetic of Eqs. 13-20)
+  mie_coated ............ pinned (mpmath 40-digit Bessel J, Y evaluation of Eqs.
+                          S1-S9; reduces to the sphere when the core and shell
+                          indices are equal, when the core vanishes, and when the
+                          shell does)
+  size_distribution ..... pinned (volume conserved, symmetry, end/centre weight
+                          ratio exp(-4.5), sigma -> 0 limit of the medium)
 """
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -73,6 +80,7 @@ class OrcBatch(ctypes.Structure):
         ("item_list", ctypes.c_void_p), ("n_list", ctypes.c_int),
         ("seed", ctypes.c_ulonglong), ("item_id_base", ctypes.c_uint),
         ("max_events", ctypes.c_longlong),
+        ("cos_incidence", ctypes.c_void_p), ("k_below", ctypes.c_void_p),
     ]
 
 
@@ -97,6 +105,12 @@ def lib():
             L.orc_hg_cos_f32.restype = ctypes.c_float
             L.orc_fresnel_f64.argtypes = [ctypes.c_double] * 3 + [ctypes.c_void_p]
             L.orc_fresnel_f64.restype = ctypes.c_double
+            L.orc_fresnel_conductor_f64.argtypes = [ctypes.c_double] * 4
+            L.orc_fresnel_conductor_f64.restype = ctypes.c_double
+            L.orc_fresnel_conductor_f32.argtypes = [ctypes.c_float] * 4
+            L.orc_fresnel_conductor_f32.restype = ctypes.c_float
+            L.orc_solar_weighted.argtypes = ([ctypes.c_int, ctypes.c_int] +
+                                             [ctypes.c_void_p] * 4)
             L.orc_mc_run.argtypes = [ctypes.POINTER(OrcBatch), ctypes.c_int, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_longlong]
             L.orc_mc_run.restype = ctypes.c_int
@@ -111,6 +125,12 @@ def lib():
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
                                              + [ctypes.c_void_p] * 11)
             L.orc_mie_properties.restype = ctypes.c_int
+            L.orc_mie_coated.argtypes = [ctypes.c_double] * 9 + [ctypes.c_void_p] * 6 + [ctypes.c_int]
+            L.orc_mie_coated.restype = ctypes.c_int
+            L.orc_mie_properties_cs.argtypes = ([ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+                                                + [ctypes.c_void_p] * 14)
+            L.orc_mie_properties_cs.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -156,6 +176,23 @@ def fresnel(ni: float, nt: float, ci: float):
     return R, ct.value
 
 
+def fresnel_conductor(ni: float, n2: float, k2: float, ci: float, fp32: bool = False) -> float:
+    """Unpolarised reflectance from real index ni into n2 + i k2 at incidence cosine ci."""
+    f = lib().orc_fresnel_conductor_f32 if fp32 else lib().orc_fresnel_conductor_f64
+    return f(ni, n2, k2, ci)
+
+
+def solar_weighted(counts, wl, G, n_stacks: int):
+    """Eq. 21 totals [n_stacks, 3] (R, A, T) from counts [n_stacks*n_wl, 6]."""
+    c = np.ascontiguousarray(counts, dtype=np.int64)
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    out = np.zeros((n_stacks, 3))
+    lib().orc_solar_weighted(int(n_stacks), int(wl.size), wl.ctypes.data, G.ctypes.data,
+                             c.ctypes.data, out.ctypes.data)
+    return out
+
+
 # ---------------------------------------------------------------------------- MC
 def mc_run(batch: dict, fp32: bool = True, photon_log: bool = False):
     """Run the oracle walk on a batch given as a dict of NumPy arrays.
@@ -163,7 +200,7 @@ def mc_run(batch: dict, fp32: bool = True, photon_log: bool = False):
     Keys mirror the fields of the C-ABI batch (see include/fos.h): n_stacks, n_wl,
     max_layers, n_layers, mu_s, mu_a, g, n_layer, thickness, n_above, n_below,
     substrate_R, n_photons, photons_per_item, photon_first, item_list, seed,
-    item_id_base, max_events.  Returns int64 counts [n_run, 6] (and the per-photon
+    item_id_base, max_events, cos_incidence, k_below.  Returns int64 counts [n_run, 6] (and the per-photon
     log [n_run, max N] of (collisions << 2 | outcome) when asked).
     """
     keep = []
@@ -182,7 +219,7 @@ def mc_run(batch: dict, fp32: bool = True, photon_log: bool = False):
     b.max_layers = int(batch["max_layers"])
     b.n_layers = arr("n_layers", np.int32)
     for name in ("mu_s", "mu_a", "g", "n_layer", "thickness", "n_above", "n_below",
-                 "substrate_R"):
+                 "substrate_R", "cos_incidence", "k_below"):
         setattr(b, name, arr(name, np.float64))
     b.n_photons = arr("n_photons", np.int64)
     b.photons_per_item = int(batch.get("photons_per_item", 0))
@@ -229,6 +266,42 @@ def mie_sphere(wl, n_p, n_m, r, with_coeffs: bool = False):
     return out
 
 
+def size_distribution(diameter, sigma, vol_frac, n=101):
+    """Section "Scattering properties", last paragraph: a diameter with standard
+    deviation sigma becomes n diameters over D +- 3 sigma; the volume fraction is shared
+    by Gaussian weights (normalised); non-positive diameters are dropped.  Plain Python."""
+    if sigma == 0 or n == 1:
+        return np.array([diameter / 2.0]), np.array([float(vol_frac)])
+    ds, ws = [], []
+    for i in range(n):
+        d = diameter - 3.0 * sigma + 6.0 * sigma * i / (n - 1)
+        if d <= 0:
+            continue
+        ds.append(d / 2.0)
+        ws.append(math.exp(-0.5 * ((d - diameter) / sigma) ** 2))
+    tot = sum(ws)
+    return np.array(ds), np.array([vol_frac * w / tot for w in ws])
+
+
+def mie_coated(wl, n_core, n_shell, n_m, a, b, with_coeffs: bool = False):
+    """Q_ext, Q_sca, g (and a_n, b_n) of a core-shell sphere (Eqs. S1-S9)."""
+    qe, qs, gg = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    nmax = ctypes.c_int()
+    cap = 2048
+    an = np.zeros(2 * cap) if with_coeffs else None
+    bn = np.zeros(2 * cap) if with_coeffs else None
+    lib().orc_mie_coated(float(wl), float(np.real(n_core)), float(np.imag(n_core)),
+                         float(np.real(n_shell)), float(np.imag(n_shell)), float(np.real(n_m)),
+                         float(np.imag(n_m)), float(a), float(b), ctypes.byref(qe), ctypes.byref(qs),
+                         ctypes.byref(gg), ctypes.byref(nmax), _ptr(an), _ptr(bn), cap)
+    out = dict(q_ext=qe.value, q_sca=qs.value, g=gg.value, n_max=nmax.value)
+    if with_coeffs:
+        k = nmax.value + 1
+        out["a"] = an[: 2 * k].view(np.complex128).copy()
+        out["b"] = bn[: 2 * k].view(np.complex128).copy()
+    return out
+
+
 def gamma_term(alpha: float) -> float:
     return lib().orc_gamma_term(float(alpha))
 
@@ -239,11 +312,13 @@ def log_deriv_psi(n: int, z: complex) -> complex:
     return complex(out[0], out[1])
 
 
-def mie_properties(wl, nm, species_group, n_p, radius, vol_frac, n_groups=None):
+def mie_properties(wl, nm, species_group, n_p, radius, vol_frac, n_groups=None,
+                   core_radius=None, n_core=None):
     """Effective-medium mu_s, mu_a, g per (group, wavelength) and per-species Q's.
 
-    wl [n_wl]; nm complex [n_groups, n_wl]; n_p complex [n_species, n_wl];
-    species_group, radius, vol_frac [n_species].
+    wl [n_wl]; nm complex [n_groups, n_wl]; n_p complex [n_species, n_wl] (the shell of
+    a core-shell species); species_group, radius (outer), vol_frac [n_species]; optional
+    core_radius [n_species] (> 0: core-shell) and n_core complex [n_species, n_wl].
     """
     wl = np.ascontiguousarray(wl, dtype=np.float64)
     nm = np.asarray(nm, dtype=np.complex128)
@@ -264,10 +339,24 @@ def mie_properties(wl, nm, species_group, n_p, radius, vol_frac, n_groups=None):
     qe = np.zeros(n_species * n_wl)
     qs = np.zeros(n_species * n_wl)
     gs = np.zeros(n_species * n_wl)
-    lib().orc_mie_properties(n_wl, wl.ctypes.data, n_groups, nm_re.ctypes.data, nm_im.ctypes.data,
-                             n_species, sg.ctypes.data, np_re.ctypes.data, np_im.ctypes.data,
-                             rad.ctypes.data, vf.ctypes.data, mu_s.ctypes.data, mu_a.ctypes.data,
-                             g.ctypes.data, qe.ctypes.data, qs.ctypes.data, gs.ctypes.data)
+    if core_radius is None:
+        lib().orc_mie_properties(n_wl, wl.ctypes.data, n_groups, nm_re.ctypes.data,
+                                 nm_im.ctypes.data, n_species, sg.ctypes.data, np_re.ctypes.data,
+                                 np_im.ctypes.data, rad.ctypes.data, vf.ctypes.data,
+                                 mu_s.ctypes.data, mu_a.ctypes.data, g.ctypes.data,
+                                 qe.ctypes.data, qs.ctypes.data, gs.ctypes.data)
+    else:
+        nc = np.asarray(n_core, dtype=np.complex128)
+        nc_re = np.ascontiguousarray(nc.real.reshape(-1))
+        nc_im = np.ascontiguousarray(nc.imag.reshape(-1))
+        cr = np.ascontiguousarray(core_radius, dtype=np.float64)
+        lib().orc_mie_properties_cs(n_wl, wl.ctypes.data, n_groups, nm_re.ctypes.data,
+                                    nm_im.ctypes.data, n_species, sg.ctypes.data,
+                                    np_re.ctypes.data, np_im.ctypes.data, nc_re.ctypes.data,
+                                    nc_im.ctypes.data, rad.ctypes.data, cr.ctypes.data,
+                                    vf.ctypes.data, mu_s.ctypes.data, mu_a.ctypes.data,
+                                    g.ctypes.data, qe.ctypes.data, qs.ctypes.data,
+                                    gs.ctypes.data)
     shp = (n_groups, n_wl)
     sshp = (n_species, n_wl)
     return dict(mu_s=mu_s.reshape(shp), mu_a=mu_a.reshape(shp), g=g.reshape(shp),

@@ -203,6 +203,40 @@ static typename M::R fresnel(typename M::R ni, typename M::R nt, typename M::R c
     return (rs * rs + rp * rp) * (R)0.5;
 }
 
+// Unpolarised Fresnel reflectance from a medium of real index ni into an absorbing
+// medium n2 + i k2 (k2 > 0, a conductor below the stack) at incidence cosine ci: with
+// w = (n2 + i k2)^2 - ni^2 (1 - ci^2) and u + i v = sqrt(w) (the refracted wave's
+// normal component times its index, Re >= 0), r_s = (ni ci - sqrt w)/(ni ci + sqrt w)
+// and r_p = ((n2 + i k2)^2 ci - ni sqrt w)/((n2 + i k2)^2 ci + ni sqrt w).  The square
+// root takes whichever of u, v is the larger from the modulus and the other by
+// division, which avoids cancellation for either sign of Re w.
+template <class M>
+static typename M::R fresnel_conductor(typename M::R ni, typename M::R n2, typename M::R k2,
+                                       typename M::R ci) {
+    typedef typename M::R R;
+    const R s2 = M::fma_(-ci, ci, (R)1);
+    const R e_re = n2 * n2 - k2 * k2;          // (n2 + i k2)^2
+    const R e_im = (n2 + n2) * k2;
+    const R w_re = e_re - (ni * ni) * s2;
+    const R w_im = e_im;
+    const R mod = M::sqrt_(w_re * w_re + w_im * w_im);
+    R u, v;
+    if (w_re >= (R)0) {
+        u = M::sqrt_((mod + w_re) * (R)0.5);
+        v = w_im / (u + u);
+    } else {
+        v = M::sqrt_((mod - w_re) * (R)0.5);
+        u = w_im / (v + v);
+    }
+    const R a = ni * ci;
+    const R rs_n = (a - u) * (a - u) + v * v;
+    const R rs_d = (a + u) * (a + u) + v * v;
+    const R c1 = e_re * ci, c2 = e_im * ci, q1 = ni * u, q2 = ni * v;
+    const R rp_n = (c1 - q1) * (c1 - q1) + (c2 - q2) * (c2 - q2);
+    const R rp_d = (c1 + q1) * (c1 + q1) + (c2 + q2) * (c2 + q2);
+    return (rs_n / rs_d + rp_n / rp_d) * (R)0.5;
+}
+
 // --------------------------------------------------------------------------------
 // Monte Carlo photon walk.
 // --------------------------------------------------------------------------------
@@ -229,6 +263,8 @@ typedef struct orc_batch {
     unsigned long long seed;
     unsigned int item_id_base;
     long long max_events;         // 0 -> 100000000
+    const double* cos_incidence;  // [n_items] in (0, 1] or NULL -> 1 (normal incidence)
+    const double* k_below;        // [n_items] >= 0 or NULL -> 0 (k > 0: conductor below)
 } orc_batch;
 }
 
@@ -253,7 +289,8 @@ struct PhotonRng {
 
 template <class M>
 static int walk_photon(const LayerP<M>* L, int nl, typename M::R n_above, typename M::R n_below,
-                       bool has_sub, typename M::R r_sub, const PhotonRng& rng,
+                       bool has_sub, typename M::R r_sub, typename M::R cos_in,
+                       typename M::R k_below, const PhotonRng& rng,
                        unsigned long long max_events, unsigned long long* n_coll,
                        unsigned long long* n_iface) {
     typedef typename M::R R;
@@ -263,21 +300,34 @@ static int walk_photon(const LayerP<M>* L, int nl, typename M::R n_above, typena
     uint32_t blk[4];
     int outcome = -1;
 
-    // Launch: normal incidence at the top surface (z = 0), from the medium above.  The
-    // entry Fresnel test reads word 3 of collision block 0: that word is the azimuth
-    // of the first collision, which is never used because mu_z is exactly +-1 until
-    // the first scattering (refraction and reflection at normal incidence keep it).
+    // Launch at the top surface (z = 0) from the medium above, at incidence cosine cos_in.
+    // Normal incidence: the entry Fresnel test reads word 3 of collision block 0, the
+    // azimuth of the first collision, which is never used because mu_z stays exactly
+    // +-1 until the first scattering.  Oblique incidence: the first collision needs its
+    // azimuth, so the entry test reads word 0 of the block at counter (p, item, 0, 2).
+    // Entry under total internal reflection (medium above denser) reflects the photon.
     rng.block(e, 0u, blk);
+    R mu_in = cos_in;
     {
         R ni = n_above, nt = L[0].n;
         if (ni != nt) {
             R ct; bool tir;
-            R Rf = fresnel<M>(ni, nt, (R)1, &ct, &tir);
-            if (M::uni(blk[3]) < Rf) { *n_coll = 0; *n_iface = 0; return OUT_R; }
+            R Rf = fresnel<M>(ni, nt, cos_in, &ct, &tir);
+            if (tir) { *n_coll = 0; *n_iface = 0; return OUT_R; }
+            R u_entry;
+            if (cos_in == (R)1) {
+                u_entry = M::uni(blk[3]);
+            } else {
+                uint32_t eb[4];
+                rng.block(0u, 2u, eb);
+                u_entry = M::uni(eb[0]);
+            }
+            if (u_entry < Rf) { *n_coll = 0; *n_iface = 0; return OUT_R; }
+            mu_in = ct;
         }
     }
     int j = 0;
-    R z = (R)0, mu = (R)1;
+    R z = (R)0, mu = mu_in;
     R tau = M::neg_log(M::uni(blk[0]));
     R u1 = M::uni(blk[1]), u2 = M::uni(blk[2]), u3 = M::uni(blk[3]);
 
@@ -326,12 +376,15 @@ static int walk_photon(const LayerP<M>* L, int nl, typename M::R n_above, typena
         events++; iface++;
         int nb = down ? j + 1 : j - 1;
         bool outside = (nb < 0) || (nb >= nl);
-        if (down && outside && has_sub) {
-            // Opaque specular reflector below the stack.
+        if (down && outside && (has_sub || k_below > (R)0)) {
+            // Opaque specular reflector below the stack, or a conductor n + ik (k > 0)
+            // reflecting with its Fresnel reflectance; what is not reflected enters the
+            // substrate and is counted as transmitted.
+            const R Rb = has_sub ? r_sub : fresnel_conductor<M>(Lj.n, n_below, k_below, am);
             rng.block(k_if >> 2, 1u, blk);
             R u = M::uni(blk[k_if & 3u]);
             k_if++;
-            if (u < r_sub) { mu = -mu; continue; }
+            if (u < Rb) { mu = -mu; continue; }
             outcome = OUT_T; break;
         }
         R ni = Lj.n;
@@ -391,6 +444,8 @@ static int run_batch(const orc_batch* b, long long* counts, int* photon_log, lon
         R nbw = b->n_below ? (R)b->n_below[it] : (R)1;
         bool has_sub = b->substrate_R != nullptr;
         R rsub = has_sub ? (R)b->substrate_R[it] : (R)0;
+        R cin = b->cos_incidence ? (R)b->cos_incidence[it] : (R)1;
+        R kbw = (b->k_below && !has_sub) ? (R)b->k_below[it] : (R)0;
         long long N = b->n_photons ? b->n_photons[it] : b->photons_per_item;
         long long first = b->photon_first ? b->photon_first[it] : 0;
         PhotonRng rng;
@@ -402,7 +457,7 @@ static int run_batch(const orc_batch* b, long long* counts, int* photon_log, lon
         for (long long i = 0; i < N; ++i) {
             rng.p = (uint32_t)(first + i);
             unsigned long long nc, ni;
-            int out = walk_photon<M>(L, nl, na, nbw, has_sub, rsub, rng, max_ev, &nc, &ni);
+            int out = walk_photon<M>(L, nl, na, nbw, has_sub, rsub, cin, kbw, rng, max_ev, &nc, &ni);
             c[out] += 1;
             c[4] += (long long)nc;
             c[5] += (long long)ni;
@@ -532,7 +587,114 @@ extern "C" int orc_mie_sphere(double wl, double npr, double npi, double nmr, dou
     return 0;
 }
 
+
+// --------------------------------------------------------------------------------
+// Core-shell sphere (supplement section 3, Eqs. S1-S9, Bohren & Huffman 8.1): core
+// radius a with index n_c, shell out to radius b with index n_s, host n_m.
+// m1 = n_c/n_m, m2 = n_s/n_m, x = k a, y = k b with k = 2 pi n_m / lambda.
+// A_n, B_n (S3, S4) are evaluated divided through by psi_n(m1 x), i.e. with the
+// logarithmic derivative D_n(m1 x) (continued fraction); psi_n, chi_n of the shell
+// arguments by upward recurrence of values (psi_n from D_n above |z|); chi_n = z y_n(z)
+// (S8), xi_n = psi_n + i chi_n (S9).
+// --------------------------------------------------------------------------------
+static void riccati_psi_chi(int nt, cd z, cd* psi, cd* chi) {
+    // psi[0..nt], chi[0..nt]
+    const double az = std::abs(z);
+    cd psi_m1 = std::cos(z), chi_m1 = std::sin(z);       // n = -1
+    psi[0] = std::sin(z);
+    chi[0] = -std::cos(z);
+    for (int n = 1; n <= nt; ++n) {
+        const cd prev_psi = (n == 1) ? psi_m1 : psi[n - 2];
+        const cd prev_chi = (n == 1) ? chi_m1 : chi[n - 2];
+        if ((double)n <= az) psi[n] = (double)(2 * n - 1) / z * psi[n - 1] - prev_psi;
+        else psi[n] = psi[n - 1] / (log_deriv_psi(n, z) + (double)n / z);
+        chi[n] = (double)(2 * n - 1) / z * chi[n - 1] - prev_chi;
+    }
+}
+
+extern "C" int orc_mie_coated(double wl, double ncr, double nci, double nsr, double nsi,
+                              double nmr, double nmi, double a, double b, double* q_ext,
+                              double* q_sca, double* g_out, int* nmax_out, double* an_out,
+                              double* bn_out, int an_cap) {
+    const cd n_c(ncr, nci), n_s(nsr, nsi), n_m(nmr, nmi);
+    const cd m1 = n_c / n_m, m2 = n_s / n_m;
+    const double kv = 2.0 * M_PI / wl;
+    const cd x = kv * a * n_m, y = kv * b * n_m;
+    const double ymax = kv * b * std::max(std::abs(n_c), std::abs(n_s));
+    const int nmax = (int)std::ceil(2.0 + ymax + 4.3 * std::cbrt(ymax));
+    const int nt = nmax + 1;
+    cd *ps2x = new cd[nt + 1], *ch2x = new cd[nt + 1], *ps2y = new cd[nt + 1], *ch2y = new cd[nt + 1];
+    cd *psy = new cd[nt + 1], *chy = new cd[nt + 1];
+    riccati_psi_chi(nt, m2 * x, ps2x, ch2x);
+    riccati_psi_chi(nt, m2 * y, ps2y, ch2y);
+    riccati_psi_chi(nt, y, psy, chy);
+    cd* an = new cd[nt + 1];
+    cd* bn = new cd[nt + 1];
+    const cd I(0.0, 1.0);
+    for (int n = 1; n <= nt; ++n) {
+        const double dn = n;
+        const cd z2x = m2 * x, z2y = m2 * y;
+        const cd D1 = log_deriv_psi(n, m1 * x);                         // psi'/psi at m1 x
+        const cd d_ps2x = ps2x[n - 1] - dn * ps2x[n] / z2x, d_ch2x = ch2x[n - 1] - dn * ch2x[n] / z2x;
+        const cd D2x = d_ps2x / ps2x[n];
+        const cd An = ps2x[n] * (m2 * D1 - m1 * D2x) / (m2 * D1 * ch2x[n] - m1 * d_ch2x);       // S3
+        const cd Bn = ps2x[n] * (m2 * D2x - m1 * D1) / (m2 * d_ch2x - m1 * D1 * ch2x[n]);       // S4
+        const cd d_ps2y = ps2y[n - 1] - dn * ps2y[n] / z2y, d_ch2y = ch2y[n - 1] - dn * ch2y[n] / z2y;
+        const cd xi = psy[n] + I * chy[n];                                   // S9
+        const cd d_psy = psy[n - 1] - dn * psy[n] / y;
+        const cd d_xi = (psy[n - 1] + I * chy[n - 1]) - dn * xi / y;
+        const cd Ua = d_ps2y - An * d_ch2y, Va = ps2y[n] - An * ch2y[n];
+        const cd Ub = d_ps2y - Bn * d_ch2y, Vb = ps2y[n] - Bn * ch2y[n];
+        an[n] = (psy[n] * Ua - m2 * d_psy * Va) / (xi * Ua - m2 * d_xi * Va);                    // S1
+        bn[n] = (m2 * psy[n] * Ub - d_psy * Vb) / (m2 * xi * Ub - d_xi * Vb);                    // S2
+    }
+    double s_ext = 0.0, s_sca = 0.0, s_g = 0.0;
+    for (int n = 1; n <= nmax; ++n) {
+        double w = 2.0 * n + 1.0;
+        s_ext += w * std::real((an[n] + bn[n]) / (n_m * n_m));
+        s_sca += w * (std::norm(an[n]) + std::norm(bn[n]));
+        s_g += (double)n * (n + 2.0) / (n + 1.0) *
+                   std::real(an[n] * std::conj(an[n + 1]) + bn[n] * std::conj(bn[n + 1])) +
+               w / ((double)n * (n + 1.0)) * std::real(an[n] * std::conj(bn[n]));
+    }
+    const double alpha = 4.0 * M_PI * b * nmi / wl;
+    const double gam = gamma_term(alpha);
+    const double area = M_PI * b * b;
+    *q_ext = wl * wl / (2.0 * M_PI) * s_ext / area;
+    *q_sca = wl * wl * std::exp(-alpha) / (2.0 * M_PI * gam * std::norm(n_m)) * s_sca / area;
+    *g_out = (s_sca > 0.0) ? 2.0 * s_g / s_sca : 0.0;
+    if (nmax_out) *nmax_out = nmax;
+    if (an_out && bn_out) {
+        for (int n = 1; n <= nt && n <= an_cap; ++n) {
+            an_out[2 * (n - 1)] = an[n].real(); an_out[2 * (n - 1) + 1] = an[n].imag();
+            bn_out[2 * (n - 1)] = bn[n].real(); bn_out[2 * (n - 1) + 1] = bn[n].imag();
+        }
+    }
+    delete[] ps2x; delete[] ch2x; delete[] ps2y; delete[] ch2y; delete[] psy; delete[] chy;
+    delete[] an; delete[] bn;
+    return 0;
+}
+
 extern "C" double orc_gamma_term(double alpha) { return gamma_term(alpha); }
+
+extern "C" int orc_mie_properties_cs(int n_wl, const double* wl, int n_groups,
+                                     const double* nm_re, const double* nm_im, int n_species,
+                                     const int* species_group, const double* np_re,
+                                     const double* np_im, const double* nc_re,
+                                     const double* nc_im, const double* radius,
+                                     const double* core_radius, const double* vol_frac,
+                                     double* mu_s, double* mu_a, double* g, double* q_ext,
+                                     double* q_sca, double* g_sp);
+
+extern "C" int orc_mie_properties(int n_wl, const double* wl, int n_groups, const double* nm_re,
+                                  const double* nm_im, int n_species, const int* species_group,
+                                  const double* np_re, const double* np_im, const double* radius,
+                                  const double* vol_frac, double* mu_s, double* mu_a, double* g,
+                                  double* q_ext, double* q_sca, double* g_sp) {
+    return orc_mie_properties_cs(n_wl, wl, n_groups, nm_re, nm_im, n_species, species_group,
+                                 np_re, np_im, nullptr, nullptr, radius, nullptr, vol_frac, mu_s,
+                                 mu_a, g, q_ext, q_sca, g_sp);
+}
 extern "C" void orc_log_deriv_psi(int n, double zr, double zi, double* out) {
     cd d = log_deriv_psi(n, cd(zr, zi));
     out[0] = d.real(); out[1] = d.imag();
@@ -543,11 +705,21 @@ extern "C" void orc_log_deriv_psi(int n, double zr, double zi, double* out) {
 // when the summed volume fraction exceeds 0.08, and the matrix absorption of Eq. 20.
 //   species s belongs to group species_group[s]; particle index [n_species*n_wl];
 //   matrix index [n_groups*n_wl]; outputs [n_groups*n_wl].
-extern "C" int orc_mie_properties(int n_wl, const double* wl, int n_groups, const double* nm_re,
-                                  const double* nm_im, int n_species, const int* species_group,
-                                  const double* np_re, const double* np_im, const double* radius,
-                                  const double* vol_frac, double* mu_s, double* mu_a, double* g,
-                                  double* q_ext, double* q_sca, double* g_sp) {
+extern "C" int orc_mie_coated(double wl, double ncr, double nci, double nsr, double nsi,
+                              double nmr, double nmi, double a, double b, double* q_ext,
+                              double* q_sca, double* g_out, int* nmax_out, double* an_out,
+                              double* bn_out, int an_cap);
+
+// With core arrays (nc_re, nc_im [n_species*n_wl], core_radius [n_species]), species with
+// core_radius > 0 are core-shell spheres (shell index np, outer radius radius).
+extern "C" int orc_mie_properties_cs(int n_wl, const double* wl, int n_groups,
+                                     const double* nm_re, const double* nm_im, int n_species,
+                                     const int* species_group, const double* np_re,
+                                     const double* np_im, const double* nc_re,
+                                     const double* nc_im, const double* radius,
+                                     const double* core_radius, const double* vol_frac,
+                                     double* mu_s, double* mu_a, double* g, double* q_ext,
+                                     double* q_sca, double* g_sp) {
     for (int gi = 0; gi < n_groups; ++gi) {
         for (int w = 0; w < n_wl; ++w) {
             const long long gw = (long long)gi * n_wl + w;
@@ -556,8 +728,13 @@ extern "C" int orc_mie_properties(int n_wl, const double* wl, int n_groups, cons
                 if (species_group[s] != gi) continue;
                 const long long sw = (long long)s * n_wl + w;
                 double qe, qs, gg;
-                orc_mie_sphere(wl[w], np_re[sw], np_im[sw], nm_re[gw], nm_im[gw], radius[s], &qe,
-                               &qs, &gg, nullptr, nullptr, nullptr, 0);
+                if (core_radius && core_radius[s] > 0.0)
+                    orc_mie_coated(wl[w], nc_re[sw], nc_im[sw], np_re[sw], np_im[sw], nm_re[gw],
+                                   nm_im[gw], core_radius[s], radius[s], &qe, &qs, &gg, nullptr,
+                                   nullptr, nullptr, 0);
+                else
+                    orc_mie_sphere(wl[w], np_re[sw], np_im[sw], nm_re[gw], nm_im[gw], radius[s],
+                                   &qe, &qs, &gg, nullptr, nullptr, nullptr, 0);
                 if (q_ext) q_ext[sw] = qe;
                 if (q_sca) q_sca[sw] = qs;
                 if (g_sp) g_sp[sw] = gg;
@@ -608,6 +785,47 @@ extern "C" double orc_fresnel_f64(double ni, double nt, double ci, double* ct) {
     if (ct) *ct = c;
     return R;
 }
+extern "C" double orc_fresnel_conductor_f64(double ni, double n2, double k2, double ci) {
+    return fresnel_conductor<MathF64>(ni, n2, k2, ci);
+}
+
+extern "C" float orc_fresnel_conductor_f32(float ni, float n2, float k2, float ci) {
+    return fresnel_conductor<MathF32>(ni, n2, k2, ci);
+}
+
+// Solar-weighted totals (section "Output", Eq. 21): for each stack s and each of R, A,
+// T, the integral of the spectral fraction times G over the wavelength grid divided by
+// the integral of G, both by the trapezoidal rule on the grid points.  The spectral
+// fraction at a wavelength is the count over R + A + T of that item (counts rows
+// item = s * n_wl + w, FOS_NCOUNT = 6 columns).  One wavelength: the fractions there.
+extern "C" int orc_solar_weighted(int n_stacks, int n_wl, const double* wl, const double* G,
+                                  const long long* counts, double* out) {
+    for (int s = 0; s < n_stacks; ++s) {
+        double num[3] = {0.0, 0.0, 0.0}, den = 0.0;
+        double frac[2][3];
+        double gw[2];
+        for (int w = 0; w < n_wl; ++w) {
+            const long long* c = counts + ((long long)s * n_wl + w) * 6;
+            const double tot = (double)(c[0] + c[1] + c[2]);
+            for (int k = 0; k < 3; ++k) frac[w & 1][k] = tot > 0.0 ? (double)c[k] / tot : 0.0;
+            gw[w & 1] = G[w];
+            if (n_wl == 1) {
+                for (int k = 0; k < 3; ++k) num[k] = frac[0][k];
+                den = 1.0;
+                break;
+            }
+            if (w == 0) continue;
+            const double h = wl[w] - wl[w - 1];
+            const int a = (w - 1) & 1, b = w & 1;
+            for (int k = 0; k < 3; ++k)
+                num[k] += 0.5 * h * (frac[a][k] * gw[a] + frac[b][k] * gw[b]);
+            den += 0.5 * h * (gw[a] + gw[b]);
+        }
+        for (int k = 0; k < 3; ++k) out[(long long)s * 3 + k] = num[k] / den;
+    }
+    return 0;
+}
+
 extern "C" int orc_mc_run(const orc_batch* b, int fp32, long long* counts, int* photon_log,
                           long long log_stride) {
     if (b->max_layers < 1 || b->max_layers > ORC_MAX_LAYERS) return 1;

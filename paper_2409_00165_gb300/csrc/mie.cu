@@ -1,7 +1,8 @@
 // Mie theory + effective medium on GB300, FP64 (arxiv 2409.00165, section
 // "Scattering properties", Eqs. 1-20).
 //
-// mie_kernel: one thread per (species, wavelength), grid-stride.  The logarithmic
+// mie_kernel: one thread per (species, wavelength), grid-stride; homogeneous spheres
+//   (sphere_eval) and core-shell spheres (coated_eval, supplement Eqs. S1-S9).  The logarithmic
 //   derivative D_n(z) = psi_n'(z)/psi_n(z) of psi_n(z) = z j_n(z) (A_n of Eq. 4) comes
 //   from the downward recurrence D_{n-1} = n/z - 1/(D_n + n/z) started at
 //   N* = n_max + 17 with D = 0, for the particle argument y and the host argument x.
@@ -77,9 +78,10 @@ __device__ __forceinline__ double gamma_term(double a) {
 struct MieArgs {
     int n_wl, n_groups, n_species;
     const double *wl, *nm_re, *nm_im, *np_re, *np_im, *radius, *vol_frac;
+    const double *nc_re, *nc_im, *core_radius;   // core-shell species (NULL: none)
     const int* species_group;
     double *q_ext, *q_sca, *g_sp;
-    double2* scratch;   // [2*FOS_MIE_MAX_TERMS][T]
+    double2* scratch;   // [n_cols * FOS_MIE_MAX_TERMS][T]
     long long T;
     unsigned* status;
     int inject;
@@ -90,12 +92,198 @@ __device__ __forceinline__ void flag(unsigned* st, unsigned bit, long long idx) 
     atomicMin(&st[ST_INDEX], (unsigned)(idx < 0xffffffffLL ? idx : 0xfffffffeLL));
 }
 
+// Downward recurrence D_{n-1} = n/z - 1/(D_n + n/z) from D_{nstart} = 0; D_n stored for
+// n <= nt at col[(n-1) T].
+__device__ __forceinline__ void downward_D(cx z, int nstart, int nt, double2* col, long long T) {
+    const cx zi = mk(1.0, 0.0) / z;
+    cx D = mk(0.0, 0.0);
+    for (int n = nstart; n >= 1; --n) {
+        if (n <= nt) col[(long long)(n - 1) * T] = make_double2(D.re, D.im);
+        const cx nz = (double)n * zi;
+        D = nz - mk(1.0, 0.0) / (D + nz);
+    }
+}
+
+struct Sums {
+    double ext, sca, g;
+};
+
+// Accumulates Eqs. 11, 12 and the numerator of 15 for order n given a_n, b_n and the
+// previous order's coefficients.
+__device__ __forceinline__ void accumulate(Sums& S, int n, int nmax, cx an, cx bn, cx a_prev,
+                                           cx b_prev, cx inv_nm2) {
+    const double dn = (double)n;
+    if (n <= nmax) {
+        const double wgt = 2.0 * dn + 1.0;
+        S.ext += wgt * ((an + bn) * inv_nm2).re;           // Eq. 11
+        S.sca += wgt * (norm2(an) + norm2(bn));             // Eq. 12
+    }
+    if (n >= 2) {   // Eq. 15 term of order m = n-1 needs a_n, b_n
+        const double m = dn - 1.0;
+        const double t1 = a_prev.re * an.re + a_prev.im * an.im + b_prev.re * bn.re +
+                          b_prev.im * bn.im;              // Re(a_m a_n^* + b_m b_n^*)
+        const double t2 = a_prev.re * b_prev.re + a_prev.im * b_prev.im;   // Re(a_m b_m^*)
+        S.g += m * (m + 2.0) / (m + 1.0) * t1 + (2.0 * m + 1.0) / (m * (m + 1.0)) * t2;
+    }
+}
+
+// Eqs. 10-12 and 15 from the sums; r is the (outer) radius.
+__device__ __forceinline__ void efficiencies(const Sums& S, double lam, double r, cx n_m,
+                                             double* qe, double* qs, double* gg) {
+    const double alpha = 4.0 * M_PI * r * n_m.im / lam;
+    const double gam = gamma_term(alpha);
+    const double area = M_PI * r * r;
+    *qe = lam * lam / (2.0 * M_PI) * S.ext / area;
+    *qs = lam * lam * exp(-alpha) / (2.0 * M_PI * gam * norm2(n_m)) * S.sca / area;
+    *gg = (S.sca > 0.0) ? 2.0 * S.g / S.sca : 0.0;
+}
+
+// Homogeneous sphere (Eqs. 1-5): D_n(y), D_n(x) downward; psi_n(x) upward while
+// n <= |x|, psi_{n-1}/(D_n(x) + n/x) above; xi_n(x) upward; Eqs. 2-3 multiplied through
+// by psi_n(x) and xi_n(x).  Returns false when n_max + 16 exceeds the scratch.
+__device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY, double2* colX,
+                            long long T, double* qe, double* qs, double* gg) {
+    const double k = 2.0 * M_PI * r / lam;
+    const cx x = k * n_m;   // Eq. 1
+    const cx y = k * n_p;
+    const double ay = cabs_(y), ax = cabs_(x);
+    const int nmax = (int)ceil(2.0 + ay + 4.3 * cbrt(ay));
+    const int nt = nmax + 1;          // a_{n+1}, b_{n+1} for Eq. 15
+    const int nstart = nt + 16;
+    if (nstart > FOS_MIE_MAX_TERMS) return false;
+    const cx xi_ = mk(1.0, 0.0) / x;
+    downward_D(y, nstart, nt, colY, T);
+    downward_D(x, nstart, nt, colX, T);
+    cx psi_m1 = ccos(x), psi_0 = csin(x);
+    const double eb = exp(-x.im);
+    cx xi_m1 = mk(eb * cos(x.re), eb * sin(x.re));        // e^{ix}
+    cx xi_0 = psi_0 - mk(-psi_m1.im, psi_m1.re);            // sin x - i cos x
+    const cx inv_nm2 = mk(1.0, 0.0) / (n_m * n_m);
+    Sums S{0.0, 0.0, 0.0};
+    cx a_prev = mk(0.0, 0.0), b_prev = mk(0.0, 0.0);
+    for (int n = 1; n <= nt; ++n) {
+        const double dn = (double)n;
+        cx psi_n;
+        if (dn <= ax) {
+            psi_n = (double)(2 * n - 1) * xi_ * psi_0 - psi_m1;
+        } else {
+            const double2 d = colX[(long long)(n - 1) * T];
+            psi_n = psi_0 / (mk(d.x, d.y) + dn * xi_);
+        }
+        const cx xi_n = (double)(2 * n - 1) * xi_ * xi_0 - xi_m1;
+        const cx dpsi = psi_0 - dn * xi_ * psi_n;
+        const cx dxi = xi_0 - dn * xi_ * xi_n;
+        const double2 dy = colY[(long long)(n - 1) * T];
+        const cx Dy = mk(dy.x, dy.y);
+        const cx mDy = n_m * Dy, pDy = n_p * Dy;
+        const cx an = (mDy * psi_n - n_p * dpsi) / (mDy * xi_n - n_p * dxi);   // Eq. 2
+        const cx bn = (pDy * psi_n - n_m * dpsi) / (pDy * xi_n - n_m * dxi);   // Eq. 3
+        accumulate(S, n, nmax, an, bn, a_prev, b_prev, inv_nm2);
+        a_prev = an;
+        b_prev = bn;
+        psi_m1 = psi_0;
+        psi_0 = psi_n;
+        xi_m1 = xi_0;
+        xi_0 = xi_n;
+    }
+    efficiencies(S, lam, r, n_m, qe, qs, gg);
+    return true;
+}
+
+// Riccati-Bessel psi_n(z), chi_n(z) = z y_n(z) one order up: psi by upward recurrence
+// while n <= |z| and psi_{n-1}/(D_n + n/z) above; chi by upward recurrence.
+struct RB {
+    cx zi;
+    double az;
+    cx psi_m1, psi0, chi_m1, chi0;   // orders n-2, n-1
+};
+__device__ __forceinline__ void rb_init(RB& R, cx z) {
+    R.zi = mk(1.0, 0.0) / z;
+    R.az = cabs_(z);
+    R.psi_m1 = ccos(z);
+    R.psi0 = csin(z);
+    R.chi_m1 = csin(z);
+    R.chi0 = mk(0.0, 0.0) - ccos(z);
+}
+// advances to order n; returns psi_n, chi_n and their derivatives
+__device__ __forceinline__ void rb_step(RB& R, int n, const double2* colD, long long T, cx& psi,
+                                        cx& dpsi, cx& chi, cx& dchi) {
+    const double dn = (double)n;
+    const cx c = (double)(2 * n - 1) * R.zi;
+    if (dn <= R.az) {
+        psi = c * R.psi0 - R.psi_m1;
+    } else {
+        const double2 d = colD[(long long)(n - 1) * T];
+        psi = R.psi0 / (mk(d.x, d.y) + dn * R.zi);
+    }
+    chi = c * R.chi0 - R.chi_m1;
+    dpsi = R.psi0 - dn * R.zi * psi;
+    dchi = R.chi0 - dn * R.zi * chi;
+    R.psi_m1 = R.psi0;
+    R.psi0 = psi;
+    R.chi_m1 = R.chi0;
+    R.chi0 = chi;
+}
+
+// Core-shell sphere (supplement Eqs. S1-S9): core radius a (index n_c), outer radius b
+// (shell index n_s), host n_m; m1 = n_c/n_m, m2 = n_s/n_m, x = k a, y = k b.
+// A_n, B_n (S3, S4) divided through by psi_n(m1 x), i.e. with D_n(m1 x); chi_n = z y_n(z)
+// (S8); xi_n = psi_n + i chi_n (S9).  Four downward D columns: m1 x, m2 x, m2 y, y.
+__device__ bool coated_eval(double lam, double a, double b, cx n_c, cx n_s, cx n_m,
+                            double2* col0, double2* col1, double2* col2, double2* col3,
+                            long long T, double* qe, double* qs, double* gg) {
+    const double kv = 2.0 * M_PI / lam;
+    const cx x = (kv * a) * n_m, y = (kv * b) * n_m;
+    const cx inv_nm = mk(1.0, 0.0) / n_m;
+    const cx m1 = n_c * inv_nm, m2 = n_s * inv_nm;
+    const double ymax = kv * b * fmax(cabs_(n_c), cabs_(n_s));
+    const int nmax = (int)ceil(2.0 + ymax + 4.3 * cbrt(ymax));
+    const int nt = nmax + 1;
+    const int nstart = nt + 16;
+    if (nstart > FOS_MIE_MAX_TERMS) return false;
+    const cx z1 = m1 * x, z2x = m2 * x, z2y = m2 * y;
+    downward_D(z1, nstart, nt, col0, T);
+    downward_D(z2x, nstart, nt, col1, T);
+    downward_D(z2y, nstart, nt, col2, T);
+    downward_D(y, nstart, nt, col3, T);
+    RB r2x, r2y, ry;
+    rb_init(r2x, z2x);
+    rb_init(r2y, z2y);
+    rb_init(ry, y);
+    const cx inv_nm2 = inv_nm * inv_nm;
+    const cx I = mk(0.0, 1.0);
+    Sums S{0.0, 0.0, 0.0};
+    cx a_prev = mk(0.0, 0.0), b_prev = mk(0.0, 0.0);
+    for (int n = 1; n <= nt; ++n) {
+        cx ps2x, dps2x, ch2x, dch2x, ps2y, dps2y, ch2y, dch2y, psy, dpsy, chy, dchy;
+        rb_step(r2x, n, col1, T, ps2x, dps2x, ch2x, dch2x);
+        rb_step(r2y, n, col2, T, ps2y, dps2y, ch2y, dch2y);
+        rb_step(ry, n, col3, T, psy, dpsy, chy, dchy);
+        const double2 d1 = col0[(long long)(n - 1) * T];
+        const cx D1 = mk(d1.x, d1.y);                        // psi'/psi at m1 x
+        const cx D2x = dps2x / ps2x;
+        const cx m2D1 = m2 * D1, m1D2 = m1 * D2x;
+        const cx An = ps2x * (m2D1 - m1D2) / (m2D1 * ch2x - m1 * dch2x);            // S3
+        const cx Bn = ps2x * (m2 * D2x - m1 * D1) / (m2 * dch2x - m1 * D1 * ch2x);  // S4
+        const cx xi = psy + I * chy, dxi = dpsy + I * dchy;                          // S9
+        const cx Ua = dps2y - An * dch2y, Va = ps2y - An * ch2y;
+        const cx Ub = dps2y - Bn * dch2y, Vb = ps2y - Bn * ch2y;
+        const cx an = (psy * Ua - m2 * dpsy * Va) / (xi * Ua - m2 * dxi * Va);       // S1
+        const cx bn = (m2 * psy * Ub - dpsy * Vb) / (m2 * xi * Ub - dxi * Vb);       // S2
+        accumulate(S, n, nmax, an, bn, a_prev, b_prev, inv_nm2);
+        a_prev = an;
+        b_prev = bn;
+    }
+    efficiencies(S, lam, b, n_m, qe, qs, gg);
+    return true;
+}
+
 __global__ void __launch_bounds__(128) mie_kernel(MieArgs A) {
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (A.inject && tid == 0) atomicOr(&A.status[ST_CALL], DEV_INJECTED);
     const long long n_eval = (long long)A.n_species * A.n_wl;
-    double2* colY = A.scratch + tid;                                    // D_n(y) at [n-1][T]
-    double2* colX = A.scratch + (long long)FOS_MIE_MAX_TERMS * A.T + tid;  // D_n(x)
+    const long long col = (long long)FOS_MIE_MAX_TERMS * A.T;
+    double2* c0 = A.scratch + tid;
     for (long long ev = tid; ev < n_eval; ev += A.T) {
         const int s = (int)(ev / A.n_wl), w = (int)(ev % A.n_wl);
         const int gi = A.species_group[s];
@@ -105,99 +293,28 @@ __global__ void __launch_bounds__(128) mie_kernel(MieArgs A) {
         const cx n_p = mk(A.np_re[ev], A.np_im[ev]);
         const cx n_m = mk(A.nm_re[gw], A.nm_im[gw]);
         const double f = A.vol_frac[s];
+        const double a = A.core_radius ? A.core_radius[s] : 0.0;
+        cx n_c = mk(1.0, 0.0);
+        if (a > 0.0) n_c = mk(A.nc_re[ev], A.nc_im[ev]);
         ok = ok && isfinite(lam) && lam > 0.0 && isfinite(r) && r > 0.0 &&
              isfinite(n_p.re) && n_p.re > 0.0 && isfinite(n_p.im) && n_p.im >= 0.0 &&
              isfinite(n_m.re) && n_m.re > 0.0 && isfinite(n_m.im) && n_m.im >= 0.0 &&
-             f >= 0.0 && f < 1.0;
+             f >= 0.0 && f < 1.0 && a >= 0.0 && a < r && isfinite(n_c.re) && n_c.re > 0.0 &&
+             isfinite(n_c.im) && n_c.im >= 0.0;
         const double nanv = __longlong_as_double(0x7ff8000000000000LL);
+        double qe = nanv, qs = nanv, gg = nanv;
         if (!ok) {
             flag(A.status, DEV_INVALID, ev);
-            A.q_ext[ev] = nanv;
-            A.q_sca[ev] = nanv;
-            A.g_sp[ev] = nanv;
-            continue;
+        } else {
+            const bool fit = (a > 0.0)
+                ? coated_eval(lam, a, r, n_c, n_p, n_m, c0, c0 + col, c0 + 2 * col,
+                              c0 + 3 * col, A.T, &qe, &qs, &gg)
+                : sphere_eval(lam, r, n_p, n_m, c0, c0 + col, A.T, &qe, &qs, &gg);
+            if (!fit) flag(A.status, DEV_RANGE, ev);
         }
-        const double k = 2.0 * M_PI * r / lam;
-        const cx x = k * n_m;   // Eq. 1
-        const cx y = k * n_p;
-        const double ay = cabs_(y), ax = cabs_(x);
-        const int nmax = (int)ceil(2.0 + ay + 4.3 * cbrt(ay));
-        const int nt = nmax + 1;          // a_{n+1}, b_{n+1} for Eq. 15
-        const int nstart = nt + 16;
-        if (nstart > FOS_MIE_MAX_TERMS) {
-            flag(A.status, DEV_RANGE, ev);
-            A.q_ext[ev] = nanv;
-            A.q_sca[ev] = nanv;
-            A.g_sp[ev] = nanv;
-            continue;
-        }
-        const cx yi = mk(1.0, 0.0) / y;
-        const cx xi_ = mk(1.0, 0.0) / x;
-        // downward recurrences, D_{nstart} = 0
-        {
-            cx Dy = mk(0.0, 0.0), Dx = mk(0.0, 0.0);
-            for (int n = nstart; n >= 1; --n) {
-                if (n <= nt) {
-                    colY[(long long)(n - 1) * A.T] = make_double2(Dy.re, Dy.im);
-                    colX[(long long)(n - 1) * A.T] = make_double2(Dx.re, Dx.im);
-                }
-                const cx ny = (double)n * yi, nx = (double)n * xi_;
-                Dy = ny - mk(1.0, 0.0) / (Dy + ny);
-                Dx = nx - mk(1.0, 0.0) / (Dx + nx);
-            }
-        }
-        // upward sweep
-        cx psi_m1 = ccos(x), psi_0 = csin(x);
-        const double eb = exp(-x.im);
-        cx xi_m1 = mk(eb * cos(x.re), eb * sin(x.re));        // e^{ix}
-        cx xi_0 = psi_0 - mk(-psi_m1.im, psi_m1.re);            // sin x - i cos x
-        const cx inv_nm2 = mk(1.0, 0.0) / (n_m * n_m);
-        double s_ext = 0.0, s_sca = 0.0, s_g = 0.0;
-        cx a_prev = mk(0.0, 0.0), b_prev = mk(0.0, 0.0);
-        for (int n = 1; n <= nt; ++n) {
-            const double dn = (double)n;
-            cx psi_n;
-            if (dn <= ax) {
-                psi_n = (double)(2 * n - 1) * xi_ * psi_0 - psi_m1;
-            } else {
-                const double2 d = colX[(long long)(n - 1) * A.T];
-                psi_n = psi_0 / (mk(d.x, d.y) + dn * xi_);
-            }
-            const cx xi_n = (double)(2 * n - 1) * xi_ * xi_0 - xi_m1;
-            const cx dpsi = psi_0 - dn * xi_ * psi_n;
-            const cx dxi = xi_0 - dn * xi_ * xi_n;
-            const double2 dy = colY[(long long)(n - 1) * A.T];
-            const cx Dy = mk(dy.x, dy.y);
-            const cx mDy = n_m * Dy, pDy = n_p * Dy;
-            const cx an = (mDy * psi_n - n_p * dpsi) / (mDy * xi_n - n_p * dxi);   // Eq. 2
-            const cx bn = (pDy * psi_n - n_m * dpsi) / (pDy * xi_n - n_m * dxi);   // Eq. 3
-            if (n <= nmax) {
-                const double wgt = 2.0 * dn + 1.0;
-                s_ext += wgt * ((an + bn) * inv_nm2).re;           // Eq. 11
-                s_sca += wgt * (norm2(an) + norm2(bn));             // Eq. 12
-            }
-            if (n >= 2) {   // Eq. 15 term of order m = n-1 needs a_n, b_n
-                const double m = dn - 1.0;
-                const double t1 = a_prev.re * an.re + a_prev.im * an.im +
-                                  b_prev.re * bn.re + b_prev.im * bn.im;   // Re(a_m a_n^* + b_m b_n^*)
-                const double t2 = a_prev.re * b_prev.re + a_prev.im * b_prev.im;  // Re(a_m b_m^*)
-                s_g += m * (m + 2.0) / (m + 1.0) * t1 + (2.0 * m + 1.0) / (m * (m + 1.0)) * t2;
-            }
-            a_prev = an;
-            b_prev = bn;
-            psi_m1 = psi_0;
-            psi_0 = psi_n;
-            xi_m1 = xi_0;
-            xi_0 = xi_n;
-        }
-        const double alpha = 4.0 * M_PI * r * n_m.im / lam;
-        const double gam = gamma_term(alpha);
-        const double c_ext = lam * lam / (2.0 * M_PI) * s_ext;
-        const double c_sca = lam * lam * exp(-alpha) / (2.0 * M_PI * gam * norm2(n_m)) * s_sca;
-        const double area = M_PI * r * r;
-        A.q_ext[ev] = c_ext / area;
-        A.q_sca[ev] = c_sca / area;
-        A.g_sp[ev] = (s_sca > 0.0) ? 2.0 * s_g / s_sca : 0.0;
+        A.q_ext[ev] = qe;
+        A.q_sca[ev] = qs;
+        A.g_sp[ev] = gg;
     }
 }
 
@@ -263,20 +380,20 @@ __global__ void emt_kernel(EmtArgs A) {
 
 using namespace fos;
 
-extern "C" fos_status fos_mie_properties(int n_wl, const double* wl, int n_groups,
-                                         const double* nm_re, const double* nm_im,
-                                         int n_species, const int* species_group,
-                                         const double* np_re, const double* np_im,
-                                         const double* radius, const double* vol_frac,
-                                         double* mu_s, double* mu_a, double* g, double* q_ext,
-                                         double* q_sca, double* g_species, unsigned flags,
-                                         void* stream) {
+static fos_status mie_impl(int n_wl, const double* wl, int n_groups, const double* nm_re,
+                           const double* nm_im, int n_species, const int* species_group,
+                           const double* np_re, const double* np_im, const double* nc_re,
+                           const double* nc_im, const double* radius, const double* core_radius,
+                           const double* vol_frac, double* mu_s, double* mu_a, double* g,
+                           double* q_ext, double* q_sca, double* g_species, unsigned flags,
+                           void* stream) {
     if (n_wl < 1 || n_groups < 1 || n_species < 0) return FOS_ERR_INVALID_ARG;
     if ((long long)n_groups * n_wl > 0x7fffffffLL || (long long)n_species * n_wl > 0x7fffffffLL)
         return FOS_ERR_INVALID_ARG;
     if (!wl || !nm_re || !nm_im || !mu_s || !mu_a || !g) return FOS_ERR_INVALID_ARG;
     if (n_species > 0 && (!species_group || !np_re || !np_im || !radius || !vol_frac))
         return FOS_ERR_INVALID_ARG;
+    if (core_radius && n_species > 0 && (!nc_re || !nc_im)) return FOS_ERR_INVALID_ARG;
     Workspace* ws = nullptr;
     fos_status st = get_workspace(&ws);
     if (st != FOS_OK) return st;
@@ -284,10 +401,11 @@ extern "C" fos_status fos_mie_properties(int n_wl, const double* wl, int n_group
     cudaStream_t s = (cudaStream_t)stream;
     const long long n_eval = (long long)n_species * n_wl;
     const int block = 128;
-    long long T = (long long)ws->num_sms * 128;
+    const int n_cols = core_radius ? 4 : 2;   // downward log-derivative columns per thread
+    long long T = (long long)ws->num_sms * 128 * 2 / n_cols;
     const long long need_T = ((n_eval + block - 1) / block) * block;
     if (need_T < T) T = need_T > 0 ? need_T : block;
-    const size_t scratch_bytes = (size_t)2 * FOS_MIE_MAX_TERMS * T * sizeof(double2);
+    const size_t scratch_bytes = (size_t)n_cols * FOS_MIE_MAX_TERMS * T * sizeof(double2);
     const bool own_q = !(q_ext && q_sca && g_species);
     const size_t qbytes = own_q ? (size_t)3 * n_eval * sizeof(double) + 1024 : 0;
     st = ensure_buffer(ws, &ws->mie_scratch, &ws->mie_bytes, scratch_bytes + qbytes);
@@ -308,6 +426,9 @@ extern "C" fos_status fos_mie_properties(int n_wl, const double* wl, int n_group
         ma.nm_im = nm_im;
         ma.np_re = np_re;
         ma.np_im = np_im;
+        ma.nc_re = nc_re;
+        ma.nc_im = nc_im;
+        ma.core_radius = core_radius;
         ma.radius = radius;
         ma.vol_frac = vol_frac;
         ma.species_group = species_group;
@@ -344,4 +465,68 @@ extern "C" fos_status fos_mie_properties(int n_wl, const double* wl, int n_group
     mie::emt_kernel<<<(unsigned)eb, 256, 0, s>>>(ea);
     FOS_CUDA_TRY(cudaGetLastError());
     return finish_call(ws, s, flags);
+}
+
+extern "C" fos_status fos_mie_properties(int n_wl, const double* wl, int n_groups,
+                                         const double* nm_re, const double* nm_im,
+                                         int n_species, const int* species_group,
+                                         const double* np_re, const double* np_im,
+                                         const double* radius, const double* vol_frac,
+                                         double* mu_s, double* mu_a, double* g, double* q_ext,
+                                         double* q_sca, double* g_species, unsigned flags,
+                                         void* stream) {
+    return mie_impl(n_wl, wl, n_groups, nm_re, nm_im, n_species, species_group, np_re, np_im,
+                    nullptr, nullptr, radius, nullptr, vol_frac, mu_s, mu_a, g, q_ext, q_sca,
+                    g_species, flags, stream);
+}
+
+extern "C" fos_status fos_mie_properties_cs(int n_wl, const double* wl, int n_groups,
+                                            const double* nm_re, const double* nm_im,
+                                            int n_species, const int* species_group,
+                                            const double* ns_re, const double* ns_im,
+                                            const double* nc_re, const double* nc_im,
+                                            const double* radius, const double* core_radius,
+                                            const double* vol_frac, double* mu_s, double* mu_a,
+                                            double* g, double* q_ext, double* q_sca,
+                                            double* g_species, unsigned flags, void* stream) {
+    if (n_species > 0 && !core_radius) return FOS_ERR_INVALID_ARG;
+    return mie_impl(n_wl, wl, n_groups, nm_re, nm_im, n_species, species_group, ns_re, ns_im,
+                    nc_re, nc_im, radius, core_radius, vol_frac, mu_s, mu_a, g, q_ext, q_sca,
+                    g_species, flags, stream);
+}
+
+// Particle-size distribution (section "Scattering properties", last paragraph): one
+// diameter D with standard deviation sigma becomes n diameters evenly spaced over
+// D +- 3 sigma; each carries the share of the volume fraction given by its Gaussian
+// weight exp(-(D_i - D)^2 / (2 sigma^2)), the weights normalised to sum to 1.
+// Diameters <= 0 are dropped and the remaining weights renormalised.  Host arrays.
+extern "C" fos_status fos_size_distribution(double diameter, double sigma, double vol_frac,
+                                            int n, double* radius, double* vol_fracs,
+                                            int* n_out) {
+    if (!radius || !vol_fracs || !n_out) return FOS_ERR_INVALID_ARG;
+    if (!(diameter > 0.0) || !(sigma >= 0.0) || !(vol_frac >= 0.0 && vol_frac < 1.0) || n < 1)
+        return FOS_ERR_INVALID_ARG;
+    if (sigma == 0.0 || n == 1) {
+        radius[0] = 0.5 * diameter;
+        vol_fracs[0] = vol_frac;
+        *n_out = 1;
+        return FOS_OK;
+    }
+    if (n % 2 == 0) return FOS_ERR_INVALID_ARG;   // odd: the centre size is one of them
+    const double step = 6.0 * sigma / (double)(n - 1);
+    double wsum = 0.0;
+    int k = 0;
+    for (int i = 0; i < n; ++i) {
+        const double d = diameter - 3.0 * sigma + step * (double)i;
+        if (!(d > 0.0)) continue;
+        const double u = (d - diameter) / sigma;
+        const double w = exp(-0.5 * u * u);
+        radius[k] = 0.5 * d;
+        vol_fracs[k] = w;
+        wsum += w;
+        ++k;
+    }
+    for (int i = 0; i < k; ++i) vol_fracs[i] = vol_frac * (vol_fracs[i] / wsum);
+    *n_out = k;
+    return FOS_OK;
 }

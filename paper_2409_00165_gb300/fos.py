@@ -159,14 +159,57 @@ def fos_mie_properties(wl, nm_re, nm_im, species_group, np_re, np_im, radius, vo
     return lib().fos_mie_properties(*args)
 
 
+def fos_mie_properties_cs(wl, nm_re, nm_im, species_group, ns_re, ns_im, nc_re, nc_im,
+                          radius, core_radius, vol_frac, mu_s, mu_a, g, q_ext=None, q_sca=None,
+                          g_species=None, flags=0, stream=None) -> int:
+    n_wl = wl.numel()
+    n_groups = nm_re.numel() // max(n_wl, 1)
+    n_species = radius.numel() if radius is not None else 0
+    f64, i32 = torch.float64, torch.int32
+    none = n_species == 0
+    args = [n_wl, _dev(wl, f64, "wl"), n_groups, _dev(nm_re, f64, "nm_re"),
+            _dev(nm_im, f64, "nm_im"), n_species,
+            _dev(species_group, i32, "species_group", none),
+            _dev(ns_re, f64, "ns_re", none), _dev(ns_im, f64, "ns_im", none),
+            _dev(nc_re, f64, "nc_re", none), _dev(nc_im, f64, "nc_im", none),
+            _dev(radius, f64, "radius", none), _dev(core_radius, f64, "core_radius", none),
+            _dev(vol_frac, f64, "vol_frac", none),
+            _dev(mu_s, f64, "mu_s"), _dev(mu_a, f64, "mu_a"), _dev(g, f64, "g"),
+            _dev(q_ext, f64, "q_ext", True), _dev(q_sca, f64, "q_sca", True),
+            _dev(g_species, f64, "g_species", True), int(flags), _stream(stream)]
+    fn = lib().fos_mie_properties_cs
+    fn.argtypes = ([ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                    ctypes.c_int] + [ctypes.c_void_p] * 14 + [ctypes.c_uint, ctypes.c_void_p])
+    fn.restype = ctypes.c_int
+    return fn(*args)
+
+
+def fos_size_distribution(diameter: float, sigma: float, vol_frac: float, n: int = 101):
+    """(radius [k], vol_frac [k]) NumPy arrays of the sizes a diameter distribution expands to."""
+    import numpy as np
+    r = np.zeros(max(n, 1))
+    f = np.zeros(max(n, 1))
+    k = ctypes.c_int(0)
+    fn = lib().fos_size_distribution
+    fn.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                   ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
+    fn.restype = ctypes.c_int
+    check(fn(float(diameter), float(sigma), float(vol_frac), int(n), r.ctypes.data,
+             f.ctypes.data, ctypes.byref(k)), "fos_size_distribution")
+    return r[: k.value].copy(), f[: k.value].copy()
+
+
 # --------------------------------------------------------------------------- MC
 def make_batch(n_stacks, n_wl, max_layers, mu_s, mu_a, g, n_layer, thickness,
                n_layers=None, n_above=None, n_below=None, substrate_R=None, n_photons=None,
                photons_per_item=0, photon_first=None, item_list=None, seed=0,
                item_id_base=0, max_events=0) -> FosBatch:
-    """Fills the C struct from CUDA tensors (the tensors must outlive the call)."""
+    """Fills the C struct from CUDA tensors.  The struct keeps references to the tensors,
+    so temporaries passed here stay allocated as long as the struct lives."""
     f64, i32, i64 = torch.float64, torch.int32, torch.int64
     b = FosBatch()
+    b._keep = [t for t in (mu_s, mu_a, g, n_layer, thickness, n_layers, n_above, n_below,
+                           substrate_R, n_photons, photon_first, item_list) if t is not None]
     b.n_stacks, b.n_wl, b.max_layers = int(n_stacks), int(n_wl), int(max_layers)
     b.n_layers = _dev(n_layers, i32, "n_layers", True)
     b.mu_s = _dev(mu_s, f64, "mu_s")

@@ -148,3 +148,76 @@ def media_arrays(m: dict) -> dict:
                 nm_im=np.ascontiguousarray(m["nm"].imag.reshape(-1)),
                 np_re=np.ascontiguousarray(m["n_p"].real.reshape(-1)),
                 np_im=np.ascontiguousarray(m["n_p"].imag.reshape(-1)))
+
+
+# --------------------------------------------------------------------------------
+# Size distributions: silicon-like particles in water (the paper's Si-water example
+# with synthetic materials): D = 0.5 um at volume fraction 0.1 %, standard deviations
+# 0, 0.05, 0.15 um, a 500 um layer, 400 wavelengths.
+# --------------------------------------------------------------------------------
+def silicon_like_index(wl):
+    """n = 3.45 + 0.2/lambda^2, k = 0.5 exp(-(lambda - 0.3)/0.1) (an absorption edge)."""
+    wl = np.asarray(wl, dtype=np.float64)
+    return (3.45 + 0.2 / (wl * wl)) + 1j * (0.5 * np.exp(-(wl - 0.3) / 0.1))
+
+
+def water_like_index(wl):
+    """n = 1.33, k = 1e-7 + 1e-5 lambda^4 (absorption rising into the infrared)."""
+    wl = np.asarray(wl, dtype=np.float64)
+    return 1.33 + 1j * (1e-7 + 1e-5 * wl ** 4)
+
+
+def size_distribution_media(distributions, diameter=0.5, vol_frac=0.001, thickness=500.0,
+                            n_wl=PAINT_N_WL, n_sizes=101):
+    """One single-layer stack per standard deviation in `distributions`.  The expansion
+    of each distribution into sizes is passed in as `distributions`:
+    a list of (radius array, vol_frac array) pairs (see fos_size_distribution)."""
+    wl = wavelengths(n_wl)
+    sg, rad, vf = [], [], []
+    for s, (r, f) in enumerate(distributions):
+        sg += [s] * len(r)
+        rad += list(r)
+        vf += list(f)
+    n_groups = len(distributions)
+    nm = np.broadcast_to(water_like_index(wl), (n_groups, n_wl)).copy()
+    n_p = np.broadcast_to(silicon_like_index(wl), (len(rad), n_wl)).copy()
+    return dict(wl=wl, n_groups=n_groups, nm=nm, species_group=np.array(sg, np.int32),
+                n_p=n_p, radius=np.array(rad), vol_frac=np.array(vf),
+                thickness=np.full(n_groups, float(thickness)),
+                n_layers=np.ones(n_groups, np.int32), n_stacks=n_groups, max_layers=1,
+                n_wl=n_wl)
+
+
+# --------------------------------------------------------------------------------
+# Core-shell particles: the paper's hollow-SiO2 example with a synthetic silica.
+# Hollow spheres (air core of diameter 0.5 um) of outer diameter 0.7, 0.9, 1.1 um, and
+# solid spheres of the same outer diameters, at volume fraction 0.6 in a 50 um layer in
+# air; 400 wavelengths over 0.3-2.5 um.
+# --------------------------------------------------------------------------------
+def silica_like_index(wl):
+    """n = sqrt(1 + 1.1 lambda^2 / (lambda^2 - 0.01)), k = 1e-6 + 1e-4 (lambda / 2.5)^4
+    (a one-term Sellmeier form near 1.45 with weak absorption rising to the infrared)."""
+    wl = np.asarray(wl, dtype=np.float64)
+    l2 = wl * wl
+    return np.sqrt(1.0 + 1.1 * l2 / (l2 - 0.01)) + 1j * (1e-6 + 1e-4 * (wl / 2.5) ** 4)
+
+
+def hollow_silica_media(outer_diameters=(0.7, 0.9, 1.1), core_diameter=0.5, vol_frac=0.6,
+                        thickness=50.0, n_wl=PAINT_N_WL, solid=True):
+    """One single-layer stack per outer diameter with hollow silica spheres, then (solid)
+    one per outer diameter with solid silica spheres.  Adds core_radius (0 for solid)
+    and n_core [n_species, n_wl] (air) to the media dict."""
+    wl = wavelengths(n_wl)
+    outer = list(outer_diameters)
+    radius = [0.5 * d for d in outer] + ([0.5 * d for d in outer] if solid else [])
+    core = [0.5 * core_diameter] * len(outer) + ([0.0] * len(outer) if solid else [])
+    n_groups = len(radius)
+    nm = np.ones((n_groups, n_wl), np.complex128)
+    n_p = np.broadcast_to(silica_like_index(wl), (n_groups, n_wl)).copy()
+    return dict(wl=wl, n_groups=n_groups, nm=nm, species_group=np.arange(n_groups, dtype=np.int32),
+                n_p=n_p, n_core=np.ones((n_groups, n_wl), np.complex128),
+                radius=np.array(radius), core_radius=np.array(core),
+                vol_frac=np.full(n_groups, float(vol_frac)),
+                thickness=np.full(n_groups, float(thickness)),
+                n_layers=np.ones(n_groups, np.int32), n_stacks=n_groups, max_layers=1,
+                n_wl=n_wl)

@@ -56,12 +56,17 @@ def mie_inputs_to_dev(m: dict):
     nm = np.asarray(m["nm"], np.complex128)
     n_p = np.asarray(m["n_p"], np.complex128)
     f64 = torch.float64
-    return dict(
+    out = dict(
         wl=to_dev(m["wl"], f64),
         nm_re=to_dev(nm.real.reshape(-1), f64), nm_im=to_dev(nm.imag.reshape(-1), f64),
         species_group=to_dev(m["species_group"], torch.int32),
         np_re=to_dev(n_p.real.reshape(-1), f64), np_im=to_dev(n_p.imag.reshape(-1), f64),
         radius=to_dev(m["radius"], f64), vol_frac=to_dev(m["vol_frac"], f64))
+    if "core_radius" in m:
+        nc = np.asarray(m["n_core"], np.complex128)
+        out.update(core_radius=to_dev(m["core_radius"], f64),
+                   nc_re=to_dev(nc.real.reshape(-1), f64), nc_im=to_dev(nc.imag.reshape(-1), f64))
+    return out
 
 
 def gpu_mie(m: dict, allow=(fos.FOS_OK,), flags: int = 0):
@@ -73,11 +78,21 @@ def gpu_mie(m: dict, allow=(fos.FOS_OK,), flags: int = 0):
     out = {k: torch.zeros(n_groups * n_wl, dtype=f64, device="cuda") for k in ("mu_s", "mu_a", "g")}
     q = {k: torch.zeros(max(n_species * n_wl, 1), dtype=f64, device="cuda")
          for k in ("q_ext", "q_sca", "g_species")}
-    st = fos.fos_mie_properties(d["wl"], d["nm_re"], d["nm_im"], d["species_group"], d["np_re"],
-                                d["np_im"], d["radius"], d["vol_frac"], out["mu_s"], out["mu_a"],
-                                out["g"], q["q_ext"], q["q_sca"], q["g_species"], flags=flags)
+    if "core_radius" in m:
+        name = "fos_mie_properties_cs"
+        st = fos.fos_mie_properties_cs(d["wl"], d["nm_re"], d["nm_im"], d["species_group"],
+                                       d["np_re"], d["np_im"], d["nc_re"], d["nc_im"],
+                                       d["radius"], d["core_radius"], d["vol_frac"], out["mu_s"],
+                                       out["mu_a"], out["g"], q["q_ext"], q["q_sca"],
+                                       q["g_species"], flags=flags)
+    else:
+        name = "fos_mie_properties"
+        st = fos.fos_mie_properties(d["wl"], d["nm_re"], d["nm_im"], d["species_group"],
+                                    d["np_re"], d["np_im"], d["radius"], d["vol_frac"],
+                                    out["mu_s"], out["mu_a"], out["g"], q["q_ext"], q["q_sca"],
+                                    q["g_species"], flags=flags)
     torch.cuda.synchronize()
-    fos.check(st, "fos_mie_properties", allow)
+    fos.check(st, name, allow)
     res = {k: v.cpu().numpy().reshape(n_groups, n_wl) for k, v in out.items()}
     res.update({k: v.cpu().numpy()[: n_species * n_wl].reshape(n_species, n_wl)
                 for k, v in q.items()})

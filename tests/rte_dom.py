@@ -5,7 +5,8 @@ An independent pin for the Monte Carlo walk: the azimuthally averaged RTE
     mu dI/dtau = -I + (omega/2) int_{-1}^{1} p0(mu, mu') I(mu') dmu' + Q(tau, mu)
 
 for a homogeneous slab of optical thickness tau_d, single-scattering albedo omega and
-a Henyey-Greenstein phase function, lit by a collimated beam at normal incidence.
+a Henyey-Greenstein phase function, lit by a collimated beam (normal or oblique
+incidence; the azimuthally averaged equation carries the fluxes either way).
 The discrete-ordinates method (Chandrasekhar; Stamnes et al. 1988) replaces the
 integral by Gauss-Legendre quadrature, solves the homogeneous system by eigen-
 decomposition (exponentials scaled so that none overflows) and the collimated
@@ -43,6 +44,19 @@ def fresnel_angle_form(n_i: float, n_t: float, mu_i: np.ndarray) -> np.ndarray:
     return out
 
 
+def fresnel_complex_angle_form(n_i: float, n_t: complex, mu_i: np.ndarray) -> np.ndarray:
+    """Reflectance into an absorbing medium n_t = n + ik: Snell's law with complex
+    angles and the sine/tangent forms (normal incidence: |(n_i - n_t)/(n_i + n_t)|^2)."""
+    mu_i = np.asarray(mu_i, dtype=np.float64)
+    ti = np.arccos(np.clip(mu_i, -1.0, 1.0))
+    tt = np.arcsin(n_i * np.sin(ti) / n_t + 0j)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rs = np.abs(np.sin(ti - tt) / np.sin(ti + tt)) ** 2
+        rp = np.abs(np.tan(ti - tt) / np.tan(ti + tt)) ** 2
+    rn = abs((n_i - n_t) / (n_i + n_t)) ** 2
+    return np.where(ti < 1e-7, rn, 0.5 * (rs + rp))
+
+
 def _hg(g: float, c: np.ndarray) -> np.ndarray:
     return (1.0 - g * g) / (1.0 + g * g - 2.0 * g * c) ** 1.5
 
@@ -66,11 +80,23 @@ def _nodes(n_in: float, n_out_top: float, n_out_bot: float, n_half: int):
 
 def slab_rat(mu_s: float, mu_a: float, g: float, d: float, n_in: float,
              n_above: float = 1.0, n_below: float = 1.0, n_half: int = 48,
-             n_phi: int = 720):
+             n_phi: int = 720, mu0: float = 1.0, k_below: float = 0.0):
+    """(R, A, T) for a beam at incidence cosine mu0 from above (refracted to mu_in in
+    the slab); k_below > 0 makes the medium below absorbing (n_below + i k_below),
+    whose entering flux counts as T."""
     mu_t = mu_s + mu_a
     tau_d = mu_t * d
     omega = mu_s / mu_t if mu_t > 0 else 0.0
-    mu, w = _nodes(n_in, n_above, n_below, n_half)
+    conductor = k_below > 0.0
+    mu, w = _nodes(n_in, n_above, n_in if conductor else n_below, n_half)
+    if conductor:
+        rbot = lambda m: fresnel_complex_angle_form(n_in, complex(n_below, k_below), m)
+    else:
+        rbot = lambda m: fresnel_angle_form(n_in, n_below, m)
+    st_in = n_above / n_in * np.sqrt(max(0.0, 1.0 - mu0 * mu0))
+    if st_in >= 1.0:
+        return 1.0, 0.0, 0.0
+    mu_in = float(np.sqrt(1.0 - st_in * st_in))
     N = mu.size
     # Azimuthally averaged phase function on the grid (periodic trapezoid in phi).
     phi = (np.arange(n_phi) + 0.5) * (2.0 * np.pi / n_phi)
@@ -85,20 +111,24 @@ def slab_rat(mu_s: float, mu_a: float, g: float, d: float, n_in: float,
     p0 *= 2.0 / (p0 @ wt)[:, None]
     # dI/dtau = M I + source
     M = (-np.eye(2 * N) + 0.5 * omega * p0 * wt[None, :]) / sgn_mu[:, None]
-    # Unscattered beam with all its specular bounces (normal incidence).
-    r_top_in = fresnel_angle_form(n_above, n_in, np.array([1.0]))[0]
-    r_t = fresnel_angle_form(n_in, n_above, np.array([1.0]))[0]
-    r_b = fresnel_angle_form(n_in, n_below, np.array([1.0]))[0]
+    # Unscattered beam with all its specular bounces, at mu_in inside the slab; D, U are
+    # its downward and upward fluxes through horizontal planes.
+    r_top_in = fresnel_angle_form(n_above, n_in, np.array([mu0]))[0]
+    r_t = fresnel_angle_form(n_in, n_above, np.array([mu_in]))[0]
+    r_b = rbot(np.array([mu_in]))[0]
     F0 = 1.0 - r_top_in
-    e_d = np.exp(-tau_d)
-    D0 = F0 / (1.0 - r_t * r_b * e_d * e_d)       # D(tau) = D0 e^{-tau}
-    U0 = r_b * D0 * e_d                           # U(tau) = U0 e^{-(tau_d - tau)}
-    # Source (omega/4pi)[D p(mu . +1) + U p(mu . -1)] = s1 e^{-tau} + s2 e^{tau - tau_d}
-    s1 = omega / (4 * np.pi) * D0 * _hg(g, sgn_mu) / sgn_mu
-    s2 = omega / (4 * np.pi) * U0 * _hg(g, -sgn_mu) / sgn_mu
+    e_d = np.exp(-tau_d / mu_in)
+    D0 = F0 / (1.0 - r_t * r_b * e_d * e_d)       # D(tau) = D0 e^{-tau/mu_in}
+    U0 = r_b * D0 * e_d                           # U(tau) = U0 e^{-(tau_d - tau)/mu_in}
+    # Beam source (omega/4pi)(flux/mu_in) p0(mu, +-mu_in), p0 the azimuthal mean of HG
+    s_in = np.sqrt(max(0.0, 1.0 - mu_in * mu_in))
+    p_dn = _hg(g, sgn_mu[:, None] * mu_in + s[:, None] * s_in * cphi[None, :]).mean(axis=1)
+    p_up = _hg(g, -sgn_mu[:, None] * mu_in + s[:, None] * s_in * cphi[None, :]).mean(axis=1)
+    s1 = omega / (4 * np.pi) * D0 / mu_in * p_dn / sgn_mu
+    s2 = omega / (4 * np.pi) * U0 / mu_in * p_up / sgn_mu
     I2 = np.eye(2 * N)
-    c1 = np.linalg.solve(-(I2 + M), s1)           # particular part of e^{-tau}
-    c2 = np.linalg.solve(I2 - M, s2)              # particular part of e^{tau - tau_d}
+    c1 = np.linalg.solve(-(I2 / mu_in + M), s1)   # particular part of e^{-tau/mu_in}
+    c2 = np.linalg.solve(I2 / mu_in - M, s2)      # particular part of e^{(tau - tau_d)/mu_in}
     lam, V = np.linalg.eig(M)
     neg = lam.real < 0
 
@@ -108,7 +138,7 @@ def slab_rat(mu_s: float, mu_a: float, g: float, d: float, n_in: float,
         return V * ex[None, :]
 
     Rf_top = fresnel_angle_form(n_in, n_above, mu)
-    Rf_bot = fresnel_angle_form(n_in, n_below, mu)
+    Rf_bot = rbot(mu)
     H0, Hd = homog(0.0), homog(tau_d)
     P0 = c1 + c2 * e_d
     Pd = c1 * e_d + c2

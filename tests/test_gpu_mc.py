@@ -262,3 +262,17 @@ def test_host_wait_is_bounded():
     assert fos.fos_sync_status(None, 1) == fos.FOS_ERR_TIMEOUT
     assert fos.fos_sync_status(None, 600000) == fos.FOS_OK
     assert int(counts[0, :4].sum()) == 20000000
+
+
+def test_batch_keeps_temporary_tensors_alive(orc):
+    """make_batch holds its tensors: a batch built from temporaries still reads them after
+    the caching allocator has handed out new blocks of the same size."""
+    ref = W.single_slab(n_photons=3000)
+    t = lambda v: torch.as_tensor(np.asarray(v, np.float64), device="cuda")
+    b = fos.make_batch(1, 1, 1, t(ref["mu_s"]), t(ref["mu_a"]), t(ref["g"]), t(ref["n_layer"]),
+                       t(ref["thickness"]), photons_per_item=3000, seed=ref["seed"])
+    junk = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in range(16)]
+    counts = torch.zeros((1, fos.FOS_NCOUNT), dtype=torch.int64, device="cuda")
+    fos.check(fos.fos_mc_spectrum(b, counts), "temporaries")
+    assert np.array_equal(counts.cpu().numpy(), orc.mc_run(ref, fp32=True))
+    del junk
