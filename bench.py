@@ -197,11 +197,13 @@ def run_fos(args):
                 sg=torch.as_tensor(m["species_group"], dtype=torch.int32),
                 radius=torch.as_tensor(m["radius"], dtype=f64),
                 vol_frac=torch.as_tensor(m["vol_frac"], dtype=f64),
-                thickness=torch.as_tensor(m["thickness"], dtype=f64))
+                thickness=torch.as_tensor(m["thickness"], dtype=f64),
+                G=torch.as_tensor(W.solar_like_irradiance(m["wl"]), dtype=f64))
     d = {k: v.to(dev) for k, v in host.items()}
     n_wl = m["n_wl"]
     mu_s, mu_a, g = (torch.zeros(n_wl, dtype=f64, device=dev) for _ in range(3))
     counts = torch.zeros((n_wl, fos.FOS_NCOUNT), dtype=i64, device=dev)
+    solar = torch.zeros(3, dtype=f64, device=dev)   # Eq. 21 R_s, A_s, T_s
     stream = torch.cuda.current_stream()
     l2 = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -218,6 +220,8 @@ def run_fos(args):
         fos.check(fos.fos_mc_spectrum(b, counts, None, 0, flags), "fos_mc_spectrum")
         if ev is not None:
             ev[1].record(stream)
+        fos.check(fos.fos_solar_weighted(1, src["wl"], src["G"], counts, solar,
+                                         flags=flags & fos.FOS_ASYNC), "fos_solar_weighted")
         return b
 
     # first call tunes the launch shape for this batch (synchronous, untimed)
@@ -273,9 +277,10 @@ def run_fos(args):
     if not args.no_e2e:
         pinned = {k: v.pin_memory() for k, v in host.items()}
         counts_h = torch.empty((n_wl, fos.FOS_NCOUNT), dtype=i64).pin_memory()
+        solar_h = torch.empty(3, dtype=f64).pin_memory()
         dd = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
         h2d = sum(v.numel() * v.element_size() for v in pinned.values())
-        d2h = counts_h.numel() * counts_h.element_size()
+        d2h = counts_h.numel() * counts_h.element_size() + solar_h.numel() * 8
         Ke = max(1, min(K, 3))
         coll_e = 0
         if world > 1:
@@ -287,6 +292,7 @@ def run_fos(args):
                 dd[kk].copy_(v, non_blocking=True)
             step(3000 + k, flags=0, src=dd)
             counts_h.copy_(counts, non_blocking=True)
+            solar_h.copy_(solar, non_blocking=True)
             torch.cuda.synchronize()
             coll_e += int(counts_h[:, 4].sum())
         dt = time.perf_counter() - t0
@@ -331,10 +337,16 @@ def run_fos(args):
             surr = run_surrogate(args.surrogate)
         except Exception as exc:  # the surrogate leg must not hide the MC number
             surr = dict(error=str(exc))
+    t1 = None
+    if args.surrogate != "off" and world == 1:
+        try:
+            t1 = run_table1(args.surrogate)
+        except Exception as exc:
+            t1 = dict(error=str(exc))
     stacks = None
     if args.stacks and world == 1:
         stacks = run_stacks()
-    dists = cs = None
+    dists = cs = bnd = None
     if world == 1:
         try:
             dists = run_distributions()
@@ -344,6 +356,10 @@ def run_fos(args):
             cs = run_core_shell()
         except Exception as exc:
             cs = dict(error=str(exc))
+        try:
+            bnd = run_boundaries()
+        except Exception as exc:
+            bnd = dict(error=str(exc))
     cpu = None
     if not args.no_cpu and world == 1:
         try:
@@ -362,9 +378,11 @@ def run_fos(args):
         photon_steps_per_photon=coll / max(photons, 1),
         e2e=e2e, roofline=roof, cpu_baseline=cpu, clocks=clocks, surrogate=surr,
         layer_stacks=stacks, size_distributions=dists, core_shell=cs,
-        gpu_launches=5 * K,
+        oblique_conductor=bnd, table1_network=t1,
+        solar_weighted=dict(zip(("R_s", "A_s", "T_s"), solar.cpu().tolist())),
+        gpu_launches=6 * K,
         gpu_launches_detail="per step: mie_kernel, emt_kernel, pack_kernel, unit_scan_kernel, "
-                            "walk_kernel",
+                            "walk_kernel, solar_kernel",
     )
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -400,6 +418,21 @@ def run_surrogate(mode: str):
                       data_seconds=t1 - t0, train_seconds=t2 - t1, members=4,
                       steps_per_member=cfg["steps"], batch=8192,
                       final_loss=[h[-1][1] for h in hist.values()])
+    r["mode"] = mode
+    return r
+
+
+def run_table1(mode: str):
+    """The network with the paper's inputs (Table 1): random slabs given by optical
+    properties (n 1-7, mu_s, mu_a log-uniform, g 0-0.99, d 5-500 um, scattering optical
+    depth <= 100), Monte Carlo labels, a 4-member ensemble, held-out slabs against Monte
+    Carlo at 1e5 photons."""
+    from paper_2409_00165_gb300 import surrogate as S
+    cfg = dict(full=dict(train_rows=1000000, train_photons=20000, steps=8000, test_rows=30000),
+               quick=dict(train_rows=200000, train_photons=10000, steps=2000,
+                          test_rows=10000))[mode]
+    r = S.table1_experiment(cfg["train_rows"], cfg["train_photons"], cfg["steps"],
+                            cfg["test_rows"], 100000, members=4, seed=40)
     r["mode"] = mode
     return r
 
@@ -472,9 +505,12 @@ def _mie_mc_leg(m, photons: int, seed: int):
                                                 d["np_im"], rad, vf, mu_s, mu_a, g, flags=fl)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     fos.check(mie(0), "mie warm-up")
+    extra = {k: t(m[k]) for k in ("cos_incidence", "n_below", "k_below") if k in m}
     b = fos.make_batch(m["n_stacks"], m["n_wl"], 1, mu_s, mu_a, g, d["nm_re"], t(m["thickness"]),
-                       photons_per_item=photons, seed=seed)
+                       photons_per_item=photons, seed=seed, **extra)
     counts = torch.zeros((n, fos.FOS_NCOUNT), dtype=torch.int64, device=dev)
+    solar = torch.zeros((m["n_stacks"], 3), dtype=f64, device=dev)
+    G = t(W.solar_like_irradiance(m["wl"]))
     fos.check(fos.fos_mc_spectrum(b, counts, None, 0, fos.FOS_AUTOTUNE), "mc warm-up")
     torch.cuda.synchronize()
     ev[0].record()
@@ -482,8 +518,10 @@ def _mie_mc_leg(m, photons: int, seed: int):
     ev[1].record()
     fos.check(fos.fos_mc_spectrum(b, counts, None, 0, fos.FOS_ASYNC), "mc")
     ev[2].record()
+    fos.check(fos.fos_solar_weighted(m["n_stacks"], wl, G, counts, solar, fos.FOS_ASYNC),
+              "solar")
     torch.cuda.synchronize()
-    fos.check(fos.fos_sync_status(), "mie + mc")
+    fos.check(fos.fos_sync_status(), "mie + mc + solar")
     t_mie, t_mc = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
     c = counts.sum(dim=0).cpu().numpy()
     evals = len(m["radius"]) * m["n_wl"]
@@ -493,7 +531,9 @@ def _mie_mc_leg(m, photons: int, seed: int):
                 mie_evals_per_s=evals / t_mie, mc_seconds=t_mc, photons=int(c[:4].sum()),
                 photon_steps=int(c[4]), photon_steps_per_s=float(c[4]) / t_mc,
                 spectra_per_s=m["n_stacks"] / (t_mie + t_mc),
-                mean_reflectance=[float(x) for x in refl.mean(axis=1)])
+                mean_reflectance=[float(x) for x in refl.mean(axis=1)],
+                solar_weighted_RAT=[[round(float(v), 6) for v in row]
+                                    for row in solar.cpu().numpy()])
 
 
 def run_distributions():
@@ -517,6 +557,16 @@ def run_core_shell():
     r = _mie_mc_leg(W.hollow_silica_media(), 1000000, 11)
     r["outer_diameters_um"] = [0.7, 0.9, 1.1]
     r["stacks"] = "3 hollow then 3 solid"
+    return r
+
+
+def run_boundaries():
+    """Oblique incidence on a conductor: the paint-layer medium, 50 um thick, on an
+    aluminium-like Drude metal, lit at 0, 30 and 60 degrees, 400 wavelengths, 1e6
+    photons per wavelength; Eq. 21 totals under a 5778 K blackbody spectrum."""
+    from paper_2409_00165_gb300 import workloads as W
+    r = _mie_mc_leg(W.oblique_conductor_media(), 1000000, 13)
+    r["incidence_deg"] = [0, 30, 60]
     return r
 
 

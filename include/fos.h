@@ -156,24 +156,29 @@ fos_status fos_size_distribution(double diameter, double sigma, double vol_frac,
  *
  * An item is one (stack, wavelength) pair, item = stack * n_wl + w.  A stack is
  * 1..max_layers homogeneous layers (layer 0 on top) between a medium above and a
- * medium below (refractive index; default air n = 1) or an opaque specular
- * reflector below.  Photons arrive at normal incidence on the top surface.  Only
- * the depth z and the direction cosine mu_z are tracked.  Each photon:
+ * medium below (refractive index; default air n = 1), a conductor below (complex
+ * index n + ik, k > 0) or an opaque specular reflector below.  Photons arrive at the
+ * top surface at incidence cosine cos_incidence (default 1, normal).  Only the depth z
+ * and the direction cosine mu_z are tracked.  Each photon:
  *   1. meets the top surface: reflected with the unpolarised Fresnel reflectance
- *      (drawn) -> R; otherwise enters layer 0 with mu_z = 1;
+ *      (drawn; always under total internal reflection) -> R; otherwise enters layer 0
+ *      with mu_z = the refraction cosine (1 at normal incidence);
  *   2. flies an optical depth tau = -ln u; inside layer j it collides after tau /
  *      mu_t; a boundary reached first is crossed with the rest of tau carried on;
  *   3. at a collision is absorbed with probability mu_a/mu_t -> A, else is deflected
  *      by a Henyey-Greenstein angle (g) and a uniform azimuth;
  *   4. at a boundary between different indices is reflected (total internal
  *      reflection, or Fresnel draw) or refracted (Snell); leaving the top -> R,
- *      leaving the bottom or absorbed by the reflector -> T;
+ *      leaving the bottom -> T; at a reflector or a conductor below it is reflected
+ *      with R_sub or with the conductor's unpolarised Fresnel reflectance at mu_z
+ *      (drawn), and otherwise enters the substrate -> T;
  *   5. after max_events collisions + boundary arrivals is stopped -> runaway.
  * The walk is FP32 with a fixed operation order; random numbers come from
  * Philox4x32-10 with key = seed and counter = (photon id, item id, event, stream):
  * collision e uses the 4 words of counter (p, item, e, 0) (free path, absorption,
- * deflection, azimuth; word 3 of block 0 is the entry Fresnel test, since the first
- * collision has mu_z = +-1 and needs no azimuth), boundary draw k uses word k mod 4 of
+ * deflection, azimuth; at normal incidence word 3 of block 0 is the entry Fresnel test,
+ * since the first collision has mu_z = +-1 and needs no azimuth; at oblique incidence the
+ * entry test is word 0 of counter (p, item, 0, 2)), boundary draw k uses word k mod 4 of
  * counter (p, item, k/4, 1).  Results depend only on (seed, item id, photon id), not
  * on launch shape, and agree bit for bit with any implementation of the same
  * operation order.
@@ -205,6 +210,11 @@ typedef struct fos_mc_batch {
     unsigned long long seed;      /* Philox key                                       */
     unsigned int item_id_base;    /* added to the item index in the Philox counter    */
     long long max_events;         /* per-photon cap, 1..2^32-1; 0 -> 100000000        */
+    const double* cos_incidence;  /* device [n_items] in (0, 1]: cosine of the incidence
+                                     angle in the medium above, or NULL (= 1)         */
+    const double* k_below;        /* device [n_items] >= 0: imaginary index below
+                                     (k > 0: conductor n_below + i k), or NULL (= 0);
+                                     k > 0 with substrate_R is FOS_ERR_INVALID_ARG     */
 } fos_mc_batch;
 
 /* counts: device int64 [n_run * FOS_NCOUNT], n_run = n_list (item_list given) or
@@ -217,6 +227,21 @@ typedef struct fos_mc_batch {
  * FOS_ERR_INVALID_ARG, FOS_ERR_CUDA, FOS_ERR_NOMEM, FOS_ERR_TIMEOUT, FOS_ERR_INJECTED. */
 fos_status fos_mc_spectrum(const fos_mc_batch* batch, long long* counts, int* photon_log,
                            long long log_stride, unsigned flags, void* stream);
+
+/* fos_solar_weighted: solar-weighted totals (section "Output", Eq. 21).  For each stack
+ * s and each of R, A, T: the integral over the wavelength grid of the spectral fraction
+ * times G, divided by the integral of G, both by the trapezoidal rule on the grid
+ * points.  The spectral fraction is count / (R + A + T) of item s*n_wl + w (0 where that
+ * sum is 0); with n_wl = 1 the totals are the fractions there.
+ *   wl      device double [n_wl], strictly increasing
+ *   G       device double [n_wl], >= 0, with a positive integral (spectral irradiance)
+ *   counts  device int64 [n_stacks*n_wl*FOS_NCOUNT], the fos_mc_spectrum output
+ *   out     device double [n_stacks*3] (R_s, A_s, T_s per stack)
+ * Errors: FOS_ERR_INVALID_ARG (sizes, NULL, unordered wl, bad G), FOS_ERR_CUDA.
+ * Synchronous unless FOS_ASYNC. */
+fos_status fos_solar_weighted(int n_stacks, int n_wl, const double* wl, const double* G,
+                              const long long* counts, double* out, unsigned flags,
+                              void* stream);
 
 /* Launch shape of the walk kernel: threads per block (multiple of 32, 64..1024) and
  * photons per thread per work unit (a warp claims 32*ppt photons at a time).
@@ -271,6 +296,14 @@ fos_status fos_surrogate_param_offsets(long long* w_off, long long* b_off);   /*
 fos_status fos_surrogate_init(void* model, int n_members, unsigned long long seed,
                               const float* feat_stats, void* stream);
 
+/* Loads member `member` of a model buffer from caller parameters: theta is a device
+ * float[fos_surrogate_param_count()] in the padded layout above (entries outside the real
+ * rows and columns are ignored and stored as 0), e.g. weights trained elsewhere or saved
+ * from the theta region of another model.  Adam state and the step count are reset, the
+ * BF16 copies rebuilt; feat_stats as for fos_surrogate_init.  Synchronous. */
+fos_status fos_surrogate_load(void* model, int member, const float* theta,
+                              const float* feat_stats, void* stream);
+
 /* Raw features of the n_designs x n_wl rows (row = design * n_wl + w) of single-layer
  * designs: wl [n_wl]; np_re, np_im, g, mu_s, mu_a [n_designs*n_wl] (the layout of
  * fos_mie_properties outputs with one group per design); radius, vol_frac, thickness
@@ -281,6 +314,19 @@ fos_status fos_surrogate_features(int n_designs, int n_wl, const double* wl,
                                   const double* thickness, const double* g,
                                   const double* mu_s, const double* mu_a, float* features,
                                   unsigned flags, void* stream);
+
+/* Raw features of homogeneous slabs given by their optical properties, the inputs of
+ * the paper's network (section "Photon transport", Table 1: matrix index, mu_s, mu_a, g,
+ * thickness), one row per slab: [n, log10(mu_s + 1e-4), log10(mu_a + 1e-4), g, log10 d,
+ * log10(mu_s d + 1e-6), log10(mu_a d + 1e-6), 0, 0] with mu in 1/um and d in um (1e-4
+ * per um = 1 per cm).  Each input maps monotonically to one feature, so the range gate of
+ * fos_surrogate_predict (feature lo/hi) can hold exactly the ranges of Table 1.
+ * n_layer, mu_s, mu_a, g, thickness: device double [n_rows]; features: device float
+ * [n_rows*9].  Non-positive d or n, negative mu, non-finite values: FOS_ERR_INVALID_ARG. */
+fos_status fos_surrogate_features_slab(long long n_rows, const double* n_layer,
+                                       const double* mu_s, const double* mu_a, const double* g,
+                                       const double* thickness, float* features,
+                                       unsigned flags, void* stream);
 
 /* Statistics of raw feature rows [n_rows*9] (device float) into stats (device float[64]
  * = mean[16] | std[16] | lo[16] | hi[16], first 9 of each used; std floored at 1e-3;

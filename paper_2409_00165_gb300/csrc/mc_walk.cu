@@ -145,6 +145,35 @@ __device__ __forceinline__ float fresnel(float ni, float nt, float ci, float& ct
     return (rs * rs + rp * rp) * 0.5f;
 }
 
+// Unpolarised Fresnel reflectance from real index ni into a conductor n2 + i k2 (k2 > 0)
+// at incidence cosine ci.  w = (n2 + i k2)^2 - ni^2 (1 - ci^2), u + i v = sqrt(w) with
+// Re >= 0 (the larger of u, v from the modulus, the other by division, so that neither
+// cancels); r_s = (ni ci - sqrt w)/(ni ci + sqrt w), r_p = ((n2+ik2)^2 ci - ni sqrt w) /
+// ((n2+ik2)^2 ci + ni sqrt w).
+__device__ __noinline__ float fresnel_conductor(float ni, float n2, float k2, float ci) {
+    const float s2 = fmaf(-ci, ci, 1.0f);
+    const float e_re = n2 * n2 - k2 * k2;
+    const float e_im = (n2 + n2) * k2;
+    const float w_re = e_re - (ni * ni) * s2;
+    const float w_im = e_im;
+    const float mod = sqrtf(w_re * w_re + w_im * w_im);
+    float u, v;
+    if (w_re >= 0.0f) {
+        u = sqrtf((mod + w_re) * 0.5f);
+        v = w_im / (u + u);
+    } else {
+        v = sqrtf((mod - w_re) * 0.5f);
+        u = w_im / (v + v);
+    }
+    const float a = ni * ci;
+    const float rs_n = (a - u) * (a - u) + v * v;
+    const float rs_d = (a + u) * (a + u) + v * v;
+    const float c1 = e_re * ci, c2 = e_im * ci, q1 = ni * u, q2 = ni * v;
+    const float rp_n = (c1 - q1) * (c1 - q1) + (c2 - q2) * (c2 - q2);
+    const float rp_d = (c1 + q1) * (c1 + q1) + (c2 + q2) * (c2 + q2);
+    return (rs_n / rs_d + rp_n / rp_d) * 0.5f;
+}
+
 // Henyey-Greenstein deflection cosine by inversion of its distribution function.
 // {1-g^2, 1+g^2, 1-g, 1/(2g)} are precomputed per layer by pack_kernel.
 __device__ __forceinline__ float hg_cos(float g, float omg2, float opg2, float omg,
@@ -167,8 +196,10 @@ __device__ __forceinline__ float hg_cos(float g, float omg2, float opg2, float o
 // Packed per-row tables (row = position in the run list).
 // ---------------------------------------------------------------------------------
 struct Tables {
-    int4* head;       // {n_layers, n_above bits, n_below bits, substrate R bits (<0: none)}
+    int4* head;       // {n_layers, n_above bits, n_below bits, substrate R bits: >= 0
+                      //  reflector, -1 none, -2 conductor}
     int4* info;       // {rng item id, first photon id, photon count, entry reflectance bits}
+    float4* edge;     // {entry mu_z (refraction cosine), cos incidence, k below, 0}
     float4* layA;     // [row*max_layers + j] {mu_t, mu_a/mu_t, g, n}
     float4* layB;     // [row*max_layers + j] {d, 1-g^2, 1+g^2, 1-g}
     float4* layC;     // [row*max_layers + j] {1/mu_t, 1/(2g), 0, 0}
@@ -178,9 +209,10 @@ struct Tables {
 static size_t tables_bytes(long long n_run, int max_layers) {
     size_t b = 0;
     b += (size_t)n_run * sizeof(int4) * 2;
+    b += (size_t)n_run * sizeof(float4);
     b += (size_t)n_run * max_layers * sizeof(float4) * 3;
     b += (size_t)(n_run + 1) * sizeof(long long);
-    return b + 7 * 256;   // each of the 6 regions is rounded up to 256 bytes
+    return b + 8 * 256;   // each of the 7 regions is rounded up to 256 bytes
 }
 
 static Tables carve(void* base, long long n_run, int max_layers) {
@@ -193,6 +225,7 @@ static Tables carve(void* base, long long n_run, int max_layers) {
     };
     t.head = (int4*)take((size_t)n_run * sizeof(int4));
     t.info = (int4*)take((size_t)n_run * sizeof(int4));
+    t.edge = (float4*)take((size_t)n_run * sizeof(float4));
     t.layA = (float4*)take((size_t)n_run * max_layers * sizeof(float4));
     t.layB = (float4*)take((size_t)n_run * max_layers * sizeof(float4));
     t.layC = (float4*)take((size_t)n_run * max_layers * sizeof(float4));
@@ -268,6 +301,13 @@ __global__ void pack_kernel(PackArgs A) {
         if (!(v >= 0.0 && v <= 1.0)) ok = false;
         rsub = (float)v;
     }
+    const double cin = b.cos_incidence ? b.cos_incidence[it] : 1.0;
+    const double kb = b.k_below ? b.k_below[it] : 0.0;
+    if (!(cin > 0.0 && cin <= 1.0) || !(kb >= 0.0 && isfinite(kb))) ok = false;
+    if (kb > 0.0 && b.substrate_R) ok = false;
+    const float cin_f = (float)cin, kb_f = (float)kb;
+    if (!(cin_f > 0.0f)) ok = false;
+    if (kb_f > 0.0f && !b.substrate_R) rsub = -2.0f;
     const long long N = b.n_photons ? b.n_photons[it] : b.photons_per_item;
     const long long first = b.photon_first ? b.photon_first[it] : 0;
     if (N < 0 || first < 0 || first + N > 4294967296LL) ok = false;
@@ -275,15 +315,17 @@ __global__ void pack_kernel(PackArgs A) {
     if (!ok) flag_invalid(A.status, r);
     A.t.head[r] = make_int4(nl, __float_as_int((float)na), __float_as_int((float)nb),
                             __float_as_int(rsub));
-    float r_entry = 0.0f;
+    float r_entry = 0.0f, mu_in = cin_f;
     {
         const float na_f = (float)na, n0 = A.t.layA[(long long)r * b.max_layers].w;
         if (na_f != n0) {
             float ct;
             bool tir;
-            r_entry = fresnel(na_f, n0, 1.0f, ct, tir);
+            r_entry = fresnel(na_f, n0, cin_f, ct, tir);   // 1 under total reflection
+            if (!tir) mu_in = ct;
         }
     }
+    A.t.edge[r] = make_float4(mu_in, cin_f, kb_f, 0.0f);
     A.t.info[r] = make_int4((int)(b.item_id_base + (unsigned)it), (int)(unsigned)first,
                             ok ? (int)(unsigned)N : 0, __float_as_int(r_entry));
 }
@@ -484,11 +526,15 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
                 kif = 0u;
                 ev = 0u;
                 const uint4 blk0 = philox_rk(make_uint4(p, item_rng, 0u, 0u), A.rk);
-                if (uni(blk0.w) < __int_as_float(inf.w)) {
+                const float2 ed = *reinterpret_cast<const float2*>(&A.t.edge[row]);
+                unsigned w_entry = blk0.w;   // normal incidence: azimuth word of block 0
+                if (ed.y != 1.0f && __int_as_float(inf.w) > 0.0f)   // oblique
+                    w_entry = philox_rk(make_uint4(p, item_rng, 0u, 2u), A.rk).x;
+                if (uni(w_entry) < __int_as_float(inf.w)) {
                     finish(O_R);
                 } else {
                     z = 0.0f;
-                    mu = 1.0f;
+                    mu = ed.x;
                     tau = neg_log_u(uni(blk0.x));
                     u1 = uni(blk0.y);
                     u2 = uni(blk0.z);
@@ -548,10 +594,13 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
                 cI++;
                 const int nb = down ? j + 1 : j - 1;
                 const bool outside = (nb < 0) || (nb >= nl);
-                if (down && outside && r_sub >= 0.0f) {
+                if (down && outside && r_sub != -1.0f) {
+                    // opaque below: reflector (R_sub) or conductor (Fresnel with n + ik)
+                    const float Rb = (r_sub >= 0.0f)
+                        ? r_sub : fresnel_conductor(l_n, n_below, A.t.edge[row].z, am);
                     const float u = uni(word(blk, kif & 3u));
                     kif++;
-                    if (u < r_sub) mu = -mu;
+                    if (u < Rb) mu = -mu;
                     else finish(O_T);
                     continue;
                 }
@@ -994,8 +1043,9 @@ constexpr long long NOALLOC_ROWS = FOS_NOALLOC_MAX_ITEMS;
 constexpr size_t NOALLOC_HDR = 512;   // status words at 0, work-queue counter at 256
 constexpr size_t NOALLOC_BYTES =
     NOALLOC_HDR + (size_t)NOALLOC_ROWS * sizeof(int4) * 2 +
+    (size_t)NOALLOC_ROWS * sizeof(float4) +
     (size_t)NOALLOC_ROWS * FOS_MAX_LAYERS * sizeof(float4) * 3 +
-    (size_t)(NOALLOC_ROWS + 1) * sizeof(long long) + 7 * 256;
+    (size_t)(NOALLOC_ROWS + 1) * sizeof(long long) + 8 * 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 

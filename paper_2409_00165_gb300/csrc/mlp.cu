@@ -384,6 +384,33 @@ __global__ void features_kernel(int n_designs, int n_wl, const double* wl, const
     }
 }
 
+// Features of a homogeneous slab given by its optical properties (the inputs of the
+// paper's network, Table 1: matrix index, mu_s, mu_a, g, thickness):
+// [n, log10(mu_s + 1e-4), log10(mu_a + 1e-4), g, log10 d, log10(mu_s d + 1e-6),
+//  log10(mu_a d + 1e-6), 0, 0].  Each raw input maps monotonically to one feature, so a
+// box in feature space is the box of Table 1; the two optical depths help the fit.
+__global__ void features_slab_kernel(long long n, const double* nl, const double* mu_s,
+                                     const double* mu_a, const double* g, const double* d,
+                                     float* out, unsigned* status) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double t = d[i], ms = mu_s[i], ma = mu_a[i];
+        float* o = out + i * N_FEAT;
+        o[0] = (float)nl[i];
+        o[1] = (float)log10(ms + 1e-4);
+        o[2] = (float)log10(ma + 1e-4);
+        o[3] = (float)g[i];
+        o[4] = (float)log10(t);
+        o[5] = (float)log10(ms * t + 1e-6);
+        o[6] = (float)log10(ma * t + 1e-6);
+        o[7] = 0.0f;
+        o[8] = 0.0f;
+        if (!(t > 0.0) || !(ms >= 0.0) || !(ma >= 0.0) || !isfinite(ms * t) ||
+            !isfinite(ma * t) || !(nl[i] > 0.0) || !isfinite(g[i]))
+            atomicOr(&status[ST_CALL], DEV_INVALID);
+    }
+}
+
 __global__ void fractions_kernel(const long long* counts, long long n, const int* rows,
                                  float* out) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -569,6 +596,38 @@ __global__ void init_kernel(float* theta, float* m, float* v, bf16* wb, bf16* wt
                 const float lim = sqrtf(6.0f / (float)real_in(l));
                 th = (2.f * u - 1.f) * lim;
             }
+        }
+        theta[idx] = th;
+        m[idx] = 0.f;
+        v[idx] = 0.f;
+        if (e >= 0) {
+            wb[lay.wb_off[l] + e] = __float2bfloat16(th);
+            if (l > 0) wt[lay.wt_off[l] + (long long)i * out_p + o] = __float2bfloat16(th);
+        }
+        if (idx == 0) step[0] = 0;
+    }
+}
+
+// Parameters given by the caller (device theta in the padded layout): entries outside
+// the real rows and columns are stored as 0; Adam state and step are reset and the bf16
+// copies rebuilt.
+__global__ void load_kernel(const float* src, float* theta, float* m, float* v, bf16* wb,
+                            bf16* wt, int* step, AdamArgs lay, long long P) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int l = 0;
+        while (l + 1 < N_LAYERS && idx >= lay.w_off[l + 1]) ++l;
+        const int in_p = lay_in(l), out_p = lay_out(l);
+        float th = 0.f;
+        long long e = -1;
+        int o = 0, i = 0;
+        if (idx < lay.b_off[l]) {
+            e = idx - lay.w_off[l];
+            o = (int)(e / in_p);
+            i = (int)(e % in_p);
+            if (o < real_out(l) && i < real_in(l)) th = src[idx];
+        } else if ((int)(idx - lay.b_off[l]) < real_out(l)) {
+            th = src[idx];
         }
         theta[idx] = th;
         m[idx] = 0.f;
@@ -1027,6 +1086,29 @@ fos_status fos_surrogate_init(void* model, int n_members, unsigned long long see
     return FOS_OK;
 }
 
+fos_status fos_surrogate_load(void* model, int member, const float* theta,
+                              const float* feat_stats, void* stream) {
+    if (!model || member < 0 || !theta || !feat_stats) return FOS_ERR_INVALID_ARG;
+    for (int f = 0; f < mlp::N_FEAT; ++f)
+        if (!(feat_stats[16 + f] > 0.f) || !(feat_stats[32 + f] <= feat_stats[48 + f]))
+            return FOS_ERR_INVALID_ARG;
+    Workspace* ws = nullptr;
+    fos_status st = mlp::prep(&ws);
+    if (st != FOS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    mlp::MemberPtrs mp = mlp::member(model, member);
+    mlp::AdamArgs lay = mlp::layout_args(mp);
+    FOS_CUDA_TRY(cudaMemsetAsync((char*)model + (size_t)member * mlp::LAY.bytes, 0,
+                                 mlp::LAY.bytes, s));
+    mlp::load_kernel<<<(unsigned)((mlp::LAY.P + 255) / 256), 256, 0, s>>>(
+        theta, mp.theta, mp.m, mp.v, mp.wb, mp.wt, mp.step, lay, mlp::LAY.P);
+    FOS_CUDA_TRY(cudaGetLastError());
+    FOS_CUDA_TRY(cudaMemcpyAsync(mp.stats, feat_stats, 64 * sizeof(float),
+                                 cudaMemcpyHostToDevice, s));
+    FOS_CUDA_TRY(cudaStreamSynchronize(s));
+    return FOS_OK;
+}
+
 fos_status fos_surrogate_features(int n_designs, int n_wl, const double* wl, const double* np_re,
                                   const double* np_im, const double* radius,
                                   const double* vol_frac, const double* thickness, const double* g,
@@ -1048,6 +1130,28 @@ fos_status fos_surrogate_features(int n_designs, int n_wl, const double* wl, con
         mlp::features_kernel<<<(unsigned)blocks, 256, 0, s>>>(n_designs, n_wl, wl, np_re, np_im,
                                                               radius, vol_frac, thickness, g, mu_s,
                                                               mu_a, features, ws->status);
+        FOS_CUDA_TRY(cudaGetLastError());
+    }
+    return finish_call(ws, s, flags);
+}
+
+fos_status fos_surrogate_features_slab(long long n_rows, const double* n_layer,
+                                       const double* mu_s, const double* mu_a, const double* g,
+                                       const double* thickness, float* features,
+                                       unsigned flags, void* stream) {
+    if (n_rows < 0) return FOS_ERR_INVALID_ARG;
+    if (n_rows > 0 && (!n_layer || !mu_s || !mu_a || !g || !thickness || !features))
+        return FOS_ERR_INVALID_ARG;
+    Workspace* ws = nullptr;
+    fos_status st = get_workspace(&ws);
+    if (st != FOS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    FOS_CUDA_TRY(cudaMemsetAsync(ws->status + ST_CALL, 0, sizeof(unsigned), s));
+    if (n_rows > 0) {
+        long long blocks = (n_rows + 255) / 256;
+        if (blocks > (long long)ws->num_sms * 16) blocks = (long long)ws->num_sms * 16;
+        mlp::features_slab_kernel<<<(unsigned)blocks, 256, 0, s>>>(
+            n_rows, n_layer, mu_s, mu_a, g, thickness, features, ws->status);
         FOS_CUDA_TRY(cudaGetLastError());
     }
     return finish_call(ws, s, flags);

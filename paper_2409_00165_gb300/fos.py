@@ -61,6 +61,7 @@ class FosBatch(ctypes.Structure):
         ("item_list", ctypes.c_void_p), ("n_list", ctypes.c_int),
         ("seed", ctypes.c_ulonglong), ("item_id_base", ctypes.c_uint),
         ("max_events", ctypes.c_longlong),
+        ("cos_incidence", ctypes.c_void_p), ("k_below", ctypes.c_void_p),
     ]
 
 
@@ -203,13 +204,14 @@ def fos_size_distribution(diameter: float, sigma: float, vol_frac: float, n: int
 def make_batch(n_stacks, n_wl, max_layers, mu_s, mu_a, g, n_layer, thickness,
                n_layers=None, n_above=None, n_below=None, substrate_R=None, n_photons=None,
                photons_per_item=0, photon_first=None, item_list=None, seed=0,
-               item_id_base=0, max_events=0) -> FosBatch:
+               item_id_base=0, max_events=0, cos_incidence=None, k_below=None) -> FosBatch:
     """Fills the C struct from CUDA tensors.  The struct keeps references to the tensors,
     so temporaries passed here stay allocated as long as the struct lives."""
     f64, i32, i64 = torch.float64, torch.int32, torch.int64
     b = FosBatch()
     b._keep = [t for t in (mu_s, mu_a, g, n_layer, thickness, n_layers, n_above, n_below,
-                           substrate_R, n_photons, photon_first, item_list) if t is not None]
+                           substrate_R, n_photons, photon_first, item_list, cos_incidence,
+                           k_below) if t is not None]
     b.n_stacks, b.n_wl, b.max_layers = int(n_stacks), int(n_wl), int(max_layers)
     b.n_layers = _dev(n_layers, i32, "n_layers", True)
     b.mu_s = _dev(mu_s, f64, "mu_s")
@@ -228,6 +230,8 @@ def make_batch(n_stacks, n_wl, max_layers, mu_s, mu_a, g, n_layer, thickness,
     b.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     b.item_id_base = int(item_id_base) & 0xFFFFFFFF
     b.max_events = int(max_events)
+    b.cos_incidence = _dev(cos_incidence, f64, "cos_incidence", True)
+    b.k_below = _dev(k_below, f64, "k_below", True)
     return b
 
 
@@ -236,6 +240,16 @@ def fos_mc_spectrum(batch: FosBatch, counts, photon_log=None, log_stride=0, flag
     return lib().fos_mc_spectrum(ctypes.byref(batch), _dev(counts, torch.int64, "counts"),
                                  _dev(photon_log, torch.int32, "photon_log", True),
                                  int(log_stride), int(flags), _stream(stream))
+
+
+def fos_solar_weighted(n_stacks: int, wl, G, counts, out, flags=0, stream=None) -> int:
+    fn = lib().fos_solar_weighted
+    fn.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 4 + [ctypes.c_uint,
+                                                                           ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    return fn(int(n_stacks), int(wl.numel()), _dev(wl, torch.float64, "wl"),
+              _dev(G, torch.float64, "G"), _dev(counts, torch.int64, "counts"),
+              _dev(out, torch.float64, "out"), int(flags), _stream(stream))
 
 
 def fos_mc_set_tuning(block: int, photons_per_thread: int) -> int:
@@ -306,6 +320,25 @@ def fos_surrogate_init(model, n_members, seed, feat_stats, stream=None) -> int:
                                        ctypes.c_void_p, ctypes.c_void_p])(
         _dev(model, torch.uint8, "model"), int(n_members), int(seed) & 0xFFFFFFFFFFFFFFFF,
         st, _stream(stream))
+
+
+def fos_surrogate_load(model, member, theta, feat_stats, stream=None) -> int:
+    """theta: device float32 [fos_surrogate_param_count()]; feat_stats: 64 host floats."""
+    st = (ctypes.c_float * 64)(*[float(v) for v in feat_stats])
+    return _sfn("fos_surrogate_load", [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p])(
+        _dev(model, torch.uint8, "model"), int(member), _dev(theta, torch.float32, "theta"),
+        st, _stream(stream))
+
+
+def fos_surrogate_features_slab(n_layer, mu_s, mu_a, g, thickness, features, flags=0,
+                                stream=None) -> int:
+    f64 = torch.float64
+    return _sfn("fos_surrogate_features_slab", [ctypes.c_longlong] + [ctypes.c_void_p] * 6 +
+                [ctypes.c_uint, ctypes.c_void_p])(
+        int(n_layer.numel()), _dev(n_layer, f64, "n_layer"), _dev(mu_s, f64, "mu_s"),
+        _dev(mu_a, f64, "mu_a"), _dev(g, f64, "g"), _dev(thickness, f64, "thickness"),
+        _dev(features, torch.float32, "features"), int(flags), _stream(stream))
 
 
 def fos_surrogate_features(wl, np_re, np_im, radius, vol_frac, thickness, g, mu_s, mu_a,

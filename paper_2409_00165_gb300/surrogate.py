@@ -94,11 +94,14 @@ def flagged_rows(needs):
 class Surrogate:
     """An ensemble of MLP members stored in one device buffer."""
 
-    def __init__(self, n_members: int, feat_stats_device, seed: int = 0, device="cuda"):
+    def __init__(self, n_members: int, feat_stats, seed: int = 0, device="cuda"):
+        """feat_stats: the 64 statistics floats, a device tensor or a host sequence."""
         self.n_members = n_members
         self.mb = fos.fos_surrogate_model_bytes()
         self.model = torch.zeros(n_members * self.mb, dtype=torch.uint8, device=device)
-        stats = feat_stats_device.cpu().numpy().tolist()
+        if isinstance(feat_stats, torch.Tensor):
+            feat_stats = feat_stats.cpu().numpy()
+        stats = [float(v) for v in feat_stats]
         fos.check(fos.fos_surrogate_init(self.model, n_members, seed, stats), "init")
         self.seed = seed
         self.steps_done = [0] * n_members
@@ -228,6 +231,103 @@ def sweep(sur: Surrogate, n_designs: int, n_wl: int, seed: int, threshold: float
         out["mc_spectra_per_s"] = phot / t_a / (n_wl * audit_photons)
         out["speedup_vs_mc"] = out["spectra_per_s"] / out["mc_spectra_per_s"]
     return out
+
+
+# ----------------------------------------------------------------------------------
+# The network with the paper's own inputs (Table 1): slabs given by optical properties.
+# ----------------------------------------------------------------------------------
+class Slabs:
+    """Homogeneous slabs in air, one row each, as device tensors."""
+
+    def __init__(self, rows: dict, device="cuda"):
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=F64, device=device)
+        self.n, self.mu_s, self.mu_a = t(rows["n"]), t(rows["mu_s"]), t(rows["mu_a"])
+        self.g, self.d = t(rows["g"]), t(rows["d"])
+        self.rows = int(self.n.numel())
+
+    def mc(self, photons: int, seed: int, item_list=None, flags=0):
+        b = fos.make_batch(self.rows, 1, 1, self.mu_s, self.mu_a, self.g, self.n, self.d,
+                           photons_per_item=photons, seed=seed, item_list=item_list)
+        n = item_list.numel() if item_list is not None else self.rows
+        counts = torch.zeros((max(n, 1), fos.FOS_NCOUNT), dtype=torch.int64,
+                             device=self.n.device)
+        fos.check(fos.fos_mc_spectrum(b, counts, None, 0, flags), "fos_mc_spectrum")
+        return counts[:n]
+
+    def features(self, flags=0):
+        out = torch.zeros((self.rows, 9), dtype=torch.float32, device=self.n.device)
+        fos.check(fos.fos_surrogate_features_slab(self.n, self.mu_s, self.mu_a, self.g, self.d,
+                                                  out, flags=flags),
+                  "fos_surrogate_features_slab")
+        return out
+
+
+def table1_stats(features) -> list:
+    """Feature statistics of the training rows with the range gate set to Table 1 (and
+    the optical-depth cap): rows outside it are flagged for Monte Carlo."""
+    st = Surrogate.stats_of(features).cpu().numpy().astype(np.float64)
+    T = W.TABLE1
+    lo = [T["n"][0], math.log10(T["mu_s"][0] + 1e-4), math.log10(T["mu_a"][0] + 1e-4),
+          T["g"][0], math.log10(T["d"][0]), -6.0, -6.0, 0.0, 0.0]
+    hi = [T["n"][1], math.log10(T["mu_s"][1] + 1e-4), math.log10(T["mu_a"][1] + 1e-4),
+          T["g"][1], math.log10(T["d"][1]), math.log10(T["tau_s_max"] + 1e-6),
+          math.log10(T["mu_a"][1] * T["d"][1] + 1e-6), 0.0, 0.0]
+    # float32 rounding of a boundary must not flag the boundary itself
+    st[32:41] = np.nextafter(np.float32(lo), np.float32(-np.inf))
+    st[48:57] = np.nextafter(np.float32(hi), np.float32(np.inf))
+    return st.astype(np.float32).tolist()
+
+
+def table1_experiment(train_rows: int, train_photons: int, steps: int, test_rows: int,
+                      test_photons: int, members: int = 4, seed: int = 40, batch: int = 8192,
+                      threshold: float = 0.01, device="cuda"):
+    """Trains an ensemble on Monte Carlo fractions of random Table 1 slabs and evaluates it
+    on held-out slabs against Monte Carlo at test_photons: accuracy, flagged rows, and
+    slab evaluations per second of the network (with fallback) against Monte Carlo."""
+    tr = Slabs(W.table1_slabs(train_rows, seed), device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    y = fractions(tr.mc(train_photons, seed=seed + 1))
+    ev[1].record()
+    f = tr.features()
+    torch.cuda.synchronize()
+    t_data = ev[0].elapsed_time(ev[1]) / 1e3
+    sur = Surrogate(members, table1_stats(f), seed=seed, device=device)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    hist = sur.fit(f, y, steps=steps, batch=batch, lr=2e-3, log_every=max(steps - 1, 1))
+    t1.record()
+    torch.cuda.synchronize()
+    t_train = t0.elapsed_time(t1) / 1e3
+    te = Slabs(W.table1_slabs(test_rows, seed + 7), device)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    ft = te.features(flags=fos.FOS_ASYNC)
+    rat, spread, needs = sur.predict(ft, threshold, flags=fos.FOS_ASYNC)
+    e[1].record()
+    flagged = flagged_rows(needs)
+    n_flag = int(flagged.numel())
+    if n_flag:
+        cf = te.mc(test_photons, seed=seed + 11, item_list=flagged)
+        fractions(cf, rows=flagged, out=rat)
+    e[2].record()
+    yt = fractions(te.mc(test_photons, seed=seed + 13))
+    e[3].record()
+    torch.cuda.synchronize()
+    fos.check(fos.fos_sync_status(), "table1")
+    t_pred = e[0].elapsed_time(e[1]) / 1e3
+    t_fb = e[1].elapsed_time(e[2]) / 1e3
+    t_mc = e[2].elapsed_time(e[3]) / 1e3
+    err = (rat - yt).abs()
+    return dict(train_rows=train_rows, train_photons=train_photons, data_seconds=t_data,
+                members=members, steps=steps, train_seconds=t_train,
+                final_loss=[h[-1][1] for h in hist.values()],
+                test_rows=test_rows, test_photons=test_photons, flagged=n_flag,
+                mae=err.mean(dim=0).cpu().tolist(), max=err.max(dim=0).values.cpu().tolist(),
+                nn_rows_per_s=test_rows / (t_pred + t_fb),
+                nn_rows_per_s_no_fallback=test_rows / t_pred,
+                mc_rows_per_s=test_rows / t_mc, speedup_vs_mc=t_mc / (t_pred + t_fb))
 
 
 def _predict_demo(rows: int, members: int, reps: int):

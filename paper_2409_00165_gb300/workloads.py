@@ -221,3 +221,67 @@ def hollow_silica_media(outer_diameters=(0.7, 0.9, 1.1), core_diameter=0.5, vol_
                 thickness=np.full(n_groups, float(thickness)),
                 n_layers=np.ones(n_groups, np.int32), n_stacks=n_groups, max_layers=1,
                 n_wl=n_wl)
+
+
+# --------------------------------------------------------------------------------
+# Boundary and incidence variants, and the solar weighting of Eq. 21.  The AM1.5
+# spectrum file is not available: a 5778 K blackbody shape stands in for G.
+# --------------------------------------------------------------------------------
+def solar_like_irradiance(wl):
+    """Planck spectral shape at 5778 K, lambda in um (arbitrary scale, peak ~1)."""
+    wl = np.asarray(wl, dtype=np.float64)
+    c2 = 14387.77   # um K
+    b = wl ** -5 / np.expm1(c2 / (wl * 5778.0))
+    return b / (0.5 ** -5 / np.expm1(c2 / (0.5 * 5778.0)))
+
+
+def aluminium_like_index(wl):
+    """Drude metal n + ik = sqrt(1 - (lambda/0.083)^2 / (1 + i lambda/12.4)), lambda in
+    um (plasma wavelength 0.083 um, damping wavelength 12.4 um)."""
+    wl = np.asarray(wl, dtype=np.float64)
+    eps = 1.0 - (wl / 0.083) ** 2 / (1.0 + 1j * wl / 12.4)
+    n = np.sqrt(eps.astype(np.complex128))
+    return np.where(n.imag < 0, -n, n)
+
+
+def oblique_conductor_media(cos_incidence=(1.0, 0.8660254037844387, 0.5), n_wl=PAINT_N_WL,
+                            thickness=50.0, radius=0.2, vol_frac=0.10):
+    """The paint-layer medium, 50 um thick, on an aluminium-like conductor, lit at 0, 30
+    and 60 degrees: one single-layer stack per incidence angle.  Adds per-item
+    cos_incidence, n_below and k_below arrays [n_stacks * n_wl]."""
+    wl = wavelengths(n_wl)
+    k = len(cos_incidence)
+    m = _media(wl, np.full((k, 1), radius), np.full((k, 1), vol_frac),
+               np.full((k, 1), thickness), np.ones(k, np.int32), 1)
+    al = aluminium_like_index(wl)
+    m.update(cos_incidence=np.repeat(np.asarray(cos_incidence, np.float64), n_wl),
+             n_below=np.tile(al.real, k), k_below=np.tile(al.imag, k))
+    return m
+
+
+# --------------------------------------------------------------------------------
+# Slabs given by optical properties, for the network with the paper's inputs (Table 1):
+# matrix index 1-7, mu_a 0-1e6 /cm, mu_s 0-2e5 /cm, g 0-1, thickness 5-500 um, air on
+# both sides.  Units here: 1/um and um (1e6 /cm = 100 /um, 2e5 /cm = 20 /um).  The
+# scattering optical depth is capped at 100: beyond it a walk takes ~tau^2 steps per
+# photon, which no training budget affords.
+# --------------------------------------------------------------------------------
+TABLE1 = dict(n=(1.0, 7.0), mu_s=(0.0, 20.0), mu_a=(0.0, 100.0), g=(0.0, 0.99),
+              d=(5.0, 500.0), tau_s_max=100.0)
+
+
+def table1_slabs(n_rows: int, seed: int, tau_s_max: float = TABLE1["tau_s_max"],
+                 zero_frac: float = 0.05) -> dict:
+    """n ~ U(1, 7), g ~ U(0, 0.99), d log-uniform on [5, 500] um, mu_s log-uniform on
+    [1e-4, min(20, tau_s_max / d)] /um, mu_a log-uniform on [1e-4, 100] /um; a fraction
+    zero_frac of rows has mu_s = 0 and another mu_a = 0 (the lower ends of Table 1)."""
+    rng = np.random.default_rng(seed)
+    lo, hi = np.log(1e-4), np.log(20.0)
+    d = np.exp(rng.uniform(np.log(5.0), np.log(500.0), n_rows))
+    top = np.log(np.minimum(20.0, tau_s_max / d))
+    mu_s = np.exp(lo + rng.uniform(size=n_rows) * (top - lo))
+    mu_a = np.exp(rng.uniform(np.log(1e-4), np.log(100.0), n_rows))
+    mu_s[rng.uniform(size=n_rows) < zero_frac] = 0.0
+    mu_a[rng.uniform(size=n_rows) < zero_frac] = 0.0
+    return dict(n=rng.uniform(1.0, 7.0, n_rows), mu_s=mu_s, mu_a=mu_a,
+                g=rng.uniform(0.0, 0.99, n_rows), d=d)

@@ -26,6 +26,8 @@ def gpu_mc(batch: dict, photon_log: bool = False, flags: int = 0, allow=(fos.FOS
         n_photons=to_dev(batch.get("n_photons"), i64),
         photon_first=to_dev(batch.get("photon_first"), i64),
         item_list=to_dev(batch.get("item_list"), i32),
+        cos_incidence=to_dev(batch.get("cos_incidence"), f64),
+        k_below=to_dev(batch.get("k_below"), f64),
     )
     b = fos.make_batch(batch["n_stacks"], batch["n_wl"], batch["max_layers"],
                        photons_per_item=int(batch.get("photons_per_item", 0)),

