@@ -63,6 +63,9 @@ def parse():
                          "design sweep with MC fallback and audit")
     ap.add_argument("--stacks", action="store_true",
                     help="also time the uneven multilayer-stack batch once")
+    ap.add_argument("--legs", choices=["on", "off"], default="on",
+                    help="workload legs after the timed steps (1 GPU only): size "
+                         "distributions, core-shell spheres, oblique incidence on a conductor")
     return ap.parse_args()
 
 
@@ -347,7 +350,7 @@ def run_fos(args):
     if args.stacks and world == 1:
         stacks = run_stacks()
     dists = cs = bnd = None
-    if world == 1:
+    if world == 1 and args.legs == "on":
         try:
             dists = run_distributions()
         except Exception as exc:
@@ -414,6 +417,18 @@ def run_surrogate(mode: str):
     t2 = time.perf_counter()
     r = S.sweep(sur, n_designs=cfg["sweep"], n_wl=300, seed=5, threshold=0.01,
                 audit_frac=0.001)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    r["roofline"] = dict(bound="tensor", kernel="infer_kernel", achieved=r["predict_tflops"],
+                         peak=peak, unit="TFLOP/s", frac=r["predict_tflops"] / peak,
+                         traffic=None,
+                         flop_per_row_member=S.FLOP_PER_ROW_MEMBER,
+                         peak_basis="measured bf16 burst" if "bf16_tflops" in peaks
+                         else "fallback 1.9 PFLOP/s")
     r["train"] = dict(rows=info["rows"], photons_per_row=info["photons_per_row"],
                       data_seconds=t1 - t0, train_seconds=t2 - t1, members=4,
                       steps_per_member=cfg["steps"], batch=8192,

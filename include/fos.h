@@ -60,8 +60,9 @@ enum {
 #define FOS_NO_GRAPH     0x2u  /* launch kernels directly instead of a cached CUDA graph */
 #define FOS_AUTOTUNE     0x4u  /* re-run the launch autotuner for this batch shape     */
 #define FOS_TEST_INJECT  0x10000u /* test only: the first kernel reports a failure      */
-#define FOS_TEST_STALL   0x20000u /* test only (fos_gemm_bf16): a pipeline stage is never
-                                     loaded, so its bounded wait runs out -> FOS_ERR_TIMEOUT */
+#define FOS_TEST_STALL   0x20000u /* test only (fos_gemm_bf16, fos_surrogate_predict): a
+                                     pipeline stage is never loaded, so its bounded wait
+                                     runs out -> FOS_ERR_TIMEOUT                        */
 
 #define FOS_MAX_LAYERS   8     /* layers per stack                                     */
 #define FOS_NCOUNT       6     /* counts per item: R, A, T, runaway, collisions, interface events */
@@ -243,7 +244,7 @@ fos_status fos_solar_weighted(int n_stacks, int n_wl, const double* wl, const do
                               const long long* counts, double* out, unsigned flags,
                               void* stream);
 
-/* Launch shape of the walk kernel: threads per block (multiple of 32, 64..1024) and
+/* Launch shape of the walk kernel: threads per block (multiple of 32, 32..128) and
  * photons per thread per work unit (a warp claims 32*ppt photons at a time).
  * fos_mc_set_tuning(0, 0) returns to autotuned/default shapes. */
 fos_status fos_mc_set_tuning(int block, int photons_per_thread);

@@ -415,8 +415,12 @@ __device__ __forceinline__ void warp_flush(bool want, int tag, unsigned c0, unsi
 }
 
 enum { O_R = 0, O_A = 1, O_T = 2, O_X = 3 };
+constexpr int WALK_MAX_BLOCK = 128;
 
-__global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
+// 128-thread blocks, 7 per SM: the register budget (72 per thread) that gives 28
+// resident warps, which hide the latency of the dependent Philox and float chains better
+// than 24 warps at 80 registers.
+__global__ void __launch_bounds__(WALK_MAX_BLOCK, 7) walk_kernel(WalkArgs A) {
     if (A.status[ST_CALL] & (DEV_INVALID | DEV_INJECTED | DEV_RANGE)) return;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -434,7 +438,6 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
     float z = 0.f, mu = 1.f, tau = 0.f, u1 = 0.f, u2 = 0.f, u3 = 0.f;
     float l_mut = 0.f, l_pabs = 0.f, l_g = 0.f, l_n = 1.f, l_d = 1.f, l_omg2 = 1.f,
           l_opg2 = 1.f, l_omg = 1.f, l_imt = 0.f, l_i2g = 0.f;
-    float n_above = 1.f, n_below = 1.f, r_sub = -1.f;
 
     // tallies of the current tag (row)
     int tag = -1;
@@ -517,9 +520,6 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
                 p_first = (unsigned)inf.y;
                 p = p_first + u_next + rank;
                 nl = hd.x;
-                n_above = __int_as_float(hd.y);
-                n_below = __int_as_float(hd.z);
-                r_sub = __int_as_float(hd.w);
                 j = 0;
                 load_layer(0);
                 e = 0u;
@@ -594,6 +594,10 @@ __global__ void __launch_bounds__(512) walk_kernel(WalkArgs A) {
                 cI++;
                 const int nb = down ? j + 1 : j - 1;
                 const bool outside = (nb < 0) || (nb >= nl);
+                // media and substrate of the row, read at boundary events only (L1-resident)
+                const int4 hd2 = A.t.head[row];
+                const float n_above = __int_as_float(hd2.y), n_below = __int_as_float(hd2.z),
+                            r_sub = __int_as_float(hd2.w);
                 if (down && outside && r_sub != -1.0f) {
                     // opaque below: reflector (R_sub) or conductor (Fresnel with n + ik)
                     const float Rb = (r_sub >= 0.0f)
@@ -663,7 +667,7 @@ __global__ void walk_math_kernel(const float* u, float* nl, float* cs, long long
 // Host side: launch sequence, CUDA graph cache, tuning.
 // ---------------------------------------------------------------------------------
 struct Tuning {
-    int block = 256;
+    int block = 128;
     int ppt = 8;
 };
 
@@ -864,10 +868,10 @@ static fos_status autotune(Workspace* ws, const fos_mc_batch* b, long long n_run
     // warp that the probe measures the steady state, not the tail of the last units
     long long cap = (1LL << 24) / (n_run > 0 ? n_run : 1);
     if (cap < 4096) cap = 4096;
-    // Candidate shapes keep 24 warps resident per SM at the kernel's register count
-    // (512-thread blocks fit only once per SM and measured 15 % slower at full size).
-    const int blocks[] = {128, 256};
-    const int ppts[] = {4, 8, 32};
+    // Candidate shapes: the kernel's 128-thread blocks (7 resident per SM) with 4 to 32
+    // photons per thread per work unit.
+    const int blocks[] = {128};
+    const int ppts[] = {4, 8, 16, 32};
     const bool verbose = getenv("FOS_AUTOTUNE_VERBOSE") != nullptr;
     cudaEvent_t e0, e1;
     FOS_CUDA_TRY(cudaEventCreate(&e0));
@@ -962,7 +966,7 @@ fos_status fos_mc_set_tuning(int block, int ppt) {
         mc::g_state.has_override = false;
         return FOS_OK;
     }
-    if (block < 64 || block > 512 || (block % 32) != 0 || ppt < 1 || ppt > 1024)
+    if (block < 32 || block > mc::WALK_MAX_BLOCK || (block % 32) != 0 || ppt < 1 || ppt > 1024)
         return FOS_ERR_INVALID_ARG;
     mc::g_state.override_t.block = block;
     mc::g_state.override_t.ppt = ppt;

@@ -278,6 +278,9 @@ __device__ bool coated_eval(double lam, double a, double b, cx n_c, cx n_s, cx n
     return true;
 }
 
+// CS = false: homogeneous spheres only (the core-shell code is compiled out, which keeps
+// the register count of the common case low); CS = true: either kind per species.
+template <bool CS>
 __global__ void __launch_bounds__(128) mie_kernel(MieArgs A) {
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (A.inject && tid == 0) atomicOr(&A.status[ST_CALL], DEV_INJECTED);
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(128) mie_kernel(MieArgs A) {
         const cx n_p = mk(A.np_re[ev], A.np_im[ev]);
         const cx n_m = mk(A.nm_re[gw], A.nm_im[gw]);
         const double f = A.vol_frac[s];
-        const double a = A.core_radius ? A.core_radius[s] : 0.0;
+        const double a = CS ? A.core_radius[s] : 0.0;
         cx n_c = mk(1.0, 0.0);
         if (a > 0.0) n_c = mk(A.nc_re[ev], A.nc_im[ev]);
         ok = ok && isfinite(lam) && lam > 0.0 && isfinite(r) && r > 0.0 &&
@@ -306,10 +309,12 @@ __global__ void __launch_bounds__(128) mie_kernel(MieArgs A) {
         if (!ok) {
             flag(A.status, DEV_INVALID, ev);
         } else {
-            const bool fit = (a > 0.0)
-                ? coated_eval(lam, a, r, n_c, n_p, n_m, c0, c0 + col, c0 + 2 * col,
-                              c0 + 3 * col, A.T, &qe, &qs, &gg)
-                : sphere_eval(lam, r, n_p, n_m, c0, c0 + col, A.T, &qe, &qs, &gg);
+            bool fit;
+            if (CS && a > 0.0)
+                fit = coated_eval(lam, a, r, n_c, n_p, n_m, c0, c0 + col, c0 + 2 * col,
+                                  c0 + 3 * col, A.T, &qe, &qs, &gg);
+            else
+                fit = sphere_eval(lam, r, n_p, n_m, c0, c0 + col, A.T, &qe, &qs, &gg);
             if (!fit) flag(A.status, DEV_RANGE, ev);
         }
         A.q_ext[ev] = qe;
@@ -439,7 +444,10 @@ static fos_status mie_impl(int n_wl, const double* wl, int n_groups, const doubl
         ma.T = T;
         ma.status = ws->status;
         ma.inject = (flags & FOS_TEST_INJECT) ? 1 : 0;
-        mie::mie_kernel<<<(unsigned)(T / block), block, 0, s>>>(ma);
+        if (core_radius)
+            mie::mie_kernel<true><<<(unsigned)(T / block), block, 0, s>>>(ma);
+        else
+            mie::mie_kernel<false><<<(unsigned)(T / block), block, 0, s>>>(ma);
         FOS_CUDA_TRY(cudaGetLastError());
     }
     mie::EmtArgs ea;

@@ -5,7 +5,8 @@
 // (R, A, T).  BF16 weights and activations on the tensor cores, FP32 accumulation,
 // FP32 master weights and Adam state.
 //
-// Every matrix product of training and inference runs in gemm_kernel: a 128 x NT output
+// Inference runs in one fused persistent kernel (infer_kernel, below).  Every matrix
+// product of training runs in gemm_kernel: a 128 x NT output
 // tile per CTA; K-major BF16 operands are staged by TMA (128-byte swizzle) through a
 // 4-stage mbarrier ring; one thread issues tcgen05.mma (M=128, N=NT, K=16) into FP32
 // accumulators in tensor memory; the 4 warps read the accumulators back with tcgen05.ld
@@ -57,11 +58,41 @@ __host__ __device__ constexpr int real_in(int l) { return l == 0 ? N_FEAT : HID;
 //   wt     bf16      : W_l^T in bf16, [in][out] for l = 1..4 (backward B operands)
 //   stats  fp32 [64] : mean[16] | std[16] | lo[16] | hi[16] of the raw features
 //   step   int32 [4]
+//   wi     bf16      : the weights as shared-memory images for the fused inference
+//                      kernel (see img_index), one contiguous block per pipeline stage
 struct Layout {
     long long w_off[N_LAYERS], b_off[N_LAYERS], P;
     long long wb_off[N_LAYERS], wt_off[N_LAYERS], n_wb, n_wt;
-    size_t theta_b, m_b, v_b, wb_b, wt_b, stats_b, step_b, bytes;
+    size_t theta_b, m_b, v_b, wb_b, wt_b, stats_b, step_b, wi_b, bytes;
 };
+
+// Weight image: the B operands of the fused inference kernel, already in the 128-byte-
+// swizzled K-major layout a stage of shared memory holds, so that one untiled bulk copy
+// fills a stage.  Layers 0-3 come in blocks of 128 output rows x 64 inputs (16 KB): layer
+// 0 as 2 blocks (row halves), layers 1-3 as 8 blocks ordered (k block, row half).  Layer 4
+// keeps its first 16 output rows (3 real) in 4 blocks of 16 x 64 (2 KB), one per k block.
+constexpr long long IMG_BLK = 128 * 64;          // elements of a 16 KB block
+constexpr long long IMG_L4_BLK = 16 * 64;        // elements of a 2 KB block
+__host__ __device__ constexpr long long img_off(int l) {
+    return l == 0 ? 0 : (l == 4 ? 26 * IMG_BLK : (2 + 8 * (l - 1)) * IMG_BLK);
+}
+constexpr long long IMG_ELEMS = 26 * IMG_BLK + 4 * IMG_L4_BLK;
+constexpr int IMG_ROWS_L4 = 16;
+
+// Element index in the image of weight (l, o, i), or -1 when the image leaves it out.
+// Row n of a block starts at n * 64 elements; its 16-byte chunk j (inputs 8j..8j+7 of
+// the k block) sits at chunk position j ^ (n mod 8).
+__host__ __device__ inline long long img_index(int l, int o, int i) {
+    const int kb = i >> 6, c = i & 63;
+    if (l == 4) {
+        if (o >= IMG_ROWS_L4) return -1;
+        return img_off(4) + (long long)kb * IMG_L4_BLK + o * 64 +
+               ((((c >> 3) ^ (o & 7)) << 3) | (c & 7));
+    }
+    const int nh = o >> 7, n = o & 127;
+    const int blk = (l == 0) ? nh : kb * 2 + nh;
+    return img_off(l) + (long long)blk * IMG_BLK + n * 64 + ((((c >> 3) ^ (n & 7)) << 3) | (c & 7));
+}
 
 static Layout make_layout() {
     Layout L;
@@ -88,6 +119,7 @@ static Layout make_layout() {
     L.wt_b = o;    o = al(o + (size_t)t * 2);
     L.stats_b = o; o = al(o + 64 * 4);
     L.step_b = o;  o = al(o + 16);
+    L.wi_b = o;    o = al(o + (size_t)IMG_ELEMS * 2);
     L.bytes = o;
     return L;
 }
@@ -95,7 +127,7 @@ static const Layout LAY = make_layout();
 
 struct MemberPtrs {
     float *theta, *m, *v, *stats;
-    bf16 *wb, *wt;
+    bf16 *wb, *wt, *wi;
     int* step;
 };
 static MemberPtrs member(void* model, int k) {
@@ -108,15 +140,14 @@ static MemberPtrs member(void* model, int k) {
     p.wt = (bf16*)(base + LAY.wt_b);
     p.stats = (float*)(base + LAY.stats_b);
     p.step = (int*)(base + LAY.step_b);
+    p.wi = (bf16*)(base + LAY.wi_b);
     return p;
 }
 
 // ----------------------------------------------------------------------- GEMM kernel
 enum Mode {
     FWD_HIDDEN = 0,    // Z = acc + b (fp32), H = GELU(Z) (bf16) and H^T
-    INFER_HIDDEN = 1,  // H = GELU(acc + b) (bf16)
     FWD_OUT = 2,       // softmax(acc + b) over 3 columns -> P; CE gradient G, G^T; loss
-    INFER_OUT = 3,     // softmax(acc + b) -> P
     BWD_HIDDEN = 4,    // dZ = acc * GELU'(Z_prev) -> dZ (bf16), dZ^T
     DW_PARTIAL = 5,    // partial[split] = acc (fp32)
 };
@@ -271,7 +302,7 @@ __global__ void __launch_bounds__(128, 1)
     const bool row_ok = m < args.M && done_ok;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     float v[16];
-    if (MODE == FWD_OUT || MODE == INFER_OUT) {
+    if (MODE == FWD_OUT) {
         tmem_ld16(trow, v);
         float li = 0.f;
         if (row_ok) {
@@ -346,15 +377,384 @@ __global__ void __launch_bounds__(128, 1)
             uint4* hd = reinterpret_cast<uint4*>(args.out_h + (long long)m * args.ldh + n);
             hd[0] = reinterpret_cast<const uint4*>(hb)[0];
             hd[1] = reinterpret_cast<const uint4*>(hb)[1];
-            if (MODE != INFER_HIDDEN) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) args.out_t[(long long)(n + i) * args.ldt + m] = hb[i];
-            }
+            for (int i = 0; i < 16; ++i) args.out_t[(long long)(n + i) * args.ldt + m] = hb[i];
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, NCOLS);
+}
+
+// ----------------------------------------------------------------- fused inference
+// The whole ensemble forward pass for 128-row tiles in one persistent kernel (one CTA
+// per SM): raw features -> standardise -> 4 x (tcgen05 MMA, bias + GELU) -> MMA, softmax
+// -> ensemble mean, spread and fallback flag.  Activations never leave the SM: each
+// hidden layer's epilogue writes its BF16 output straight into shared memory in the
+// 128-byte-swizzled K-major layout that the next layer's MMA reads as its A operand.
+// Weights stream from the model's weight image (L2-resident) through a 10-slot ring of
+// 16 KB stages filled by untiled bulk copies: a whole hidden layer (8 stages) is fetched
+// while the previous layer's epilogue runs, so the MMAs of a layer issue back to back.
+//
+// Roles: the epilogue warps (FI_EPI_WARPS, a multiple of 4); warp w reads TMEM lanes
+// 32 (w mod 4) .. +31 (its tile rows) and the columns of its column group w / 4, which are
+// whole k blocks of the next layer's input.  The warps with w < 4 also build the layer-0
+// input and keep the ensemble sums of their rows.  Lane 0 of the last warp issues the
+// bulk copies and the MMAs.
+// Barriers: full/empty per ring slot; `acc` (one MMA commit per layer: accumulator
+// ready); `a_ready` (512 arrivals: the A operand is written and the accumulator read
+// out).  Every wait is bounded; a wait that gives up sets DEV_TIMEOUT and the kernel
+// drains its copies and MMAs and returns.
+constexpr int FI_CTAS = 1;                               // CTAs per SM
+constexpr int FI_STAGES = 8;
+constexpr int FI_SLOT = 16384;
+constexpr int FI_H_BYTES = 4 * 128 * 128;               // 128 rows x 256 bf16 (4 k blocks)
+constexpr int FI_ITEMS = 2 + 8 * 3 + 4;                  // ring items per tile and member
+// Per-member parameters staged in shared memory: biases of the 5 layers (256 each) and
+// the feature means and standard deviations (16 each); slots for up to 4 members.
+constexpr int FI_PAR_FLOATS = N_LAYERS * 256 + 32;
+constexpr int FI_PAR_SLOTS = 4;
+constexpr int FI_PAR_BYTES = FI_PAR_SLOTS * FI_PAR_FLOATS * 4;
+constexpr int FI_BAR_BYTES = 8 * (2 * FI_STAGES + 3) + 16;
+constexpr int FI_SMEM = FI_H_BYTES + FI_STAGES * FI_SLOT + FI_PAR_BYTES + FI_BAR_BYTES;
+constexpr int FI_EPI_WARPS = 16;
+constexpr int FI_THREADS = 32 * (FI_EPI_WARPS + 1);
+constexpr int FI_CG = FI_EPI_WARPS / 4;                  // column groups of epilogue warps
+constexpr int FI_KB_PER = 4 / FI_CG;                     // k blocks each epilogue warp writes
+static_assert(FI_EPI_WARPS % 4 == 0 && 4 % FI_CG == 0, "epilogue warps: 4, 8 or 16");
+
+struct InferArgs {
+    const float* feat;          // raw features [n_rows][9]
+    long long n_rows;
+    int n_members;
+    const uint8_t* model;
+    size_t member_bytes, theta_b, stats_b, wi_b;
+    long long b_off[N_LAYERS];  // bias offsets in theta (floats)
+    float* rat;                 // [n_rows][3]
+    float* spread;              // [n_rows] or NULL
+    unsigned char* needs;       // [n_rows] or NULL
+    float thr;
+    unsigned* status;
+    long long wait_limit;
+    int test_stall;             // test only: the first weight copy is never issued
+};
+
+// Ring item q of a tile-member: its layer, k block, row half, source and size.
+struct FiItem {
+    int layer, kb, nh;
+    long long src;   // element offset in the weight image
+    uint32_t bytes;
+};
+__device__ __forceinline__ FiItem fi_item(int q) {
+    FiItem it;
+    if (q < 2) {
+        it.layer = 0; it.kb = 0; it.nh = q;
+        it.src = img_off(0) + (long long)q * IMG_BLK;
+        it.bytes = FI_SLOT;
+    } else if (q < 26) {
+        const int j = q - 2;
+        it.layer = 1 + j / 8;
+        it.kb = (j % 8) >> 1;
+        it.nh = j & 1;
+        it.src = img_off(it.layer) + (long long)(j % 8) * IMG_BLK;
+        it.bytes = FI_SLOT;
+    } else {
+        it.layer = 4; it.kb = q - 26; it.nh = 0;
+        it.src = img_off(4) + (long long)(q - 26) * IMG_L4_BLK;
+        it.bytes = (uint32_t)(IMG_L4_BLK * 2);
+    }
+    return it;
+}
+
+// Writes 8 bf16 (one 16-byte chunk) of row r, columns 8j..8j+7 of k block kb, into the
+// swizzled A tile at h.
+__device__ __forceinline__ void fi_store_chunk(uint32_t h, int r, int kb, int j, uint4 v) {
+    const uint32_t a = h + (uint32_t)kb * 16384u + (uint32_t)(r >> 3) * 1024u +
+                       (uint32_t)(r & 7) * 128u + (uint32_t)((j ^ (r & 7)) << 4);
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&p);
+}
+
+__global__ void __launch_bounds__(FI_THREADS, FI_CTAS) infer_kernel(InferArgs A) {
+    extern __shared__ __align__(1024) uint8_t fi_smem[];
+    const uint32_t base = smem_u32(fi_smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t H = base;
+    const uint32_t ring = base + FI_H_BYTES;
+    float* par = reinterpret_cast<float*>(fi_smem + FI_H_BYTES + FI_STAGES * FI_SLOT);
+    const uint32_t bars = ring + FI_STAGES * FI_SLOT + FI_PAR_BYTES;
+    const uint32_t bar_full = bars, bar_empty = bars + 8 * FI_STAGES;
+    const uint32_t bar_acc = bars + 16 * FI_STAGES, bar_a = bar_acc + 8;
+    const uint32_t bar_p = bar_a + 8;   // parameter staging done (epilogue warps)
+    const uint32_t tslot = bar_p + 8;
+    uint8_t* bars_g = fi_smem + FI_H_BYTES + FI_STAGES * FI_SLOT + FI_PAR_BYTES;
+    volatile uint32_t* tslot_ptr =
+        reinterpret_cast<volatile uint32_t*>(bars_g + 16 * FI_STAGES + 24);
+    volatile int& abort_flag = *reinterpret_cast<volatile int*>(bars_g + 16 * FI_STAGES + 28);
+
+    if ((base & 1023u) != 0u) {   // the swizzled tiles need 1024-byte alignment
+        if (threadIdx.x == 0) atomicOr(&A.status[ST_CALL], DEV_RANGE);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < FI_STAGES; ++i) {
+            mbar_init(bar_full + 8 * i, 1);
+            mbar_init(bar_empty + 8 * i, 1);
+        }
+        mbar_init(bar_acc, 1);
+        mbar_init(bar_a, 32 * FI_EPI_WARPS);
+        mbar_init(bar_p, 32 * FI_EPI_WARPS);
+        abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncwarp();
+    if (warp == 0) tmem_alloc(tslot, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot_ptr;
+
+    const long long n_tiles = (A.n_rows + 127) / 128;
+    const int M = A.n_members;
+
+    if (warp == FI_EPI_WARPS) {
+        // ------------------------------------------------------------ copies + MMAs
+        if (lane == 0) {
+            const long long my_tiles =
+                n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+            const long long total = my_tiles * M * FI_ITEMS;
+            long long issued = 0, consumed = 0;
+            uint32_t pa = 0;
+            bool ok = true;
+            auto fill = [&](long long upto) {
+                while (ok && issued < upto && issued < total) {
+                    const int slot = (int)(issued % FI_STAGES);
+                    if (issued >= FI_STAGES) {
+                        const uint32_t ph = (uint32_t)((issued / FI_STAGES) - 1) & 1u;
+                        if (!mbar_wait(bar_empty + 8 * slot, ph, A.wait_limit)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    const FiItem it = fi_item((int)(issued % FI_ITEMS));
+                    const int member = (int)((issued / FI_ITEMS) % M);
+                    const uint8_t* src = A.model + (size_t)member * A.member_bytes + A.wi_b +
+                                         (size_t)it.src * 2;
+                    if (!(A.test_stall && issued == 0)) {
+                        mbar_arrive_expect_tx(bar_full + 8 * slot, it.bytes);
+                        bulk_load(ring + slot * FI_SLOT, src, it.bytes, bar_full + 8 * slot);
+                    }
+                    ++issued;
+                }
+            };
+            for (long long t = 0; t < my_tiles && ok; ++t) {
+                for (int k = 0; k < M && ok; ++k) {
+                    int q = 0;
+                    for (int l = 0; l < N_LAYERS && ok; ++l) {
+                        fill(consumed + FI_STAGES);
+                        if (!ok) break;
+                        if (!mbar_wait(bar_a, pa, A.wait_limit)) {
+                            ok = false;
+                            break;
+                        }
+                        pa ^= 1u;
+                        tc_fence_after();
+                        const int n_items = (l == 0) ? 2 : (l == 4 ? 4 : 8);
+                        for (int x = 0; x < n_items; ++x, ++q) {
+                            fill(consumed + FI_STAGES);
+                            if (!ok) break;
+                            const int slot = (int)(consumed % FI_STAGES);
+                            const uint32_t ph = (uint32_t)(consumed / FI_STAGES) & 1u;
+                            if (!mbar_wait(bar_full + 8 * slot, ph, A.wait_limit)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const FiItem it = fi_item(q);
+                            const uint32_t b_s = ring + slot * FI_SLOT;
+                            const uint32_t a_s = H + (uint32_t)it.kb * 16384u;
+                            const uint32_t d = tmem + (uint32_t)(it.nh * 128);
+                            const uint32_t idesc = (l == 4) ? idesc_bf16(128, 16)
+                                                            : idesc_bf16(128, 128);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                mma_bf16(d, desc_sw128(a_s + kk * 32), desc_sw128(b_s + kk * 32),
+                                         idesc, (it.kb > 0 || kk > 0) ? 1u : 0u);
+                            mma_commit(bar_empty + 8 * slot);
+                            ++consumed;
+                        }
+                        if (ok) mma_commit(bar_acc);
+                    }
+                }
+            }
+            if (!ok) {
+                atomicOr(&A.status[ST_CALL], DEV_TIMEOUT);
+                abort_flag = 1;
+            }
+            // drain: every issued copy has landed and every MMA has finished before exit
+            for (long long g = consumed; g < issued; ++g) {
+                if (A.test_stall && g == 0) continue;   // never issued
+                mbar_wait(bar_full + 8 * (int)(g % FI_STAGES),
+                          (uint32_t)(g / FI_STAGES) & 1u, 1000000000LL);
+            }
+            if (consumed > 0) {
+                const long long g = consumed - 1;
+                mbar_wait(bar_empty + 8 * (int)(g % FI_STAGES), (uint32_t)(g / FI_STAGES) & 1u,
+                          1000000000LL);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ epilogue warps
+        const int quarter = warp & 3, cg = warp >> 2;       // TMEM lane quarter, k block
+        const int r = quarter * 32 + lane;                  // tile row = TMEM lane
+        const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+        const bool lead = cg == 0;                          // builds X0, keeps the ensemble
+        const int et = threadIdx.x;                         // 0 .. 32 * FI_EPI_WARPS - 1
+        // stages member k's biases and feature statistics into parameter slot k mod 4,
+        // then waits (bounded) until every epilogue thread has written its share
+        uint32_t pp = 0;
+        bool ok = true;
+        auto stage = [&](int k) {
+            const uint8_t* mb = A.model + (size_t)k * A.member_bytes;
+            const float* th = reinterpret_cast<const float*>(mb + A.theta_b);
+            const float* st = reinterpret_cast<const float*>(mb + A.stats_b);
+            float* dst = par + (k % FI_PAR_SLOTS) * FI_PAR_FLOATS;
+            for (int i = et; i < FI_PAR_FLOATS; i += 32 * FI_EPI_WARPS) {
+                float v;
+                if (i < N_LAYERS * 256) {
+                    const int l = i >> 8, c = i & 255;
+                    v = (c < real_out(l)) ? __ldg(th + A.b_off[l] + c) : 0.f;
+                } else {
+                    v = __ldg(st + (i - N_LAYERS * 256));   // mean[16] | std[16]
+                }
+                dst[i] = v;
+            }
+            mbar_arrive(bar_p);
+            if (!mbar_wait(bar_p, pp, A.wait_limit)) ok = false;
+            pp ^= 1u;
+        };
+        const bool staged_once = M <= FI_PAR_SLOTS;
+        if (staged_once)
+            for (int k = 0; k < M && ok; ++k) stage(k);
+        uint32_t pacc = 0;
+        for (long long t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+            const long long row = t * 128 + r;
+            const bool live = row < A.n_rows;
+            float x[N_FEAT];
+#pragma unroll
+            for (int f = 0; f < N_FEAT; ++f)
+                x[f] = (lead && live) ? A.feat[row * N_FEAT + f] : 0.f;
+            float mean[3] = {0.f, 0.f, 0.f}, lo[3] = {3.f, 3.f, 3.f}, hi[3] = {-3.f, -3.f, -3.f};
+            for (int k = 0; k < M && ok; ++k) {
+                if (!staged_once) {
+                    stage(k);
+                    if (!ok) break;
+                }
+                const float* pk_par = par + (k % FI_PAR_SLOTS) * FI_PAR_FLOATS;
+                if (lead) {   // layer-0 input: standardised features in columns 0-8, zeros to 63
+                    const float* st = pk_par + N_LAYERS * 256;
+                    float z[N_FEAT];
+#pragma unroll
+                    for (int f = 0; f < N_FEAT; ++f) z[f] = (x[f] - st[f]) / st[16 + f];
+                    fi_store_chunk(H, r, 0, 0,
+                                   make_uint4(pack_bf16(z[0], z[1]), pack_bf16(z[2], z[3]),
+                                              pack_bf16(z[4], z[5]), pack_bf16(z[6], z[7])));
+                    fi_store_chunk(H, r, 0, 1, make_uint4(pack_bf16(z[8], 0.f), 0u, 0u, 0u));
+#pragma unroll
+                    for (int j = 2; j < 8; ++j)
+                        fi_store_chunk(H, r, 0, j, make_uint4(0u, 0u, 0u, 0u));
+                    fence_proxy_async_smem();
+                }
+                tc_fence_before();
+                mbar_arrive(bar_a);
+                for (int l = 0; l < N_LAYERS; ++l) {
+                    if (!mbar_wait(bar_acc, pacc, A.wait_limit)) {
+                        ok = false;
+                        break;
+                    }
+                    pacc ^= 1u;
+                    tc_fence_after();
+                    const float* bias = pk_par + l * 256;
+                    if (l < 4) {
+#pragma unroll 1
+                        for (int hh = 0; hh < 2 * FI_KB_PER; ++hh) {
+                            const int kb = cg * FI_KB_PER + (hh >> 1), h = hh & 1;
+                            const int c0 = kb * 64 + h * 32;
+                            float v[32];
+                            tmem_ld32(trow + (uint32_t)c0, v);
+                            uint32_t pk[16];
+#pragma unroll
+                            for (int i = 0; i < 32; i += 4) {
+                                const float4 b4 = *reinterpret_cast<const float4*>(bias + c0 + i);
+                                pk[i / 2] = pack_bf16(gelu_f(v[i] + b4.x), gelu_f(v[i + 1] + b4.y));
+                                pk[i / 2 + 1] = pack_bf16(gelu_f(v[i + 2] + b4.z),
+                                                          gelu_f(v[i + 3] + b4.w));
+                            }
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                fi_store_chunk(H, r, kb, h * 4 + q,
+                                               make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2],
+                                                          pk[4 * q + 3]));
+                        }
+                        fence_proxy_async_smem();
+                        tc_fence_before();
+                        mbar_arrive(bar_a);
+                    } else if (lead) {
+                        float v[16];
+                        tmem_ld16(trow, v);
+                        float lg[N_OUT], mx = -3.0e38f;
+#pragma unroll
+                        for (int c = 0; c < N_OUT; ++c) {
+                            lg[c] = v[c] + bias[c];
+                            mx = fmaxf(mx, lg[c]);
+                        }
+                        float p[N_OUT], sum = 0.f;
+#pragma unroll
+                        for (int c = 0; c < N_OUT; ++c) {
+                            p[c] = expf(lg[c] - mx);
+                            sum += p[c];
+                        }
+                        const float inv = 1.0f / sum;
+#pragma unroll
+                        for (int c = 0; c < N_OUT; ++c) {
+                            const float q = p[c] * inv;
+                            mean[c] += q;
+                            lo[c] = fminf(lo[c], q);
+                            hi[c] = fmaxf(hi[c], q);
+                        }
+                    }
+                }
+                if (abort_flag) ok = false;
+            }
+            if (ok && lead && live) {
+                float spr = 0.f;
+#pragma unroll
+                for (int c = 0; c < N_OUT; ++c) {
+                    A.rat[row * 3 + c] = mean[c] / (float)M;
+                    spr = fmaxf(spr, hi[c] - lo[c]);
+                }
+                if (A.spread) A.spread[row] = spr;
+                if (A.needs) {
+                    const float* st0 = reinterpret_cast<const float*>(A.model + A.stats_b);
+                    bool out = spr > A.thr;
+#pragma unroll
+                    for (int f = 0; f < N_FEAT; ++f)
+                        out = out || !(x[f] >= __ldg(st0 + 32 + f) && x[f] <= __ldg(st0 + 48 + f));
+                    A.needs[row] = out ? 1 : 0;
+                }
+            }
+        }
+        if (!ok) atomicOr(&A.status[ST_CALL], DEV_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
 // ----------------------------------------------------------------------- small kernels
@@ -480,15 +880,6 @@ __global__ void gather_kernel(const float* feat, const float* targets, long long
 }
 
 // Inference input: standardised features of rows [r0, r0+n) -> X0 [n][64].
-__global__ void normalize_kernel(const float* feat, long long r0, long long n, const float* stats,
-                                 bf16* X0) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        for (int f = 0; f < N_FEAT; ++f)
-            X0[i * IN_PAD + f] = __float2bfloat16((feat[(r0 + i) * N_FEAT + f] - stats[f]) / stats[16 + f]);
-    }
-}
-
 // Column sums of a bf16 [rows][ld] matrix (bias gradients): one block per 64 columns.
 __global__ void colsum_kernel(const bf16* G, int rows, int ld, int ncols, float* out) {
     __shared__ float part[4][64];
@@ -505,7 +896,7 @@ __global__ void colsum_kernel(const bf16* G, int rows, int ld, int ncols, float*
 
 struct AdamArgs {
     float *theta, *m, *v;
-    bf16 *wb, *wt;
+    bf16 *wb, *wt, *wi;
     long long w_off[N_LAYERS], b_off[N_LAYERS], wb_off[N_LAYERS], wt_off[N_LAYERS];
     const float* part[N_LAYERS];   // split-K partials of dW_l [splits][out][in]
     const float* db[N_LAYERS];     // bias gradients [out]
@@ -544,8 +935,11 @@ __global__ void adam_kernel(AdamArgs A, long long P) {
         const float th = A.theta[idx] - A.lr * (mm / A.c1) / (sqrtf(vv / A.c2) + A.eps);
         A.theta[idx] = th;
         if (e >= 0) {
-            A.wb[A.wb_off[l] + e] = __float2bfloat16(th);
-            if (l > 0) A.wt[A.wt_off[l] + (long long)i * out_p + o] = __float2bfloat16(th);
+            const bf16 tb = __float2bfloat16(th);
+            A.wb[A.wb_off[l] + e] = tb;
+            if (l > 0) A.wt[A.wt_off[l] + (long long)i * out_p + o] = tb;
+            const long long ii = img_index(l, o, i);
+            if (ii >= 0) A.wi[ii] = tb;
         }
     }
 }
@@ -575,8 +969,9 @@ __global__ void grad_kernel(AdamArgs A, long long P, float* grad) {
 
 // He-uniform initial weights (hash of seed, member, index -> uniform), zero biases,
 // zero Adam state, bf16 copies, step 0.
-__global__ void init_kernel(float* theta, float* m, float* v, bf16* wb, bf16* wt, int* step,
-                            unsigned seed, unsigned member, AdamArgs lay, long long P) {
+__global__ void init_kernel(float* theta, float* m, float* v, bf16* wb, bf16* wt, bf16* wi,
+                            int* step, unsigned seed, unsigned member, AdamArgs lay,
+                            long long P) {
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
          idx += (long long)gridDim.x * blockDim.x) {
         int l = 0;
@@ -601,8 +996,11 @@ __global__ void init_kernel(float* theta, float* m, float* v, bf16* wb, bf16* wt
         m[idx] = 0.f;
         v[idx] = 0.f;
         if (e >= 0) {
-            wb[lay.wb_off[l] + e] = __float2bfloat16(th);
-            if (l > 0) wt[lay.wt_off[l] + (long long)i * out_p + o] = __float2bfloat16(th);
+            const bf16 tb = __float2bfloat16(th);
+            wb[lay.wb_off[l] + e] = tb;
+            if (l > 0) wt[lay.wt_off[l] + (long long)i * out_p + o] = tb;
+            const long long ii = img_index(l, o, i);
+            if (ii >= 0) wi[ii] = tb;
         }
         if (idx == 0) step[0] = 0;
     }
@@ -612,7 +1010,7 @@ __global__ void init_kernel(float* theta, float* m, float* v, bf16* wb, bf16* wt
 // the real rows and columns are stored as 0; Adam state and step are reset and the bf16
 // copies rebuilt.
 __global__ void load_kernel(const float* src, float* theta, float* m, float* v, bf16* wb,
-                            bf16* wt, int* step, AdamArgs lay, long long P) {
+                            bf16* wt, bf16* wi, int* step, AdamArgs lay, long long P) {
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
          idx += (long long)gridDim.x * blockDim.x) {
         int l = 0;
@@ -633,44 +1031,13 @@ __global__ void load_kernel(const float* src, float* theta, float* m, float* v, 
         m[idx] = 0.f;
         v[idx] = 0.f;
         if (e >= 0) {
-            wb[lay.wb_off[l] + e] = __float2bfloat16(th);
-            if (l > 0) wt[lay.wt_off[l] + (long long)i * out_p + o] = __float2bfloat16(th);
+            const bf16 tb = __float2bfloat16(th);
+            wb[lay.wb_off[l] + e] = tb;
+            if (l > 0) wt[lay.wt_off[l] + (long long)i * out_p + o] = tb;
+            const long long ii = img_index(l, o, i);
+            if (ii >= 0) wi[ii] = tb;
         }
         if (idx == 0) step[0] = 0;
-    }
-}
-
-// Mean over members, spread = max over R, A, T of (max - min across members), and the
-// fallback flag: spread > threshold or any raw feature outside the training range.
-__global__ void ensemble_kernel(const float* probs, int n_members, long long n, long long r0,
-                                const float* feat, const float* stats, float* rat, float* spread,
-                                unsigned char* needs, float thr) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        float mean[3] = {0.f, 0.f, 0.f}, lo[3] = {3.f, 3.f, 3.f}, hi[3] = {-3.f, -3.f, -3.f};
-        for (int k = 0; k < n_members; ++k) {
-            const float4 p = *reinterpret_cast<const float4*>(probs + ((long long)k * n + i) * 4);
-            const float q[3] = {p.x, p.y, p.z};
-            for (int c = 0; c < 3; ++c) {
-                mean[c] += q[c];
-                lo[c] = fminf(lo[c], q[c]);
-                hi[c] = fmaxf(hi[c], q[c]);
-            }
-        }
-        float spr = 0.f;
-        for (int c = 0; c < 3; ++c) {
-            rat[(r0 + i) * 3 + c] = mean[c] / (float)n_members;
-            spr = fmaxf(spr, hi[c] - lo[c]);
-        }
-        if (spread) spread[r0 + i] = spr;
-        if (needs) {
-            bool out = spr > thr;
-            for (int f = 0; f < N_FEAT; ++f) {
-                const float x = feat[(r0 + i) * N_FEAT + f];
-                out = out || !(x >= stats[32 + f] && x <= stats[48 + f]);
-            }
-            needs[r0 + i] = out ? 1 : 0;
-        }
     }
 }
 
@@ -850,6 +1217,7 @@ static AdamArgs layout_args(const MemberPtrs& mp) {
     a.v = mp.v;
     a.wb = mp.wb;
     a.wt = mp.wt;
+    a.wi = mp.wi;
     for (int l = 0; l < N_LAYERS; ++l) {
         a.w_off[l] = LAY.w_off[l];
         a.b_off[l] = LAY.b_off[l];
@@ -963,74 +1331,38 @@ static fos_status train_step(Workspace* ws, const MemberPtrs& mp, const float* f
 }
 
 // Inference workspace: rows per chunk.
-struct InferWs {
-    long long rows = 0;
-    int members = 0;
-    void* mem = nullptr;
-    bf16 *X0, *H[2];
-    float* P;
-};
-static InferWs g_iws[64];
-constexpr long long INFER_CHUNK = 1 << 19;
-
-static fos_status ensure_infer_ws(int dev, int members) {
-    InferWs& w = g_iws[dev];
-    if (w.mem && w.members >= members) return FOS_OK;
-    if (w.mem) {
-        FOS_CUDA_TRY(cudaDeviceSynchronize());
-        cudaFree(w.mem);
-        w.mem = nullptr;
-    }
-    const long long R = INFER_CHUNK;
-    const size_t bx = (size_t)R * IN_PAD * 2, bh = (size_t)R * HID * 2,
-                 bp = (size_t)members * R * 4 * 4;
-    void* mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, bx + 2 * bh + bp + 4096);
-    if (e != cudaSuccess) return from_cuda(e);
-    FOS_CUDA_TRY(cudaMemset(mem, 0, bx));
-    w.mem = mem;
-    w.X0 = (bf16*)mem;
-    w.H[0] = (bf16*)((char*)mem + bx);
-    w.H[1] = (bf16*)((char*)mem + bx + bh);
-    w.P = (float*)((char*)mem + bx + 2 * bh);
-    w.rows = R;
-    w.members = members;
-    return FOS_OK;
-}
-
 static fos_status predict(Workspace* ws, void* model, int n_members, const float* feat,
                           long long n_rows, float* rat, float* spread, unsigned char* needs,
-                          float thr, cudaStream_t s) {
-    InferWs& w = g_iws[ws->device];
-    for (long long r0 = 0; r0 < n_rows; r0 += INFER_CHUNK) {
-        const long long n = (n_rows - r0 < INFER_CHUNK) ? n_rows - r0 : INFER_CHUNK;
-        for (int k = 0; k < n_members; ++k) {
-            MemberPtrs mp = member(model, k);
-            normalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(feat, r0, n, mp.stats, w.X0);
-            FOS_CUDA_TRY(cudaGetLastError());
-            for (int l = 0; l < 4; ++l) {
-                Operand A = (l == 0) ? Operand{w.X0, n, IN_PAD, IN_PAD}
-                                     : Operand{w.H[(l - 1) & 1], n, HID, HID};
-                Operand Bm{mp.wb + LAY.wb_off[l], HID, lay_in(l), lay_in(l)};
-                GemmArgs g = gargs(ws->status);
-                g.M = (int)n; g.N = HID; g.bias = mp.theta + LAY.b_off[l];
-                g.out_h = w.H[l & 1]; g.ldh = HID;
-                fos_status st = gemm<256, INFER_HIDDEN>(A, Bm, 1, g, s);
-                if (st != FOS_OK) return st;
-            }
-            GemmArgs g = gargs(ws->status);
-            g.M = (int)n; g.N = OUT_PAD; g.bias = mp.theta + LAY.b_off[4];
-            g.out_f = w.P + (long long)k * n * 4;
-            fos_status st = gemm<64, INFER_OUT>(Operand{w.H[1], n, HID, HID},
-                                                Operand{mp.wb + LAY.wb_off[4], OUT_PAD, HID, HID},
-                                                1, g, s);
-            if (st != FOS_OK) return st;
-        }
-        MemberPtrs m0 = member(model, 0);
-        ensemble_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-            w.P, n_members, n, r0, feat, m0.stats, rat, spread, needs, thr);
-        FOS_CUDA_TRY(cudaGetLastError());
+                          float thr, bool stall, cudaStream_t s) {
+    static bool attr_set[64] = {};
+    if (!attr_set[ws->device]) {
+        FOS_CUDA_TRY(cudaFuncSetAttribute(infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          FI_SMEM));
+        attr_set[ws->device] = true;
     }
+    InferArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.feat = feat;
+    a.n_rows = n_rows;
+    a.n_members = n_members;
+    a.model = (const uint8_t*)model;
+    a.member_bytes = LAY.bytes;
+    a.theta_b = LAY.theta_b;
+    a.stats_b = LAY.stats_b;
+    a.wi_b = LAY.wi_b;
+    for (int l = 0; l < N_LAYERS; ++l) a.b_off[l] = LAY.b_off[l];
+    a.rat = rat;
+    a.spread = spread;
+    a.needs = needs;
+    a.thr = thr;
+    a.status = ws->status;
+    a.wait_limit = stall ? 2000000LL : 4000000000LL;
+    a.test_stall = stall ? 1 : 0;
+    const long long tiles = (n_rows + 127) / 128;
+    long long grid = (long long)ws->num_sms * FI_CTAS;
+    if (grid > tiles) grid = tiles;
+    infer_kernel<<<(unsigned)grid, FI_THREADS, FI_SMEM, s>>>(a);
+    FOS_CUDA_TRY(cudaGetLastError());
     return FOS_OK;
 }
 
@@ -1076,7 +1408,7 @@ fos_status fos_surrogate_init(void* model, int n_members, unsigned long long see
         mlp::AdamArgs lay = mlp::layout_args(mp);
         FOS_CUDA_TRY(cudaMemsetAsync((char*)model + (size_t)k * mlp::LAY.bytes, 0, mlp::LAY.bytes, s));
         mlp::init_kernel<<<(unsigned)((mlp::LAY.P + 255) / 256), 256, 0, s>>>(
-            mp.theta, mp.m, mp.v, mp.wb, mp.wt, mp.step, (unsigned)(seed ^ (seed >> 32)),
+            mp.theta, mp.m, mp.v, mp.wb, mp.wt, mp.wi, mp.step, (unsigned)(seed ^ (seed >> 32)),
             (unsigned)k, lay, mlp::LAY.P);
         FOS_CUDA_TRY(cudaGetLastError());
         FOS_CUDA_TRY(cudaMemcpyAsync(mp.stats, feat_stats, 64 * sizeof(float),
@@ -1101,7 +1433,7 @@ fos_status fos_surrogate_load(void* model, int member, const float* theta,
     FOS_CUDA_TRY(cudaMemsetAsync((char*)model + (size_t)member * mlp::LAY.bytes, 0,
                                  mlp::LAY.bytes, s));
     mlp::load_kernel<<<(unsigned)((mlp::LAY.P + 255) / 256), 256, 0, s>>>(
-        theta, mp.theta, mp.m, mp.v, mp.wb, mp.wt, mp.step, lay, mlp::LAY.P);
+        theta, mp.theta, mp.m, mp.v, mp.wb, mp.wt, mp.wi, mp.step, lay, mlp::LAY.P);
     FOS_CUDA_TRY(cudaGetLastError());
     FOS_CUDA_TRY(cudaMemcpyAsync(mp.stats, feat_stats, 64 * sizeof(float),
                                  cudaMemcpyHostToDevice, s));
@@ -1227,11 +1559,10 @@ fos_status fos_surrogate_predict(void* model, int n_members, const float* featur
     Workspace* ws = nullptr;
     fos_status st = mlp::prep(&ws);
     if (st != FOS_OK) return st;
-    st = mlp::ensure_infer_ws(ws->device, n_members);
-    if (st != FOS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     FOS_CUDA_TRY(cudaMemsetAsync(ws->status + ST_CALL, 0, sizeof(unsigned), s));
-    st = mlp::predict(ws, model, n_members, features, n_rows, rat, spread, needs_mc, threshold, s);
+    st = mlp::predict(ws, model, n_members, features, n_rows, rat, spread, needs_mc, threshold,
+                      (flags & FOS_TEST_STALL) != 0, s);
     if (st != FOS_OK) return st;
     return finish_call(ws, s, flags);
 }

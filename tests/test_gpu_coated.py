@@ -63,13 +63,18 @@ def test_mixed_species_edge_cases(orc):
 
 
 def test_zero_core_is_the_homogeneous_path():
+    """A zero core takes the homogeneous-sphere evaluation.  The core-shell entry runs it
+    in another kernel instantiation, whose multiply-add contraction may differ, so the
+    two agree to a few ulps rather than bit for bit."""
     m = W.hollow_silica_media(n_wl=37)
     m["core_radius"] = np.zeros_like(m["core_radius"])
     cs = gpu_mie(m)
     plain = {k: v for k, v in m.items() if k not in ("core_radius", "n_core")}
     g = gpu_mie(plain)
-    for k in ("mu_s", "mu_a", "g", "q_ext", "q_sca", "g_species"):
-        assert np.array_equal(cs[k], g[k]), k
+    for k in ("mu_s", "g", "q_ext", "q_sca", "g_species"):
+        assert np.all(np.abs(cs[k] - g[k]) <= 1e-13 * np.abs(g[k])), k
+    # mu_a is a difference of extinction and scattering (Eqs. 13-14): bounded by extinction
+    assert np.all(np.abs(cs["mu_a"] - g["mu_a"]) <= 1e-13 * (g["mu_s"] + g["mu_a"]))
 
 
 def test_invalid_core_radius_and_range():

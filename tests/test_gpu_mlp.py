@@ -327,3 +327,62 @@ def test_in_kernel_wait_gives_up_and_reports_timeout():
     assert st == fos.FOS_OK
     ref = A.float().double().cpu().numpy() @ B.float().double().cpu().numpy().T
     assert np.allclose(C[0].double().cpu().numpy(), ref, rtol=1e-4, atol=1e-3)
+
+
+def test_fused_ensemble_matches_oracle_on_a_ragged_batch():
+    """Three members with host-drawn parameters over 50,001 rows (390 full tiles and a
+    ragged one, more tiles than CTAs): mean, spread and fallback flags on sampled rows
+    against the bf16-mirrored oracle forward of each member."""
+    n = 50001
+    x, _ = _data(n, 6)
+    st, mean, std = _stats(x)
+    mb = fos.fos_surrogate_model_bytes()
+    model = torch.zeros(3 * mb, dtype=torch.uint8, device="cuda")
+    params = []
+    for k in range(3):
+        theta, ps = _host_theta(100 + k)
+        fos.check(fos.fos_surrogate_load(model[k * mb:(k + 1) * mb], 0,
+                                         torch.as_tensor(theta).cuda(), st), "load")
+        params.append(ps)
+    xx = x.copy()
+    xx[17, 2] = 5.0          # outside the training range of feature 2
+    feats = torch.as_tensor(xx, dtype=torch.float32).cuda().contiguous()
+    rat = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    spread = torch.zeros(n, dtype=torch.float32, device="cuda")
+    needs = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    thr = 0.05
+    fos.check(fos.fos_surrogate_predict(model, 3, feats, rat, spread, needs, thr), "predict")
+    rng = np.random.default_rng(3)
+    rows = np.unique(np.concatenate([rng.integers(0, n, 1500), [0, 17, n - 1, n - 2]]))
+    xs = np.asarray(xx, np.float32).astype(np.float64)[rows]
+    outs = np.stack([M.forward(ps, xs, mean.astype(np.float32), std.astype(np.float32),
+                               round_fn=M.bf16_round) for ps in params])
+    got_rat = rat.double().cpu().numpy()[rows]
+    got_spr = spread.double().cpu().numpy()[rows]
+    assert np.max(np.abs(got_rat - outs.mean(axis=0))) < 6e-3
+    want_spr = (outs.max(axis=0) - outs.min(axis=0)).max(axis=1)
+    assert np.max(np.abs(got_spr - want_spr)) < 1.2e-2
+    got_need = needs.cpu().numpy()[rows]
+    clear = np.abs(want_spr - thr) > 1.2e-2          # away from the threshold
+    lo, hi = st[32:41], st[48:57]
+    out_rng = np.any((xs < lo) | (xs > hi), axis=1)
+    want_need = (want_spr > thr) | out_rng
+    assert np.array_equal(got_need[clear], want_need[clear])
+    assert got_need[list(rows).index(17)] == 1
+
+
+def test_fused_inference_wait_gives_up_and_reports_timeout():
+    """The fused inference kernel with its first weight copy withheld (test flag): the
+    bounded waits run out, the kernel drains and returns FOS_ERR_TIMEOUT, and the next
+    call succeeds with the same results as before."""
+    x, _ = _data(3000, 7)
+    st, _, _ = _stats(x)
+    model, _, _ = _loaded_model(st, 21)
+    feats = torch.as_tensor(x, dtype=torch.float32).cuda().contiguous()
+    r1 = torch.zeros((3000, 3), dtype=torch.float32, device="cuda")
+    fos.check(fos.fos_surrogate_predict(model, 1, feats, r1), "predict")
+    r2 = torch.zeros((3000, 3), dtype=torch.float32, device="cuda")
+    assert fos.fos_surrogate_predict(model, 1, feats, r2, flags=fos.FOS_TEST_STALL) == \
+        fos.FOS_ERR_TIMEOUT
+    fos.check(fos.fos_surrogate_predict(model, 1, feats, r2), "predict again")
+    assert torch.equal(r1, r2)
