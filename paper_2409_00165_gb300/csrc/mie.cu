@@ -407,7 +407,10 @@ static fos_status mie_impl(int n_wl, const double* wl, int n_groups, const doubl
     const long long n_eval = (long long)n_species * n_wl;
     const int block = 128;
     const int n_cols = core_radius ? 4 : 2;   // downward log-derivative columns per thread
-    long long T = (long long)ws->num_sms * 128 * 2 / n_cols;
+    // 4 blocks of 128 threads per SM, so that several warps hide the FP64 latency; the
+    // scratch holds the log-derivative columns of every thread (n_cols x 512 orders x
+    // 16 B each)
+    long long T = (long long)ws->num_sms * 128 * 4;
     const long long need_T = ((n_eval + block - 1) / block) * block;
     if (need_T < T) T = need_T > 0 ? need_T : block;
     const size_t scratch_bytes = (size_t)n_cols * FOS_MIE_MAX_TERMS * T * sizeof(double2);

@@ -68,15 +68,15 @@ struct Layout {
 
 // Weight image: the B operands of the fused inference kernel, already in the 128-byte-
 // swizzled K-major layout a stage of shared memory holds, so that one untiled bulk copy
-// fills a stage.  Layers 0-3 come in blocks of 128 output rows x 64 inputs (16 KB): layer
-// 0 as 2 blocks (row halves), layers 1-3 as 8 blocks ordered (k block, row half).  Layer 4
-// keeps its first 16 output rows (3 real) in 4 blocks of 16 x 64 (2 KB), one per k block.
-constexpr long long IMG_BLK = 128 * 64;          // elements of a 16 KB block
+// fills a stage.  Layers 0-3 come in blocks of all 256 output rows x 64 inputs (32 KB),
+// one per k block (1 for layer 0, 4 for layers 1-3).  Layer 4 keeps its first 16 output
+// rows (3 real) as 4 blocks of 16 x 64 (2 KB), one per k block, copied as one stage.
+constexpr long long IMG_BLK = 256 * 64;          // elements of a 32 KB block
 constexpr long long IMG_L4_BLK = 16 * 64;        // elements of a 2 KB block
 __host__ __device__ constexpr long long img_off(int l) {
-    return l == 0 ? 0 : (l == 4 ? 26 * IMG_BLK : (2 + 8 * (l - 1)) * IMG_BLK);
+    return l == 0 ? 0 : (l == 4 ? 13 * IMG_BLK : (1 + 4 * (l - 1)) * IMG_BLK);
 }
-constexpr long long IMG_ELEMS = 26 * IMG_BLK + 4 * IMG_L4_BLK;
+constexpr long long IMG_ELEMS = 13 * IMG_BLK + 4 * IMG_L4_BLK;
 constexpr int IMG_ROWS_L4 = 16;
 
 // Element index in the image of weight (l, o, i), or -1 when the image leaves it out.
@@ -84,14 +84,9 @@ constexpr int IMG_ROWS_L4 = 16;
 // the k block) sits at chunk position j ^ (n mod 8).
 __host__ __device__ inline long long img_index(int l, int o, int i) {
     const int kb = i >> 6, c = i & 63;
-    if (l == 4) {
-        if (o >= IMG_ROWS_L4) return -1;
-        return img_off(4) + (long long)kb * IMG_L4_BLK + o * 64 +
-               ((((c >> 3) ^ (o & 7)) << 3) | (c & 7));
-    }
-    const int nh = o >> 7, n = o & 127;
-    const int blk = (l == 0) ? nh : kb * 2 + nh;
-    return img_off(l) + (long long)blk * IMG_BLK + n * 64 + ((((c >> 3) ^ (n & 7)) << 3) | (c & 7));
+    const long long blk = (l == 4) ? IMG_L4_BLK : IMG_BLK;
+    if (l == 4 && o >= IMG_ROWS_L4) return -1;
+    return img_off(l) + (long long)kb * blk + o * 64 + ((((c >> 3) ^ (o & 7)) << 3) | (c & 7));
 }
 
 static Layout make_layout() {
@@ -392,36 +387,32 @@ __global__ void __launch_bounds__(128, 1)
 // -> ensemble mean, spread and fallback flag.  Activations never leave the SM: each
 // hidden layer's epilogue writes its BF16 output straight into shared memory in the
 // 128-byte-swizzled K-major layout that the next layer's MMA reads as its A operand.
-// Weights stream from the model's weight image (L2-resident) through a 10-slot ring of
-// 16 KB stages filled by untiled bulk copies: a whole hidden layer (8 stages) is fetched
-// while the previous layer's epilogue runs, so the MMAs of a layer issue back to back.
+// Weights stream from the model's weight image (L2-resident) through a 4-slot ring of
+// 32 KB stages (one k block of a layer, all 256 output rows) filled by untiled bulk
+// copies, so a whole hidden layer is fetched while the previous layer's epilogue runs.
 //
-// Roles: the epilogue warps (FI_EPI_WARPS, a multiple of 4); warp w reads TMEM lanes
-// 32 (w mod 4) .. +31 (its tile rows) and the columns of its column group w / 4, which are
-// whole k blocks of the next layer's input.  The warps with w < 4 also build the layer-0
-// input and keep the ensemble sums of their rows.  Lane 0 of the last warp issues the
-// bulk copies and the MMAs.
-// Barriers: full/empty per ring slot; `acc` (one MMA commit per layer: accumulator
-// ready); `a_ready` (512 arrivals: the A operand is written and the accumulator read
-// out).  Every wait is bounded; a wait that gives up sets DEV_TIMEOUT and the kernel
-// drains its copies and MMAs and returns.
-constexpr int FI_CTAS = 1;                               // CTAs per SM
-constexpr int FI_STAGES = 8;
-constexpr int FI_SLOT = 16384;
+// Roles: the epilogue warps 0-15; warp w reads TMEM lanes 32 (w mod 4) .. +31 (its tile
+// rows) and columns 64 (w / 4) .. +63, which are exactly k block w / 4 of the next
+// layer's input.  The warps with w < 4 also build the layer-0 input and keep the
+// ensemble sums of their rows.  Lane 0 of warp 16 issues the bulk copies; lane 0 of
+// warp 17 issues the MMAs.  Barriers: full/empty per ring slot; `acc` (one MMA commit
+// per layer: accumulator ready); `a_ready` (512 arrivals: the A operand is written and the
+// accumulator read out); `par` (parameter staging).  Every wait is bounded; a wait that
+// gives up sets DEV_TIMEOUT, and the kernel drains its copies and MMAs and returns.
+constexpr int FI_STAGES = 4;
+constexpr int FI_SLOT = 32768;
 constexpr int FI_H_BYTES = 4 * 128 * 128;               // 128 rows x 256 bf16 (4 k blocks)
-constexpr int FI_ITEMS = 2 + 8 * 3 + 4;                  // ring items per tile and member
-// Per-member parameters staged in shared memory: biases of the 5 layers (256 each) and
-// the feature means and standard deviations (16 each); slots for up to 4 members.
+constexpr int FI_ITEMS = 1 + 4 * 3 + 1;                  // ring items per tile and member
+// Per-member parameters staged in shared memory: biases of the 5 layers (256 each; the
+// hidden layers' halved, see the epilogue) and the feature means and standard deviations
+// (16 each); slots for up to 4 members.
 constexpr int FI_PAR_FLOATS = N_LAYERS * 256 + 32;
 constexpr int FI_PAR_SLOTS = 4;
 constexpr int FI_PAR_BYTES = FI_PAR_SLOTS * FI_PAR_FLOATS * 4;
-constexpr int FI_BAR_BYTES = 8 * (2 * FI_STAGES + 3) + 16;
+constexpr int FI_BAR_BYTES = 8 * (2 * FI_STAGES + 4) + 16;
 constexpr int FI_SMEM = FI_H_BYTES + FI_STAGES * FI_SLOT + FI_PAR_BYTES + FI_BAR_BYTES;
 constexpr int FI_EPI_WARPS = 16;
-constexpr int FI_THREADS = 32 * (FI_EPI_WARPS + 1);
-constexpr int FI_CG = FI_EPI_WARPS / 4;                  // column groups of epilogue warps
-constexpr int FI_KB_PER = 4 / FI_CG;                     // k blocks each epilogue warp writes
-static_assert(FI_EPI_WARPS % 4 == 0 && 4 % FI_CG == 0, "epilogue warps: 4, 8 or 16");
+constexpr int FI_THREADS = 32 * (FI_EPI_WARPS + 2);
 
 struct InferArgs {
     const float* feat;          // raw features [n_rows][9]
@@ -439,31 +430,20 @@ struct InferArgs {
     int test_stall;             // test only: the first weight copy is never issued
 };
 
-// Ring item q of a tile-member: its layer, k block, row half, source and size.
-struct FiItem {
-    int layer, kb, nh;
-    long long src;   // element offset in the weight image
-    uint32_t bytes;
-};
-__device__ __forceinline__ FiItem fi_item(int q) {
-    FiItem it;
-    if (q < 2) {
-        it.layer = 0; it.kb = 0; it.nh = q;
-        it.src = img_off(0) + (long long)q * IMG_BLK;
-        it.bytes = FI_SLOT;
-    } else if (q < 26) {
-        const int j = q - 2;
-        it.layer = 1 + j / 8;
-        it.kb = (j % 8) >> 1;
-        it.nh = j & 1;
-        it.src = img_off(it.layer) + (long long)(j % 8) * IMG_BLK;
-        it.bytes = FI_SLOT;
+// Ring item q (0..13) of a tile-member: layer, k block, source offset in the image
+// (elements) and size.  Item 13 is layer 4 whole (its four 2 KB k blocks).
+__device__ __forceinline__ void fi_item(int q, int& layer, int& kb, long long& src,
+                                        uint32_t& bytes) {
+    if (q == 0) {
+        layer = 0; kb = 0;
+    } else if (q < 13) {
+        layer = 1 + (q - 1) / 4;
+        kb = (q - 1) & 3;
     } else {
-        it.layer = 4; it.kb = q - 26; it.nh = 0;
-        it.src = img_off(4) + (long long)(q - 26) * IMG_L4_BLK;
-        it.bytes = (uint32_t)(IMG_L4_BLK * 2);
+        layer = 4; kb = 0;
     }
-    return it;
+    src = img_off(layer) + (long long)kb * IMG_BLK;
+    bytes = (layer == 4) ? (uint32_t)(4 * IMG_L4_BLK * 2) : (uint32_t)FI_SLOT;
 }
 
 // Writes 8 bf16 (one 16-byte chunk) of row r, columns 8j..8j+7 of k block kb, into the
@@ -479,8 +459,16 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&p);
 }
+// GELU (tanh form) of z = 2 hz from hz = z/2 = acc/2 + bias/2: hz (1 + tanh(u)) with
+// u = z (c0 + c1 z^2) = hz (2 c0 + 8 c1 hz^2), c0 = sqrt(2/pi), c1 = 0.044715 c0.
+__device__ __forceinline__ float gelu_half(float acc, float half_bias) {
+    const float hz = fmaf(0.5f, acc, half_bias);
+    const float h2 = hz * hz;
+    const float t = tanh_fast(hz * fmaf(0.2854192648f, h2, 1.5957691216f));
+    return fmaf(hz, t, hz);
+}
 
-__global__ void __launch_bounds__(FI_THREADS, FI_CTAS) infer_kernel(InferArgs A) {
+__global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
     extern __shared__ __align__(1024) uint8_t fi_smem[];
     const uint32_t base = smem_u32(fi_smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -489,13 +477,15 @@ __global__ void __launch_bounds__(FI_THREADS, FI_CTAS) infer_kernel(InferArgs A)
     float* par = reinterpret_cast<float*>(fi_smem + FI_H_BYTES + FI_STAGES * FI_SLOT);
     const uint32_t bars = ring + FI_STAGES * FI_SLOT + FI_PAR_BYTES;
     const uint32_t bar_full = bars, bar_empty = bars + 8 * FI_STAGES;
-    const uint32_t bar_acc = bars + 16 * FI_STAGES, bar_a = bar_acc + 8;
+    // acc_lo / acc_hi: accumulator columns 0-127 / 128-255 of the layer complete
+    const uint32_t bar_acc_lo = bars + 16 * FI_STAGES, bar_acc_hi = bar_acc_lo + 8;
+    const uint32_t bar_a = bar_acc_hi + 8;
     const uint32_t bar_p = bar_a + 8;   // parameter staging done (epilogue warps)
     const uint32_t tslot = bar_p + 8;
     uint8_t* bars_g = fi_smem + FI_H_BYTES + FI_STAGES * FI_SLOT + FI_PAR_BYTES;
     volatile uint32_t* tslot_ptr =
-        reinterpret_cast<volatile uint32_t*>(bars_g + 16 * FI_STAGES + 24);
-    volatile int& abort_flag = *reinterpret_cast<volatile int*>(bars_g + 16 * FI_STAGES + 28);
+        reinterpret_cast<volatile uint32_t*>(bars_g + 16 * FI_STAGES + 32);
+    volatile int& abort_flag = *reinterpret_cast<volatile int*>(bars_g + 16 * FI_STAGES + 36);
 
     if ((base & 1023u) != 0u) {   // the swizzled tiles need 1024-byte alignment
         if (threadIdx.x == 0) atomicOr(&A.status[ST_CALL], DEV_RANGE);
@@ -506,7 +496,8 @@ __global__ void __launch_bounds__(FI_THREADS, FI_CTAS) infer_kernel(InferArgs A)
             mbar_init(bar_full + 8 * i, 1);
             mbar_init(bar_empty + 8 * i, 1);
         }
-        mbar_init(bar_acc, 1);
+        mbar_init(bar_acc_lo, 1);
+        mbar_init(bar_acc_hi, 1);
         mbar_init(bar_a, 32 * FI_EPI_WARPS);
         mbar_init(bar_p, 32 * FI_EPI_WARPS);
         abort_flag = 0;
@@ -521,74 +512,124 @@ __global__ void __launch_bounds__(FI_THREADS, FI_CTAS) infer_kernel(InferArgs A)
 
     const long long n_tiles = (A.n_rows + 127) / 128;
     const int M = A.n_members;
+    const long long my_tiles =
+        n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long total = my_tiles * M * FI_ITEMS;
 
     if (warp == FI_EPI_WARPS) {
-        // ------------------------------------------------------------ copies + MMAs
+        // ------------------------------------------------------------ bulk copies
         if (lane == 0) {
-            const long long my_tiles =
-                n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-            const long long total = my_tiles * M * FI_ITEMS;
-            long long issued = 0, consumed = 0;
-            uint32_t pa = 0;
+            long long issued = 0;
+            int slot = 0, item = 0, member = 0;
+            uint32_t phase = 0;
             bool ok = true;
-            auto fill = [&](long long upto) {
-                while (ok && issued < upto && issued < total) {
-                    const int slot = (int)(issued % FI_STAGES);
-                    if (issued >= FI_STAGES) {
-                        const uint32_t ph = (uint32_t)((issued / FI_STAGES) - 1) & 1u;
-                        if (!mbar_wait(bar_empty + 8 * slot, ph, A.wait_limit)) {
-                            ok = false;
-                            break;
-                        }
-                    }
-                    const FiItem it = fi_item((int)(issued % FI_ITEMS));
-                    const int member = (int)((issued / FI_ITEMS) % M);
-                    const uint8_t* src = A.model + (size_t)member * A.member_bytes + A.wi_b +
-                                         (size_t)it.src * 2;
-                    if (!(A.test_stall && issued == 0)) {
-                        mbar_arrive_expect_tx(bar_full + 8 * slot, it.bytes);
-                        bulk_load(ring + slot * FI_SLOT, src, it.bytes, bar_full + 8 * slot);
-                    }
-                    ++issued;
+            const uint8_t* wi0 = A.model + A.wi_b;
+            for (; issued < total && ok && !abort_flag; ++issued) {
+                if (issued >= FI_STAGES &&
+                    !mbar_wait_sleep(bar_empty + 8 * slot, phase ^ 1u, A.wait_limit)) {
+                    ok = false;
+                    break;
                 }
-            };
+                int layer, kb;
+                long long src;
+                uint32_t bytes;
+                fi_item(item, layer, kb, src, bytes);
+                if (!(A.test_stall && issued == 0)) {
+                    mbar_arrive_expect_tx(bar_full + 8 * slot, bytes);
+                    bulk_load(ring + slot * FI_SLOT,
+                              wi0 + (size_t)member * A.member_bytes + (size_t)src * 2, bytes,
+                              bar_full + 8 * slot);
+                }
+                if (++slot == FI_STAGES) {
+                    slot = 0;
+                    phase ^= 1u;
+                }
+                if (++item == FI_ITEMS) {
+                    item = 0;
+                    if (++member == M) member = 0;
+                }
+            }
+            if (!ok) {
+                atomicOr(&A.status[ST_CALL], DEV_TIMEOUT);
+                abort_flag = 1;
+            }
+            // the last copy of each slot has landed before the CTA exits
+            const long long first = issued > FI_STAGES ? issued - FI_STAGES : 0;
+            for (long long g = first; g < issued; ++g) {
+                if (A.test_stall && g == 0) continue;   // never issued
+                mbar_wait(bar_full + 8 * (int)(g % FI_STAGES), (uint32_t)(g / FI_STAGES) & 1u,
+                          1000000000LL);
+            }
+        }
+        __syncwarp();
+    } else if (warp == FI_EPI_WARPS + 1) {
+        // ------------------------------------------------------------ MMAs
+        if (lane == 0) {
+            int slot = 0;
+            uint32_t phase = 0, pa = 0;
+            long long consumed = 0;
+            bool ok = true;
+            const uint64_t dh = desc_sw128(H);
+            const uint64_t dring = desc_sw128(ring);
+            constexpr uint32_t ID128 = idesc_bf16(128, 128), ID16 = idesc_bf16(128, 16);
             for (long long t = 0; t < my_tiles && ok; ++t) {
                 for (int k = 0; k < M && ok; ++k) {
                     int q = 0;
                     for (int l = 0; l < N_LAYERS && ok; ++l) {
-                        fill(consumed + FI_STAGES);
-                        if (!ok) break;
-                        if (!mbar_wait(bar_a, pa, A.wait_limit)) {
+                        if (!mbar_wait_sleep(bar_a, pa, A.wait_limit) || abort_flag) {
                             ok = false;
                             break;
                         }
                         pa ^= 1u;
                         tc_fence_after();
-                        const int n_items = (l == 0) ? 2 : (l == 4 ? 4 : 8);
-                        for (int x = 0; x < n_items; ++x, ++q) {
-                            fill(consumed + FI_STAGES);
-                            if (!ok) break;
-                            const int slot = (int)(consumed % FI_STAGES);
-                            const uint32_t ph = (uint32_t)(consumed / FI_STAGES) & 1u;
-                            if (!mbar_wait(bar_full + 8 * slot, ph, A.wait_limit)) {
+                        const int n_items = (l == 1 || l == 2 || l == 3) ? 4 : 1;
+                        // wait for the layer's stages (a hidden layer fills the ring)
+                        int slots[4];
+                        for (int x = 0; x < n_items && ok; ++x, ++q) {
+                            if (!mbar_wait(bar_full + 8 * slot, phase, A.wait_limit)) {
                                 ok = false;
                                 break;
                             }
-                            tc_fence_after();
-                            const FiItem it = fi_item(q);
-                            const uint32_t b_s = ring + slot * FI_SLOT;
-                            const uint32_t a_s = H + (uint32_t)it.kb * 16384u;
-                            const uint32_t d = tmem + (uint32_t)(it.nh * 128);
-                            const uint32_t idesc = (l == 4) ? idesc_bf16(128, 16)
-                                                            : idesc_bf16(128, 128);
-#pragma unroll
-                            for (int kk = 0; kk < 4; ++kk)
-                                mma_bf16(d, desc_sw128(a_s + kk * 32), desc_sw128(b_s + kk * 32),
-                                         idesc, (it.kb > 0 || kk > 0) ? 1u : 0u);
-                            mma_commit(bar_empty + 8 * slot);
+                            slots[x] = slot;
                             ++consumed;
+                            if (++slot == FI_STAGES) {
+                                slot = 0;
+                                phase ^= 1u;
+                            }
                         }
-                        if (ok) mma_commit(bar_acc);
+                        if (!ok) break;
+                        tc_fence_after();
+                        if (l < 4) {
+                            // output columns 0-127 first, so that half of the epilogue can
+                            // run while the MMAs of columns 128-255 do
+#pragma unroll 1
+                            for (int nh = 0; nh < 2; ++nh) {
+                                for (int x = 0; x < n_items; ++x) {
+                                    const uint64_t da = dh + (uint64_t)(x * (16384 >> 4));
+                                    const uint64_t db = dring +
+                                        (uint64_t)(slots[x] * (FI_SLOT >> 4) + nh * (16384 >> 4));
+#pragma unroll
+                                    for (int kk = 0; kk < 4; ++kk)
+                                        mma_bf16(tmem + (uint32_t)(nh * 128), da + 2 * kk,
+                                                 db + 2 * kk, ID128, (x > 0 || kk > 0) ? 1u : 0u);
+                                    if (nh == 1) mma_commit(bar_empty + 8 * slots[x]);
+                                }
+                                mma_commit(nh == 0 ? bar_acc_lo : bar_acc_hi);
+                            }
+                        } else {
+                            const uint64_t db = dring + (uint64_t)(slots[0] * (FI_SLOT >> 4));
+#pragma unroll
+                            for (int kb = 0; kb < 4; ++kb)
+#pragma unroll
+                                for (int kk = 0; kk < 4; ++kk)
+                                    mma_bf16(tmem, dh + (uint64_t)(kb * (16384 >> 4)) + 2 * kk,
+                                             db + (uint64_t)(kb * ((int)IMG_L4_BLK * 2 >> 4)) +
+                                                 2 * kk,
+                                             ID16, (kb > 0 || kk > 0) ? 1u : 0u);
+                            mma_commit(bar_empty + 8 * slots[0]);
+                            mma_commit(bar_acc_lo);
+                            mma_commit(bar_acc_hi);
+                        }
                     }
                 }
             }
@@ -596,12 +637,7 @@ __global__ void __launch_bounds__(FI_THREADS, FI_CTAS) infer_kernel(InferArgs A)
                 atomicOr(&A.status[ST_CALL], DEV_TIMEOUT);
                 abort_flag = 1;
             }
-            // drain: every issued copy has landed and every MMA has finished before exit
-            for (long long g = consumed; g < issued; ++g) {
-                if (A.test_stall && g == 0) continue;   // never issued
-                mbar_wait(bar_full + 8 * (int)(g % FI_STAGES),
-                          (uint32_t)(g / FI_STAGES) & 1u, 1000000000LL);
-            }
+            // every MMA has finished before the CTA exits (commits complete in order)
             if (consumed > 0) {
                 const long long g = consumed - 1;
                 mbar_wait(bar_empty + 8 * (int)(g % FI_STAGES), (uint32_t)(g / FI_STAGES) & 1u,
@@ -615,11 +651,13 @@ __global__ void __launch_bounds__(FI_THREADS, FI_CTAS) infer_kernel(InferArgs A)
         const int r = quarter * 32 + lane;                  // tile row = TMEM lane
         const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
         const bool lead = cg == 0;                          // builds X0, keeps the ensemble
+        const uint32_t bar_acc = cg < 2 ? bar_acc_lo : bar_acc_hi;   // my accumulator half
         const int et = threadIdx.x;                         // 0 .. 32 * FI_EPI_WARPS - 1
-        // stages member k's biases and feature statistics into parameter slot k mod 4,
-        // then waits (bounded) until every epilogue thread has written its share
         uint32_t pp = 0;
         bool ok = true;
+        // stages member k's biases (hidden layers halved, for gelu_half) and feature
+        // statistics into parameter slot k mod 4, then waits (bounded) until every
+        // epilogue thread has written its share
         auto stage = [&](int k) {
             const uint8_t* mb = A.model + (size_t)k * A.member_bytes;
             const float* th = reinterpret_cast<const float*>(mb + A.theta_b);
@@ -630,13 +668,14 @@ __global__ void __launch_bounds__(FI_THREADS, FI_CTAS) infer_kernel(InferArgs A)
                 if (i < N_LAYERS * 256) {
                     const int l = i >> 8, c = i & 255;
                     v = (c < real_out(l)) ? __ldg(th + A.b_off[l] + c) : 0.f;
+                    if (l < 4) v *= 0.5f;
                 } else {
                     v = __ldg(st + (i - N_LAYERS * 256));   // mean[16] | std[16]
                 }
                 dst[i] = v;
             }
             mbar_arrive(bar_p);
-            if (!mbar_wait(bar_p, pp, A.wait_limit)) ok = false;
+            if (!mbar_wait_sleep(bar_p, pp, A.wait_limit)) ok = false;
             pp ^= 1u;
         };
         const bool staged_once = M <= FI_PAR_SLOTS;
@@ -674,7 +713,7 @@ __global__ void __launch_bounds__(FI_THREADS, FI_CTAS) infer_kernel(InferArgs A)
                 tc_fence_before();
                 mbar_arrive(bar_a);
                 for (int l = 0; l < N_LAYERS; ++l) {
-                    if (!mbar_wait(bar_acc, pacc, A.wait_limit)) {
+                    if (!mbar_wait_sleep(bar_acc, pacc, A.wait_limit)) {
                         ok = false;
                         break;
                     }
@@ -682,26 +721,32 @@ __global__ void __launch_bounds__(FI_THREADS, FI_CTAS) infer_kernel(InferArgs A)
                     tc_fence_after();
                     const float* bias = pk_par + l * 256;
                     if (l < 4) {
-#pragma unroll 1
-                        for (int hh = 0; hh < 2 * FI_KB_PER; ++hh) {
-                            const int kb = cg * FI_KB_PER + (hh >> 1), h = hh & 1;
-                            const int c0 = kb * 64 + h * 32;
-                            float v[32];
-                            tmem_ld32(trow + (uint32_t)c0, v);
+                        // two 32-column halves; the second half's TMEM read is in flight
+                        // while the first half is computed
+                        uint32_t ra[32], rb[32];
+                        tmem_ld32_async(trow + (uint32_t)(cg * 64), ra);
+                        tmem_wait_ld(ra);
+                        tmem_ld32_async(trow + (uint32_t)(cg * 64 + 32), rb);
+                        auto half = [&](const uint32_t (&rv)[32], int h) {
+                            const int c0 = cg * 64 + h * 32;
                             uint32_t pk[16];
 #pragma unroll
                             for (int i = 0; i < 32; i += 4) {
                                 const float4 b4 = *reinterpret_cast<const float4*>(bias + c0 + i);
-                                pk[i / 2] = pack_bf16(gelu_f(v[i] + b4.x), gelu_f(v[i + 1] + b4.y));
-                                pk[i / 2 + 1] = pack_bf16(gelu_f(v[i + 2] + b4.z),
-                                                          gelu_f(v[i + 3] + b4.w));
+                                pk[i / 2] = pack_bf16(gelu_half(__uint_as_float(rv[i]), b4.x),
+                                                      gelu_half(__uint_as_float(rv[i + 1]), b4.y));
+                                pk[i / 2 + 1] = pack_bf16(gelu_half(__uint_as_float(rv[i + 2]), b4.z),
+                                                          gelu_half(__uint_as_float(rv[i + 3]), b4.w));
                             }
 #pragma unroll
                             for (int q = 0; q < 4; ++q)
-                                fi_store_chunk(H, r, kb, h * 4 + q,
+                                fi_store_chunk(H, r, cg, h * 4 + q,
                                                make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2],
                                                           pk[4 * q + 3]));
-                        }
+                        };
+                        half(ra, 0);
+                        tmem_wait_ld(rb);
+                        half(rb, 1);
                         fence_proxy_async_smem();
                         tc_fence_before();
                         mbar_arrive(bar_a);
@@ -1359,7 +1404,7 @@ static fos_status predict(Workspace* ws, void* model, int n_members, const float
     a.wait_limit = stall ? 2000000LL : 4000000000LL;
     a.test_stall = stall ? 1 : 0;
     const long long tiles = (n_rows + 127) / 128;
-    long long grid = (long long)ws->num_sms * FI_CTAS;
+    long long grid = (long long)ws->num_sms;
     if (grid > tiles) grid = tiles;
     infer_kernel<<<(unsigned)grid, FI_THREADS, FI_SMEM, s>>>(a);
     FOS_CUDA_TRY(cudaGetLastError());

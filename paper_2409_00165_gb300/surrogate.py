@@ -358,13 +358,35 @@ def _predict_demo(rows: int, members: int, reps: int):
           f"{flops / s / 1e12:.1f} TFLOP/s (algorithmic)")
 
 
+def _mie_demo(designs: int, n_wl: int, reps: int):
+    """Mie + effective medium over single-layer designs (a profiling target)."""
+    d = W.single_layer_designs(designs, seed=5, n_wl=n_wl)
+    m = Media(d["radius"], d["vol_frac"], d["thickness"], d["wl"])
+    for _ in range(2):
+        m.mie()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        m.mie(flags=fos.FOS_ASYNC)
+    b.record()
+    torch.cuda.synchronize()
+    fos.check(fos.fos_sync_status(), "mie demo")
+    s = a.elapsed_time(b) / 1e3 / reps
+    print(f"mie {m.rows} evaluations: {s * 1e3:.3f} ms, {m.rows / s:.3e} evaluations/s")
+
+
 if __name__ == "__main__":
     import argparse
     ap = argparse.ArgumentParser()
     ap.add_argument("--predict-demo", action="store_true")
+    ap.add_argument("--mie-demo", action="store_true")
+    ap.add_argument("--designs", type=int, default=10000)
+    ap.add_argument("--wl", type=int, default=300)
     ap.add_argument("--rows", type=int, default=1 << 19)
     ap.add_argument("--members", type=int, default=4)
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args()
     if a.predict_demo:
         _predict_demo(a.rows, a.members, a.reps)
+    if a.mie_demo:
+        _mie_demo(a.designs, a.wl, a.reps)
