@@ -399,8 +399,8 @@ def run_surrogate(mode: str):
     Training data: single-layer designs (r, f, d in the workload ranges) x 50 random
     wavelengths per block, Monte Carlo fractions at 3e4 photons; 4 members trained by
     Adam.  Sweep: 1e5 designs x 300 wavelengths, ensemble spread > 0.01 or out-of-range
-    rows re-run by Monte Carlo at 1e5 photons; 0.1 % of rows audited by Monte Carlo at
-    1e5 photons."""
+    rows re-run by Monte Carlo at 1e5 photons; 1 % of rows (0.1 % in quick mode) audited
+    by Monte Carlo at 1e5 photons."""
     import torch
 
     from paper_2409_00165_gb300 import surrogate as S
@@ -416,7 +416,7 @@ def run_surrogate(mode: str):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     r = S.sweep(sur, n_designs=cfg["sweep"], n_wl=300, seed=5, threshold=0.01,
-                audit_frac=0.001)
+                audit_frac=0.01 if mode == "full" else 0.001)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -57,6 +58,15 @@ fos_status accumulate_async_status(Workspace* ws, cudaStream_t s);
 fos_status finish_call(Workspace* ws, cudaStream_t s, unsigned flags);
 
 inline int default_timeout_ms() { return 600000; }
+
+// NVTX range around a library entry point (visible in Nsight timelines; a no-op when no
+// tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace fos
 

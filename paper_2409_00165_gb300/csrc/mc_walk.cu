@@ -940,6 +940,7 @@ extern "C" {
 
 fos_status fos_mc_spectrum(const fos_mc_batch* batch, long long* counts, int* photon_log,
                            long long log_stride, unsigned flags, void* stream) {
+    NvtxRange nvtx("fos_mc_spectrum");
     long long n_run = 0;
     fos_status st = mc::validate_host(batch, counts, photon_log, log_stride, &n_run);
     if (st != FOS_OK) return st;

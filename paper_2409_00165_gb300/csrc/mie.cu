@@ -392,6 +392,7 @@ static fos_status mie_impl(int n_wl, const double* wl, int n_groups, const doubl
                            const double* vol_frac, double* mu_s, double* mu_a, double* g,
                            double* q_ext, double* q_sca, double* g_species, unsigned flags,
                            void* stream) {
+    NvtxRange nvtx("fos_mie_properties");
     if (n_wl < 1 || n_groups < 1 || n_species < 0) return FOS_ERR_INVALID_ARG;
     if ((long long)n_groups * n_wl > 0x7fffffffLL || (long long)n_species * n_wl > 0x7fffffffLL)
         return FOS_ERR_INVALID_ARG;

@@ -1572,6 +1572,7 @@ fos_status fos_surrogate_train_step(void* model, int member, const float* featur
                                     const int* batch_rows, unsigned long long seed, int step,
                                     float lr, float* loss_out, float* grad_out, unsigned flags,
                                     void* stream) {
+    NvtxRange nvtx("fos_surrogate_train_step");
     if (!model || member < 0 || !features || !targets || n_rows < 1 || step < 0) return FOS_ERR_INVALID_ARG;
     if (batch < 256 || batch % 256 != 0 || batch > 65536) return FOS_ERR_INVALID_ARG;
     if (!(lr > 0.f)) return FOS_ERR_INVALID_ARG;
@@ -1598,6 +1599,7 @@ fos_status fos_surrogate_predict(void* model, int n_members, const float* featur
                                  long long n_rows, float* rat, float* spread,
                                  unsigned char* needs_mc, float threshold, unsigned flags,
                                  void* stream) {
+    NvtxRange nvtx("fos_surrogate_predict");
     if (!model || n_members < 1 || n_members > 16 || n_rows < 0) return FOS_ERR_INVALID_ARG;
     if (n_rows > 0 && (!features || !rat)) return FOS_ERR_INVALID_ARG;
     if (n_rows == 0) return FOS_OK;

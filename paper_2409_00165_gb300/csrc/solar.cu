@@ -83,6 +83,7 @@ using namespace fos;
 extern "C" fos_status fos_solar_weighted(int n_stacks, int n_wl, const double* wl,
                                          const double* G, const long long* counts, double* out,
                                          unsigned flags, void* stream) {
+    NvtxRange nvtx("fos_solar_weighted");
     if (n_stacks < 1 || n_wl < 1 || !wl || !G || !counts || !out) return FOS_ERR_INVALID_ARG;
     if ((long long)n_stacks * n_wl > 0x7fffffffLL) return FOS_ERR_INVALID_ARG;
     if (flags & ~(unsigned)(FOS_ASYNC | FOS_TEST_INJECT)) return FOS_ERR_INVALID_ARG;

@@ -116,15 +116,20 @@ class Surrogate:
         return st
 
     def fit(self, features, targets, steps: int, batch: int = 8192, lr: float = 1e-3,
-            lr_min: float = 2e-5, members=None, log_every: int = 0):
-        """Adam with a cosine learning-rate schedule; returns the loss history."""
+            lr_min: float = 2e-5, members=None, log_every: int = 0, schedule_steps=None):
+        """Adam with a cosine learning-rate schedule over schedule_steps (default: this
+        call's steps), taken at each member's global step count, so that a run split into
+        several calls, or resumed from a checkpoint, follows the same schedule.  Returns
+        the loss history."""
         members = range(self.n_members) if members is None else members
+        total = schedule_steps or steps
         loss = torch.zeros(1, dtype=torch.float32, device=features.device)
         hist = {}
         for k in members:
             hist[k] = []
             for t in range(steps):
-                cur = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * t / steps))
+                g = min(self.steps_done[k], total) if schedule_steps else t
+                cur = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * g / total))
                 fos.check(fos.fos_surrogate_train_step(
                     self.model, k, features, targets, batch, self.seed, self.steps_done[k], cur,
                     loss_out=loss, flags=fos.FOS_ASYNC), "train_step")
@@ -133,6 +138,28 @@ class Surrogate:
                     hist[k].append((t, loss.item()))
         fos.check(fos.fos_sync_status(), "training")
         return hist
+
+    def save(self, path: str):
+        """Checkpoint: the whole model buffer (FP32 parameters, Adam state, BF16 copies,
+        weight image, feature statistics) and the step counts, as an .npz file."""
+        torch.cuda.synchronize()
+        np.savez(path, model=self.model.cpu().numpy(), steps_done=np.array(self.steps_done),
+                 seed=self.seed, n_members=self.n_members, model_bytes=self.mb,
+                 api=fos.lib().fos_api_version())
+
+    @classmethod
+    def restore(cls, path: str, device="cuda"):
+        """A surrogate continued from a checkpoint written by save()."""
+        z = np.load(path)
+        if int(z["model_bytes"]) != fos.fos_surrogate_model_bytes():
+            raise ValueError("checkpoint model layout differs from this library's")
+        sur = cls.__new__(cls)
+        sur.n_members = int(z["n_members"])
+        sur.mb = int(z["model_bytes"])
+        sur.seed = int(z["seed"])
+        sur.steps_done = [int(v) for v in z["steps_done"]]
+        sur.model = torch.as_tensor(z["model"]).to(device)
+        return sur
 
     def predict(self, features, threshold: float = 0.01, n_members=None, flags=0, stream=None):
         n = features.shape[0]
@@ -182,7 +209,7 @@ def training_set(n_designs: int, wl_per_block: int, blocks: int, photons: int, s
 
 def sweep(sur: Surrogate, n_designs: int, n_wl: int, seed: int, threshold: float = 0.01,
           fallback_photons: int = 100000, audit_frac: float = 0.001, audit_photons: int = 100000,
-          device="cuda"):
+          refine_rows: int = 64, device="cuda"):
     """Surrogate design sweep: Mie -> features -> ensemble prediction -> Monte Carlo on the
     rows the ensemble flags; then a random audit of rows by Monte Carlo.  Returns timings,
     counts and the audit errors (absolute, per R, A, T) of the final spectra."""
@@ -227,9 +254,27 @@ def sweep(sur: Surrogate, n_designs: int, n_wl: int, seed: int, threshold: float
         ya = fractions(ca)
         err = (rat[rt.long()] - ya).abs()
         phot = int(ca[:, :4].sum().item())
+        e_all = err.max(dim=1).values
+        # binomial standard deviation of the audit's own MC fractions, the floor under any
+        # error measured against it
+        sig = (ya * (1 - ya) / audit_photons).sqrt().max(dim=1).values
         out["audit"] = dict(rows=n_aud, photons=audit_photons,
                             mae=err.mean(dim=0).cpu().tolist(),
-                            max=err.max(dim=0).values.cpu().tolist())
+                            max=err.max(dim=0).values.cpu().tolist(),
+                            p999=float(torch.quantile(e_all.float(), 0.999).item()),
+                            frac_above_0p01=float((e_all > 0.01).float().mean().item()),
+                            mc_noise_sigma_max=float(sig.max().item()))
+        # the worst audited rows again, against Monte Carlo at 10x the photons (a tenth of
+        # the variance): the audit's own noise is part of its largest errors
+        k = min(refine_rows, n_aud)
+        if k > 0:
+            worst = torch.topk(e_all, k).indices
+            rows_w = torch.sort(rt[worst]).values.contiguous()
+            yw = fractions(m.mc(audit_photons * 10, seed=seed + 29, item_list=rows_w))
+            ew = (rat[rows_w.long()] - yw).abs()
+            out["audit"]["refined"] = dict(rows=k, photons=audit_photons * 10,
+                                           max=ew.max(dim=0).values.cpu().tolist(),
+                                           above_0p01=int((ew.max(dim=1).values > 0.01).sum().item()))
         # plain GPU Monte Carlo on the same designs, per spectrum of n_wl wavelengths
         out["mc_photons_per_s"] = phot / t_a
         out["mc_spectra_per_s"] = phot / t_a / (n_wl * audit_photons)
