@@ -409,7 +409,8 @@ def run_surrogate(mode: str):
                quick=dict(designs=4000, blocks=10, wl=24, photons=10000, steps=2500,
                           sweep=20000))[mode]
     t0 = time.perf_counter()
-    f, y, info = S.training_set(cfg["designs"], cfg["wl"], cfg["blocks"], cfg["photons"], seed=4)
+    f, y, info = S.training_set(cfg["designs"], cfg["wl"], cfg["blocks"], cfg["photons"], seed=4,
+                                log_share=0.5)
     sur = S.Surrogate(4, S.Surrogate.stats_of(f), seed=7)
     t1 = time.perf_counter()
     hist = sur.fit(f, y, steps=cfg["steps"], batch=8192, lr=2e-3, log_every=cfg["steps"] - 1)

@@ -174,14 +174,14 @@ class Surrogate:
 
 
 def training_set(n_designs: int, wl_per_block: int, blocks: int, photons: int, seed: int,
-                 device="cuda"):
+                 device="cuda", log_share: float = 0.0):
     """Monte Carlo training rows of single-layer designs (workload ranges of r, f, d).
 
     The designs are split into `blocks`; each block gets its own sorted random
     wavelength set drawn from U(0.3, 2.5) um plus both ends of that range, so that the
     training rows cover the whole spectrum.  Returns (features, fractions, info)."""
     rng = np.random.default_rng(seed)
-    d = W.single_layer_designs(n_designs, seed=seed, n_wl=None)
+    d = W.single_layer_designs(n_designs, seed=seed, n_wl=None, log_share=log_share)
     per = n_designs // blocks
     feats, targs = [], []
     coll = phot = 0
@@ -272,9 +272,20 @@ def sweep(sur: Surrogate, n_designs: int, n_wl: int, seed: int, threshold: float
             rows_w = torch.sort(rt[worst]).values.contiguous()
             yw = fractions(m.mc(audit_photons * 10, seed=seed + 29, item_list=rows_w))
             ew = (rat[rows_w.long()] - yw).abs()
+            emax = ew.max(dim=1).values
             out["audit"]["refined"] = dict(rows=k, photons=audit_photons * 10,
                                            max=ew.max(dim=0).values.cpu().tolist(),
-                                           above_0p01=int((ew.max(dim=1).values > 0.01).sum().item()))
+                                           above_0p01=int((emax > 0.01).sum().item()))
+            # the designs of the worst refined rows: where the network is weakest
+            top = torch.topk(emax, min(8, k)).indices
+            rw = rows_w[top].cpu().numpy()
+            dd, ww = rw // n_wl, rw % n_wl
+            out["audit"]["worst"] = [
+                dict(wl=float(d["wl"][w]), radius=float(d["radius"][i]),
+                     vol_frac=float(d["vol_frac"][i]), thickness=float(d["thickness"][i]),
+                     err=[round(float(v), 5) for v in ew[j].cpu().tolist()],
+                     spread=float(spread[int(r)].item()))
+                for i, w, j, r in zip(dd, ww, top.cpu().tolist(), rw)]
         # plain GPU Monte Carlo on the same designs, per spectrum of n_wl wavelengths
         out["mc_photons_per_s"] = phot / t_a
         out["mc_spectra_per_s"] = phot / t_a / (n_wl * audit_photons)

@@ -122,16 +122,24 @@ def layer_stacks(n_designs: int = STACK_N_DESIGNS, n_wl: int = STACK_N_WL, seed:
 
 
 def single_layer_designs(n_designs: int, seed: int, n_wl: int | None = SWEEP_N_WL,
-                         random_wl: bool = False) -> dict:
-    """Single-layer designs in the ranges of the multilayer batch (r, f, d).
+                         random_wl: bool = False, log_share: float = 0.0) -> dict:
+    """Single-layer designs in the ranges of the multilayer batch (r, f, d), uniform.
 
-    With random_wl, each design gets one wavelength drawn from U(0.3, 2.5) um (the
-    surrogate training set); otherwise every design uses the n_wl-point grid.
+    With random_wl, each design gets one wavelength drawn from U(0.3, 2.5) um; otherwise
+    every design uses the n_wl-point grid.  A fraction log_share of the designs draws f
+    and d log-uniformly over the same ranges instead, which puts more of them near the
+    thin, dilute end (a training-set choice: the sweep itself is uniform).
     """
     rng = np.random.default_rng(seed)
     radius = rng.uniform(0.05, 1.0, size=n_designs)
     vol_frac = rng.uniform(0.01, 0.3, size=n_designs)
     thickness = rng.uniform(10.0, 500.0, size=n_designs)
+    if log_share > 0.0:
+        pick = rng.uniform(size=n_designs) < log_share
+        lf = np.exp(rng.uniform(np.log(0.01), np.log(0.3), size=n_designs))
+        ld = np.exp(rng.uniform(np.log(10.0), np.log(500.0), size=n_designs))
+        vol_frac = np.where(pick, lf, vol_frac)
+        thickness = np.where(pick, ld, thickness)
     if random_wl:
         wl = rng.uniform(0.3, 2.5, size=n_designs)
     elif n_wl:
