@@ -319,8 +319,9 @@ fos_status fos_surrogate_features(int n_designs, int n_wl, const double* wl,
 /* Raw features of homogeneous slabs given by their optical properties, the inputs of
  * the paper's network (section "Photon transport", Table 1: matrix index, mu_s, mu_a, g,
  * thickness), one row per slab: [n, log10(mu_s + 1e-4), log10(mu_a + 1e-4), g, log10 d,
- * log10(mu_s d + 1e-6), log10(mu_a d + 1e-6), 0, 0] with mu in 1/um and d in um (1e-4
- * per um = 1 per cm).  Each input maps monotonically to one feature, so the range gate of
+ * log10(mu_s d + 1e-6), log10(mu_a d + 1e-6), log10(1 - g + 1e-3),
+ * log10(mu_s (1 - g) d + 1e-6)] with mu in 1/um and d in um (1e-4 per um = 1 per cm).
+ * Each input maps monotonically to one of the first five features, so the range gate of
  * fos_surrogate_predict (feature lo/hi) can hold exactly the ranges of Table 1.
  * n_layer, mu_s, mu_a, g, thickness: device double [n_rows]; features: device float
  * [n_rows*9].  Non-positive d or n, negative mu, non-finite values: FOS_ERR_INVALID_ARG. */

@@ -832,8 +832,10 @@ __global__ void features_kernel(int n_designs, int n_wl, const double* wl, const
 // Features of a homogeneous slab given by its optical properties (the inputs of the
 // paper's network, Table 1: matrix index, mu_s, mu_a, g, thickness):
 // [n, log10(mu_s + 1e-4), log10(mu_a + 1e-4), g, log10 d, log10(mu_s d + 1e-6),
-//  log10(mu_a d + 1e-6), 0, 0].  Each raw input maps monotonically to one feature, so a
-// box in feature space is the box of Table 1; the two optical depths help the fit.
+//  log10(mu_a d + 1e-6), log10(1 - g + 1e-3), log10(mu_s (1 - g) d + 1e-6)].  Each raw
+// input maps monotonically to one of the first five features, so a box in feature space
+// holds the box of Table 1; the optical depths, 1 - g and the reduced scattering depth
+// help the fit (transport near g = 1 depends on mu_s (1 - g)).
 __global__ void features_slab_kernel(long long n, const double* nl, const double* mu_s,
                                      const double* mu_a, const double* g, const double* d,
                                      float* out, unsigned* status) {
@@ -848,8 +850,8 @@ __global__ void features_slab_kernel(long long n, const double* nl, const double
         o[4] = (float)log10(t);
         o[5] = (float)log10(ms * t + 1e-6);
         o[6] = (float)log10(ma * t + 1e-6);
-        o[7] = 0.0f;
-        o[8] = 0.0f;
+        o[7] = (float)log10(1.0 - g[i] + 1e-3);
+        o[8] = (float)log10(ms * (1.0 - g[i]) * t + 1e-6);
         if (!(t > 0.0) || !(ms >= 0.0) || !(ma >= 0.0) || !isfinite(ms * t) ||
             !isfinite(ma * t) || !(nl[i] > 0.0) || !isfinite(g[i]))
             atomicOr(&status[ST_CALL], DEV_INVALID);

@@ -327,11 +327,15 @@ def table1_stats(features) -> list:
     the optical-depth cap): rows outside it are flagged for Monte Carlo."""
     st = Surrogate.stats_of(features).cpu().numpy().astype(np.float64)
     T = W.TABLE1
+    # features 5-8 are functions of the first five; their bounds only admit every value
+    # the Table 1 box can produce, except the scattering depth, capped at tau_s_max
     lo = [T["n"][0], math.log10(T["mu_s"][0] + 1e-4), math.log10(T["mu_a"][0] + 1e-4),
-          T["g"][0], math.log10(T["d"][0]), -6.0, -6.0, 0.0, 0.0]
+          T["g"][0], math.log10(T["d"][0]), -6.0, -6.0,
+          math.log10(1.0 - T["g"][1] + 1e-3), -6.0]
     hi = [T["n"][1], math.log10(T["mu_s"][1] + 1e-4), math.log10(T["mu_a"][1] + 1e-4),
           T["g"][1], math.log10(T["d"][1]), math.log10(T["tau_s_max"] + 1e-6),
-          math.log10(T["mu_a"][1] * T["d"][1] + 1e-6), 0.0, 0.0]
+          math.log10(T["mu_a"][1] * T["d"][1] + 1e-6), math.log10(1.0 - T["g"][0] + 1e-3),
+          math.log10(T["tau_s_max"] + 1e-6)]
     # float32 rounding of a boundary must not flag the boundary itself
     st[32:41] = np.nextafter(np.float32(lo), np.float32(-np.inf))
     st[48:57] = np.nextafter(np.float32(hi), np.float32(np.inf))
@@ -344,7 +348,7 @@ def table1_experiment(train_rows: int, train_photons: int, steps: int, test_rows
     """Trains an ensemble on Monte Carlo fractions of random Table 1 slabs and evaluates it
     on held-out slabs against Monte Carlo at test_photons: accuracy, flagged rows, and
     slab evaluations per second of the network (with fallback) against Monte Carlo."""
-    tr = Slabs(W.table1_slabs(train_rows, seed), device)
+    tr = Slabs(W.table1_slabs(train_rows, seed, g_log_share=0.5, n_log_share=0.3), device)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record()
     y = fractions(tr.mc(train_photons, seed=seed + 1))
@@ -380,6 +384,17 @@ def table1_experiment(train_rows: int, train_photons: int, steps: int, test_rows
     t_fb = e[1].elapsed_time(e[2]) / 1e3
     t_mc = e[2].elapsed_time(e[3]) / 1e3
     err = (rat - yt).abs()
+    emax = err.max(dim=1).values
+    top = torch.topk(emax, min(8, test_rows)).indices
+    rows_t = torch.sort(top).values.to(torch.int32).contiguous()
+    # the worst rows again at 10x the photons, with their inputs
+    yr = fractions(te.mc(test_photons * 10, seed=seed + 17, item_list=rows_t))
+    er = (rat[rows_t.long()] - yr).abs()
+    worst = [dict(n=float(te.n[i]), mu_s=float(te.mu_s[i]), mu_a=float(te.mu_a[i]),
+                  g=float(te.g[i]), d=float(te.d[i]),
+                  err=[round(float(v), 5) for v in er[j].cpu().tolist()],
+                  spread=float(spread[i].item()))
+             for j, i in enumerate(rows_t.long().cpu().tolist())]
     return dict(train_rows=train_rows, train_photons=train_photons, data_seconds=t_data,
                 members=members, steps=steps, train_seconds=t_train,
                 final_loss=[h[-1][1] for h in hist.values()],
@@ -387,7 +402,8 @@ def table1_experiment(train_rows: int, train_photons: int, steps: int, test_rows
                 mae=err.mean(dim=0).cpu().tolist(), max=err.max(dim=0).values.cpu().tolist(),
                 nn_rows_per_s=test_rows / (t_pred + t_fb),
                 nn_rows_per_s_no_fallback=test_rows / t_pred,
-                mc_rows_per_s=test_rows / t_mc, speedup_vs_mc=t_mc / (t_pred + t_fb))
+                mc_rows_per_s=test_rows / t_mc, speedup_vs_mc=t_mc / (t_pred + t_fb),
+                refined_max=er.max(dim=0).values.cpu().tolist(), worst=worst)
 
 
 def _predict_demo(rows: int, members: int, reps: int):

@@ -279,10 +279,15 @@ TABLE1 = dict(n=(1.0, 7.0), mu_s=(0.0, 20.0), mu_a=(0.0, 100.0), g=(0.0, 0.99),
 
 
 def table1_slabs(n_rows: int, seed: int, tau_s_max: float = TABLE1["tau_s_max"],
-                 zero_frac: float = 0.05) -> dict:
+                 zero_frac: float = 0.05, g_log_share: float = 0.0,
+                 n_log_share: float = 0.0) -> dict:
     """n ~ U(1, 7), g ~ U(0, 0.99), d log-uniform on [5, 500] um, mu_s log-uniform on
     [1e-4, min(20, tau_s_max / d)] /um, mu_a log-uniform on [1e-4, 100] /um; a fraction
-    zero_frac of rows has mu_s = 0 and another mu_a = 0 (the lower ends of Table 1)."""
+    zero_frac of rows has mu_s = 0 and another mu_a = 0 (the lower ends of Table 1).  A
+    fraction g_log_share of the rows draws 1 - g log-uniformly on [0.01, 1] instead,
+    which puts more of them near g = 1, and a fraction n_log_share draws n - 1
+    log-uniformly on [1e-3, 6], which puts more of them near an index-matched slab
+    (training-set choices)."""
     rng = np.random.default_rng(seed)
     lo, hi = np.log(1e-4), np.log(20.0)
     d = np.exp(rng.uniform(np.log(5.0), np.log(500.0), n_rows))
@@ -291,5 +296,12 @@ def table1_slabs(n_rows: int, seed: int, tau_s_max: float = TABLE1["tau_s_max"],
     mu_a = np.exp(rng.uniform(np.log(1e-4), np.log(100.0), n_rows))
     mu_s[rng.uniform(size=n_rows) < zero_frac] = 0.0
     mu_a[rng.uniform(size=n_rows) < zero_frac] = 0.0
-    return dict(n=rng.uniform(1.0, 7.0, n_rows), mu_s=mu_s, mu_a=mu_a,
-                g=rng.uniform(0.0, 0.99, n_rows), d=d)
+    n = rng.uniform(1.0, 7.0, n_rows)
+    g = rng.uniform(0.0, 0.99, n_rows)
+    if g_log_share > 0.0:
+        pick = rng.uniform(size=n_rows) < g_log_share
+        g = np.where(pick, 1.0 - np.exp(rng.uniform(np.log(0.01), 0.0, n_rows)), g)
+    if n_log_share > 0.0:
+        pick = rng.uniform(size=n_rows) < n_log_share
+        n = np.where(pick, 1.0 + np.exp(rng.uniform(np.log(1e-3), np.log(6.0), n_rows)), n)
+    return dict(n=n, mu_s=mu_s, mu_a=mu_a, g=g, d=d)

@@ -19,7 +19,8 @@ def test_slab_features_closed_form():
     f = sl.features().cpu().numpy().astype(np.float64)
     want = np.column_stack([r["n"], np.log10(r["mu_s"] + 1e-4), np.log10(r["mu_a"] + 1e-4),
                             r["g"], np.log10(r["d"]), np.log10(r["mu_s"] * r["d"] + 1e-6),
-                            np.log10(r["mu_a"] * r["d"] + 1e-6), np.zeros((5000, 2))])
+                            np.log10(r["mu_a"] * r["d"] + 1e-6), np.log10(1 - r["g"] + 1e-3),
+                            np.log10(r["mu_s"] * (1 - r["g"]) * r["d"] + 1e-6)])
     assert np.allclose(f, want.astype(np.float32), rtol=2e-7, atol=2e-7)
     bad = dict(r, d=np.where(np.arange(5000) == 7, 0.0, r["d"]))
     out = torch.zeros((5000, 9), dtype=torch.float32, device="cuda")
