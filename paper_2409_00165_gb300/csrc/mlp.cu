@@ -926,19 +926,32 @@ __global__ void gather_kernel(const float* feat, const float* targets, long long
     for (int c = 0; c < N_OUT; ++c) Y[(long long)b * 3 + c] = targets[src * 3 + c];
 }
 
-// Inference input: standardised features of rows [r0, r0+n) -> X0 [n][64].
-// Column sums of a bf16 [rows][ld] matrix (bias gradients): one block per 64 columns.
-__global__ void colsum_kernel(const bf16* G, int rows, int ld, int ncols, float* out) {
-    __shared__ float part[4][64];
+// Column sums of a bf16 [rows][ld] matrix (bias gradients), in two deterministic
+// passes.  Pass 1: block (x, y) sums rows y*chunk .. +chunk of columns 64x .. +63 (4 row
+// phases, then a fixed combine) into part[y][c].  Pass 2 sums the COLSUM_SPLITS partials
+// of each column in order.
+constexpr int COLSUM_SPLITS = 64;
+__global__ void colsum_partial_kernel(const bf16* G, int rows, int ld, int ncols, float* part) {
+    __shared__ float ph[4][64];
     const int c = blockIdx.x * 64 + (threadIdx.x & 63);
     const int q = threadIdx.x >> 6;   // 4 row phases
+    const int chunk = (rows + COLSUM_SPLITS - 1) / COLSUM_SPLITS;
+    const int r0 = blockIdx.y * chunk, r1 = min(rows, r0 + chunk);
     float acc = 0.f;
     if (c < ncols)
-        for (int r = q; r < rows; r += 4) acc += __bfloat162float(G[(long long)r * ld + c]);
-    part[q][threadIdx.x & 63] = acc;
+        for (int r = r0 + q; r < r1; r += 4) acc += __bfloat162float(G[(long long)r * ld + c]);
+    ph[q][threadIdx.x & 63] = acc;
     __syncthreads();
     if (q == 0 && c < ncols)
-        out[c] = part[0][threadIdx.x] + part[1][threadIdx.x] + part[2][threadIdx.x] + part[3][threadIdx.x];
+        part[blockIdx.y * ncols + c] =
+            ph[0][threadIdx.x] + ph[1][threadIdx.x] + ph[2][threadIdx.x] + ph[3][threadIdx.x];
+}
+__global__ void colsum_final_kernel(const float* part, int ncols, float* out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    float acc = 0.f;
+    for (int y = 0; y < COLSUM_SPLITS; ++y) acc += part[y * ncols + c];
+    out[c] = acc;
 }
 
 struct AdamArgs {
@@ -1201,7 +1214,7 @@ struct TrainWs {
     void* mem = nullptr;
     size_t bytes = 0;
     bf16 *X0, *X0T, *H[4], *HT[4], *G4, *G4T, *dZ[2], *dZT[2];
-    float *Z[4], *P, *Y, *part[N_LAYERS], *db[N_LAYERS], *loss;
+    float *Z[4], *P, *Y, *part[N_LAYERS], *db[N_LAYERS], *loss, *colpart;
 };
 static TrainWs g_tws[64];
 
@@ -1237,6 +1250,7 @@ static fos_status ensure_train_ws(int dev, int B) {
     for (int l = 0; l < N_LAYERS; ++l) {
         add((void**)&w.part[l], (size_t)splits * lay_out(l) * lay_in(l) * 4);
         add((void**)&w.db[l], (size_t)lay_out(l) * 4);
+        if (l == 0) add((void**)&w.colpart, (size_t)COLSUM_SPLITS * HID * 4);
     }
     add((void**)&w.loss, 16);
     for (auto& it : items) o = al(o + it.bytes);
@@ -1326,7 +1340,11 @@ static fos_status train_step(Workspace* ws, const MemberPtrs& mp, const float* f
     int gcols = OUT_PAD;
     for (int l = 4; l >= 0; --l) {
         // bias gradient
-        colsum_kernel<<<(real_out(l) + 63) / 64, 256, 0, s>>>(Gcur, B, gcols, real_out(l), w.db[l]);
+        colsum_partial_kernel<<<dim3((real_out(l) + 63) / 64, COLSUM_SPLITS), 256, 0, s>>>(
+            Gcur, B, gcols, real_out(l), w.colpart);
+        FOS_CUDA_TRY(cudaGetLastError());
+        colsum_final_kernel<<<(real_out(l) + 255) / 256, 256, 0, s>>>(w.colpart, real_out(l),
+                                                                      w.db[l]);
         FOS_CUDA_TRY(cudaGetLastError());
         // weight gradient dW_l = G^T · H_{l-1}  (A = G^T [out][B], B = H_{l-1}^T [in][B])
         {
