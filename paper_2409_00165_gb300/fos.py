@@ -290,10 +290,17 @@ def fos_walk_math_f32(u, neg_log=None, cos2pi=None, stream=None) -> int:
 
 
 # --------------------------------------------------------------------------- surrogate
+_SFN = {}
+
+
 def _sfn(name, argtypes, restype=ctypes.c_int):
-    fn = getattr(lib(), name)
-    fn.argtypes = argtypes
-    fn.restype = restype
+    """The library function `name`, its ctypes signature set once."""
+    fn = _SFN.get(name)
+    if fn is None:
+        fn = getattr(lib(), name)
+        fn.argtypes = argtypes
+        fn.restype = restype
+        _SFN[name] = fn
     return fn
 
 
