@@ -277,3 +277,33 @@ def test_batch_keeps_temporary_tensors_alive(orc):
     fos.check(fos.fos_mc_spectrum(b, counts), "temporaries")
     assert np.array_equal(counts.cpu().numpy(), orc.mc_run(ref, fp32=True))
     del junk
+
+
+def test_layer_stacks_full_size_sampled_photons(orc):
+    """The 64-design x 200-wavelength uneven stack batch (log-uniform 1e4-1e6 photons per
+    item, reflector below) in the bench's autotuned launch shape: every item conserves
+    its photons.  Then 12 sampled items run again with per-photon logs (same counts: the
+    walk does not depend on the launch shape), and 60 sampled photons match the oracle's
+    one-photon walks."""
+    m = W.layer_stacks()
+    props = orc.mie_properties(m["wl"], m["nm"], m["species_group"], m["n_p"], m["radius"],
+                               m["vol_frac"], n_groups=m["n_groups"])
+    b = mc_batch_from_media(m, props)
+    c, _ = gpu_mc(b, flags=fos.FOS_AUTOTUNE)
+    assert np.array_equal(c[:, :4].sum(axis=1), m["n_photons"])
+    assert np.all(c[:, 3] == 0)
+    rng = np.random.default_rng(77)
+    items = np.sort(rng.choice(m["n_stacks"] * m["n_wl"], size=12, replace=False)).astype(np.int32)
+    bl = dict(b, item_list=items)
+    c2, log, _ = gpu_mc(bl, photon_log=True)
+    assert np.array_equal(c2, c[items])
+    for _ in range(60):
+        k = int(rng.integers(0, len(items)))
+        it = int(items[k])
+        p = int(rng.integers(0, m["n_photons"][it]))
+        one = dict(b)
+        one["item_list"] = np.array([it], np.int32)
+        one["n_photons"] = np.ones_like(m["n_photons"])
+        one["photon_first"] = np.full(len(m["n_photons"]), p, np.int64)
+        _, lo = orc.mc_run(one, fp32=True, photon_log=True)
+        assert log[k, p] == lo[0, 0], (it, p)
