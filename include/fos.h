@@ -5,14 +5,19 @@
  * The library computes the spectral reflectance, absorptance and transmittance of
  * particle-filled layers:
  *   fos_mie_properties  Mie theory + effective medium -> mu_s, mu_a, g per layer and
- *                       wavelength (section "Scattering properties", Eqs. 1-20).
+ *                       wavelength (section "Scattering properties", Eqs. 1-20);
+ *                       fos_mie_properties_cs adds core-shell spheres (supplement Eqs.
+ *                       S1-S9) and fos_size_distribution expands a size distribution.
  *   fos_mc_spectrum     Monte Carlo photon transport through layer stacks -> integer
- *                       photon counts R, A, T per (stack, wavelength) (section
- *                       "Photon transport").
+ *                       photon counts R, A, T per (stack, wavelength), at normal or
+ *                       oblique incidence, over a dielectric, a conductor or a reflector
+ *                       (section "Photon transport").
+ *   fos_solar_weighted  solar-weighted R, A, T of a spectrum (section "Output", Eq. 21).
  *   fos_surrogate_*     a learned MLP that predicts R, A, T from (wavelength, n, k,
- *                       radius, volume fraction, thickness, g, mu_s, mu_a), trained on
- *                       spectra from fos_mc_spectrum (the paper's "machine learning
- *                       method" of section "Photon transport").
+ *                       radius, volume fraction, thickness, g, mu_s, mu_a), or from the
+ *                       slab inputs of Table 1, trained on spectra from fos_mc_spectrum
+ *                       (the paper's "machine learning method" of section "Photon
+ *                       transport").
  *
  * Conventions for every entry point:
  *   - Plain C types only.  Pointers documented "device" point to CUDA device memory
