@@ -409,7 +409,7 @@ constexpr int FI_ITEMS = 1 + 4 * 3 + 1;                  // ring items per tile 
 constexpr int FI_PAR_FLOATS = N_LAYERS * 256 + 32;
 constexpr int FI_PAR_SLOTS = 4;
 constexpr int FI_PAR_BYTES = FI_PAR_SLOTS * FI_PAR_FLOATS * 4;
-constexpr int FI_BAR_BYTES = 8 * (2 * FI_STAGES + 4) + 16;
+constexpr int FI_BAR_BYTES = 8 * (2 * FI_STAGES + 5) + 16;
 constexpr int FI_SMEM = FI_H_BYTES + FI_STAGES * FI_SLOT + FI_PAR_BYTES + FI_BAR_BYTES;
 constexpr int FI_EPI_WARPS = 16;
 constexpr int FI_THREADS = 32 * (FI_EPI_WARPS + 2);
@@ -479,13 +479,15 @@ __global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
     const uint32_t bar_full = bars, bar_empty = bars + 8 * FI_STAGES;
     // acc_lo / acc_hi: accumulator columns 0-127 / 128-255 of the layer complete
     const uint32_t bar_acc_lo = bars + 16 * FI_STAGES, bar_acc_hi = bar_acc_lo + 8;
-    const uint32_t bar_a = bar_acc_hi + 8;
-    const uint32_t bar_p = bar_a + 8;   // parameter staging done (epilogue warps)
+    // a_lo / a_hi: k blocks 0-1 / 2-3 of the A tile are written and accumulator columns
+    // 0-127 / 128-255 read out (column groups 0-1 / 2-3 of the epilogue warps)
+    const uint32_t bar_a_lo = bar_acc_hi + 8, bar_a_hi = bar_a_lo + 8;
+    const uint32_t bar_p = bar_a_hi + 8;   // parameter staging done (epilogue warps)
     const uint32_t tslot = bar_p + 8;
     uint8_t* bars_g = fi_smem + FI_H_BYTES + FI_STAGES * FI_SLOT + FI_PAR_BYTES;
     volatile uint32_t* tslot_ptr =
-        reinterpret_cast<volatile uint32_t*>(bars_g + 16 * FI_STAGES + 32);
-    volatile int& abort_flag = *reinterpret_cast<volatile int*>(bars_g + 16 * FI_STAGES + 36);
+        reinterpret_cast<volatile uint32_t*>(bars_g + 16 * FI_STAGES + 40);
+    volatile int& abort_flag = *reinterpret_cast<volatile int*>(bars_g + 16 * FI_STAGES + 44);
 
     if ((base & 1023u) != 0u) {   // the swizzled tiles need 1024-byte alignment
         if (threadIdx.x == 0) atomicOr(&A.status[ST_CALL], DEV_RANGE);
@@ -498,7 +500,8 @@ __global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
         }
         mbar_init(bar_acc_lo, 1);
         mbar_init(bar_acc_hi, 1);
-        mbar_init(bar_a, 32 * FI_EPI_WARPS);
+        mbar_init(bar_a_lo, 16 * FI_EPI_WARPS);
+        mbar_init(bar_a_hi, 16 * FI_EPI_WARPS);
         mbar_init(bar_p, 32 * FI_EPI_WARPS);
         abort_flag = 0;
         fence_barrier_init();
@@ -576,12 +579,6 @@ __global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
                 for (int k = 0; k < M && ok; ++k) {
                     int q = 0;
                     for (int l = 0; l < N_LAYERS && ok; ++l) {
-                        if (!mbar_wait_sleep(bar_a, pa, A.wait_limit) || abort_flag) {
-                            ok = false;
-                            break;
-                        }
-                        pa ^= 1u;
-                        tc_fence_after();
                         const int n_items = (l == 1 || l == 2 || l == 3) ? 4 : 1;
                         // wait for the layer's stages (a hidden layer fills the ring)
                         int slots[4];
@@ -598,38 +595,72 @@ __global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
                             }
                         }
                         if (!ok) break;
-                        tc_fence_after();
-                        if (l < 4) {
-                            // output columns 0-127 first, so that half of the epilogue can
-                            // run while the MMAs of columns 128-255 do
-#pragma unroll 1
-                            for (int nh = 0; nh < 2; ++nh) {
-                                for (int x = 0; x < n_items; ++x) {
-                                    const uint64_t da = dh + (uint64_t)(x * (16384 >> 4));
-                                    const uint64_t db = dring +
-                                        (uint64_t)(slots[x] * (FI_SLOT >> 4) + nh * (16384 >> 4));
-#pragma unroll
-                                    for (int kk = 0; kk < 4; ++kk)
-                                        mma_bf16(tmem + (uint32_t)(nh * 128), da + 2 * kk,
-                                                 db + 2 * kk, ID128, (x > 0 || kk > 0) ? 1u : 0u);
-                                    if (nh == 1) mma_commit(bar_empty + 8 * slots[x]);
-                                }
-                                mma_commit(nh == 0 ? bar_acc_lo : bar_acc_hi);
+                        // the A tile's first half (k blocks 0-1) and accumulator columns
+                        // 0-127 are free once column groups 0-1 are done; the MMAs that
+                        // need only those start while groups 2-3 still work
+                        auto wait_a = [&](uint32_t bar) {
+                            if (!mbar_wait_sleep(bar, pa, A.wait_limit) || abort_flag) {
+                                ok = false;
+                                return;
                             }
+                            tc_fence_after();
+                        };
+                        auto mma_kb = [&](int x, int kb, int nh) {   // one 64-wide k block
+                            const uint64_t da = dh + (uint64_t)(kb * (16384 >> 4));
+                            const uint64_t db = dring +
+                                (uint64_t)(slots[x] * (FI_SLOT >> 4) + nh * (16384 >> 4));
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                mma_bf16(tmem + (uint32_t)(nh * 128), da + 2 * kk, db + 2 * kk,
+                                         ID128, (kb > 0 || kk > 0) ? 1u : 0u);
+                        };
+                        if (l == 0) {
+                            wait_a(bar_a_lo);
+                            if (ok) wait_a(bar_a_hi);
+                            if (!ok) break;
+                            mma_kb(0, 0, 0);
+                            mma_commit(bar_acc_lo);
+                            mma_kb(0, 0, 1);
+                            mma_commit(bar_empty + 8 * slots[0]);
+                            mma_commit(bar_acc_hi);
+                        } else if (l < 4) {
+                            wait_a(bar_a_lo);
+                            if (!ok) break;
+                            mma_kb(0, 0, 0);
+                            mma_kb(1, 1, 0);
+                            wait_a(bar_a_hi);
+                            if (!ok) break;
+                            mma_kb(2, 2, 0);
+                            mma_kb(3, 3, 0);
+                            mma_commit(bar_acc_lo);
+                            for (int x = 0; x < 4; ++x) {
+                                mma_kb(x, x, 1);
+                                mma_commit(bar_empty + 8 * slots[x]);
+                            }
+                            mma_commit(bar_acc_hi);
                         } else {
                             const uint64_t db = dring + (uint64_t)(slots[0] * (FI_SLOT >> 4));
-#pragma unroll
-                            for (int kb = 0; kb < 4; ++kb)
+                            auto mma_l4 = [&](int kb) {
 #pragma unroll
                                 for (int kk = 0; kk < 4; ++kk)
                                     mma_bf16(tmem, dh + (uint64_t)(kb * (16384 >> 4)) + 2 * kk,
                                              db + (uint64_t)(kb * ((int)IMG_L4_BLK * 2 >> 4)) +
                                                  2 * kk,
                                              ID16, (kb > 0 || kk > 0) ? 1u : 0u);
+                            };
+                            wait_a(bar_a_lo);
+                            if (!ok) break;
+                            mma_l4(0);
+                            mma_l4(1);
+                            wait_a(bar_a_hi);
+                            if (!ok) break;
+                            mma_l4(2);
+                            mma_l4(3);
                             mma_commit(bar_empty + 8 * slots[0]);
                             mma_commit(bar_acc_lo);
                             mma_commit(bar_acc_hi);
                         }
+                        pa ^= 1u;
                     }
                 }
             }
@@ -652,6 +683,7 @@ __global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
         const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
         const bool lead = cg == 0;                          // builds X0, keeps the ensemble
         const uint32_t bar_acc = cg < 2 ? bar_acc_lo : bar_acc_hi;   // my accumulator half
+        const uint32_t bar_a = cg < 2 ? bar_a_lo : bar_a_hi;         // my half of the A tile
         const int et = threadIdx.x;                         // 0 .. 32 * FI_EPI_WARPS - 1
         uint32_t pp = 0;
         bool ok = true;
@@ -713,23 +745,22 @@ __global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
                 tc_fence_before();
                 mbar_arrive(bar_a);
                 for (int l = 0; l < N_LAYERS; ++l) {
+                    // pacc: parity of this layer's phase of acc_lo and acc_hi
                     if (!mbar_wait_sleep(bar_acc, pacc, A.wait_limit)) {
                         ok = false;
                         break;
                     }
-                    pacc ^= 1u;
                     tc_fence_after();
                     const float* bias = pk_par + l * 256;
                     if (l < 4) {
                         // two 32-column halves; the second half's TMEM read is in flight
                         // while the first half is computed
-                        uint32_t ra[32], rb[32];
+                        uint32_t ra[32], rb[32], pk0[16], pk1[16];
                         tmem_ld32_async(trow + (uint32_t)(cg * 64), ra);
                         tmem_wait_ld(ra);
                         tmem_ld32_async(trow + (uint32_t)(cg * 64 + 32), rb);
-                        auto half = [&](const uint32_t (&rv)[32], int h) {
+                        auto half = [&](const uint32_t (&rv)[32], int h, uint32_t (&pk)[16]) {
                             const int c0 = cg * 64 + h * 32;
-                            uint32_t pk[16];
 #pragma unroll
                             for (int i = 0; i < 32; i += 4) {
                                 const float4 b4 = *reinterpret_cast<const float4*>(bias + c0 + i);
@@ -738,42 +769,62 @@ __global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
                                 pk[i / 2 + 1] = pack_bf16(gelu_half(__uint_as_float(rv[i + 2]), b4.z),
                                                           gelu_half(__uint_as_float(rv[i + 3]), b4.w));
                             }
-#pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                fi_store_chunk(H, r, cg, h * 4 + q,
-                                               make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2],
-                                                          pk[4 * q + 3]));
                         };
-                        half(ra, 0);
+                        half(ra, 0, pk0);
                         tmem_wait_ld(rb);
-                        half(rb, 1);
+                        half(rb, 1, pk1);
+                        // columns 0-127 are ready while the MMAs of columns 128-255 still
+                        // read the A tile: groups 0-1 store only once every MMA of the
+                        // layer has finished
+                        if (cg < 2 && !mbar_wait_sleep(bar_acc_hi, pacc, A.wait_limit)) {
+                            ok = false;
+                            break;
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            fi_store_chunk(H, r, cg, q,
+                                           make_uint4(pk0[4 * q], pk0[4 * q + 1], pk0[4 * q + 2],
+                                                      pk0[4 * q + 3]));
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            fi_store_chunk(H, r, cg, 4 + q,
+                                           make_uint4(pk1[4 * q], pk1[4 * q + 1], pk1[4 * q + 2],
+                                                      pk1[4 * q + 3]));
                         fence_proxy_async_smem();
                         tc_fence_before();
                         mbar_arrive(bar_a);
-                    } else if (lead) {
-                        float v[16];
-                        tmem_ld16(trow, v);
-                        float lg[N_OUT], mx = -3.0e38f;
+                    } else {
+                        if (lead) {
+                            float v[16];
+                            tmem_ld16(trow, v);
+                            float lg[N_OUT], mx = -3.0e38f;
 #pragma unroll
-                        for (int c = 0; c < N_OUT; ++c) {
-                            lg[c] = v[c] + bias[c];
-                            mx = fmaxf(mx, lg[c]);
+                            for (int c = 0; c < N_OUT; ++c) {
+                                lg[c] = v[c] + bias[c];
+                                mx = fmaxf(mx, lg[c]);
+                            }
+                            float p[N_OUT], sum = 0.f;
+#pragma unroll
+                            for (int c = 0; c < N_OUT; ++c) {
+                                p[c] = expf(lg[c] - mx);
+                                sum += p[c];
+                            }
+                            const float inv = 1.0f / sum;
+#pragma unroll
+                            for (int c = 0; c < N_OUT; ++c) {
+                                const float q = p[c] * inv;
+                                mean[c] += q;
+                                lo[c] = fminf(lo[c], q);
+                                hi[c] = fmaxf(hi[c], q);
+                            }
                         }
-                        float p[N_OUT], sum = 0.f;
-#pragma unroll
-                        for (int c = 0; c < N_OUT; ++c) {
-                            p[c] = expf(lg[c] - mx);
-                            sum += p[c];
-                        }
-                        const float inv = 1.0f / sum;
-#pragma unroll
-                        for (int c = 0; c < N_OUT; ++c) {
-                            const float q = p[c] * inv;
-                            mean[c] += q;
-                            lo[c] = fminf(lo[c], q);
-                            hi[c] = fmaxf(hi[c], q);
+                        // keep step with the acc_hi phases (groups 0-1 wait on it each layer)
+                        if (cg < 2 && !mbar_wait_sleep(bar_acc_hi, pacc, A.wait_limit)) {
+                            ok = false;
+                            break;
                         }
                     }
+                    pacc ^= 1u;
                 }
                 if (abort_flag) ok = false;
             }
