@@ -7,7 +7,7 @@ order than the oracle's, so they agree to rounding."""
 import numpy as np
 import pytest
 
-from gpu_helpers import gpu_mc, to_dev
+from gpu_helpers import gpu_mc, mc_batch_from_media, to_dev
 from paper_2409_00165_gb300 import fos
 from paper_2409_00165_gb300 import workloads as W
 
@@ -132,3 +132,30 @@ def test_solar_weighted_errors():
     _, st = _solar(1, wl, np.ones(3), c, allow=(fos.FOS_ERR_INJECTED,),
                    flags=fos.FOS_TEST_INJECT)
     assert st == fos.FOS_ERR_INJECTED
+
+
+def test_oblique_conductor_full_size_sampled_photons(orc):
+    """The bench's oblique-incidence leg at full size: the paint-layer medium, 50 um thick,
+    on the aluminium-like metal at 0, 30 and 60 degrees, 400 wavelengths x 1e6 photons.
+    Every item conserves its photons; 8 logged items give 40 sampled photons that match
+    the oracle's one-photon walks."""
+    m = W.oblique_conductor_media()
+    props = orc.mie_properties(m["wl"], m["nm"], m["species_group"], m["n_p"], m["radius"],
+                               m["vol_frac"], n_groups=m["n_groups"])
+    b = mc_batch_from_media(m, props, photons=1000000)
+    b.update(cos_incidence=m["cos_incidence"], n_below=m["n_below"], k_below=m["k_below"],
+             seed=13)
+    c, _ = gpu_mc(b, flags=fos.FOS_AUTOTUNE)
+    assert np.all(c[:, :4].sum(axis=1) == 1000000)
+    rng = np.random.default_rng(5)
+    items = np.sort(rng.choice(len(m["cos_incidence"]), size=8, replace=False)).astype(np.int32)
+    c2, log, _ = gpu_mc(dict(b, item_list=items), photon_log=True)
+    assert np.array_equal(c2, c[items])
+    for _ in range(40):
+        k = int(rng.integers(0, len(items)))
+        it = int(items[k])
+        p = int(rng.integers(0, 1000000))
+        one = dict(b, item_list=np.array([it], np.int32), photons_per_item=1,
+                   photon_first=np.full(len(m["cos_incidence"]), p, np.int64))
+        _, lo = orc.mc_run(one, fp32=True, photon_log=True)
+        assert log[k, p] == lo[0, 0], (it, p)
