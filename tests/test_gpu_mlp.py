@@ -386,3 +386,30 @@ def test_fused_inference_wait_gives_up_and_reports_timeout():
         fos.FOS_ERR_TIMEOUT
     fos.check(fos.fos_surrogate_predict(model, 1, feats, r2), "predict again")
     assert torch.equal(r1, r2)
+
+
+def test_fused_ensemble_with_more_members_than_parameter_slots():
+    """Six members: more than the kernel's four shared-memory parameter slots, so the
+    biases and statistics are staged member by member.  Mean and spread against the
+    bf16-mirrored oracle forward of each member."""
+    n = 3000
+    x, _ = _data(n, 9)
+    st, mean, std = _stats(x)
+    mb = fos.fos_surrogate_model_bytes()
+    model = torch.zeros(6 * mb, dtype=torch.uint8, device="cuda")
+    params = []
+    for k in range(6):
+        theta, ps = _host_theta(200 + k)
+        fos.check(fos.fos_surrogate_load(model[k * mb:(k + 1) * mb], 0,
+                                         torch.as_tensor(theta).cuda(), st), "load")
+        params.append(ps)
+    feats = torch.as_tensor(x, dtype=torch.float32).cuda().contiguous()
+    rat = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    spread = torch.zeros(n, dtype=torch.float32, device="cuda")
+    fos.check(fos.fos_surrogate_predict(model, 6, feats, rat, spread), "predict")
+    xs = np.asarray(x, np.float32).astype(np.float64)
+    outs = np.stack([M.forward(ps, xs, mean.astype(np.float32), std.astype(np.float32),
+                               round_fn=M.bf16_round) for ps in params])
+    assert np.max(np.abs(rat.double().cpu().numpy() - outs.mean(axis=0))) < 6e-3
+    want_spr = (outs.max(axis=0) - outs.min(axis=0)).max(axis=1)
+    assert np.max(np.abs(spread.double().cpu().numpy() - want_spr)) < 1.2e-2
