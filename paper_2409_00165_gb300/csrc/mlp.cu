@@ -68,10 +68,13 @@ struct Layout {
 
 // Weight image: the B operands of the fused inference kernel, already in the 128-byte-
 // swizzled K-major layout a stage of shared memory holds, so that one untiled bulk copy
-// fills a stage.  Layers 0-3 come in blocks of all 256 output rows x 64 inputs (32 KB),
-// one per k block (1 for layer 0, 4 for layers 1-3).  Layer 4 keeps its first 16 output
-// rows (3 real) as 4 blocks of 16 x 64 (2 KB), one per k block, copied as one stage.
-constexpr long long IMG_BLK = 256 * 64;          // elements of a 32 KB block
+// fills a stage (32 KB).  Layer 0 is one stage: all 256 output rows x 64 inputs (9 real).
+// Layers 1-3 are four stages each, (output half h, input pair j) in the order 2h + j:
+// 128 output rows x inputs 128 j .. +127, as two k blocks of 128 x 64 (16 KB).  Layer 4
+// keeps its first 16 output rows (3 real) as 4 blocks of 16 x 64 (2 KB), one per k
+// block, copied as one stage.
+constexpr long long IMG_BLK = 256 * 64;          // elements of a 32 KB stage
+constexpr long long IMG_HALF_KB = 128 * 64;      // elements of a 16 KB k block of a half
 constexpr long long IMG_L4_BLK = 16 * 64;        // elements of a 2 KB block
 __host__ __device__ constexpr long long img_off(int l) {
     return l == 0 ? 0 : (l == 4 ? 13 * IMG_BLK : (1 + 4 * (l - 1)) * IMG_BLK);
@@ -84,9 +87,14 @@ constexpr int IMG_ROWS_L4 = 16;
 // the k block) sits at chunk position j ^ (n mod 8).
 __host__ __device__ inline long long img_index(int l, int o, int i) {
     const int kb = i >> 6, c = i & 63;
-    const long long blk = (l == 4) ? IMG_L4_BLK : IMG_BLK;
-    if (l == 4 && o >= IMG_ROWS_L4) return -1;
-    return img_off(l) + (long long)kb * blk + o * 64 + ((((c >> 3) ^ (o & 7)) << 3) | (c & 7));
+    const long long swz = (((c >> 3) ^ (o & 7)) << 3) | (c & 7);
+    if (l == 4) {
+        if (o >= IMG_ROWS_L4) return -1;
+        return img_off(l) + (long long)kb * IMG_L4_BLK + o * 64 + swz;
+    }
+    if (l == 0) return img_off(l) + o * 64 + swz;
+    return img_off(l) + (long long)((o >> 7) * 2 + (kb >> 1)) * IMG_BLK +
+           (long long)(kb & 1) * IMG_HALF_KB + (o & 127) * 64 + swz;
 }
 
 static Layout make_layout() {
@@ -384,24 +392,35 @@ __global__ void __launch_bounds__(128, 1)
 // ----------------------------------------------------------------- fused inference
 // The whole ensemble forward pass for 128-row tiles in one persistent kernel (one CTA
 // per SM): raw features -> standardise -> 4 x (tcgen05 MMA, bias + GELU) -> MMA, softmax
-// -> ensemble mean, spread and fallback flag.  Activations never leave the SM: each
-// hidden layer's epilogue writes its BF16 output straight into shared memory in the
-// 128-byte-swizzled K-major layout that the next layer's MMA reads as its A operand.
-// Weights stream from the model's weight image (L2-resident) through a 4-slot ring of
-// 32 KB stages (one k block of a layer, all 256 output rows) filled by untiled bulk
-// copies, so a whole hidden layer is fetched while the previous layer's epilogue runs.
+// -> ensemble mean, spread and fallback flag.  Activations never leave the SM: they live
+// in tensor memory, which holds the FP32 accumulator (columns 0-255) and two BF16
+// activation buffers (columns 256-383 and 384-511, one 128 x 256 tile each, two elements
+// per column).  A layer's MMAs read their A operand from one buffer while its epilogue
+// writes the next layer's input into the other.
 //
-// Roles: the epilogue warps 0-15; warp w reads TMEM lanes 32 (w mod 4) .. +31 (its tile
-// rows) and columns 64 (w / 4) .. +63, which are exactly k block w / 4 of the next
-// layer's input.  The warps with w < 4 also build the layer-0 input and keep the
-// ensemble sums of their rows.  Lane 0 of warp 16 issues the bulk copies; lane 0 of
-// warp 17 issues the MMAs.  Barriers: full/empty per ring slot; `acc` (one MMA commit
-// per layer: accumulator ready); `a_ready` (512 arrivals: the A operand is written and the
-// accumulator read out); `par` (parameter staging).  Every wait is bounded; a wait that
-// gives up sets DEV_TIMEOUT, and the kernel drains its copies and MMAs and returns.
-constexpr int FI_STAGES = 4;
+// Each layer's output is produced in two halves of 128 columns (MMAs with N = 128, the
+// narrowest that keeps the tensor pipe at full rate; one commit per half), so that the
+// epilogue of half 0 runs while the MMAs of half 1 do.  Half h of the epilogue is k
+// blocks 2h, 2h + 1 of the next layer's input, and the next layer's first MMAs take
+// those k blocks as soon as the half is written: only k blocks 2-3 wait for the
+// epilogue of half 1.
+//
+// Weights stream from the model's weight image (L2-resident) through a ring of 32 KB
+// stages filled by untiled bulk copies, in the order the MMAs use them: layer 0 whole,
+// then per hidden layer (half 0, inputs 0-127), (half 0, inputs 128-255), (half 1, ...),
+// then layer 4 (16 output rows).
+//
+// Roles: the epilogue warps 0-15; warp w reads and writes TMEM lanes 32 (w mod 4) .. +31
+// (its tile rows), and in each half the 32 columns 32 (w / 4) .. +31.  The warps with
+// w < 4 also build the layer-0 input and keep the ensemble sums of their rows.  Lane 0 of
+// warp 16 issues the bulk copies; lane 0 of warp 17 issues the MMAs.  Barriers: full and
+// empty per ring slot; `acc` h (an MMA commit: output half h of the layer is
+// accumulated); `a_rdy` h (512 arrivals: k blocks 2h, 2h + 1 of the next layer's input are
+// written and output half h read out); `par` (parameter staging).  Every wait is
+// bounded; a wait that gives up sets DEV_TIMEOUT, and the kernel drains its copies and
+// MMAs and returns.
+constexpr int FI_STAGES = 6;
 constexpr int FI_SLOT = 32768;
-constexpr int FI_H_BYTES = 4 * 128 * 128;               // 128 rows x 256 bf16 (4 k blocks)
 constexpr int FI_ITEMS = 1 + 4 * 3 + 1;                  // ring items per tile and member
 // Per-member parameters staged in shared memory: biases of the 5 layers (256 each; the
 // hidden layers' halved, see the epilogue) and the feature means and standard deviations
@@ -409,10 +428,14 @@ constexpr int FI_ITEMS = 1 + 4 * 3 + 1;                  // ring items per tile 
 constexpr int FI_PAR_FLOATS = N_LAYERS * 256 + 32;
 constexpr int FI_PAR_SLOTS = 4;
 constexpr int FI_PAR_BYTES = FI_PAR_SLOTS * FI_PAR_FLOATS * 4;
-constexpr int FI_BAR_BYTES = 8 * (2 * FI_STAGES + 5) + 16;
-constexpr int FI_SMEM = FI_H_BYTES + FI_STAGES * FI_SLOT + FI_PAR_BYTES + FI_BAR_BYTES;
+constexpr int FI_NBARS = 2 * FI_STAGES + 2 + 2 + 1;
+constexpr int FI_BAR_BYTES = 8 * FI_NBARS + 16;
+constexpr int FI_SMEM = FI_STAGES * FI_SLOT + FI_PAR_BYTES + FI_BAR_BYTES;
 constexpr int FI_EPI_WARPS = 16;
 constexpr int FI_THREADS = 32 * (FI_EPI_WARPS + 2);
+constexpr uint32_t FI_TMEM_COLS = 512;
+constexpr uint32_t FI_ACC = 0;      // accumulator columns 0-255
+constexpr uint32_t FI_ABUF = 256;   // activation buffers: 256 + 128 b, b = 0, 1
 
 struct InferArgs {
     const float* feat;          // raw features [n_rows][9]
@@ -430,66 +453,76 @@ struct InferArgs {
     int test_stall;             // test only: the first weight copy is never issued
 };
 
-// Ring item q (0..13) of a tile-member: layer, k block, source offset in the image
-// (elements) and size.  Item 13 is layer 4 whole (its four 2 KB k blocks).
-__device__ __forceinline__ void fi_item(int q, int& layer, int& kb, long long& src,
+// Ring item q (0..13) of a tile-member: layer, stage index within the layer (2h + j for
+// layers 1-3), source offset in the image (elements) and size.  Item 13 is layer 4 whole
+// (its four 2 KB k blocks).
+__device__ __forceinline__ void fi_item(int q, int& layer, int& blk, long long& src,
                                         uint32_t& bytes) {
     if (q == 0) {
-        layer = 0; kb = 0;
+        layer = 0; blk = 0;
     } else if (q < 13) {
         layer = 1 + (q - 1) / 4;
-        kb = (q - 1) & 3;
+        blk = (q - 1) & 3;
     } else {
-        layer = 4; kb = 0;
+        layer = 4; blk = 0;
     }
-    src = img_off(layer) + (long long)kb * IMG_BLK;
+    src = img_off(layer) + (long long)blk * IMG_BLK;
     bytes = (layer == 4) ? (uint32_t)(4 * IMG_L4_BLK * 2) : (uint32_t)FI_SLOT;
 }
 
-// Writes 8 bf16 (one 16-byte chunk) of row r, columns 8j..8j+7 of k block kb, into the
-// swizzled A tile at h.
-__device__ __forceinline__ void fi_store_chunk(uint32_t h, int r, int kb, int j, uint4 v) {
-    const uint32_t a = h + (uint32_t)kb * 16384u + (uint32_t)(r >> 3) * 1024u +
-                       (uint32_t)(r & 7) * 128u + (uint32_t)((j ^ (r & 7)) << 4);
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y),
-                 "r"(v.z), "r"(v.w)
-                 : "memory");
-}
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&p);
 }
-// GELU (tanh form) of z = 2 hz from hz = z/2 = acc/2 + bias/2: hz (1 + tanh(u)) with
-// u = z (c0 + c1 z^2) = hz (2 c0 + 8 c1 hz^2), c0 = sqrt(2/pi), c1 = 0.044715 c0.
-__device__ __forceinline__ float gelu_half(float acc, float half_bias) {
-    const float hz = fmaf(0.5f, acc, half_bias);
-    const float h2 = hz * hz;
-    const float t = tanh_fast(hz * fmaf(0.2854192648f, h2, 1.5957691216f));
-    return fmaf(hz, t, hz);
+// Two-lane FP32 arithmetic (one instruction for both lanes, each lane rounded as the
+// scalar operation would be).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+// GELU (tanh form) of z = 2 hz from hz = z/2 = acc/2 + bias/2, for two columns: hz (1 +
+// tanh(u)) with u = z (c0 + c1 z^2) = hz (2 c0 + 8 c1 hz^2), c0 = sqrt(2/pi), c1 =
+// 0.044715 c0; returned as a packed BF16 pair.
+__device__ __forceinline__ uint32_t gelu_half2(float acc0, float acc1, float hb0, float hb1) {
+    const float2 hz = fma2(make_float2(0.5f, 0.5f), make_float2(acc0, acc1), make_float2(hb0, hb1));
+    const float2 h2 = mul2(hz, hz);
+    const float2 u = mul2(hz, fma2(make_float2(0.2854192648f, 0.2854192648f), h2,
+                                   make_float2(1.5957691216f, 1.5957691216f)));
+    const float2 g = fma2(hz, make_float2(tanh_fast(u.x), tanh_fast(u.y)), hz);
+    return pack_bf16(g.x, g.y);
 }
 
 __global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
     extern __shared__ __align__(1024) uint8_t fi_smem[];
     const uint32_t base = smem_u32(fi_smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t H = base;
-    const uint32_t ring = base + FI_H_BYTES;
-    float* par = reinterpret_cast<float*>(fi_smem + FI_H_BYTES + FI_STAGES * FI_SLOT);
+    const uint32_t ring = base;
+    float* par = reinterpret_cast<float*>(fi_smem + FI_STAGES * FI_SLOT);
     const uint32_t bars = ring + FI_STAGES * FI_SLOT + FI_PAR_BYTES;
     const uint32_t bar_full = bars, bar_empty = bars + 8 * FI_STAGES;
-    // acc_lo / acc_hi: accumulator columns 0-127 / 128-255 of the layer complete
-    const uint32_t bar_acc_lo = bars + 16 * FI_STAGES, bar_acc_hi = bar_acc_lo + 8;
-    // a_lo / a_hi: k blocks 0-1 / 2-3 of the A tile are written and accumulator columns
-    // 0-127 / 128-255 read out (column groups 0-1 / 2-3 of the epilogue warps)
-    const uint32_t bar_a_lo = bar_acc_hi + 8, bar_a_hi = bar_a_lo + 8;
-    const uint32_t bar_p = bar_a_hi + 8;   // parameter staging done (epilogue warps)
+    const uint32_t bar_acc = bars + 16 * FI_STAGES;   // 2: output half h accumulated
+    const uint32_t bar_a = bar_acc + 16;              // 2: input k blocks 2h, 2h+1 written
+    const uint32_t bar_p = bar_a + 16;                // parameter staging done
     const uint32_t tslot = bar_p + 8;
-    uint8_t* bars_g = fi_smem + FI_H_BYTES + FI_STAGES * FI_SLOT + FI_PAR_BYTES;
-    volatile uint32_t* tslot_ptr =
-        reinterpret_cast<volatile uint32_t*>(bars_g + 16 * FI_STAGES + 40);
-    volatile int& abort_flag = *reinterpret_cast<volatile int*>(bars_g + 16 * FI_STAGES + 44);
+    uint8_t* bars_g = fi_smem + FI_STAGES * FI_SLOT + FI_PAR_BYTES;
+    volatile uint32_t* tslot_ptr = reinterpret_cast<volatile uint32_t*>(bars_g + 8 * FI_NBARS);
+    volatile int& abort_flag = *reinterpret_cast<volatile int*>(bars_g + 8 * FI_NBARS + 4);
 
-    if ((base & 1023u) != 0u) {   // the swizzled tiles need 1024-byte alignment
+    if ((base & 1023u) != 0u) {   // the swizzled stages need 1024-byte alignment
         if (threadIdx.x == 0) atomicOr(&A.status[ST_CALL], DEV_RANGE);
         return;
     }
@@ -498,16 +531,16 @@ __global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
             mbar_init(bar_full + 8 * i, 1);
             mbar_init(bar_empty + 8 * i, 1);
         }
-        mbar_init(bar_acc_lo, 1);
-        mbar_init(bar_acc_hi, 1);
-        mbar_init(bar_a_lo, 16 * FI_EPI_WARPS);
-        mbar_init(bar_a_hi, 16 * FI_EPI_WARPS);
+        for (int h = 0; h < 2; ++h) {
+            mbar_init(bar_acc + 8 * h, 1);
+            mbar_init(bar_a + 8 * h, 32 * FI_EPI_WARPS);
+        }
         mbar_init(bar_p, 32 * FI_EPI_WARPS);
         abort_flag = 0;
         fence_barrier_init();
     }
     __syncwarp();
-    if (warp == 0) tmem_alloc(tslot, 256);
+    if (warp == 0) tmem_alloc(tslot, FI_TMEM_COLS);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -533,10 +566,10 @@ __global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
                     ok = false;
                     break;
                 }
-                int layer, kb;
+                int layer, blk;
                 long long src;
                 uint32_t bytes;
-                fi_item(item, layer, kb, src, bytes);
+                fi_item(item, layer, blk, src, bytes);
                 if (!(A.test_stall && issued == 0)) {
                     mbar_arrive_expect_tx(bar_full + 8 * slot, bytes);
                     bulk_load(ring + slot * FI_SLOT,
@@ -572,93 +605,80 @@ __global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
             uint32_t phase = 0, pa = 0;
             long long consumed = 0;
             bool ok = true;
-            const uint64_t dh = desc_sw128(H);
             const uint64_t dring = desc_sw128(ring);
             constexpr uint32_t ID128 = idesc_bf16(128, 128), ID16 = idesc_bf16(128, 16);
+            // next ring slot, once its copy has landed (bounded wait)
+            auto take = [&](int& s) {
+                if (!mbar_wait(bar_full + 8 * slot, phase, A.wait_limit)) return false;
+                s = slot;
+                ++consumed;
+                if (++slot == FI_STAGES) {
+                    slot = 0;
+                    phase ^= 1u;
+                }
+                return true;
+            };
+            // k blocks 2h, 2h + 1 of the layer's input are written (bounded wait)
+            auto wait_a = [&](int h) {
+                if (!mbar_wait_sleep(bar_a + 8 * h, pa, A.wait_limit) || abort_flag) return false;
+                tc_fence_after();
+                return true;
+            };
+            auto bdesc = [&](int s) { return dring + (uint64_t)(s * (FI_SLOT >> 4)); };
             for (long long t = 0; t < my_tiles && ok; ++t) {
                 for (int k = 0; k < M && ok; ++k) {
-                    int q = 0;
                     for (int l = 0; l < N_LAYERS && ok; ++l) {
-                        const int n_items = (l == 1 || l == 2 || l == 3) ? 4 : 1;
-                        // wait for the layer's stages (a hidden layer fills the ring)
-                        int slots[4];
-                        for (int x = 0; x < n_items && ok; ++x, ++q) {
-                            if (!mbar_wait(bar_full + 8 * slot, phase, A.wait_limit)) {
-                                ok = false;
-                                break;
-                            }
-                            slots[x] = slot;
-                            ++consumed;
-                            if (++slot == FI_STAGES) {
-                                slot = 0;
-                                phase ^= 1u;
-                            }
-                        }
-                        if (!ok) break;
-                        // the A tile's first half (k blocks 0-1) and accumulator columns
-                        // 0-127 are free once column groups 0-1 are done; the MMAs that
-                        // need only those start while groups 2-3 still work
-                        auto wait_a = [&](uint32_t bar) {
-                            if (!mbar_wait_sleep(bar, pa, A.wait_limit) || abort_flag) {
-                                ok = false;
-                                return;
-                            }
-                            tc_fence_after();
-                        };
-                        auto mma_kb = [&](int x, int kb, int nh) {   // one 64-wide k block
-                            const uint64_t da = dh + (uint64_t)(kb * (16384 >> 4));
-                            const uint64_t db = dring +
-                                (uint64_t)(slots[x] * (FI_SLOT >> 4) + nh * (16384 >> 4));
-#pragma unroll
-                            for (int kk = 0; kk < 4; ++kk)
-                                mma_bf16(tmem + (uint32_t)(nh * 128), da + 2 * kk, db + 2 * kk,
-                                         ID128, (kb > 0 || kk > 0) ? 1u : 0u);
-                        };
+                        const uint32_t ta = tmem + FI_ABUF + (uint32_t)((l & 1) * 128);
+                        int s = 0;
                         if (l == 0) {
-                            wait_a(bar_a_lo);
-                            if (ok) wait_a(bar_a_hi);
-                            if (!ok) break;
-                            mma_kb(0, 0, 0);
-                            mma_commit(bar_acc_lo);
-                            mma_kb(0, 0, 1);
-                            mma_commit(bar_empty + 8 * slots[0]);
-                            mma_commit(bar_acc_hi);
+                            // K = 16 covers the 9 features; half h of the 256 output rows
+                            // starts 128 rows (16 KB) into the stage
+                            if (!(ok = take(s))) break;
+                            ok = wait_a(0) && wait_a(1);
+                            if (ok)
+                                for (int h = 0; h < 2; ++h) {
+                                    mma_bf16_ts(tmem + FI_ACC + (uint32_t)(h * 128), ta,
+                                                bdesc(s) + (uint64_t)(h * (16384 >> 4)), ID128, 0u);
+                                    mma_commit(bar_acc + 8 * h);
+                                }
+                            mma_commit(bar_empty + 8 * s);
                         } else if (l < 4) {
-                            wait_a(bar_a_lo);
-                            if (!ok) break;
-                            mma_kb(0, 0, 0);
-                            mma_kb(1, 1, 0);
-                            wait_a(bar_a_hi);
-                            if (!ok) break;
-                            mma_kb(2, 2, 0);
-                            mma_kb(3, 3, 0);
-                            mma_commit(bar_acc_lo);
-                            for (int x = 0; x < 4; ++x) {
-                                mma_kb(x, x, 1);
-                                mma_commit(bar_empty + 8 * slots[x]);
+                            // stage (h, j): output rows 128 h .. +127 x k blocks 2j, 2j + 1
+                            for (int h = 0; h < 2 && ok; ++h) {
+                                for (int j = 0; j < 2 && ok; ++j) {
+                                    if (!(ok = take(s))) break;
+                                    if (h == 0 && !(ok = wait_a(j))) {
+                                        mma_commit(bar_empty + 8 * s);
+                                        break;
+                                    }
+#pragma unroll
+                                    for (int x = 0; x < 2; ++x) {
+                                        const int kb = 2 * j + x;
+#pragma unroll
+                                        for (int kk = 0; kk < 4; ++kk)
+                                            mma_bf16_ts(tmem + FI_ACC + (uint32_t)(h * 128),
+                                                        ta + (uint32_t)(kb * 32 + kk * 8),
+                                                        bdesc(s) + (uint64_t)(x * (16384 >> 4) + 2 * kk),
+                                                        ID128, (kb > 0 || kk > 0) ? 1u : 0u);
+                                    }
+                                    mma_commit(bar_empty + 8 * s);
+                                }
+                                if (ok) mma_commit(bar_acc + 8 * h);
                             }
-                            mma_commit(bar_acc_hi);
                         } else {
-                            const uint64_t db = dring + (uint64_t)(slots[0] * (FI_SLOT >> 4));
-                            auto mma_l4 = [&](int kb) {
+                            // the 16 padded output columns (3 real), four 2 KB k blocks
+                            if (!(ok = take(s))) break;
+                            for (int kb = 0; kb < 4 && ok; ++kb) {
+                                if ((kb & 1) == 0 && !(ok = wait_a(kb >> 1))) break;
 #pragma unroll
                                 for (int kk = 0; kk < 4; ++kk)
-                                    mma_bf16(tmem, dh + (uint64_t)(kb * (16384 >> 4)) + 2 * kk,
-                                             db + (uint64_t)(kb * ((int)IMG_L4_BLK * 2 >> 4)) +
-                                                 2 * kk,
-                                             ID16, (kb > 0 || kk > 0) ? 1u : 0u);
-                            };
-                            wait_a(bar_a_lo);
-                            if (!ok) break;
-                            mma_l4(0);
-                            mma_l4(1);
-                            wait_a(bar_a_hi);
-                            if (!ok) break;
-                            mma_l4(2);
-                            mma_l4(3);
-                            mma_commit(bar_empty + 8 * slots[0]);
-                            mma_commit(bar_acc_lo);
-                            mma_commit(bar_acc_hi);
+                                    mma_bf16_ts(tmem + FI_ACC, ta + (uint32_t)(kb * 32 + kk * 8),
+                                                bdesc(s) + (uint64_t)(kb * ((int)IMG_L4_BLK * 2 >> 4) + 2 * kk),
+                                                ID16, (kb > 0 || kk > 0) ? 1u : 0u);
+                            }
+                            mma_commit(bar_empty + 8 * s);
+                            if (ok)
+                                for (int h = 0; h < 2; ++h) mma_commit(bar_acc + 8 * h);
                         }
                         pa ^= 1u;
                     }
@@ -678,12 +698,10 @@ __global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue warps
-        const int quarter = warp & 3, cg = warp >> 2;       // TMEM lane quarter, k block
-        const int r = quarter * 32 + lane;                  // tile row = TMEM lane
-        const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+        const int lq = warp & 3, cg = warp >> 2;            // TMEM lane quarter, column group
+        const int r = lq * 32 + lane;                       // tile row = TMEM lane
+        const uint32_t trow = tmem + ((uint32_t)(lq * 32) << 16);
         const bool lead = cg == 0;                          // builds X0, keeps the ensemble
-        const uint32_t bar_acc = cg < 2 ? bar_acc_lo : bar_acc_hi;   // my accumulator half
-        const uint32_t bar_a = cg < 2 ? bar_a_lo : bar_a_hi;         // my half of the A tile
         const int et = threadIdx.x;                         // 0 .. 32 * FI_EPI_WARPS - 1
         uint32_t pp = 0;
         bool ok = true;
@@ -728,100 +746,80 @@ __global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
                     if (!ok) break;
                 }
                 const float* pk_par = par + (k % FI_PAR_SLOTS) * FI_PAR_FLOATS;
-                if (lead) {   // layer-0 input: standardised features in columns 0-8, zeros to 63
+                if (lead) {   // layer-0 input: standardised features in k 0-8, zeros to 15
                     const float* st = pk_par + N_LAYERS * 256;
                     float z[N_FEAT];
 #pragma unroll
                     for (int f = 0; f < N_FEAT; ++f) z[f] = (x[f] - st[f]) / st[16 + f];
-                    fi_store_chunk(H, r, 0, 0,
-                                   make_uint4(pack_bf16(z[0], z[1]), pack_bf16(z[2], z[3]),
-                                              pack_bf16(z[4], z[5]), pack_bf16(z[6], z[7])));
-                    fi_store_chunk(H, r, 0, 1, make_uint4(pack_bf16(z[8], 0.f), 0u, 0u, 0u));
-#pragma unroll
-                    for (int j = 2; j < 8; ++j)
-                        fi_store_chunk(H, r, 0, j, make_uint4(0u, 0u, 0u, 0u));
-                    fence_proxy_async_smem();
+                    const uint32_t pk[8] = {pack_bf16(z[0], z[1]), pack_bf16(z[2], z[3]),
+                                            pack_bf16(z[4], z[5]), pack_bf16(z[6], z[7]),
+                                            pack_bf16(z[8], 0.f), 0u, 0u, 0u};
+                    tmem_st8(trow + FI_ABUF, pk);
+                    tmem_wait_st();
                 }
                 tc_fence_before();
                 mbar_arrive(bar_a);
-                for (int l = 0; l < N_LAYERS; ++l) {
-                    // pacc: parity of this layer's phase of acc_lo and acc_hi
-                    if (!mbar_wait_sleep(bar_acc, pacc, A.wait_limit)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
+                mbar_arrive(bar_a + 8);
+                for (int l = 0; l < N_LAYERS && ok; ++l) {
+                    // pacc: parity of this layer's phase of the acc barriers; every thread
+                    // waits for both halves of every layer (a parity wait that fell two
+                    // phases behind its barrier would return at once)
                     const float* bias = pk_par + l * 256;
-                    if (l < 4) {
-                        // two 32-column halves; the second half's TMEM read is in flight
-                        // while the first half is computed
-                        uint32_t ra[32], rb[32], pk0[16], pk1[16];
-                        tmem_ld32_async(trow + (uint32_t)(cg * 64), ra);
-                        tmem_wait_ld(ra);
-                        tmem_ld32_async(trow + (uint32_t)(cg * 64 + 32), rb);
-                        auto half = [&](const uint32_t (&rv)[32], int h, uint32_t (&pk)[16]) {
-                            const int c0 = cg * 64 + h * 32;
-#pragma unroll
-                            for (int i = 0; i < 32; i += 4) {
-                                const float4 b4 = *reinterpret_cast<const float4*>(bias + c0 + i);
-                                pk[i / 2] = pack_bf16(gelu_half(__uint_as_float(rv[i]), b4.x),
-                                                      gelu_half(__uint_as_float(rv[i + 1]), b4.y));
-                                pk[i / 2 + 1] = pack_bf16(gelu_half(__uint_as_float(rv[i + 2]), b4.z),
-                                                          gelu_half(__uint_as_float(rv[i + 3]), b4.w));
-                            }
-                        };
-                        half(ra, 0, pk0);
-                        tmem_wait_ld(rb);
-                        half(rb, 1, pk1);
-                        // columns 0-127 are ready while the MMAs of columns 128-255 still
-                        // read the A tile: groups 0-1 store only once every MMA of the
-                        // layer has finished
-                        if (cg < 2 && !mbar_wait_sleep(bar_acc_hi, pacc, A.wait_limit)) {
+                    const uint32_t dst = trow + FI_ABUF + (uint32_t)(((l + 1) & 1) * 128);
+                    for (int h = 0; h < 2; ++h) {
+                        if (!mbar_wait_sleep(bar_acc + 8 * h, pacc, A.wait_limit)) {
                             ok = false;
                             break;
                         }
+                        if (l == 4) continue;
+                        tc_fence_after();
+                        uint32_t v[32];
+                        tmem_ld32_async(trow + FI_ACC + (uint32_t)(h * 128 + cg * 32), v);
+                        tmem_wait_ld(v);
+                        // output columns 128 h + 32 cg .. +31 = next-layer inputs, two per
+                        // TMEM column, stored 16 at a time
 #pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            fi_store_chunk(H, r, cg, q,
-                                           make_uint4(pk0[4 * q], pk0[4 * q + 1], pk0[4 * q + 2],
-                                                      pk0[4 * q + 3]));
+                        for (int c16 = 0; c16 < 32; c16 += 16) {
+                            const float* b = bias + h * 128 + cg * 32 + c16;
+                            uint32_t pk[8];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            fi_store_chunk(H, r, cg, 4 + q,
-                                           make_uint4(pk1[4 * q], pk1[4 * q + 1], pk1[4 * q + 2],
-                                                      pk1[4 * q + 3]));
-                        fence_proxy_async_smem();
+                            for (int i = 0; i < 16; i += 4) {
+                                const float4 b4 = *reinterpret_cast<const float4*>(b + i);
+                                pk[i / 2] = gelu_half2(__uint_as_float(v[c16 + i]),
+                                                       __uint_as_float(v[c16 + i + 1]), b4.x, b4.y);
+                                pk[i / 2 + 1] = gelu_half2(__uint_as_float(v[c16 + i + 2]),
+                                                           __uint_as_float(v[c16 + i + 3]), b4.z,
+                                                           b4.w);
+                            }
+                            tmem_st8(dst + (uint32_t)(h * 64 + cg * 16 + c16 / 2), pk);
+                        }
+                        tmem_wait_st();
                         tc_fence_before();
-                        mbar_arrive(bar_a);
-                    } else {
-                        if (lead) {
-                            float v[16];
-                            tmem_ld16(trow, v);
-                            float lg[N_OUT], mx = -3.0e38f;
+                        mbar_arrive(bar_a + 8 * h);
+                    }
+                    if (ok && l == 4 && lead) {
+                        tc_fence_after();
+                        float v[16];
+                        tmem_ld16(trow + FI_ACC, v);
+                        float lg[N_OUT], mx = -3.0e38f;
 #pragma unroll
-                            for (int c = 0; c < N_OUT; ++c) {
-                                lg[c] = v[c] + bias[c];
-                                mx = fmaxf(mx, lg[c]);
-                            }
-                            float p[N_OUT], sum = 0.f;
-#pragma unroll
-                            for (int c = 0; c < N_OUT; ++c) {
-                                p[c] = expf(lg[c] - mx);
-                                sum += p[c];
-                            }
-                            const float inv = 1.0f / sum;
-#pragma unroll
-                            for (int c = 0; c < N_OUT; ++c) {
-                                const float q = p[c] * inv;
-                                mean[c] += q;
-                                lo[c] = fminf(lo[c], q);
-                                hi[c] = fmaxf(hi[c], q);
-                            }
+                        for (int c = 0; c < N_OUT; ++c) {
+                            lg[c] = v[c] + bias[c];
+                            mx = fmaxf(mx, lg[c]);
                         }
-                        // keep step with the acc_hi phases (groups 0-1 wait on it each layer)
-                        if (cg < 2 && !mbar_wait_sleep(bar_acc_hi, pacc, A.wait_limit)) {
-                            ok = false;
-                            break;
+                        float p[N_OUT], sum = 0.f;
+#pragma unroll
+                        for (int c = 0; c < N_OUT; ++c) {
+                            p[c] = expf(lg[c] - mx);
+                            sum += p[c];
+                        }
+                        const float inv = 1.0f / sum;
+#pragma unroll
+                        for (int c = 0; c < N_OUT; ++c) {
+                            const float q = p[c] * inv;
+                            mean[c] += q;
+                            lo[c] = fminf(lo[c], q);
+                            hi[c] = fmaxf(hi[c], q);
                         }
                     }
                     pacc ^= 1u;
@@ -850,7 +848,7 @@ __global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 256);
+    if (warp == 0) tmem_dealloc(tmem, FI_TMEM_COLS);
 }
 
 // ----------------------------------------------------------------------- small kernels
