@@ -371,6 +371,44 @@ def test_fused_ensemble_matches_oracle_on_a_ragged_batch():
     assert got_need[list(rows).index(17)] == 1
 
 
+def test_fused_ensemble_small_and_empty_batches():
+    """Batches of 0, 1, 127, 128 and 129 rows (fewer tiles than CTAs, one full tile, a
+    full tile plus one row): an empty call succeeds and writes nothing; every row of the
+    others matches the bf16-mirrored oracle forward, and a row's result does not depend on
+    the batch it comes in (bit for bit)."""
+    x, _ = _data(129, 11)
+    st, mean, std = _stats(x)
+    mb = fos.fos_surrogate_model_bytes()
+    model = torch.zeros(2 * mb, dtype=torch.uint8, device="cuda")
+    params = []
+    for k in range(2):
+        theta, ps = _host_theta(200 + k)
+        fos.check(fos.fos_surrogate_load(model[k * mb:(k + 1) * mb], 0,
+                                         torch.as_tensor(theta).cuda(), st), "load")
+        params.append(ps)
+    feats = torch.as_tensor(x, dtype=torch.float32).cuda().contiguous()
+    rat0 = torch.full((1, 3), -1.0, dtype=torch.float32, device="cuda")
+    assert fos.fos_surrogate_predict(model, 2, feats[:0], rat0[:0]) == fos.FOS_OK
+    assert torch.all(rat0 == -1.0)
+    xs = np.asarray(x, np.float32).astype(np.float64)
+    outs = np.stack([M.forward(ps, xs, mean.astype(np.float32), std.astype(np.float32),
+                               round_fn=M.bf16_round) for ps in params])
+    want = outs.mean(axis=0)
+    results = {}
+    for n in (1, 127, 128, 129):
+        rat = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+        spread = torch.zeros(n, dtype=torch.float32, device="cuda")
+        fos.check(fos.fos_surrogate_predict(model, 2, feats[:n].contiguous(), rat, spread),
+                  f"predict {n}")
+        got = rat.double().cpu().numpy()
+        assert np.max(np.abs(got - want[:n])) < 6e-3, n
+        assert np.allclose(got.sum(axis=1), 1.0, atol=1e-5)
+        results[n] = (rat.cpu(), spread.cpu())
+    for n in (1, 127, 128):
+        assert torch.equal(results[n][0], results[129][0][:n])
+        assert torch.equal(results[n][1], results[129][1][:n])
+
+
 def test_fused_inference_wait_gives_up_and_reports_timeout():
     """The fused inference kernel with its first weight copy withheld (test flag): the
     bounded waits run out, the kernel drains and returns FOS_ERR_TIMEOUT, and the next
