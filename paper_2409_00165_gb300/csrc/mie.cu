@@ -93,11 +93,12 @@ __device__ __forceinline__ void flag(unsigned* st, unsigned bit, long long idx) 
 }
 
 // Downward recurrence D_{n-1} = n/z - 1/(D_n + n/z) from D_{nstart} = 0; D_n stored for
-// n <= nt at col[(n-1) T].
-__device__ __forceinline__ void downward_D(cx z, int nstart, int nt, double2* col, long long T) {
+// nlow <= n <= nt at col[(n-1) T] (orders below nlow are not needed by the caller).
+__device__ __forceinline__ void downward_D(cx z, int nstart, int nt, double2* col, long long T,
+                                           int nlow = 1) {
     const cx zi = mk(1.0, 0.0) / z;
     cx D = mk(0.0, 0.0);
-    for (int n = nstart; n >= 1; --n) {
+    for (int n = nstart; n >= nlow; --n) {
         if (n <= nt) col[(long long)(n - 1) * T] = make_double2(D.re, D.im);
         const cx nz = (double)n * zi;
         D = nz - mk(1.0, 0.0) / (D + nz);
@@ -107,6 +108,20 @@ __device__ __forceinline__ void downward_D(cx z, int nstart, int nt, double2* co
 struct Sums {
     double ext, sca, g;
 };
+
+// Order weights of Eq. 15: m (m + 2) / (m + 1) and (2m + 1) / (m (m + 1)), m = 1 .. 511,
+// evaluated by the compiler (IEEE double, as the kernel would) into constant memory.
+struct Eq15Weights {
+    double c1[FOS_MIE_MAX_TERMS], c2[FOS_MIE_MAX_TERMS];
+    constexpr Eq15Weights() : c1(), c2() {
+        for (int i = 1; i < FOS_MIE_MAX_TERMS; ++i) {
+            const double m = (double)i;
+            c1[i] = m * (m + 2.0) / (m + 1.0);
+            c2[i] = (2.0 * m + 1.0) / (m * (m + 1.0));
+        }
+    }
+};
+__constant__ Eq15Weights g_eq15 = Eq15Weights();
 
 // Accumulates Eqs. 11, 12 and the numerator of 15 for order n given a_n, b_n and the
 // previous order's coefficients.
@@ -119,11 +134,10 @@ __device__ __forceinline__ void accumulate(Sums& S, int n, int nmax, cx an, cx b
         S.sca += wgt * (norm2(an) + norm2(bn));             // Eq. 12
     }
     if (n >= 2) {   // Eq. 15 term of order m = n-1 needs a_n, b_n
-        const double m = dn - 1.0;
         const double t1 = a_prev.re * an.re + a_prev.im * an.im + b_prev.re * bn.re +
                           b_prev.im * bn.im;              // Re(a_m a_n^* + b_m b_n^*)
         const double t2 = a_prev.re * b_prev.re + a_prev.im * b_prev.im;   // Re(a_m b_m^*)
-        S.g += m * (m + 2.0) / (m + 1.0) * t1 + (2.0 * m + 1.0) / (m * (m + 1.0)) * t2;
+        S.g += g_eq15.c1[n - 1] * t1 + g_eq15.c2[n - 1] * t2;
     }
 }
 
@@ -138,9 +152,11 @@ __device__ __forceinline__ void efficiencies(const Sums& S, double lam, double r
     *gg = (S.sca > 0.0) ? 2.0 * S.g / S.sca : 0.0;
 }
 
-// Homogeneous sphere (Eqs. 1-5): D_n(y), D_n(x) downward; psi_n(x) upward while
-// n <= |x|, psi_{n-1}/(D_n(x) + n/x) above; xi_n(x) upward; Eqs. 2-3 multiplied through
-// by psi_n(x) and xi_n(x).  Returns false when n_max + 16 exceeds the scratch.
+// Homogeneous sphere (Eqs. 1-5): D_n(y), D_n(x) downward (the latter only for n > |x|);
+// psi_n(x) upward while n <= |x|, psi_{n-1}/(D_n(x) + n/x) above; xi_n(x) upward; Eqs. 2-3
+// multiplied through by psi_n(x) and xi_n(x), and a_n divided through by n_p, b_n by n_m:
+// a_n = (q D_n(y) psi_n - psi_n') / (q D_n(y) xi_n - xi_n'), q = n_m / n_p, and b_n the
+// same with 1/q.  Returns false when n_max + 16 exceeds the scratch.
 __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY, double2* colX,
                             long long T, double* qe, double* qs, double* gg) {
     const double k = 2.0 * M_PI * r / lam;
@@ -153,31 +169,33 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
     if (nstart > FOS_MIE_MAX_TERMS) return false;
     const cx xi_ = mk(1.0, 0.0) / x;
     downward_D(y, nstart, nt, colY, T);
-    downward_D(x, nstart, nt, colX, T);
+    downward_D(x, nstart, nt, colX, T, (int)fmin(floor(ax) + 1.0, (double)nstart));
     cx psi_m1 = ccos(x), psi_0 = csin(x);
     const double eb = exp(-x.im);
     cx xi_m1 = mk(eb * cos(x.re), eb * sin(x.re));        // e^{ix}
     cx xi_0 = psi_0 - mk(-psi_m1.im, psi_m1.re);            // sin x - i cos x
     const cx inv_nm2 = mk(1.0, 0.0) / (n_m * n_m);
+    const cx q = n_m / n_p, qi = n_p / n_m;
     Sums S{0.0, 0.0, 0.0};
     cx a_prev = mk(0.0, 0.0), b_prev = mk(0.0, 0.0);
     for (int n = 1; n <= nt; ++n) {
         const double dn = (double)n;
+        const cx c = (double)(2 * n - 1) * xi_, nx = dn * xi_;
         cx psi_n;
         if (dn <= ax) {
-            psi_n = (double)(2 * n - 1) * xi_ * psi_0 - psi_m1;
+            psi_n = c * psi_0 - psi_m1;
         } else {
             const double2 d = colX[(long long)(n - 1) * T];
-            psi_n = psi_0 / (mk(d.x, d.y) + dn * xi_);
+            psi_n = psi_0 / (mk(d.x, d.y) + nx);
         }
-        const cx xi_n = (double)(2 * n - 1) * xi_ * xi_0 - xi_m1;
-        const cx dpsi = psi_0 - dn * xi_ * psi_n;
-        const cx dxi = xi_0 - dn * xi_ * xi_n;
+        const cx xi_n = c * xi_0 - xi_m1;
+        const cx dpsi = psi_0 - nx * psi_n;
+        const cx dxi = xi_0 - nx * xi_n;
         const double2 dy = colY[(long long)(n - 1) * T];
         const cx Dy = mk(dy.x, dy.y);
-        const cx mDy = n_m * Dy, pDy = n_p * Dy;
-        const cx an = (mDy * psi_n - n_p * dpsi) / (mDy * xi_n - n_p * dxi);   // Eq. 2
-        const cx bn = (pDy * psi_n - n_m * dpsi) / (pDy * xi_n - n_m * dxi);   // Eq. 3
+        const cx qa = q * Dy, qb = qi * Dy;
+        const cx an = (qa * psi_n - dpsi) / (qa * xi_n - dxi);   // Eq. 2
+        const cx bn = (qb * psi_n - dpsi) / (qb * xi_n - dxi);   // Eq. 3
         accumulate(S, n, nmax, an, bn, a_prev, b_prev, inv_nm2);
         a_prev = an;
         b_prev = bn;
