@@ -32,7 +32,9 @@ __device__ __forceinline__ cx operator*(cx a, cx b) {
 }
 __device__ __forceinline__ cx operator*(double s, cx a) { return cx{s * a.re, s * a.im}; }
 // Complex division a/b = a conj(b) / |b|^2 with one real division; Smith's algorithm
-// (no intermediate overflow) when |b| is outside [1e-150, 1e150].
+// (no intermediate overflow) when the larger part of b is outside [2^-490, 2^491).  The
+// range test reads the exponent fields with integer instructions, which keeps it off the
+// FP64 pipe that bounds this kernel.
 __device__ __forceinline__ cx div_smith(cx a, cx b) {
     if (fabs(b.re) >= fabs(b.im)) {
         const double r = b.im / b.re, d = b.re + b.im * r;
@@ -42,9 +44,12 @@ __device__ __forceinline__ cx div_smith(cx a, cx b) {
         return cx{(a.re * r + a.im) / d, (a.im * r - a.re) / d};
     }
 }
+__device__ __forceinline__ int exponent_field(double v) {
+    return (__double2hiint(v) >> 20) & 0x7ff;
+}
 __device__ __forceinline__ cx operator/(cx a, cx b) {
-    const double m = fmax(fabs(b.re), fabs(b.im));
-    if (m > 1e150 || m < 1e-150) return div_smith(a, b);
+    const int e = max(exponent_field(b.re), exponent_field(b.im));
+    if (e > 1023 + 490 || e < 1023 - 490) return div_smith(a, b);
     const double inv = 1.0 / (b.re * b.re + b.im * b.im);
     return cx{(a.re * b.re + a.im * b.im) * inv, (a.im * b.re - a.re * b.im) * inv};
 }
