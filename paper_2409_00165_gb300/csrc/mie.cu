@@ -53,6 +53,13 @@ __device__ __forceinline__ cx operator/(cx a, cx b) {
     const double inv = 1.0 / (b.re * b.re + b.im * b.im);
     return cx{(a.re * b.re + a.im * b.im) * inv, (a.im * b.re - a.re * b.im) * inv};
 }
+// 1/b = conj(b) / |b|^2 (the quotient above with a = 1, without its products by 0).
+__device__ __forceinline__ cx crcp(cx b) {
+    const int e = max(exponent_field(b.re), exponent_field(b.im));
+    if (e > 1023 + 490 || e < 1023 - 490) return div_smith(cx{1.0, 0.0}, b);
+    const double inv = 1.0 / (b.re * b.re + b.im * b.im);
+    return cx{b.re * inv, -b.im * inv};
+}
 __device__ __forceinline__ double norm2(cx a) { return a.re * a.re + a.im * a.im; }
 __device__ __forceinline__ double cabs_(cx a) { return hypot(a.re, a.im); }
 __device__ __forceinline__ cx csin(cx z) {
@@ -101,12 +108,12 @@ __device__ __forceinline__ void flag(unsigned* st, unsigned bit, long long idx) 
 // nlow <= n <= nt at col[(n-1) T] (orders below nlow are not needed by the caller).
 __device__ __forceinline__ void downward_D(cx z, int nstart, int nt, double2* col, long long T,
                                            int nlow = 1) {
-    const cx zi = mk(1.0, 0.0) / z;
+    const cx zi = crcp(z);
     cx D = mk(0.0, 0.0);
     for (int n = nstart; n >= nlow; --n) {
         if (n <= nt) col[(long long)(n - 1) * T] = make_double2(D.re, D.im);
         const cx nz = (double)n * zi;
-        D = nz - mk(1.0, 0.0) / (D + nz);
+        D = nz - crcp(D + nz);
     }
 }
 
@@ -172,14 +179,17 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
     const int nt = nmax + 1;          // a_{n+1}, b_{n+1} for Eq. 15
     const int nstart = nt + 16;
     if (nstart > FOS_MIE_MAX_TERMS) return false;
-    const cx xi_ = mk(1.0, 0.0) / x;
+    const cx xi_ = crcp(x);
     downward_D(y, nstart, nt, colY, T);
-    downward_D(x, nstart, nt, colX, T, (int)fmin(floor(ax) + 1.0, (double)nstart));
+    // orders n <= n_up (n <= |x|) take psi_n(x) from the upward recurrence; integer
+    // comparisons keep the per-order test off the FP64 pipe
+    const int n_up = (int)fmin(floor(ax), (double)nstart);
+    downward_D(x, nstart, nt, colX, T, n_up + 1);
     cx psi_m1 = ccos(x), psi_0 = csin(x);
     const double eb = exp(-x.im);
     cx xi_m1 = mk(eb * cos(x.re), eb * sin(x.re));        // e^{ix}
     cx xi_0 = psi_0 - mk(-psi_m1.im, psi_m1.re);            // sin x - i cos x
-    const cx inv_nm2 = mk(1.0, 0.0) / (n_m * n_m);
+    const cx inv_nm2 = crcp(n_m * n_m);
     const cx q = n_m / n_p, qi = n_p / n_m;
     Sums S{0.0, 0.0, 0.0};
     cx a_prev = mk(0.0, 0.0), b_prev = mk(0.0, 0.0);
@@ -187,7 +197,7 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
         const double dn = (double)n;
         const cx c = (double)(2 * n - 1) * xi_, nx = dn * xi_;
         cx psi_n;
-        if (dn <= ax) {
+        if (n <= n_up) {
             psi_n = c * psi_0 - psi_m1;
         } else {
             const double2 d = colX[(long long)(n - 1) * T];
@@ -217,12 +227,12 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
 // while n <= |z| and psi_{n-1}/(D_n + n/z) above; chi by upward recurrence.
 struct RB {
     cx zi;
-    double az;
+    int n_up;                        // orders n <= |z|: psi by the upward recurrence
     cx psi_m1, psi0, chi_m1, chi0;   // orders n-2, n-1
 };
 __device__ __forceinline__ void rb_init(RB& R, cx z) {
-    R.zi = mk(1.0, 0.0) / z;
-    R.az = cabs_(z);
+    R.zi = crcp(z);
+    R.n_up = (int)fmin(floor(cabs_(z)), (double)FOS_MIE_MAX_TERMS);
     R.psi_m1 = ccos(z);
     R.psi0 = csin(z);
     R.chi_m1 = csin(z);
@@ -233,7 +243,7 @@ __device__ __forceinline__ void rb_step(RB& R, int n, const double2* colD, long 
                                         cx& dpsi, cx& chi, cx& dchi) {
     const double dn = (double)n;
     const cx c = (double)(2 * n - 1) * R.zi;
-    if (dn <= R.az) {
+    if (n <= R.n_up) {
         psi = c * R.psi0 - R.psi_m1;
     } else {
         const double2 d = colD[(long long)(n - 1) * T];
@@ -257,7 +267,7 @@ __device__ bool coated_eval(double lam, double a, double b, cx n_c, cx n_s, cx n
                             long long T, double* qe, double* qs, double* gg) {
     const double kv = 2.0 * M_PI / lam;
     const cx x = (kv * a) * n_m, y = (kv * b) * n_m;
-    const cx inv_nm = mk(1.0, 0.0) / n_m;
+    const cx inv_nm = crcp(n_m);
     const cx m1 = n_c * inv_nm, m2 = n_s * inv_nm;
     const double ymax = kv * b * fmax(cabs_(n_c), cabs_(n_s));
     const int nmax = (int)ceil(2.0 + ymax + 4.3 * cbrt(ymax));
