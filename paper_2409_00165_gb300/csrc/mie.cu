@@ -121,7 +121,14 @@ __device__ __forceinline__ void downward_D(cx z, int nstart, int nt, double2* co
     for (int n = nstart; n >= nlow; --n) {
         if (n <= nt) col[(long long)(n - 1) * T] = make_double2(D.re, D.im);
         const cx nz = (double)n * zi;
-        D = nz - crcp(D + nz);
+        const cx w = D + nz;   // D_{n-1} = nz - conj(w) / |w|^2
+        const int e = max(exponent_field(w.re), exponent_field(w.im));
+        if (e > 1023 + 490 || e < 1023 - 490) {
+            D = nz - div_smith(mk(1.0, 0.0), w);
+        } else {
+            const double inv = 1.0 / (w.re * w.re + w.im * w.im);
+            D = mk(fma(-w.re, inv, nz.re), fma(w.im, inv, nz.im));
+        }
     }
 }
 
