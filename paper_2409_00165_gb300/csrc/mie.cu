@@ -61,10 +61,13 @@ __device__ __forceinline__ cx crcp(cx b) {
     return cx{b.re * inv, -b.im * inv};
 }
 __device__ __forceinline__ double norm2(cx a) { return a.re * a.re + a.im * a.im; }
-// a b - c and c - a b with the subtraction folded into the fused multiply-adds (two FP64
-// instructions per part instead of three).
+// a b - c, a b + c and c - a b with the addition folded into the fused multiply-adds (two
+// FP64 instructions per part instead of three).
 __device__ __forceinline__ cx mul_sub(cx a, cx b, cx c) {
     return cx{fma(a.re, b.re, fma(-a.im, b.im, -c.re)), fma(a.re, b.im, fma(a.im, b.re, -c.im))};
+}
+__device__ __forceinline__ cx mul_add(cx a, cx b, cx c) {
+    return cx{fma(a.re, b.re, fma(-a.im, b.im, c.re)), fma(a.re, b.im, fma(a.im, b.re, c.im))};
 }
 __device__ __forceinline__ cx sub_mul(cx c, cx a, cx b) {
     return cx{fma(-a.re, b.re, fma(a.im, b.im, c.re)), fma(-a.re, b.im, fma(-a.im, b.re, c.im))};
@@ -188,7 +191,9 @@ __device__ __forceinline__ void efficiencies(const Sums& S, double lam, double r
 // psi_n(x) upward while n <= |x|, psi_{n-1}/(D_n(x) + n/x) above; xi_n(x) upward; Eqs. 2-3
 // multiplied through by psi_n(x) and xi_n(x), and a_n divided through by n_p, b_n by n_m:
 // a_n = (q D_n(y) psi_n - psi_n') / (q D_n(y) xi_n - xi_n'), q = n_m / n_p, and b_n the
-// same with 1/q.  Returns false when n_max + 16 exceeds the scratch.
+// same with 1/q; with the derivatives from the recurrence this is
+// a_n = ((q D_n(y) + n/x) psi_n - psi_{n-1}) / ((q D_n(y) + n/x) xi_n - xi_{n-1}).
+// Returns false when n_max + 16 exceeds the scratch.
 __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY, double2* colX,
                             long long T, double* qe, double* qs, double* gg) {
     const double k = 2.0 * M_PI * r / lam;
@@ -224,13 +229,13 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
             psi_n = psi_0 / (mk(d.x, d.y) + nx);
         }
         const cx xi_n = mul_sub(c, xi_0, xi_m1);
-        const cx dpsi = sub_mul(psi_0, nx, psi_n);
-        const cx dxi = sub_mul(xi_0, nx, xi_n);
+        // with psi_n' = psi_{n-1} - (n/x) psi_n (and the same for xi_n), q D psi_n - psi_n'
+        // = (q D + n/x) psi_n - psi_{n-1}
         const double2 dy = colY[(long long)(n - 1) * T];
         const cx Dy = mk(dy.x, dy.y);
-        const cx qa = q * Dy, qb = qi * Dy;
-        const cx an = mul_sub(qa, psi_n, dpsi) / mul_sub(qa, xi_n, dxi);   // Eq. 2
-        const cx bn = mul_sub(qb, psi_n, dpsi) / mul_sub(qb, xi_n, dxi);   // Eq. 3
+        const cx qa = mul_add(q, Dy, nx), qb = mul_add(qi, Dy, nx);
+        const cx an = mul_sub(qa, psi_n, psi_0) / mul_sub(qa, xi_n, xi_0);   // Eq. 2
+        const cx bn = mul_sub(qb, psi_n, psi_0) / mul_sub(qb, xi_n, xi_0);   // Eq. 3
         accumulate(S, n, nmax, an, bn, a_prev, b_prev);
         a_prev = an;
         b_prev = bn;
