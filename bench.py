@@ -404,7 +404,7 @@ def run_surrogate(mode: str):
     import torch
 
     from paper_2409_00165_gb300 import surrogate as S
-    cfg = dict(full=dict(designs=20000, blocks=20, wl=50, photons=30000, steps=20000,
+    cfg = dict(full=dict(designs=20000, blocks=20, wl=50, photons=30000, steps=30000,
                          sweep=100000),
                quick=dict(designs=4000, blocks=10, wl=24, photons=10000, steps=2500,
                           sweep=20000))[mode]
