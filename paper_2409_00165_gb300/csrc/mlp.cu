@@ -861,18 +861,27 @@ __global__ void features_kernel(int n_designs, int n_wl, const double* wl, const
     const long long n = (long long)n_designs * n_wl;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const int d = (int)(i / n_wl), w = (int)(i % n_wl);
+        int d, w;
+        if (n <= 0xffffffffLL) {   // 32-bit division where the row count allows it
+            d = (int)((unsigned)i / (unsigned)n_wl);
+            w = (int)((unsigned)i - (unsigned)d * (unsigned)n_wl);
+        } else {
+            d = (int)(i / n_wl);
+            w = (int)(i % n_wl);
+        }
         const double t = thick[d];
         float* o = out + i * N_FEAT;
+        // the logarithms in FP32: the features are FP32, and an FP64 log10 costs tens of
+        // instructions on GB300's narrow FP64 pipe
         o[0] = (float)wl[w];
         o[1] = (float)np_re[i];
-        o[2] = (float)log10(fmax(np_im[i], 1e-12));
+        o[2] = log10f((float)fmax(np_im[i], 1e-12));
         o[3] = (float)radius[d];
         o[4] = (float)vf[d];
-        o[5] = (float)log10(t);
+        o[5] = log10f((float)t);
         o[6] = (float)g[i];
-        o[7] = (float)log10(mu_s[i] * t + 1e-6);
-        o[8] = (float)log10(mu_a[i] * t + 1e-6);
+        o[7] = log10f((float)(mu_s[i] * t + 1e-6));
+        o[8] = log10f((float)(mu_a[i] * t + 1e-6));
         if (!(t > 0.0) || !isfinite(mu_s[i]) || !isfinite(mu_a[i]))
             atomicOr(&status[ST_CALL], DEV_INVALID);
     }
