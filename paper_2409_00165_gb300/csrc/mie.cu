@@ -405,7 +405,14 @@ __global__ void emt_kernel(EmtArgs A) {
     const long long total = (long long)A.n_groups * A.n_wl;
     for (long long gw = blockIdx.x * (long long)blockDim.x + threadIdx.x; gw < total;
          gw += (long long)gridDim.x * blockDim.x) {
-        const int gi = (int)(gw / A.n_wl), w = (int)(gw % A.n_wl);
+        int gi, w;
+        if (total <= 0xffffffffLL) {   // 32-bit division where the count allows it
+            gi = (int)((unsigned)gw / (unsigned)A.n_wl);
+            w = (int)((unsigned)gw - (unsigned)gi * (unsigned)A.n_wl);
+        } else {
+            gi = (int)(gw / A.n_wl);
+            w = (int)(gw % A.n_wl);
+        }
         const int s0 = lower_bound(A.species_group, A.n_species, gi);
         const int s1 = lower_bound(A.species_group, A.n_species, gi + 1);
         const double lam = A.wl[w];
@@ -414,10 +421,11 @@ __global__ void emt_kernel(EmtArgs A) {
             const long long sw = (long long)s * A.n_wl + w;
             const double f = A.vol_frac[s], rr = A.radius[s];
             const double qe = A.q_ext[sw], qs = A.q_sca[sw], gg = A.g_sp[sw];
+            const double k = 0.75 * f / rr;            // 3 f / (4 r): one division
             sum_f += f;
-            ms += 1.5 * qs * f / (2.0 * rr);           // Eq. 13
-            ma += 1.5 * (qe - qs) * f / (2.0 * rr);    // Eq. 14
-            mg += 1.5 * qs * f * gg / (2.0 * rr);      // numerator of Eq. 16
+            ms += qs * k;                              // Eq. 13
+            ma += (qe - qs) * k;                       // Eq. 14
+            mg += qs * gg * k;                         // numerator of Eq. 16
         }
         const double km = A.nm_im[gw], nr = A.nm_re[gw];
         if (!(sum_f < 1.0) || !(isfinite(km) && km >= 0.0) || !(isfinite(nr) && nr > 0.0) ||
