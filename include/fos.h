@@ -363,7 +363,10 @@ fos_status fos_mask_to_rows(const unsigned char* mask, long long n, int* rows, l
  * from a hash of (seed, member, step, slot).  Loss: mean soft-label cross-entropy,
  * written to loss_out (device float) if non-NULL.  If grad_out (device float
  * [fos_surrogate_param_count()]) is non-NULL the gradient is written there and the
- * parameters are NOT updated (diagnostic).  Synchronous unless FOS_ASYNC. */
+ * parameters are NOT updated (diagnostic).  Synchronous unless FOS_ASYNC.
+ * The library keeps one activation workspace per member slot (member mod 4): steps of
+ * members in different slots may run concurrently on different streams (with
+ * FOS_ASYNC); steps of members in the same slot must be ordered (one stream). */
 fos_status fos_surrogate_train_step(void* model, int member, const float* features,
                                     const float* targets, long long n_rows, int batch,
                                     const int* batch_rows, unsigned long long seed, int step,

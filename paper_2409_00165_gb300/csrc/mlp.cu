@@ -1274,10 +1274,13 @@ struct TrainWs {
     bf16 *X0, *X0T, *H[4], *HT[4], *G4, *G4T, *dZ[2], *dZT[2];
     float *Z[4], *P, *Y, *part[N_LAYERS], *db[N_LAYERS], *loss, *colpart;
 };
-static TrainWs g_tws[64];
+// One training workspace per device and member slot (member mod TRAIN_SLOTS), so that
+// the steps of up to TRAIN_SLOTS members can run concurrently on separate streams.
+constexpr int TRAIN_SLOTS = 4;
+static TrainWs g_tws[64][TRAIN_SLOTS];
 
-static fos_status ensure_train_ws(int dev, int B) {
-    TrainWs& w = g_tws[dev];
+static fos_status ensure_train_ws(int dev, int slot, int B) {
+    TrainWs& w = g_tws[dev][slot];
     if (w.mem && w.B == B) return FOS_OK;
     if (w.mem) {
         FOS_CUDA_TRY(cudaDeviceSynchronize());
@@ -1355,11 +1358,11 @@ static GemmArgs gargs(unsigned* status) {
 }
 
 // Forward + backward + Adam for one member on one batch (all on stream s).
-static fos_status train_step(Workspace* ws, const MemberPtrs& mp, const float* feat,
+static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, const float* feat,
                              const float* targets, long long n_rows, int B, unsigned seed,
                              unsigned step, const int* rows, float lr, float* grad_out,
                              cudaStream_t s) {
-    TrainWs& w = g_tws[ws->device];
+    TrainWs& w = g_tws[ws->device][slot];
     const int splits = w.splits;
     FOS_CUDA_TRY(cudaMemsetAsync(w.loss, 0, 4, s));
     gather_kernel<<<(B + 255) / 256, 256, 0, s>>>(feat, targets, n_rows, B, seed, step, rows,
@@ -1657,17 +1660,18 @@ fos_status fos_surrogate_train_step(void* model, int member, const float* featur
     Workspace* ws = nullptr;
     fos_status st = mlp::prep(&ws);
     if (st != FOS_OK) return st;
-    st = mlp::ensure_train_ws(ws->device, batch);
+    const int slot = member % mlp::TRAIN_SLOTS;
+    st = mlp::ensure_train_ws(ws->device, slot, batch);
     if (st != FOS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     FOS_CUDA_TRY(cudaMemsetAsync(ws->status + ST_CALL, 0, sizeof(unsigned), s));
     mlp::MemberPtrs mp = mlp::member(model, member);
-    st = mlp::train_step(ws, mp, features, targets, n_rows, batch,
+    st = mlp::train_step(ws, slot, mp, features, targets, n_rows, batch,
                          (unsigned)(seed ^ (seed >> 32)) ^ (unsigned)(member * 0x9E3779B9u),
                          (unsigned)step, batch_rows, lr, grad_out, s);
     if (st != FOS_OK) return st;
     if (loss_out) {
-        mlp::TrainWs& w = mlp::g_tws[ws->device];
+        mlp::TrainWs& w = mlp::g_tws[ws->device][slot];
         FOS_CUDA_TRY(cudaMemcpyAsync(loss_out, w.loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
     }
     return finish_call(ws, s, flags);

@@ -121,21 +121,32 @@ class Surrogate:
         call's steps), taken at each member's global step count, so that a run split into
         several calls, or resumed from a checkpoint, follows the same schedule.  Returns
         the loss history."""
-        members = range(self.n_members) if members is None else members
+        members = list(range(self.n_members) if members is None else members)
         total = schedule_steps or steps
-        loss = torch.zeros(1, dtype=torch.float32, device=features.device)
-        hist = {}
-        for k in members:
-            hist[k] = []
-            for t in range(steps):
+        dev = features.device
+        # members in different workspace slots (member mod 4) step concurrently, one
+        # stream per slot; a member's own steps stay in order on its slot's stream
+        streams = {k % 4: torch.cuda.Stream(device=dev) for k in members}
+        loss = {k: torch.zeros(1, dtype=torch.float32, device=dev) for k in members}
+        hist = {k: [] for k in members}
+        cur_stream = torch.cuda.current_stream(dev)
+        for st in streams.values():
+            st.wait_stream(cur_stream)
+        for t in range(steps):
+            for k in members:
                 g = min(self.steps_done[k], total) if schedule_steps else t
                 cur = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * g / total))
                 fos.check(fos.fos_surrogate_train_step(
                     self.model, k, features, targets, batch, self.seed, self.steps_done[k], cur,
-                    loss_out=loss, flags=fos.FOS_ASYNC), "train_step")
+                    loss_out=loss[k], flags=fos.FOS_ASYNC, stream=streams[k % 4]),
+                    "train_step")
                 self.steps_done[k] += 1
                 if log_every and (t % log_every == 0 or t == steps - 1):
-                    hist[k].append((t, loss.item()))
+                    streams[k % 4].synchronize()
+                    hist[k].append((t, loss[k].item()))
+        for st in streams.values():
+            cur_stream.wait_stream(st)
+        torch.cuda.synchronize(dev)
         fos.check(fos.fos_sync_status(), "training")
         return hist
 
