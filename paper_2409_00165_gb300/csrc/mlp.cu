@@ -989,8 +989,22 @@ __global__ void gather_kernel(const float* feat, const float* targets, long long
 // phases, then a fixed combine) into part[y][c].  Pass 2 sums the COLSUM_SPLITS partials
 // of each column in order.
 constexpr int COLSUM_SPLITS = 64;
-__global__ void colsum_partial_kernel(const bf16* G, int rows, int ld, int ncols, float* part) {
+// Bias gradients of all layers in one launch (blockIdx.z = layer): per-split column sums
+// part[l][split][c] of layer l's output gradient G_l [rows][ld]; Adam adds the splits in
+// a fixed order, so the result does not depend on scheduling.
+struct ColsumArgs {
+    const bf16* G[N_LAYERS];
+    int ld[N_LAYERS];
+    float* part[N_LAYERS];
+    int rows;
+};
+__global__ void colsum_layers_kernel(ColsumArgs A) {
     __shared__ float ph[4][64];
+    const int l = blockIdx.z;
+    const int ncols = real_out(l), rows = A.rows, ld = A.ld[l];
+    if ((int)blockIdx.x * 64 >= ncols) return;   // the whole block: no column of this layer
+    const bf16* G = A.G[l];
+    float* part = A.part[l];
     const int c = blockIdx.x * 64 + (threadIdx.x & 63);
     const int q = threadIdx.x >> 6;   // 4 row phases
     const int chunk = (rows + COLSUM_SPLITS - 1) / COLSUM_SPLITS;
@@ -1004,12 +1018,11 @@ __global__ void colsum_partial_kernel(const bf16* G, int rows, int ld, int ncols
         part[blockIdx.y * ncols + c] =
             ph[0][threadIdx.x] + ph[1][threadIdx.x] + ph[2][threadIdx.x] + ph[3][threadIdx.x];
 }
-__global__ void colsum_final_kernel(const float* part, int ncols, float* out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncols) return;
+// Bias gradient of output o of layer l from its per-split column sums, in split order.
+__device__ __forceinline__ float bias_grad(const float* part, int ncols, int o) {
     float acc = 0.f;
-    for (int y = 0; y < COLSUM_SPLITS; ++y) acc += part[y * ncols + c];
-    out[c] = acc;
+    for (int y = 0; y < COLSUM_SPLITS; ++y) acc += part[y * ncols + o];
+    return acc;
 }
 
 struct AdamArgs {
@@ -1017,7 +1030,7 @@ struct AdamArgs {
     bf16 *wb, *wt, *wi;
     long long w_off[N_LAYERS], b_off[N_LAYERS], wb_off[N_LAYERS], wt_off[N_LAYERS];
     const float* part[N_LAYERS];   // split-K partials of dW_l [splits][out][in]
-    const float* db[N_LAYERS];     // bias gradients [out]
+    const float* bpart[N_LAYERS];  // per-split column sums of G_l [COLSUM_SPLITS][real out]
     int splits;
     float lr, b1, b2, eps, c1, c2;  // c1 = 1 - b1^t, c2 = 1 - b2^t
 };
@@ -1044,7 +1057,7 @@ __global__ void adam_kernel(AdamArgs A, long long P) {
         } else {
             o = (int)(idx - A.b_off[l]);
             if (o >= real_out(l)) continue;
-            g = A.db[l][o];
+            g = bias_grad(A.bpart[l], real_out(l), o);
         }
         const float mm = A.b1 * A.m[idx] + (1.f - A.b1) * g;
         const float vv = A.b2 * A.v[idx] + (1.f - A.b2) * g * g;
@@ -1079,7 +1092,7 @@ __global__ void grad_kernel(AdamArgs A, long long P, float* grad) {
             }
         } else {
             const int o = (int)(idx - A.b_off[l]);
-            if (o < real_out(l)) g = A.db[l][o];
+            if (o < real_out(l)) g = bias_grad(A.bpart[l], real_out(l), o);
         }
         grad[idx] = g;
     }
@@ -1271,8 +1284,8 @@ struct TrainWs {
     int splits = 0;
     void* mem = nullptr;
     size_t bytes = 0;
-    bf16 *X0, *X0T, *H[4], *HT[4], *G4, *G4T, *dZ[2], *dZT[2];
-    float *Z[4], *P, *Y, *part[N_LAYERS], *db[N_LAYERS], *loss, *colpart;
+    bf16 *X0, *X0T, *H[4], *HT[4], *G4, *G4T, *dZ[4], *dZT[4];
+    float *Z[4], *P, *Y, *part[N_LAYERS], *colpart[N_LAYERS], *loss;
 };
 // One training workspace per device and member slot (member mod TRAIN_SLOTS), so that
 // the steps of up to TRAIN_SLOTS members can run concurrently on separate streams.
@@ -1304,14 +1317,13 @@ static fos_status ensure_train_ws(int dev, int slot, int B) {
     add((void**)&w.Y, (size_t)B * 3 * 4);
     add((void**)&w.G4, (size_t)B * OUT_PAD * 2);
     add((void**)&w.G4T, (size_t)OUT_PAD * B * 2);
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 4; ++k) {   // the output gradient of hidden layer k
         add((void**)&w.dZ[k], (size_t)B * HID * 2);
         add((void**)&w.dZT[k], (size_t)HID * B * 2);
     }
     for (int l = 0; l < N_LAYERS; ++l) {
         add((void**)&w.part[l], (size_t)splits * lay_out(l) * lay_in(l) * 4);
-        add((void**)&w.db[l], (size_t)lay_out(l) * 4);
-        if (l == 0) add((void**)&w.colpart, (size_t)COLSUM_SPLITS * HID * 4);
+        add((void**)&w.colpart[l], (size_t)COLSUM_SPLITS * real_out(l) * 4);
     }
     add((void**)&w.loss, 16);
     for (auto& it : items) o = al(o + it.bytes);
@@ -1399,14 +1411,13 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
     const bf16* Gcur = w.G4;
     const bf16* GcurT = w.G4T;
     int gcols = OUT_PAD;
+    ColsumArgs ca;
+    ca.rows = B;
     for (int l = 4; l >= 0; --l) {
-        // bias gradient
-        colsum_partial_kernel<<<dim3((real_out(l) + 63) / 64, COLSUM_SPLITS), 256, 0, s>>>(
-            Gcur, B, gcols, real_out(l), w.colpart);
-        FOS_CUDA_TRY(cudaGetLastError());
-        colsum_final_kernel<<<(real_out(l) + 255) / 256, 256, 0, s>>>(w.colpart, real_out(l),
-                                                                      w.db[l]);
-        FOS_CUDA_TRY(cudaGetLastError());
+        // the bias gradient's column sums wait for one launch after the loop
+        ca.G[l] = Gcur;
+        ca.ld[l] = gcols;
+        ca.part[l] = w.colpart[l];
         // weight gradient dW_l = G^T · H_{l-1}  (A = G^T [out][B], B = H_{l-1}^T [in][B])
         {
             Operand A{GcurT, lay_out(l), B, B};
@@ -1420,8 +1431,8 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
         if (l == 0) break;
         // dZ_{l-1} = (G · W_l) * GELU'(Z_{l-1})  (A = G [B][out], B = W_l^T [in][out])
         {
-            bf16* dz = w.dZ[l & 1];
-            bf16* dzt = w.dZT[l & 1];
+            bf16* dz = w.dZ[l - 1];
+            bf16* dzt = w.dZT[l - 1];
             Operand A{Gcur, B, lay_out(l), gcols};
             Operand Bm{wt[l], HID, lay_out(l), lay_out(l)};
             GemmArgs g = gargs(ws->status);
@@ -1434,11 +1445,13 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
             gcols = HID;
         }
     }
+    colsum_layers_kernel<<<dim3(HID / 64, COLSUM_SPLITS, N_LAYERS), 256, 0, s>>>(ca);
+    FOS_CUDA_TRY(cudaGetLastError());
     // Adam
     AdamArgs a = layout_args(mp);
     for (int l = 0; l < N_LAYERS; ++l) {
         a.part[l] = w.part[l];
-        a.db[l] = w.db[l];
+        a.bpart[l] = w.colpart[l];
     }
     a.splits = splits;
     if (grad_out) {   // diagnostic: export the gradient instead of updating
