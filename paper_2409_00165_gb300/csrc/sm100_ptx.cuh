@@ -5,8 +5,10 @@
 //   * operands are K-major BF16 tiles loaded by TMA with 128-byte swizzle: a tile of R
 //     rows x 64 elements occupies R*128 bytes, 8-row groups 1024 bytes apart; the tile
 //     base is 1024-byte aligned;
-//   * tcgen05.mma.kind::f16 with M = 128, N = 64..256, K = 16 per instruction, FP32
-//     accumulation in TMEM (row i of the tile in TMEM lane i, column j in column j).
+//   * tcgen05.mma.kind::f16 with M = 128, N = 16..256, K = 16 per instruction, FP32
+//     accumulation in TMEM (row i of the tile in TMEM lane i, column j in column j);
+//   * an A operand may instead sit in TMEM (mma_bf16_ts): row i in lane i, two BF16
+//     elements per 32-bit column, the lower k in the low half.
 #pragma once
 
 #include <cuda.h>
