@@ -200,7 +200,7 @@ struct Tables {
                       //  reflector, -1 none, -2 conductor}
     int4* info;       // {rng item id, first photon id, photon count, entry reflectance bits}
     float4* edge;     // {entry mu_z (refraction cosine), cos incidence, k below, 0}
-    float4* layA;     // [row*max_layers + j] {mu_t, mu_a/mu_t, g, n}
+    float4* layA;     // [row*max_layers + j] {mu_t, absorption threshold (uint bits), g, n}
     float4* layB;     // [row*max_layers + j] {d, 1-g^2, 1+g^2, 1-g}
     float4* layC;     // [row*max_layers + j] {1/mu_t, 1/(2g), 0, 0}
     long long* prefix;  // [n_run + 1] exclusive prefix of work units
@@ -283,7 +283,11 @@ __global__ void pack_kernel(PackArgs A) {
             const float pabs = (mt > 0.0f) ? maf / mt : 0.0f;
             if (!isfinite(mt) || !isfinite((float)dd) || (float)dd <= 0.0f || (float)nn <= 0.0f)
                 ok = false;
-            la = make_float4(mt, pabs, gf, (float)nn);
+            // absorption test on the word itself: uni(w) = (2k+1) 2^-24 with k = w >> 9,
+            // and (2k+1) 2^-24 < pabs exactly when k < ceil((pabs 2^24 - 1) / 2)
+            const double kab = fmin(fmax(ceil(((double)pabs * 16777216.0 - 1.0) * 0.5), 0.0),
+                                    8388608.0);
+            la = make_float4(mt, __uint_as_float((unsigned)kab), gf, (float)nn);
             lb = make_float4((float)dd, 1.0f - gf * gf, 1.0f + gf * gf, 1.0f - gf);
             lc = make_float4((mt > 0.0f) ? 1.0f / mt : 0.0f,
                              (fabsf(gf) < 0x1.0c6f7ap-20f) ? 0.0f : 1.0f / (gf + gf), 0.f, 0.f);
@@ -435,8 +439,10 @@ __global__ void __launch_bounds__(WALK_MAX_BLOCK, 7) walk_kernel(WalkArgs A) {
     bool alive = false;
     int row = 0, j = 0, nl = 1;
     unsigned item_rng = 0, p = 0, p_first = 0, e = 0, kif = 0, ev = 0;
-    float z = 0.f, mu = 1.f, tau = 0.f, u1 = 0.f, u2 = 0.f, u3 = 0.f;
-    float l_mut = 0.f, l_pabs = 0.f, l_g = 0.f, l_n = 1.f, l_d = 1.f, l_omg2 = 1.f,
+    float z = 0.f, mu = 1.f, tau = 0.f, u2 = 0.f, u3 = 0.f;
+    unsigned w1 = 0u;   // the absorption draw's Philox word
+    unsigned l_kabs = 0u;
+    float l_mut = 0.f, l_g = 0.f, l_n = 1.f, l_d = 1.f, l_omg2 = 1.f,
           l_opg2 = 1.f, l_omg = 1.f, l_imt = 0.f, l_i2g = 0.f;
 
     // tallies of the current tag (row)
@@ -449,17 +455,21 @@ __global__ void __launch_bounds__(WALK_MAX_BLOCK, 7) walk_kernel(WalkArgs A) {
         const float4 a = A.t.layA[li];
         const float4 b = A.t.layB[li];
         const float2 c = *reinterpret_cast<const float2*>(&A.t.layC[li]);
-        l_mut = a.x; l_pabs = a.y; l_g = a.z; l_n = a.w;
+        l_mut = a.x; l_kabs = __float_as_uint(a.y); l_g = a.z; l_n = a.w;
         l_d = b.x; l_omg2 = b.y; l_opg2 = b.z; l_omg = b.w;
         l_imt = c.x; l_i2g = c.y;
     };
+    // The photon's collisions are its scatterings e (+ 1 if the last one absorbed it) and
+    // its boundary events the rest of its ev events: tallied here, once per photon.
     auto finish = [&](int out) {
         if (out == O_R) cR++;
         else if (out == O_A) cA++;
         else if (out == O_T) cT++;
         else cX++;
+        const unsigned long long coll = (unsigned long long)e + (out == O_A ? 1ull : 0ull);
+        cC += coll;
+        cI += (unsigned long long)ev - coll;
         if (A.photon_log) {
-            const unsigned long long coll = (unsigned long long)e + (out == O_A ? 1ull : 0ull);
             unsigned long long rec = (coll << 2) | (unsigned long long)out;
             if (rec > 0x7fffffffull) rec = 0x7fffffffull;
             A.photon_log[(long long)row * A.log_stride + (p - p_first)] = (int)rec;
@@ -536,7 +546,7 @@ __global__ void __launch_bounds__(WALK_MAX_BLOCK, 7) walk_kernel(WalkArgs A) {
                     z = 0.0f;
                     mu = ed.x;
                     tau = neg_log_u(uni(blk0.x));
-                    u1 = uni(blk0.y);
+                    w1 = blk0.y;
                     u2 = uni(blk0.z);
                     u3 = uni(blk0.w);
                     alive = true;
@@ -565,8 +575,7 @@ __global__ void __launch_bounds__(WALK_MAX_BLOCK, 7) walk_kernel(WalkArgs A) {
                 const float s = tau * l_imt;
                 z = fmaf(mu, s, z);
                 ev++;
-                cC++;
-                if (u1 < l_pabs) {
+                if ((w1 >> 9) < l_kabs) {   // uni(w1) < mu_a / mu_t
                     finish(O_A);
                     continue;
                 }
@@ -581,7 +590,7 @@ __global__ void __launch_bounds__(WALK_MAX_BLOCK, 7) walk_kernel(WalkArgs A) {
                 }
                 e++;
                 tau = neg_log_u(uni(blk.x));
-                u1 = uni(blk.y);
+                w1 = blk.y;
                 u2 = uni(blk.z);
                 u3 = uni(blk.w);
             } else {
@@ -591,7 +600,6 @@ __global__ void __launch_bounds__(WALK_MAX_BLOCK, 7) walk_kernel(WalkArgs A) {
                 const bool down = mu > 0.0f;
                 z = down ? l_d : 0.0f;
                 ev++;
-                cI++;
                 const int nb = down ? j + 1 : j - 1;
                 const bool outside = (nb < 0) || (nb >= nl);
                 // media and substrate of the row, read at boundary events only (L1-resident)
