@@ -21,8 +21,11 @@ enum : unsigned {
 };
 
 // status words on the device: [0] the current call, [1] accumulated FOS_ASYNC work,
-// [2] first offending index of the current call (for diagnostics).
-enum { ST_CALL = 0, ST_ASYNC = 1, ST_INDEX = 2, ST_WORDS = 4 };
+// [2] first offending index of the current call (for diagnostics).  The buffer holds
+// ST_REGIONS such groups: region 0 for the calls of the default path; regions 1.. for
+// calls that may run concurrently on other streams (the surrogate's training slots),
+// each with its own call word, all accumulating into region 0's async word.
+enum { ST_CALL = 0, ST_ASYNC = 1, ST_INDEX = 2, ST_WORDS = 4, ST_REGIONS = 5 };
 
 struct Workspace {
     int device = -1;
@@ -51,11 +54,12 @@ fos_status status_from_bits(unsigned bits);
 // Bounded wait: polls the stream until it is idle or timeout_ms passes.
 fos_status wait_stream(cudaStream_t s, int timeout_ms);
 
-// Enqueues work that moves the call status into the accumulated async status.
-fos_status accumulate_async_status(Workspace* ws, cudaStream_t s);
+// Enqueues work that moves the call status of `region` into the accumulated async status.
+fos_status accumulate_async_status(Workspace* ws, cudaStream_t s, int region = 0);
 
-// Ends a call: for synchronous calls waits (bounded) and converts the status word.
-fos_status finish_call(Workspace* ws, cudaStream_t s, unsigned flags);
+// Ends a call: for synchronous calls waits (bounded) and converts the call word of
+// `region`.
+fos_status finish_call(Workspace* ws, cudaStream_t s, unsigned flags, int region = 0);
 
 inline int default_timeout_ms() { return 600000; }
 

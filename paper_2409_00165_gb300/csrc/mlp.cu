@@ -1290,6 +1290,7 @@ struct TrainWs {
 // One training workspace per device and member slot (member mod TRAIN_SLOTS), so that
 // the steps of up to TRAIN_SLOTS members can run concurrently on separate streams.
 constexpr int TRAIN_SLOTS = 4;
+static_assert(TRAIN_SLOTS + 1 <= ST_REGIONS, "a status region per training slot");
 static TrainWs g_tws[64][TRAIN_SLOTS];
 
 static fos_status ensure_train_ws(int dev, int slot, int B) {
@@ -1375,6 +1376,7 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
                              unsigned step, const int* rows, float lr, float* grad_out,
                              cudaStream_t s) {
     TrainWs& w = g_tws[ws->device][slot];
+    unsigned* status = ws->status + ST_WORDS * (1 + slot);   // this slot's status region
     const int splits = w.splits;
     FOS_CUDA_TRY(cudaMemsetAsync(w.loss, 0, 4, s));
     gather_kernel<<<(B + 255) / 256, 256, 0, s>>>(feat, targets, n_rows, B, seed, step, rows,
@@ -1393,14 +1395,14 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
     for (int l = 0; l < 4; ++l) {
         Operand A = (l == 0) ? Operand{w.X0, B, IN_PAD, IN_PAD} : Operand{w.H[l - 1], B, HID, HID};
         Operand Bm{wb[l], HID, lay_in(l), lay_in(l)};
-        GemmArgs g = gargs(ws->status);
+        GemmArgs g = gargs(status);
         g.M = B; g.N = HID; g.bias = bias[l];
         g.out_f = w.Z[l]; g.ldf = HID; g.out_h = w.H[l]; g.ldh = HID; g.out_t = w.HT[l]; g.ldt = B;
         st = gemm<128, FWD_HIDDEN>(A, Bm, 1, g, s);
         if (st != FOS_OK) return st;
     }
     {
-        GemmArgs g = gargs(ws->status);
+        GemmArgs g = gargs(status);
         g.M = B; g.N = OUT_PAD; g.bias = bias[4];
         g.out_f = w.P; g.out_h = w.G4; g.ldh = OUT_PAD; g.out_t = w.G4T; g.ldt = B;
         g.aux = w.Y; g.loss_sum = w.loss; g.inv_batch = 1.0f / (float)B;
@@ -1422,7 +1424,7 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
         {
             Operand A{GcurT, lay_out(l), B, B};
             Operand Bm = (l == 0) ? Operand{w.X0T, IN_PAD, B, B} : Operand{w.HT[l - 1], HID, B, B};
-            GemmArgs g = gargs(ws->status);
+            GemmArgs g = gargs(status);
             g.M = lay_out(l); g.N = lay_in(l); g.out_f = w.part[l]; g.ldf = lay_in(l);
             if (l == 0) st = gemm<64, DW_PARTIAL>(A, Bm, splits, g, s);
             else st = gemm<256, DW_PARTIAL>(A, Bm, splits, g, s);
@@ -1435,7 +1437,7 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
             bf16* dzt = w.dZT[l - 1];
             Operand A{Gcur, B, lay_out(l), gcols};
             Operand Bm{wt[l], HID, lay_out(l), lay_out(l)};
-            GemmArgs g = gargs(ws->status);
+            GemmArgs g = gargs(status);
             g.M = B; g.N = HID; g.aux = w.Z[l - 1]; g.ld_aux = HID;
             g.out_h = dz; g.ldh = HID; g.out_t = dzt; g.ldt = B;
             st = gemm<128, BWD_HIDDEN>(A, Bm, 1, g, s);
@@ -1677,7 +1679,8 @@ fos_status fos_surrogate_train_step(void* model, int member, const float* featur
     st = mlp::ensure_train_ws(ws->device, slot, batch);
     if (st != FOS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    FOS_CUDA_TRY(cudaMemsetAsync(ws->status + ST_CALL, 0, sizeof(unsigned), s));
+    const int region = 1 + slot;   // concurrent slots keep separate call words
+    FOS_CUDA_TRY(cudaMemsetAsync(ws->status + ST_WORDS * region + ST_CALL, 0, sizeof(unsigned), s));
     mlp::MemberPtrs mp = mlp::member(model, member);
     st = mlp::train_step(ws, slot, mp, features, targets, n_rows, batch,
                          (unsigned)(seed ^ (seed >> 32)) ^ (unsigned)(member * 0x9E3779B9u),
@@ -1687,7 +1690,7 @@ fos_status fos_surrogate_train_step(void* model, int member, const float* featur
         mlp::TrainWs& w = mlp::g_tws[ws->device][slot];
         FOS_CUDA_TRY(cudaMemcpyAsync(loss_out, w.loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
     }
-    return finish_call(ws, s, flags);
+    return finish_call(ws, s, flags, region);
 }
 
 fos_status fos_surrogate_predict(void* model, int n_members, const float* features,

@@ -12,9 +12,9 @@ namespace {
 std::mutex g_mutex;
 Workspace g_ws[64];
 
-__global__ void accumulate_status_kernel(unsigned* st) {
+__global__ void accumulate_status_kernel(const unsigned* call, unsigned* st) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        unsigned v = st[ST_CALL];
+        unsigned v = call[ST_CALL];
         if (v) atomicOr(&st[ST_ASYNC], v);
     }
 }
@@ -53,8 +53,8 @@ fos_status get_workspace(Workspace** out) {
         ws.num_sms = prop.multiProcessorCount;
         ws.cc_major = prop.major;
         ws.cc_minor = prop.minor;
-        FOS_CUDA_TRY(cudaMalloc(&ws.status, ST_WORDS * sizeof(unsigned)));
-        FOS_CUDA_TRY(cudaMemset(ws.status, 0, ST_WORDS * sizeof(unsigned)));
+        FOS_CUDA_TRY(cudaMalloc(&ws.status, ST_REGIONS * ST_WORDS * sizeof(unsigned)));
+        FOS_CUDA_TRY(cudaMemset(ws.status, 0, ST_REGIONS * ST_WORDS * sizeof(unsigned)));
         FOS_CUDA_TRY(cudaMalloc(&ws.cursor, 4 * sizeof(unsigned long long)));
         FOS_CUDA_TRY(cudaMemset(ws.cursor, 0, 4 * sizeof(unsigned long long)));
         FOS_CUDA_TRY(cudaStreamCreateWithFlags(&ws.side, cudaStreamNonBlocking));
@@ -99,17 +99,17 @@ fos_status wait_stream(cudaStream_t s, int timeout_ms) {
     }
 }
 
-fos_status accumulate_async_status(Workspace* ws, cudaStream_t s) {
-    accumulate_status_kernel<<<1, 32, 0, s>>>(ws->status);
+fos_status accumulate_async_status(Workspace* ws, cudaStream_t s, int region) {
+    accumulate_status_kernel<<<1, 32, 0, s>>>(ws->status + region * ST_WORDS, ws->status);
     return from_cuda(cudaGetLastError());
 }
 
-fos_status finish_call(Workspace* ws, cudaStream_t s, unsigned flags) {
-    if (flags & FOS_ASYNC) return accumulate_async_status(ws, s);
+fos_status finish_call(Workspace* ws, cudaStream_t s, unsigned flags, int region) {
+    if (flags & FOS_ASYNC) return accumulate_async_status(ws, s, region);
     fos_status st = wait_stream(s, default_timeout_ms());
     if (st != FOS_OK) return st;
     unsigned bits = 0;
-    FOS_CUDA_TRY(cudaMemcpy(&bits, ws->status + ST_CALL, sizeof(unsigned),
+    FOS_CUDA_TRY(cudaMemcpy(&bits, ws->status + region * ST_WORDS + ST_CALL, sizeof(unsigned),
                             cudaMemcpyDeviceToHost));
     return status_from_bits(bits);
 }
