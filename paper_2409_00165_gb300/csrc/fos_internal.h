@@ -31,7 +31,7 @@ struct Workspace {
     int device = -1;
     int num_sms = 0;
     int cc_major = 0, cc_minor = 0;
-    unsigned* status = nullptr;             // device [ST_WORDS]
+    unsigned* status = nullptr;             // device [ST_REGIONS * ST_WORDS]
     unsigned long long* cursor = nullptr;   // device work-queue counter(s) [4]
     void* mc_tables = nullptr;              // packed item tables + unit prefix
     size_t mc_bytes = 0;
