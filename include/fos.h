@@ -361,7 +361,8 @@ fos_status fos_mask_to_rows(const unsigned char* mask, long long n, int* rows, l
  * [n_rows*9] / targets [n_rows*3] (device float; target rows sum to 1).  Rows are
  * batch_rows [batch] (device int32) if given, else drawn uniformly with replacement
  * from a hash of (seed, member, step, slot).  Loss: mean soft-label cross-entropy,
- * written to loss_out (device float) if non-NULL.  If grad_out (device float
+ * written to loss_out (device float) if non-NULL; it is summed with atomics, so its last
+ * bits may differ between runs (the parameter update does not).  If grad_out (device float
  * [fos_surrogate_param_count()]) is non-NULL the gradient is written there and the
  * parameters are NOT updated (diagnostic).  Synchronous unless FOS_ASYNC.
  * The library keeps one activation workspace per member slot (member mod 4): steps of
