@@ -393,6 +393,29 @@ fos_status fos_surrogate_predict(void* model, int n_members, const float* featur
 fos_status fos_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K,
                          int splits, unsigned flags, void* stream);
 
+/* Diagnostic: hardware rates of the current GPU that the kernels above are measured
+ * against, each from one timed launch after a warm-up (synchronous; takes about a
+ * second; allocates ~1 MB):
+ *   fp64_tflops       FP64 FMA rate (8 independent DFMA chains per thread);
+ *   tanh_per_s        MUFU tanh.approx.f32 results per second (whole GPU);
+ *   tanh_f16x2_per_s  the same for tanh.approx.f16x2, counting both halves;
+ *   mma_ts_tflops[i]  tcgen05.mma kind::f16, M = 128, K = 16, N = 64, 128, 256 (i = 0..2),
+ *                     one issuing thread per SM, A operand in tensor memory;
+ *   mma_ss_tflops[i]  the same with the A operand in shared memory;
+ *   bulk_tbps         L2 -> shared memory untiled bulk copies (32 KB, 4 in flight per SM,
+ *                     every SM reading the same 448 KB), TB/s over the GPU.
+ * Returns FOS_OK, FOS_ERR_UNSUPPORTED (not an sm_100-family GPU), FOS_ERR_TIMEOUT (a
+ * bounded in-kernel wait ran out) or FOS_ERR_CUDA. */
+typedef struct {
+    double fp64_tflops;
+    double tanh_per_s;
+    double tanh_f16x2_per_s;
+    double mma_ts_tflops[3];
+    double mma_ss_tflops[3];
+    double bulk_tbps;
+} fos_hw_rates;
+fos_status fos_measure_hw_rates(fos_hw_rates* out);
+
 /* --------------------------------------------------------------------------------
  * fos_mc_spectrum_noalloc: fos_mc_spectrum for callers that cannot allocate device
  * memory.  The paper has no counterpart; this is a property of the library only.

@@ -24,7 +24,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
 EXTRA = {
     "mc_walk.cu": ["-fmad=false"],
 }
-SOURCES = ["runtime.cu", "mc_walk.cu", "mie.cu", "mlp.cu", "solar.cu"]
+SOURCES = ["runtime.cu", "mc_walk.cu", "mie.cu", "mlp.cu", "solar.cu", "hw_rates.cu"]
 
 
 def _nvcc() -> str:

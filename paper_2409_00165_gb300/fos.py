@@ -399,6 +399,24 @@ def fos_surrogate_train_step(model, member, features, targets, batch, seed, step
         _dev(grad_out, f32, "grad_out", True), int(flags), _stream(stream))
 
 
+class FosHwRates(ctypes.Structure):
+    _fields_ = [("fp64_tflops", ctypes.c_double), ("tanh_per_s", ctypes.c_double),
+                ("tanh_f16x2_per_s", ctypes.c_double),
+                ("mma_ts_tflops", ctypes.c_double * 3), ("mma_ss_tflops", ctypes.c_double * 3),
+                ("bulk_tbps", ctypes.c_double)]
+
+
+def fos_measure_hw_rates() -> dict:
+    r = FosHwRates()
+    check(_sfn("fos_measure_hw_rates", [ctypes.POINTER(FosHwRates)])(ctypes.byref(r)),
+          "fos_measure_hw_rates")
+    return dict(fp64_tflops=r.fp64_tflops, tanh_per_s=r.tanh_per_s,
+                tanh_f16x2_per_s=r.tanh_f16x2_per_s,
+                mma_ts_tflops=dict(zip((64, 128, 256), list(r.mma_ts_tflops))),
+                mma_ss_tflops=dict(zip((64, 128, 256), list(r.mma_ss_tflops))),
+                bulk_tbps=r.bulk_tbps)
+
+
 def fos_surrogate_predict(model, n_members, features, rat, spread=None, needs_mc=None,
                           threshold=0.01, flags=0, stream=None) -> int:
     f32 = torch.float32
