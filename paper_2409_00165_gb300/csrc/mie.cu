@@ -61,6 +61,24 @@ __device__ __forceinline__ cx crcp(cx b) {
     return cx{b.re * inv, -b.im * inv};
 }
 __device__ __forceinline__ double norm2(cx a) { return a.re * a.re + a.im * a.im; }
+// Two quotients na/da, nb/db with one real division: 1/|da|^2 = |db|^2 / (|da|^2 |db|^2)
+// and the same for db, when both denominators' larger parts lie within 2^(+-240) (the
+// product of the squared moduli then neither overflows nor underflows); otherwise two
+// divisions.
+__device__ __forceinline__ void div_pair(cx na, cx da, cx nb, cx db, cx& qa, cx& qb) {
+    const int ea = max(exponent_field(da.re), exponent_field(da.im));
+    const int eb = max(exponent_field(db.re), exponent_field(db.im));
+    if (ea > 1023 + 240 || ea < 1023 - 240 || eb > 1023 + 240 || eb < 1023 - 240) {
+        qa = na / da;
+        qb = nb / db;
+        return;
+    }
+    const double pa = da.re * da.re + da.im * da.im, pb = db.re * db.re + db.im * db.im;
+    const double inv = 1.0 / (pa * pb);
+    const double ia = pb * inv, ib = pa * inv;
+    qa = cx{(na.re * da.re + na.im * da.im) * ia, (na.im * da.re - na.re * da.im) * ia};
+    qb = cx{(nb.re * db.re + nb.im * db.im) * ib, (nb.im * db.re - nb.re * db.im) * ib};
+}
 // a b - c, a b + c and c - a b with the addition folded into the fused multiply-adds (two
 // FP64 instructions per part instead of three).
 __device__ __forceinline__ cx mul_sub(cx a, cx b, cx c) {
@@ -234,8 +252,9 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
         const double2 dy = colY[(long long)(n - 1) * T];
         const cx Dy = mk(dy.x, dy.y);
         const cx qa = mul_add(q, Dy, nx), qb = mul_add(qi, Dy, nx);
-        const cx an = mul_sub(qa, psi_n, psi_0) / mul_sub(qa, xi_n, xi_0);   // Eq. 2
-        const cx bn = mul_sub(qb, psi_n, psi_0) / mul_sub(qb, xi_n, xi_0);   // Eq. 3
+        cx an, bn;   // Eqs. 2 and 3
+        div_pair(mul_sub(qa, psi_n, psi_0), mul_sub(qa, xi_n, xi_0), mul_sub(qb, psi_n, psi_0),
+                 mul_sub(qb, xi_n, xi_0), an, bn);
         accumulate(S, n, nmax, an, bn, a_prev, b_prev);
         a_prev = an;
         b_prev = bn;
