@@ -18,6 +18,9 @@
  *                       slab inputs of Table 1, trained on spectra from fos_mc_spectrum
  *                       (the paper's "machine learning method" of section "Photon
  *                       transport").
+ *   diagnostics         fos_philox4x32_10, fos_walk_math_f32 and fos_gemm_bf16 expose
+ *                       building blocks to the parity tests; fos_measure_hw_rates the
+ *                       hardware rates the kernels are measured against.
  *
  * Conventions for every entry point:
  *   - Plain C types only.  Pointers documented "device" point to CUDA device memory
