@@ -17,10 +17,15 @@ Parity status per function (the pins live in ``tests/test_oracle_*.py``):
   hg_cos ................ pinned (sampled mean cosine = g; chi-square vs HG pdf)
   fresnel ............... pinned (normal-incidence closed form, Brewster, TIR,
                           angle-form Fresnel equations)
-  mc_run ................ pinned (Beer-Lambert; closed-form Fresnel slab; opaque
+  mc_run (definition) .. pinned (Beer-Lambert; closed-form Fresnel slab; opaque
                           reflector closed form; two-layer adding; conservation;
-                          scattering slab vs an independent discrete-ordinates
-                          solution of the radiative transfer equation)
+                          oblique and conductor closed forms; scattering slabs,
+                          the paint layer's optical depths included, vs an
+                          independent discrete-ordinates solution of the
+                          radiative transfer equation)
+  mc_run (FP32 mirror,
+   FP64 order) ......... pinned (the same closed forms and solver; agrees with
+                          the definition within binomial noise)
   mie_sphere ............ pinned (mpmath 50-digit Bessel evaluation of Eqs. 2-5;
                           Rayleigh limit; optical theorem; phase-function
                           quadrature for g; large-sphere extinction limit)
@@ -194,8 +199,16 @@ def solar_weighted(counts, wl, G, n_stacks: int):
 
 
 # ---------------------------------------------------------------------------- MC
-def mc_run(batch: dict, fp32: bool = True, photon_log: bool = False):
+MODE_F64_ORDER, MODE_F32_MIRROR, MODE_DEFINITION = 0, 1, 2
+
+
+def mc_run(batch: dict, fp32: bool = True, photon_log: bool = False, mode=None):
     """Run the oracle walk on a batch given as a dict of NumPy arrays.
+
+    mode: MODE_DEFINITION (the walk as the paper states it, FP64, its own sequential
+    random stream), MODE_F32_MIRROR (the GPU walk's order and random layout in FP32,
+    bit-exact with it) or MODE_F64_ORDER (that order and layout in FP64); None picks
+    the mirror if fp32 else the FP64 order.
 
     Keys mirror the fields of the C-ABI batch (see include/fos.h): n_stacks, n_wl,
     max_layers, n_layers, mu_s, mu_a, g, n_layer, thickness, n_above, n_below,
@@ -240,11 +253,39 @@ def mc_run(batch: dict, fp32: bool = True, photon_log: bool = False):
         else:
             stride = b.photons_per_item
         log = np.full((n_run, max(stride, 1)), -1, dtype=np.int32)
-    rc = lib().orc_mc_run(ctypes.byref(b), 1 if fp32 else 0, counts.ctypes.data,
+    if mode is None:
+        mode = MODE_F32_MIRROR if fp32 else MODE_F64_ORDER
+    rc = lib().orc_mc_run(ctypes.byref(b), int(mode), counts.ctypes.data,
                           _ptr(log), stride)
     if rc != 0:
         raise ValueError(f"oracle mc_run rejected the batch (code {rc})")
     return (counts, log) if photon_log else counts
+
+
+def mc_run_threads(batch: dict, mode: int = MODE_DEFINITION, threads: int = 0):
+    """mc_run split over host threads by photon range (the library call releases the
+    GIL); counts depend only on photon ids, so the shard sums equal one run exactly."""
+    from concurrent.futures import ThreadPoolExecutor
+    threads = threads or (os.cpu_count() or 1)
+    n_items = int(batch["n_stacks"]) * int(batch["n_wl"])
+    if batch.get("n_photons") is not None:
+        N = np.asarray(batch["n_photons"], np.int64).reshape(-1)
+    else:
+        N = np.full(n_items, int(batch.get("photons_per_item", 0)), np.int64)
+    first0 = (np.zeros(n_items, np.int64) if batch.get("photon_first") is None
+              else np.asarray(batch["photon_first"], np.int64).reshape(-1))
+    shards = []
+    for t in range(threads):
+        lo = N * t // threads
+        hi = N * (t + 1) // threads
+        b = dict(batch)
+        b["n_photons"] = hi - lo
+        b["photon_first"] = first0 + lo
+        b.pop("photons_per_item", None)
+        shards.append(b)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(lambda b: mc_run(b, mode=mode), shards))
+    return sum(parts)
 
 
 # ---------------------------------------------------------------------------- Mie

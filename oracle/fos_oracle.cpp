@@ -11,13 +11,17 @@
 //     tracks only depth z and the direction cosine mu_z; step size from the
 //     extinction coefficient, absorb-or-scatter from mu_a/mu_t, new direction from
 //     Henyey-Greenstein with g; Fresnel reflection at boundaries with the matrix
-//     index).  Two arithmetic modes:
-//       - FP64: plain double arithmetic with libm log/cos/sqrt.
-//       - FP32 mirror: the same walk in IEEE single precision with an explicit
-//         operation order (no contraction; fma only where written) and
+//     index).  Three forms:
+//       - definition (walk_photon_definition): the walk in plain double arithmetic
+//         in the order the section describes it, with a sequential random stream
+//         of its own; the statistical judge of the other two.
+//       - FP32 mirror: the GPU walk's operation order and random-number layout in
+//         IEEE single precision (no contraction; fma only where written) with
 //         self-contained series for -ln(u) and cos(2 pi u) built from +,*,/,fma,
 //         so that any other implementation of the same operation order reproduces
-//         it bit for bit.
+//         it bit for bit: the photon-for-photon judge of the GPU walk.
+//       - the same order and layout in double precision with libm (walk_photon
+//         with MathF64), which separates the effect of FP32 from that of the order.
 //   * Mie theory for a sphere in an absorbing host (Eqs. 1-5, 10-12, 15), with the
 //     Riccati-Bessel logarithmic derivative D_n evaluated per order by Lentz's
 //     continued fraction for j_{n-1}/j_n, psi_n by upward recurrence below |x| and
@@ -416,6 +420,217 @@ static int walk_photon(const LayerP<M>* L, int nl, typename M::R n_above, typena
     *n_coll = coll;
     *n_iface = iface;
     return outcome;
+}
+
+// --------------------------------------------------------------------------------
+// The walk as the paper states it, in double precision: the definition that both
+// fast walks (the FP32 mirror above and the GPU kernel) are judged against
+// statistically.  Section "Photon transport": a photon enters through the top
+// surface (specular Fresnel reflection there), travels a step drawn from the
+// extinction coefficient, is absorbed with probability mu_a/mu_t at a collision or
+// else scattered into a new direction drawn from Henyey-Greenstein with g; at a
+// boundary it is reflected or refracted by Fresnel's equations with the matrix
+// indices, and it leaves the stack through the top (R) or the bottom (T).
+//
+// Written straight from that description, with none of the fast walks' choices:
+//   * the step is a length, s = -ln(u) / mu_t, compared with the distance to the
+//     boundary along the direction, s_b = (d - z)/mu_z or -z/mu_z (divisions, no
+//     reciprocals); at a boundary the unused part of the step is kept as optical
+//     depth, (s - s_b) mu_t, and becomes a length in the next layer (MCML's
+//     carry-over, the reading of the paper taken throughout);
+//   * the deflection is the closed-form inverse of the HG distribution function,
+//     (1 + g^2 - ((1 - g^2)/(1 - g + 2 g u))^2) / (2 g), and the azimuth
+//     phi = 2 pi u with libm's cos; sin(theta) from sqrt(1 - cos^2(theta));
+//   * uniforms are drawn one at a time, in the order the walk needs them, from a
+//     sequential stream of its own: the words of the Philox4x32-10 blocks at
+//     counter (photon, item, k, 3), k = 0, 1, 2, ..., each word x mapped to
+//     (x + 1/2) 2^-32 (a finer grid than the fast walks' 2^-23).
+// So it shares neither operation order nor random-number layout with the fast walks;
+// agreement with them is statistical (binomial), and its own pins are closed forms
+// and the discrete-ordinates solution of the transfer equation.
+// --------------------------------------------------------------------------------
+struct SeqStream {
+    uint32_t key[2];
+    uint32_t p, item;
+    uint32_t k;
+    int i;
+    uint32_t w[4];
+    void start(uint32_t photon) { p = photon; k = 0; i = 4; }
+    double next() {
+        if (i == 4) {
+            uint32_t c[4] = {p, item, k, 3u};
+            philox4x32_10(c, key, w);
+            ++k;
+            i = 0;
+        }
+        return ((double)w[i++] + 0.5) * 0x1p-32;
+    }
+};
+
+struct DefLayer {
+    double mu_s, mu_a, g, n, d;
+};
+
+static double hg_cos_definition(double g, double u) {
+    if (std::fabs(g) < 1e-6) return 2.0 * u - 1.0;
+    const double t = (1.0 - g * g) / (1.0 - g + 2.0 * g * u);
+    double c = (1.0 + g * g - t * t) / (2.0 * g);
+    if (c < -1.0) c = -1.0;
+    if (c > 1.0) c = 1.0;
+    return c;
+}
+
+static int walk_photon_definition(const DefLayer* L, int nl, double n_above, double n_below,
+                                  bool has_sub, double r_sub, double cos_in, double k_below,
+                                  SeqStream& rs, unsigned long long max_events,
+                                  unsigned long long* n_coll, unsigned long long* n_iface) {
+    unsigned long long events = 0, coll = 0, iface = 0;
+    *n_coll = 0;
+    *n_iface = 0;
+    // Entry through the top surface at incidence cosine cos_in.
+    double mu = cos_in;
+    if (n_above != L[0].n) {
+        double ct;
+        bool tir;
+        const double Rf = fresnel<MathF64>(n_above, L[0].n, cos_in, &ct, &tir);
+        if (tir) return OUT_R;
+        if (rs.next() < Rf) return OUT_R;
+        mu = ct;
+    }
+    int j = 0;
+    double z = 0.0;
+    double tau = -std::log(rs.next());   // optical depth still to travel before colliding
+    for (;;) {
+        if (events >= max_events) {
+            *n_coll = coll;
+            *n_iface = iface;
+            return OUT_RUNAWAY;
+        }
+        const DefLayer& Lj = L[j];
+        const double mu_t = Lj.mu_s + Lj.mu_a;
+        const double inf = std::numeric_limits<double>::infinity();
+        const double s = (mu_t > 0.0) ? tau / mu_t : inf;                  // step length
+        const double s_b = (mu > 0.0) ? (Lj.d - z) / mu : (mu < 0.0) ? -z / mu : inf;
+        if (s < s_b) {
+            // Collision inside layer j.
+            z = z + mu * s;
+            events++;
+            coll++;
+            if (rs.next() < Lj.mu_a / mu_t) {
+                *n_coll = coll;
+                *n_iface = iface;
+                return OUT_A;
+            }
+            const double cost = hg_cos_definition(Lj.g, rs.next());
+            const double phi = 2.0 * M_PI * rs.next();
+            if (std::fabs(mu) > 1.0 - 1e-5) {
+                mu = (mu > 0.0) ? cost : -cost;
+            } else {
+                const double sint = std::sqrt(1.0 - cost * cost);
+                mu = mu * cost + std::sqrt(1.0 - mu * mu) * sint * std::cos(phi);
+                if (mu < -1.0) mu = -1.0;
+                if (mu > 1.0) mu = 1.0;
+            }
+            tau = -std::log(rs.next());
+            continue;
+        }
+        // The boundary of layer j comes first (a photon travelling parallel to the
+        // layers in a transparent layer is sent to the top one).
+        const bool down = mu > 0.0;
+        if (s_b < inf) tau = tau - mu_t * s_b;
+        if (tau < 0.0) tau = 0.0;   // rounding only
+        z = down ? Lj.d : 0.0;
+        events++;
+        iface++;
+        const int nb = down ? j + 1 : j - 1;
+        const bool outside = (nb < 0) || (nb >= nl);
+        if (down && outside && (has_sub || k_below > 0.0)) {
+            const double Rb = has_sub ? r_sub
+                                      : fresnel_conductor<MathF64>(Lj.n, n_below, k_below,
+                                                                   std::fabs(mu));
+            if (rs.next() < Rb) {
+                mu = -mu;
+                continue;
+            }
+            *n_coll = coll;
+            *n_iface = iface;
+            return OUT_T;
+        }
+        const double ni = Lj.n;
+        const double nt = outside ? (down ? n_below : n_above) : L[nb].n;
+        double mu_next = mu;
+        bool transmit = true;
+        if (ni != nt) {
+            double ct;
+            bool tir;
+            const double Rf = fresnel<MathF64>(ni, nt, std::fabs(mu), &ct, &tir);
+            if (tir || rs.next() < Rf) transmit = false;
+            else mu_next = down ? ct : -ct;
+        }
+        if (!transmit) {
+            mu = -mu;
+            continue;
+        }
+        if (outside) {
+            *n_coll = coll;
+            *n_iface = iface;
+            return down ? OUT_T : OUT_R;
+        }
+        j = nb;
+        mu = mu_next;
+        z = down ? 0.0 : L[nb].d;
+    }
+}
+
+static int run_batch_definition(const orc_batch* b, long long* counts, int* photon_log,
+                                long long log_stride) {
+    const long long n_items = (long long)b->n_stacks * b->n_wl;
+    const int n_run = b->item_list ? b->n_list : (int)n_items;
+    const unsigned long long max_ev = b->max_events > 0 ? (unsigned long long)b->max_events
+                                                        : 100000000ull;
+    for (int r = 0; r < n_run; ++r) {
+        const long long it = b->item_list ? b->item_list[r] : r;
+        const int s = (int)(it / b->n_wl), w = (int)(it % b->n_wl);
+        const int nl = b->n_layers ? b->n_layers[s] : b->max_layers;
+        DefLayer L[ORC_MAX_LAYERS];
+        for (int j = 0; j < nl; ++j) {
+            const long long pi = ((long long)s * b->max_layers + j) * b->n_wl + w;
+            L[j].mu_s = b->mu_s[pi];
+            L[j].mu_a = b->mu_a[pi];
+            L[j].g = b->g[pi];
+            L[j].n = b->n_layer[pi];
+            L[j].d = b->thickness[(long long)s * b->max_layers + j];
+        }
+        const double na = b->n_above ? b->n_above[it] : 1.0;
+        const double nbw = b->n_below ? b->n_below[it] : 1.0;
+        const bool has_sub = b->substrate_R != nullptr;
+        const double rsub = has_sub ? b->substrate_R[it] : 0.0;
+        const double cin = b->cos_incidence ? b->cos_incidence[it] : 1.0;
+        const double kbw = (b->k_below && !has_sub) ? b->k_below[it] : 0.0;
+        const long long N = b->n_photons ? b->n_photons[it] : b->photons_per_item;
+        const long long first = b->photon_first ? b->photon_first[it] : 0;
+        SeqStream rs;
+        rs.key[0] = (uint32_t)(b->seed & 0xffffffffull);
+        rs.key[1] = (uint32_t)(b->seed >> 32);
+        rs.item = b->item_id_base + (uint32_t)it;
+        long long* c = counts + (long long)r * 6;
+        for (int q = 0; q < 6; ++q) c[q] = 0;
+        for (long long i = 0; i < N; ++i) {
+            rs.start((uint32_t)(first + i));
+            unsigned long long nc, ni;
+            const int out = walk_photon_definition(L, nl, na, nbw, has_sub, rsub, cin, kbw, rs,
+                                                   max_ev, &nc, &ni);
+            c[out] += 1;
+            c[4] += (long long)nc;
+            c[5] += (long long)ni;
+            if (photon_log) {
+                const unsigned long long rec = (nc << 2) | (unsigned long long)out;
+                photon_log[(long long)r * log_stride + i] =
+                    (int)(rec > 0x7fffffffull ? 0x7fffffffull : rec);
+            }
+        }
+    }
+    return 0;
 }
 
 template <class M>
@@ -826,9 +1041,12 @@ extern "C" int orc_solar_weighted(int n_stacks, int n_wl, const double* wl, cons
     return 0;
 }
 
-extern "C" int orc_mc_run(const orc_batch* b, int fp32, long long* counts, int* photon_log,
+// mode 0: the fast walk's operation order and random-number layout in FP64 (libm);
+// mode 1: the FP32 mirror of the GPU walk; mode 2: the definition walk above.
+extern "C" int orc_mc_run(const orc_batch* b, int mode, long long* counts, int* photon_log,
                           long long log_stride) {
     if (b->max_layers < 1 || b->max_layers > ORC_MAX_LAYERS) return 1;
-    if (fp32) return run_batch<MathF32>(b, counts, photon_log, log_stride);
+    if (mode == 1) return run_batch<MathF32>(b, counts, photon_log, log_stride);
+    if (mode == 2) return run_batch_definition(b, counts, photon_log, log_stride);
     return run_batch<MathF64>(b, counts, photon_log, log_stride);
 }
