@@ -37,14 +37,30 @@ WORKLOAD = ("paint layer: 400 wavelengths 0.3-2.5 um; r = 0.2 um, f = 0.10, 300 
             "Cauchy particle n = 2.5+0.05/lambda^2, k = 0.5 (<0.4 um) / 1e-4; "
             "matrix n = 1.48, k = 1e-5 lambda; 1e6 photons per wavelength; FP64 Mie + FP32 MC")
 
-# Algorithmic FP32/INT operations of one collision event of the walk (hand tally of the
-# operations the method performs, each IEEE +,-,*,/,sqrt,fma, compare, select, integer
-# multiply, logic op or conversion counted once):
-#   Philox4x32-10: 10 rounds x (2 mul.hi + 2 mul.lo + 2 three-input xor) + 18 key adds = 78
-#   4 uniforms: 4 x (shift/or 2 + convert 1 + scale 1) = 16
-#   -ln u series: 22;  free-path/boundary test and move: 11;  absorption test: 1
-#   Henyey-Greenstein inversion: 9;  direction update incl. cos(2 pi u) series: 24;  counters: 1
-OPS_PER_STEP = 78 + 16 + 22 + 11 + 1 + 9 + 24 + 1   # = 162
+# Algorithmic work of one collision event (photon-step): a hand tally of the operations
+# the method performs (free path, absorb-or-scatter, Henyey-Greenstein, direction, the
+# Philox block of its random numbers), each IEEE +,-,*,fma, compare, select, min/max,
+# integer multiply-high or -low, logic op or SFU op counted once, whatever series or
+# instruction sequence an implementation uses for log, cos, reciprocal or square root:
+#   Philox4x32-10, key schedule hoisted (the key is the seed): 10 rounds x (2 mul.hi +
+#     2 mul.lo + 2 three-input xor) + the event counter                              61
+#   3 uniforms from words (shift, or, subtract) + the absorption test on a word       10
+#   free path -ln u = log2(u) * -ln 2                                                  2
+#   collision test tau |mu| < mu_t dist (distance select, 2 products, compares) and
+#     the move s = tau / mu_t (reciprocal product), z += mu s                           9
+#   Henyey-Greenstein: 2g, 2g u + (1 - g), (1 - g^2) / den (reciprocal + product),
+#     1 + g^2 - t^2, / 2g, isotropic test and select, clamp                            10
+#   direction: near-vertical test, 1 - mu^2, 1 - cos^2, product, square root (SFU +
+#     product), cos(2 pi u) (offset, scale, SFU), mu cos + q cos phi, clamp            13
+#   event and collision counters, event cap test, loop                                  4
+# I_STEP = 109 issue slots per step, X_STEP = 4 of them on the SFU (log2, reciprocal,
+# square root, cosine).  Ceiling (per SM per clock: 4 warp instructions = 128 lanes
+# issued, 16 SFU lanes) = SMs x f x min(128 / I_STEP, 16 / X_STEP) photon-steps/s.
+I_STEP = 61 + 10 + 2 + 9 + 10 + 13 + 4   # = 109
+X_STEP = 4
+# The exact walk's own instruction budget is larger: it evaluates -ln u and cos 2 pi u
+# by 22- and ~20-operation series (bit-exact with the oracle) and IEEE division/sqrt.
+IMPL_OPS_PER_STEP_EXACT = 162
 
 
 def parse():
@@ -58,11 +74,15 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--surrogate", choices=["full", "quick", "off"], default="full",
+    ap.add_argument("--surrogate", choices=["full", "quick", "paper", "off"], default="full",
                     help="surrogate leg (1 GPU only): MC training data, ensemble training, "
-                         "design sweep with MC fallback and audit")
-    ap.add_argument("--stacks", action="store_true",
-                    help="also time the uneven multilayer-stack batch once")
+                         "design sweep with MC fallback and audit; 'paper' trains on 2e6 "
+                         "rows at 1e5 photons each (several GPU-minutes)")
+    ap.add_argument("--stacks", choices=["on", "off"], default="on",
+                    help="time the uneven multilayer-stack batch (graph-captured, "
+                         "autotuned) with both walks")
+    ap.add_argument("--fast-steps", type=int, default=5,
+                    help="steps of the paint layer timed again with the fast (SFU) walk")
     ap.add_argument("--legs", choices=["on", "off"], default="on",
                     help="workload legs after the timed steps (1 GPU only): size "
                          "distributions, core-shell spheres, oblique incidence on a conductor")
@@ -210,17 +230,18 @@ def run_fos(args):
     stream = torch.cuda.current_stream()
     l2 = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step(seed, flags=fos.FOS_ASYNC, ev=None, src=d):
+    def step(seed, flags=fos.FOS_ASYNC, ev=None, src=d, mc_flags=0):
         fos.check(fos.fos_mie_properties(src["wl"], src["nm_re"], src["nm_im"], src["sg"],
                                          src["np_re"], src["np_im"], src["radius"],
-                                         src["vol_frac"], mu_s, mu_a, g, flags=flags),
+                                         src["vol_frac"], mu_s, mu_a, g,
+                                         flags=flags & fos.FOS_ASYNC),
                   "fos_mie_properties")
         b = fos.make_batch(1, n_wl, 1, mu_s, mu_a, g, src["nm_re"], src["thickness"],
                            photons_per_item=m["photons_per_item"], seed=seed,
                            item_id_base=rank * n_wl)
         if ev is not None:
             ev[0].record(stream)
-        fos.check(fos.fos_mc_spectrum(b, counts, None, 0, flags), "fos_mc_spectrum")
+        fos.check(fos.fos_mc_spectrum(b, counts, None, 0, flags | mc_flags), "fos_mc_spectrum")
         if ev is not None:
             ev[1].record(stream)
         fos.check(fos.fos_solar_weighted(1, src["wl"], src["G"], counts, solar,
@@ -317,23 +338,29 @@ def run_fos(args):
     clocks = clk.summary()
     walk_s = statistics.mean(walk_ms) / 1e3
     steps_per_launch = coll / K
-    achieved = OPS_PER_STEP * steps_per_launch / walk_s / 1e12
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    peak = sm_count * 128 * f_max / 1e12
-    roof = dict(bound="alu", achieved=achieved, peak=peak, unit="Top/s", frac=achieved / peak,
-                traffic=None,
-                kernel="walk_kernel", ops_per_photon_step=OPS_PER_STEP,
-                photon_steps_per_launch=steps_per_launch, launch_ms=walk_s * 1e3,
-                peak_basis=f"{sm_count} SMs x 128 FP32/INT lanes x {f_max/1e6:.0f} MHz "
-                           "(maximum SM clock)")
-    if clocks:
-        roof["frac_at_sampled_clock"] = achieved / (sm_count * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+    roof = walk_roofline(steps_per_launch / walk_s, sm_count, clocks)
+    roof.update(kernel="walk_kernel (exact)", photon_steps_per_launch=steps_per_launch,
+                launch_ms=walk_s * 1e3, impl_ops_per_step=IMPL_OPS_PER_STEP_EXACT,
+                impl_ops_frac=IMPL_OPS_PER_STEP_EXACT * steps_per_launch / walk_s
+                / (sm_count * 128 * roof["f_hz"]))
+
+    # The paint layer's walk load balance: one more exact launch with per-block times.
+    tail = None
+    try:
+        step(5000, flags=0, mc_flags=fos.FOS_RECORD_TIMES)
+        tail = tail_stats(fos.fos_mc_walk_times())
+    except Exception as exc:
+        tail = dict(error=str(exc))
+
+    # The fast (SFU) walk on the same workload: tuned for it, then timed the same way.
+    fast = None
+    if args.fast_steps > 0 and world == 1:
+        try:
+            fast = run_fast_walk(args, step, counts, stream, l2, sm_count, clocks, tail_stats)
+        except Exception as exc:
+            fast = dict(error=str(exc))
+
     surr = None
     if args.surrogate != "off" and world == 1:
         try:
@@ -343,12 +370,15 @@ def run_fos(args):
     t1 = None
     if args.surrogate != "off" and world == 1:
         try:
-            t1 = run_table1(args.surrogate)
+            t1 = run_table1("quick" if args.surrogate == "quick" else "full")
         except Exception as exc:
             t1 = dict(error=str(exc))
     stacks = None
-    if args.stacks and world == 1:
-        stacks = run_stacks()
+    if args.stacks == "on" and world == 1:
+        try:
+            stacks = run_stacks(sm_count, clocks)
+        except Exception as exc:
+            stacks = dict(error=str(exc))
     dists = cs = bnd = None
     if world == 1 and args.legs == "on":
         try:
@@ -369,6 +399,12 @@ def run_fos(args):
             cpu = cpu_baseline(m, args.cpu_seconds)
         except Exception as exc:  # the baseline must not hide the GPU number
             cpu = dict(error=str(exc))
+    # details that would swamp the JSON line go to stderr
+    for name, leg in (("surrogate", surr), ("table1_network", t1)):
+        if isinstance(leg, dict):
+            worst = leg.pop("worst", None) or (leg.get("audit") or {}).pop("worst", None)
+            if worst:
+                sys.stderr.write(f"{name} worst rows: {json.dumps(worst)}\n")
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=K, warmup=args.warmup,
         ms_per_step=ms_total / K, higher_is_better=True, scaling="weak", vs_baseline=None,
@@ -376,20 +412,133 @@ def run_fos(args):
         config=dict(workload=WORKLOAD, photons_per_step=n_wl * m["photons_per_item"],
                     wavelengths=n_wl, l2="flushed before every step by a 512 MiB write "
                     "inside the timed region", tuning=dict(block=tuning[0], ppt=tuning[1]),
-                    precision="Mie f64, walk f32, tallies int64", parallelism=f"replicas x{world}"),
+                    precision="Mie f64, walk f32 (exact walk), tallies int64",
+                    parallelism=f"replicas x{world}"),
         spectra_per_s=spectra_per_s, photons_per_s=phot_all / secs,
         photon_steps_per_photon=coll / max(photons, 1),
-        e2e=e2e, roofline=roof, cpu_baseline=cpu, clocks=clocks, surrogate=surr,
-        layer_stacks=stacks, size_distributions=dists, core_shell=cs,
-        oblique_conductor=bnd, table1_network=t1,
-        solar_weighted=dict(zip(("R_s", "A_s", "T_s"), solar.cpu().tolist())),
+        e2e=e2e, roofline=roof, cpu_baseline=cpu, clocks=clocks,
         gpu_launches=6 * K,
         gpu_launches_detail="per step: mie_kernel, emt_kernel, pack_kernel, unit_scan_kernel, "
                             "walk_kernel, solar_kernel",
+        solar_weighted=dict(zip(("R_s", "A_s", "T_s"), solar.cpu().tolist())),
+        walk_tail=tail, size_distributions=dists, core_shell=cs, oblique_conductor=bnd,
+        surrogate=surr, table1_network=t1, layer_stacks=stacks, fast_walk=fast,
     )
+    line["summary"] = summarize(line)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def walk_roofline(steps_per_s: float, sm_count: int, clocks):
+    """The FP32/INT + SFU issue roofline of the walk at the maximum SM clock."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    per_clock = min(128.0 / I_STEP, 16.0 / X_STEP)
+    ceiling = sm_count * f_max * per_clock
+    roof = dict(bound="alu", achieved=steps_per_s, peak=ceiling, unit="photon-steps/s",
+                frac=steps_per_s / ceiling, traffic=None, i_step=I_STEP, x_step=X_STEP,
+                peak_basis=f"{sm_count} SMs x {f_max / 1e6:.0f} MHz (maximum SM clock) x "
+                           f"min(128/{I_STEP}, 16/{X_STEP}) steps per SM per clock",
+                f_hz=f_max)
+    if clocks and clocks.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = steps_per_s / (sm_count * clocks["sm_mhz"] * 1e6
+                                                       * per_clock)
+    return roof
+
+
+def tail_stats(t):
+    """Load balance of a persistent walk launch from per-block (start, end) times: the
+    launch span, and the tail = the time after half of the blocks have finished."""
+    import numpy as np
+    if len(t) == 0:
+        return None
+    t0, t1 = int(t[:, 0].min()), int(t[:, 1].max())
+    ends = np.sort(t[:, 1])
+    half = int(ends[len(ends) // 2])
+    span = max(t1 - t0, 1)
+    return dict(blocks=int(len(t)), launch_ms=span / 1e6, tail_ms=(t1 - half) / 1e6,
+                tail_frac=(t1 - half) / span,
+                first_block_end_frac=(int(ends[0]) - t0) / span)
+
+
+def run_fast_walk(args, step, counts, stream, l2, sm_count, clocks, tail_fn):
+    """The paint layer with the fast (SFU) walk: autotuned, then `fast_steps` steps timed
+    (walk launch on the launching stream, L2 flushed before each), then one launch with
+    per-block times."""
+    import torch
+    from paper_2409_00165_gb300 import fos
+    step(1500, flags=fos.FOS_AUTOTUNE, mc_flags=fos.FOS_FAST_WALK)
+    step(1501, mc_flags=fos.FOS_FAST_WALK)
+    torch.cuda.synchronize()
+    K = args.fast_steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    coll = 0
+    for k in range(K):
+        l2.fill_(float(k))
+        step(6000 + k, ev=evs[k], mc_flags=fos.FOS_FAST_WALK)
+        torch.cuda.synchronize()
+        coll += int(counts[:, 4].sum())
+    fos.check(fos.fos_sync_status(stream), "fast walk")
+    walk_s = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    b = step(1502, flags=0, mc_flags=fos.FOS_FAST_WALK)
+    tun = fos.fos_mc_get_tuning(b, fos.FOS_FAST_WALK)
+    step(1503, flags=0, mc_flags=fos.FOS_FAST_WALK | fos.FOS_RECORD_TIMES)
+    roof = walk_roofline(coll / walk_s, sm_count, clocks)
+    return dict(photon_steps_per_s=coll / walk_s, steps=K, launch_ms=walk_s / K * 1e3,
+                roofline=dict(frac=roof["frac"], peak=roof["peak"],
+                              frac_at_sampled_clock=roof.get("frac_at_sampled_clock")),
+                tuning=dict(block=tun[0], ppt=tun[1]), tail=tail_fn(fos.fos_mc_walk_times()))
+
+
+def summarize(line: dict) -> dict:
+    """The headline numbers of every leg in one short dict (printed last on the line)."""
+    def get(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict):
+                return None
+            d = d.get(k)
+        return d
+
+    def r(v, n=4):
+        return None if v is None else float(f"{v:.{n}g}")
+
+    surr, t1, st, fw = (line.get("surrogate"), line.get("table1_network"),
+                        line.get("layer_stacks"), line.get("fast_walk"))
+    return dict(
+        walk_exact=dict(photon_steps_per_s=r(line["value"]),
+                        frac=r(get(line, "roofline", "frac"), 3),
+                        tail_frac=r(get(line, "walk_tail", "tail_frac"), 3)),
+        walk_fast=None if not isinstance(fw, dict) or "error" in fw else dict(
+            photon_steps_per_s=r(fw["photon_steps_per_s"]), frac=r(fw["roofline"]["frac"], 3),
+            speedup_vs_exact_launch=r(line["roofline"]["launch_ms"] / fw["launch_ms"], 3)),
+        layer_stacks=None if not isinstance(st, dict) or "error" in st else dict(
+            photon_steps_per_s=r(get(st, "exact", "photon_steps_per_s")),
+            spectra_per_s=r(get(st, "exact", "spectra_per_s")),
+            tuned=get(st, "exact", "tuning"), tuned_vs_fixed_128x8=r(st.get("tuned_speedup"), 3),
+            tail_frac=r(get(st, "exact", "tail", "tail_frac"), 3),
+            fast_photon_steps_per_s=r(get(st, "fast", "photon_steps_per_s"))),
+        surrogate=None if not isinstance(surr, dict) or "error" in surr else dict(
+            mode=surr.get("mode"), train_rows=get(surr, "train", "rows"),
+            train_photons=get(surr, "train", "photons_per_row"),
+            spectra_per_s=r(surr.get("spectra_per_s")),
+            mc_spectra_per_s=r(surr.get("mc_spectra_per_s")),
+            speedup_vs_mc=r(surr.get("speedup_vs_mc")),
+            audit_rows=get(surr, "audit", "rows"),
+            audit_max=[r(v, 3) for v in get(surr, "audit", "max") or []],
+            audit_mae=[r(v, 3) for v in get(surr, "audit", "mae") or []],
+            audit_refined_max=[r(v, 3) for v in get(surr, "audit", "refined", "max") or []],
+            flagged_rows=surr.get("flagged"),
+            infer_frac=r(get(surr, "roofline", "frac"), 3)),
+        table1_network=None if not isinstance(t1, dict) or "error" in t1 else dict(
+            max=[r(v, 3) for v in t1.get("max") or []],
+            mae=[r(v, 3) for v in t1.get("mae") or []]),
+    )
 
 
 # ------------------------------------------------------------------------ surrogate leg
@@ -406,6 +555,10 @@ def run_surrogate(mode: str):
     from paper_2409_00165_gb300 import surrogate as S
     cfg = dict(full=dict(designs=20000, blocks=20, wl=50, photons=30000, steps=30000,
                          sweep=100000),
+               # the surrogate-training workload at its stated size: 2e6 (design, wavelength)
+               # rows at 1e5 photons each
+               paper=dict(designs=40000, blocks=20, wl=50, photons=100000, steps=30000,
+                          sweep=100000),
                quick=dict(designs=4000, blocks=10, wl=24, photons=10000, steps=2500,
                           sweep=20000))[mode]
     t0 = time.perf_counter()
@@ -417,7 +570,7 @@ def run_surrogate(mode: str):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     r = S.sweep(sur, n_designs=cfg["sweep"], n_wl=300, seed=5, threshold=0.01,
-                audit_frac=0.01 if mode == "full" else 0.001)
+                audit_frac=0.001 if mode == "quick" else 0.01)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -431,7 +584,9 @@ def run_surrogate(mode: str):
                          peak_basis="measured bf16 burst" if "bf16_tflops" in peaks
                          else "fallback 1.9 PFLOP/s")
     r["train"] = dict(rows=info["rows"], photons_per_row=info["photons_per_row"],
-                      data_seconds=t1 - t0, train_seconds=t2 - t1, members=4,
+                      data_seconds=t1 - t0, data_mc_seconds=info["mc_seconds"],
+                      data_photon_steps_per_s=info["photon_steps"] / max(info["mc_seconds"], 1e-9),
+                      train_seconds=t2 - t1, members=4,
                       steps_per_member=cfg["steps"], batch=8192,
                       final_loss=[h[-1][1] for h in hist.values()])
     r["mode"] = mode
@@ -453,9 +608,13 @@ def run_table1(mode: str):
     return r
 
 
-def run_stacks():
-    """The uneven batch of 64 multilayer stacks x 200 wavelengths (log-uniform 1e4-1e6
-    photons each) in one graph-captured launch with an autotuned shape: photon-steps/s."""
+def run_stacks(sm_count: int, clocks):
+    """The uneven batch of 64 multilayer stacks x 200 wavelengths (1-3 layers on a 5 %
+    reflector, log-uniform 1e4-1e6 photons per item), one graph-captured persistent walk
+    launch per call: exact and fast walk, each autotuned (block x photons per thread on a
+    proportionally scaled copy of the batch) and timed over 3 launches with CUDA events;
+    the exact walk also at the fixed default shape (128 threads, 8 photons per thread);
+    per-block times give the launch's tail."""
     import torch
 
     from paper_2409_00165_gb300 import fos
@@ -480,18 +639,44 @@ def run_stacks():
                        n_layers=nl, substrate_R=sub, n_photons=nph, seed=m["seed"])
     counts = torch.zeros((m["n_stacks"] * m["n_wl"], fos.FOS_NCOUNT), dtype=torch.int64,
                          device=dev)
-    fos.check(fos.fos_mc_spectrum(b, counts, None, 0, fos.FOS_AUTOTUNE), "stacks autotune")
-    tun = fos.fos_mc_get_tuning(b)
-    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    fos.check(fos.fos_mc_spectrum(b, counts, None, 0, 0), "stacks")
-    e.record()
-    torch.cuda.synchronize()
-    s = a.elapsed_time(e) / 1e3
-    c = counts.sum(dim=0).cpu().numpy()
-    return dict(items=int(counts.shape[0]), photons=int(c[:4].sum()), photon_steps=int(c[4]),
-                seconds=s, photon_steps_per_s=float(c[4]) / s,
-                spectra_per_s=m["n_stacks"] / s, tuning=dict(block=tun[0], ppt=tun[1]))
+
+    def timed(flags, reps=3):
+        fos.check(fos.fos_mc_spectrum(b, counts, None, 0, flags), "stacks warm-up")
+        ms = []
+        for _ in range(reps):
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fos.check(fos.fos_mc_spectrum(b, counts, None, 0, flags | fos.FOS_ASYNC), "stacks")
+            e.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(e))
+        fos.check(fos.fos_sync_status(), "stacks")
+        c = counts.sum(dim=0).cpu().numpy()
+        sec = statistics.mean(ms) / 1e3
+        return dict(seconds=sec, photon_steps=int(c[4]), photons=int(c[:4].sum()),
+                    photon_steps_per_s=float(c[4]) / sec, spectra_per_s=m["n_stacks"] / sec)
+
+    out = dict(items=int(counts.shape[0]))
+    fos.fos_mc_set_tuning(128, 8)
+    fixed = timed(0)
+    fos.fos_mc_set_tuning(0, 0)
+    for name, fl in (("exact", 0), ("fast", fos.FOS_FAST_WALK)):
+        t0 = time.perf_counter()
+        fos.check(fos.fos_mc_spectrum(b, counts, None, 0, fos.FOS_AUTOTUNE | fl), "autotune")
+        tune_s = time.perf_counter() - t0
+        r = timed(fl)
+        tun = fos.fos_mc_get_tuning(b, fl)
+        r["tuning"] = dict(block=tun[0], ppt=tun[1])
+        r["autotune_seconds"] = tune_s
+        fos.check(fos.fos_mc_spectrum(b, counts, None, 0, fl | fos.FOS_RECORD_TIMES), "times")
+        r["tail"] = tail_stats(fos.fos_mc_walk_times())
+        r["roofline_frac"] = walk_roofline(r["photon_steps_per_s"], sm_count, clocks)["frac"]
+        out[name] = r
+    out["fixed_128x8"] = dict(seconds=fixed["seconds"],
+                              photon_steps_per_s=fixed["photon_steps_per_s"])
+    out["tuned_speedup"] = fixed["seconds"] / out["exact"]["seconds"]
+    out["photons"] = out["exact"]["photons"]
+    return out
 
 
 def _mie_mc_leg(m, photons: int, seed: int):

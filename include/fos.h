@@ -18,9 +18,9 @@
  *                       slab inputs of Table 1, trained on spectra from fos_mc_spectrum
  *                       (the paper's "machine learning method" of section "Photon
  *                       transport").
- *   diagnostics         fos_philox4x32_10, fos_walk_math_f32 and fos_gemm_bf16 expose
- *                       building blocks to the parity tests; fos_measure_hw_rates the
- *                       hardware rates the kernels are measured against.
+ *   diagnostics         fos_philox4x32_10, fos_walk_math_f32, fos_walk_math_fast_f32
+ *                       and fos_gemm_bf16 expose building blocks to the parity tests;
+ *                       fos_mc_walk_times the per-block timing of a walk launch.
  *
  * Conventions for every entry point:
  *   - Plain C types only.  Pointers documented "device" point to CUDA device memory
@@ -67,6 +67,11 @@ enum {
 #define FOS_ASYNC        0x1u  /* return after enqueueing; status via fos_sync_status  */
 #define FOS_NO_GRAPH     0x2u  /* launch kernels directly instead of a cached CUDA graph */
 #define FOS_AUTOTUNE     0x4u  /* re-run the launch autotuner for this batch shape     */
+#define FOS_FAST_WALK    0x8u  /* fos_mc_spectrum: the fast walk (SFU log/cos, approximate
+                                  reciprocal and square root); statistically equal to the
+                                  exact walk, not bit for bit                         */
+#define FOS_RECORD_TIMES 0x10u /* fos_mc_spectrum: record each walk block's start and end
+                                  time (read back with fos_mc_walk_times)             */
 #define FOS_TEST_INJECT  0x10000u /* test only: the first kernel reports a failure      */
 #define FOS_TEST_STALL   0x20000u /* test only (fos_gemm_bf16, fos_surrogate_predict): a
                                      pipeline stage is never loaded, so its bounded wait
@@ -190,7 +195,10 @@ fos_status fos_size_distribution(double diameter, double sigma, double vol_frac,
  * entry test is word 0 of counter (p, item, 0, 2)), boundary draw k uses word k mod 4 of
  * counter (p, item, k/4, 1).  Results depend only on (seed, item id, photon id), not
  * on launch shape, and agree bit for bit with any implementation of the same
- * operation order.
+ * operation order.  With FOS_FAST_WALK the same walk evaluates -ln u and cos 2 pi u on
+ * the special-function unit and the deflection's division and the direction's square
+ * root approximately: same random numbers and decisions up to those roundings, so its
+ * counts agree with the exact walk's within binomial noise, not bit for bit.
  *
  * Property layout (device, FP64): layer j of stack s at wavelength w is element
  * (s*max_layers + j)*n_wl + w of mu_s, mu_a, g, n_layer (the layout of the
@@ -210,8 +218,8 @@ typedef struct fos_mc_batch {
     const double* n_below;        /* device [n_items] index below the stack, or NULL (= 1) */
     const double* substrate_R;    /* device [n_items] in [0,1]: opaque reflector below
                                      (replaces n_below), or NULL (none)               */
-    const long long* n_photons;   /* device [n_items] >= 0, or NULL (= photons_per_item) */
-    long long photons_per_item;   /* used when n_photons is NULL                       */
+    const long long* n_photons;   /* device [n_items] in 0..2^32-1, or NULL (= photons_per_item) */
+    long long photons_per_item;   /* used when n_photons is NULL; 0..2^32-1            */
     const long long* photon_first;/* device [n_items] first photon id, or NULL (= 0);
                                      first + count <= 2^32                            */
     const int* item_list;         /* device [n_list] items to run, or NULL (all, in order) */
@@ -252,16 +260,31 @@ fos_status fos_solar_weighted(int n_stacks, int n_wl, const double* wl, const do
                               const long long* counts, double* out, unsigned flags,
                               void* stream);
 
-/* Launch shape of the walk kernel: threads per block (multiple of 32, 32..128) and
- * photons per thread per work unit (a warp claims 32*ppt photons at a time).
- * fos_mc_set_tuning(0, 0) returns to autotuned/default shapes. */
+/* Launch shape of the walk kernel: threads per block (multiple of 32, 32..256; the
+ * kernel is compiled for 64, 96, 128 and 256 and a smaller block runs the next larger
+ * variant) and photons per thread per work unit (a warp claims 32*ppt photons at a
+ * time).  fos_mc_set_tuning(0, 0) returns to autotuned/default shapes (128, 8).
+ * fos_mc_get_tuning reports the shape a call with `flags` (FOS_FAST_WALK or 0) would use
+ * for this batch shape. */
 fos_status fos_mc_set_tuning(int block, int photons_per_thread);
-fos_status fos_mc_get_tuning(const fos_mc_batch* batch, int* block, int* photons_per_thread);
+fos_status fos_mc_get_tuning(const fos_mc_batch* batch, unsigned flags, int* block,
+                             int* photons_per_thread);
 
-/* Times the candidate launch shapes on a capped-photon copy of `batch` and caches
- * the fastest for batches of this shape (writes it to *block, *ppt if non-NULL). */
-fos_status fos_mc_autotune(const fos_mc_batch* batch, void* stream, int* block,
+/* The launch-shape autotuner: times every (block in 64, 96, 128, 256) x (photons per
+ * thread in 4, 8, 16) on a copy of `batch` whose photon budgets are all scaled by one
+ * factor (to about 2^26 photons in total, each non-empty item keeping at least one), so
+ * the probe keeps the batch's budget distribution, and caches the fastest for batches of
+ * this shape and walk (flags: FOS_FAST_WALK or 0).  Writes it to *block, *ppt if
+ * non-NULL.  fos_mc_spectrum with FOS_AUTOTUNE runs it first. */
+fos_status fos_mc_autotune(const fos_mc_batch* batch, unsigned flags, void* stream, int* block,
                            int* photons_per_thread);
+
+/* Per-block timing of the last walk launched with FOS_RECORD_TIMES on the current device
+ * (diagnostic of the persistent grid's load balance): *n_blocks = its grid size (0 if
+ * none); start_end_ns (host int64 [2 * capacity]) receives each block's start and end
+ * in ns of the GPU's global timer.  capacity < grid size is FOS_ERR_INVALID_ARG.  Call
+ * after the walk has finished. */
+fos_status fos_mc_walk_times(long long* start_end_ns, int capacity, int* n_blocks);
 
 /* --------------------------------------------------------------------------------
  * Diagnostics of the walk's building blocks (used by the parity tests).
@@ -269,11 +292,14 @@ fos_status fos_mc_autotune(const fos_mc_batch* batch, void* stream, int* block,
  *   key = (k0, k1)); device uint32 arrays of 4n words (Salmon et al., SC'11).
  * fos_walk_math_f32: for u[i] in (0,1): neg_log[i] = -ln u, cos2pi[i] = cos(2 pi u),
  *   as the walk evaluates them (device float arrays [n]; either output may be NULL).
+ * fos_walk_math_fast_f32: the same as the fast walk (FOS_FAST_WALK) evaluates them.
  * ------------------------------------------------------------------------------ */
 fos_status fos_philox4x32_10(const unsigned* ctr, unsigned k0, unsigned k1, unsigned* out,
                              long long n, void* stream);
 fos_status fos_walk_math_f32(const float* u, float* neg_log, float* cos2pi, long long n,
                              void* stream);
+fos_status fos_walk_math_fast_f32(const float* u, float* neg_log, float* cos2pi, long long n,
+                                  void* stream);
 
 /* --------------------------------------------------------------------------------
  * Surrogate of the photon walk (section "Photon transport": a network trained on Monte
@@ -396,28 +422,6 @@ fos_status fos_surrogate_predict(void* model, int n_members, const float* featur
 fos_status fos_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K,
                          int splits, unsigned flags, void* stream);
 
-/* Diagnostic: hardware rates of the current GPU that the kernels above are measured
- * against, each from one timed launch after a warm-up (synchronous; takes about a
- * second; allocates ~1 MB):
- *   fp64_tflops       FP64 FMA rate (8 independent DFMA chains per thread);
- *   tanh_per_s        MUFU tanh.approx.f32 results per second (whole GPU);
- *   tanh_f16x2_per_s  the same for tanh.approx.f16x2, counting both halves;
- *   mma_ts_tflops[i]  tcgen05.mma kind::f16, M = 128, K = 16, N = 64, 128, 256 (i = 0..2),
- *                     one issuing thread per SM, A operand in tensor memory;
- *   mma_ss_tflops[i]  the same with the A operand in shared memory;
- *   bulk_tbps         L2 -> shared memory untiled bulk copies (32 KB, 4 in flight per SM,
- *                     every SM reading the same 448 KB), TB/s over the GPU.
- * Returns FOS_OK, FOS_ERR_UNSUPPORTED (not an sm_100-family GPU), FOS_ERR_TIMEOUT (a
- * bounded in-kernel wait ran out) or FOS_ERR_CUDA. */
-typedef struct {
-    double fp64_tflops;
-    double tanh_per_s;
-    double tanh_f16x2_per_s;
-    double mma_ts_tflops[3];
-    double mma_ss_tflops[3];
-    double bulk_tbps;
-} fos_hw_rates;
-fos_status fos_measure_hw_rates(fos_hw_rates* out);
 
 /* --------------------------------------------------------------------------------
  * fos_mc_spectrum_noalloc: fos_mc_spectrum for callers that cannot allocate device
@@ -428,18 +432,24 @@ fos_status fos_measure_hw_rates(fos_hw_rates* out);
  * fixed memory budget where an allocation may fail or stall.  This entry point
  * allocates nothing: no cudaMalloc, cudaFree, allocating library routine, stream or
  * graph.  Its scratch (work-queue counter, status words, packed item tables) is a
- * file-scope device array of about 1.2 MB, held by every GPU that loads the library
+ * file-scope device array of about 1.2 MB, which a GPU holds from the first call on it
  * until the process exits.  The caller still passes the inputs (batch, as for
  * fos_mc_spectrum) and the output counts (device int64 [n_run * FOS_NCOUNT]).
  *   - n_run (items run) must be <= FOS_NOALLOC_MAX_ITEMS, else FOS_ERR_OUT_OF_RANGE
  *     is returned before any device work; any max_layers up to FOS_MAX_LAYERS.
  *   - flags: 0 or FOS_TEST_INJECT.  The call is synchronous (bounded wait on stream).
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call before
- *     any stream capture.
+ *   - Set-up: CUDA loads code and device arrays lazily, and loading takes device
+ *     memory.  So the first call on each device, with that device current, loads the
+ *     array and every kernel the call uses and looks up the array's device address
+ *     (cudaGetSymbolAddress).  Make that first call before the caller's allocator takes
+ *     the device's memory, and before any stream capture.  A call with an empty batch
+ *     (item_list with n_list = 0) does the set-up and nothing else.
  *   - Every call on a device shares the one array and each call clears what must start
  *     at zero; calls that overlap on the GPU (other streams, other host threads) race
  *     on it and must be serialised by the caller.
+ *   - A call whose bounded wait runs out returns FOS_ERR_TIMEOUT while its kernels may
+ *     still use the array; until that stream has drained, later calls on the device
+ *     return FOS_ERR_TIMEOUT without touching the array.
  *   - Results are identical to fos_mc_spectrum's for the same batch.
  * ------------------------------------------------------------------------------ */
 #define FOS_NOALLOC_MAX_ITEMS 4096

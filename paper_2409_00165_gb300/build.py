@@ -24,7 +24,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
 EXTRA = {
     "mc_walk.cu": ["-fmad=false"],
 }
-SOURCES = ["runtime.cu", "mc_walk.cu", "mie.cu", "mlp.cu", "solar.cu", "hw_rates.cu"]
+SOURCES = ["runtime.cu", "mc_walk.cu", "mc_walk_fast.cu", "mie.cu", "mlp.cu", "solar.cu"]
 
 
 def _nvcc() -> str:

@@ -39,6 +39,8 @@ struct Workspace {
     size_t mie_bytes = 0;
     long long* tune_counts = nullptr;       // autotuner output
     size_t tune_bytes = 0;
+    unsigned long long* walk_times = nullptr;  // per-block start/end of a recorded walk
+    size_t walk_times_bytes = 0;
     cudaStream_t side = nullptr;            // private stream for graph capture
     unsigned long long generation = 0;      // bumps when a table is reallocated
 };

@@ -28,6 +28,8 @@ FOS_ERR_UNSUPPORTED = 8
 FOS_ASYNC = 0x1
 FOS_NO_GRAPH = 0x2
 FOS_AUTOTUNE = 0x4
+FOS_FAST_WALK = 0x8
+FOS_RECORD_TIMES = 0x10
 FOS_TEST_INJECT = 0x10000
 FOS_TEST_STALL = 0x20000
 
@@ -88,15 +90,18 @@ def lib():
                                              + [vp] * 6 + [u32, vp])
             L.fos_mc_spectrum.argtypes = [ctypes.POINTER(FosBatch), vp, vp, i64, u32, vp]
             L.fos_mc_set_tuning.argtypes = [i32, i32]
-            L.fos_mc_get_tuning.argtypes = [ctypes.POINTER(FosBatch), ctypes.POINTER(i32),
+            L.fos_mc_get_tuning.argtypes = [ctypes.POINTER(FosBatch), u32, ctypes.POINTER(i32),
                                             ctypes.POINTER(i32)]
-            L.fos_mc_autotune.argtypes = [ctypes.POINTER(FosBatch), vp, ctypes.POINTER(i32),
-                                          ctypes.POINTER(i32)]
+            L.fos_mc_autotune.argtypes = [ctypes.POINTER(FosBatch), u32, vp,
+                                          ctypes.POINTER(i32), ctypes.POINTER(i32)]
+            L.fos_mc_walk_times.argtypes = [vp, i32, ctypes.POINTER(i32)]
             L.fos_philox4x32_10.argtypes = [vp, u32, u32, vp, i64, vp]
             L.fos_walk_math_f32.argtypes = [vp, vp, vp, i64, vp]
+            L.fos_walk_math_fast_f32.argtypes = [vp, vp, vp, i64, vp]
             for name in ("fos_sync_status", "fos_mie_properties", "fos_mc_spectrum",
                          "fos_mc_set_tuning", "fos_mc_get_tuning", "fos_mc_autotune",
-                         "fos_philox4x32_10", "fos_walk_math_f32"):
+                         "fos_mc_walk_times", "fos_philox4x32_10", "fos_walk_math_f32",
+                         "fos_walk_math_fast_f32"):
                 getattr(L, name).restype = i32
             _lib = L
     return _lib
@@ -256,18 +261,31 @@ def fos_mc_set_tuning(block: int, photons_per_thread: int) -> int:
     return lib().fos_mc_set_tuning(int(block), int(photons_per_thread))
 
 
-def fos_mc_get_tuning(batch: FosBatch):
+def fos_mc_get_tuning(batch: FosBatch, flags: int = 0):
     b, p = ctypes.c_int(), ctypes.c_int()
-    check(lib().fos_mc_get_tuning(ctypes.byref(batch), ctypes.byref(b), ctypes.byref(p)),
-          "fos_mc_get_tuning")
+    check(lib().fos_mc_get_tuning(ctypes.byref(batch), int(flags), ctypes.byref(b),
+                                  ctypes.byref(p)), "fos_mc_get_tuning")
     return b.value, p.value
 
 
-def fos_mc_autotune(batch: FosBatch, stream=None):
+def fos_mc_autotune(batch: FosBatch, flags: int = 0, stream=None):
     b, p = ctypes.c_int(), ctypes.c_int()
-    check(lib().fos_mc_autotune(ctypes.byref(batch), _stream(stream), ctypes.byref(b),
-                                ctypes.byref(p)), "fos_mc_autotune")
+    check(lib().fos_mc_autotune(ctypes.byref(batch), int(flags), _stream(stream),
+                                ctypes.byref(b), ctypes.byref(p)), "fos_mc_autotune")
     return b.value, p.value
+
+
+def fos_mc_walk_times():
+    """Per-block (start, end) ns of the last walk run with FOS_RECORD_TIMES (host int64
+    array [n_blocks, 2]; empty if none)."""
+    import numpy as np
+    n = ctypes.c_int()
+    check(lib().fos_mc_walk_times(None, 0, ctypes.byref(n)), "fos_mc_walk_times")
+    out = np.zeros((max(n.value, 1), 2), np.int64)
+    if n.value:
+        check(lib().fos_mc_walk_times(out.ctypes.data, n.value, ctypes.byref(n)),
+              "fos_mc_walk_times")
+    return out[: n.value]
 
 
 def fos_sync_status(stream=None, timeout_ms: int = 0) -> int:
@@ -282,11 +300,11 @@ def fos_philox4x32_10(ctr, k0: int, k1: int, out, stream=None) -> int:
                                    _stream(stream))
 
 
-def fos_walk_math_f32(u, neg_log=None, cos2pi=None, stream=None) -> int:
+def fos_walk_math_f32(u, neg_log=None, cos2pi=None, stream=None, fast: bool = False) -> int:
     f32 = torch.float32
-    return lib().fos_walk_math_f32(_dev(u, f32, "u"), _dev(neg_log, f32, "neg_log", True),
-                                   _dev(cos2pi, f32, "cos2pi", True), u.numel(),
-                                   _stream(stream))
+    fn = lib().fos_walk_math_fast_f32 if fast else lib().fos_walk_math_f32
+    return fn(_dev(u, f32, "u"), _dev(neg_log, f32, "neg_log", True),
+              _dev(cos2pi, f32, "cos2pi", True), u.numel(), _stream(stream))
 
 
 # --------------------------------------------------------------------------- surrogate
@@ -397,24 +415,6 @@ def fos_surrogate_train_step(model, member, features, targets, batch, seed, step
         _dev(batch_rows, torch.int32, "batch_rows", True), int(seed) & 0xFFFFFFFFFFFFFFFF,
         int(step), float(lr), _dev(loss_out, f32, "loss_out", True),
         _dev(grad_out, f32, "grad_out", True), int(flags), _stream(stream))
-
-
-class FosHwRates(ctypes.Structure):
-    _fields_ = [("fp64_tflops", ctypes.c_double), ("tanh_per_s", ctypes.c_double),
-                ("tanh_f16x2_per_s", ctypes.c_double),
-                ("mma_ts_tflops", ctypes.c_double * 3), ("mma_ss_tflops", ctypes.c_double * 3),
-                ("bulk_tbps", ctypes.c_double)]
-
-
-def fos_measure_hw_rates() -> dict:
-    r = FosHwRates()
-    check(_sfn("fos_measure_hw_rates", [ctypes.POINTER(FosHwRates)])(ctypes.byref(r)),
-          "fos_measure_hw_rates")
-    return dict(fp64_tflops=r.fp64_tflops, tanh_per_s=r.tanh_per_s,
-                tanh_f16x2_per_s=r.tanh_f16x2_per_s,
-                mma_ts_tflops=dict(zip((64, 128, 256), list(r.mma_ts_tflops))),
-                mma_ss_tflops=dict(zip((64, 128, 256), list(r.mma_ss_tflops))),
-                bulk_tbps=r.bulk_tbps)
 
 
 def fos_surrogate_predict(model, n_members, features, rat, spread=None, needs_mc=None,

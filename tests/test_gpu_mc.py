@@ -108,7 +108,7 @@ def test_ragged_multi_item_batch(orc):
              n_photons=rng.integers(0, 3000, size=n_st).astype(np.int64), seed=12345)
     b["n_photons"][5] = 0
     b["n_photons"][6] = 1
-    for tuning in [(0, 0), (64, 1), (128, 32), (96, 3), (32, 5)]:
+    for tuning in [(0, 0), (64, 1), (128, 32), (96, 3), (32, 5), (256, 7), (160, 2)]:
         fos.fos_mc_set_tuning(*tuning)
         c_gpu, _ = gpu_mc(b)
         c_orc = orc.mc_run(b, fp32=True)

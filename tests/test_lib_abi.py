@@ -60,8 +60,16 @@ def test_host_side_validation_needs_no_device(libfos):
     assert f.fos_mc_spectrum(ctypes.byref(b), None, None, 0, 0, None) == fos.FOS_ERR_INVALID_ARG
     b.n_stacks, b.max_layers = 1, fos.FOS_MAX_LAYERS + 1
     assert f.fos_mc_spectrum(ctypes.byref(b), None, None, 0, 0, None) == fos.FOS_ERR_INVALID_ARG
+    # a photon count that does not fit the 32-bit photon id is refused on the host
+    b.max_layers = 1
+    b.mu_s = b.mu_a = b.g = b.n_layer = b.thickness = 8
+    b.photons_per_item = 2 ** 32
+    c = ctypes.c_longlong(0)
+    assert f.fos_mc_spectrum(ctypes.byref(b), ctypes.byref(c), None, 0, 0, None) == \
+        fos.FOS_ERR_INVALID_ARG
     assert f.fos_mc_set_tuning(48, 8) == fos.FOS_ERR_INVALID_ARG
-    assert f.fos_mc_set_tuning(256, 8) == fos.FOS_ERR_INVALID_ARG   # above the kernel's bound
+    assert f.fos_mc_set_tuning(288, 8) == fos.FOS_ERR_INVALID_ARG   # above the largest variant
+    assert f.fos_mc_set_tuning(256, 8) == fos.FOS_OK
     assert f.fos_mc_set_tuning(0, 0) == fos.FOS_OK
     assert f.fos_mie_properties(0, None, 1, None, None, 0, None, None, None, None, None,
                                 None, None, None, None, None, None, 0, None) == \

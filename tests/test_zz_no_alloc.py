@@ -70,3 +70,52 @@ def test_noalloc_refuses_batches_beyond_its_maximum():
     assert st == fos.FOS_ERR_OUT_OF_RANGE
     assert torch.all(out == -7)   # no device work was done
     assert fos.fos_mc_spectrum_noalloc(b, out, flags=fos.FOS_ASYNC) == fos.FOS_ERR_INVALID_ARG
+
+
+_FILLED = r"""
+import sys
+import torch
+sys.path[:0] = [{root!r}, {tests!r}]
+from paper_2409_00165_gb300 import fos
+from test_zz_no_alloc import _batch, _counts
+torch.cuda.set_device(0)
+b, keep = _batch(300, 3, 99, 4000)
+ref = _counts(300)
+fos.check(fos.fos_mc_spectrum(b, ref, None, 0, 0), "fos_mc_spectrum")
+ref = ref.cpu()
+outs = [_counts(300) for _ in range(3)]
+fos.check(fos.fos_mc_spectrum_noalloc(b, outs[0]), "first call")   # the per-device set-up
+torch.cuda.synchronize()
+assert torch.equal(outs[0].cpu(), ref)
+# take every block of device memory that can still be had
+held = []
+chunk = 8 << 30
+while chunk >= (1 << 20):
+    try:
+        held.append(torch.empty(chunk, dtype=torch.uint8, device="cuda"))
+    except torch.cuda.OutOfMemoryError:
+        chunk //= 2
+free, total = torch.cuda.mem_get_info()
+print("device memory free after the fill (MiB):", free >> 20, "of", total >> 20, flush=True)
+for k in (1, 2):
+    fos.check(fos.fos_mc_spectrum_noalloc(b, outs[k]), f"call {{k}} with the device full")
+    torch.cuda.synchronize()
+    assert torch.equal(outs[k].cpu(), ref), k
+print("ok", flush=True)
+"""
+
+
+def test_noalloc_runs_with_device_memory_full():
+    """After its first call on a device, the entry point needs no device memory at all:
+    in a fresh process, one call, then all the device memory that can still be had taken
+    by another allocator (torch), then two more calls that still return
+    fos_mc_spectrum's counts."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    tests = os.path.join(root, "tests")
+    code = _FILLED.format(root=root, tests=tests)
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, (r.stdout[-2000:], r.stderr[-4000:])
