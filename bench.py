@@ -11,7 +11,9 @@ is reported beside it.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fos|reference]
 
 Under torchrun every rank runs its own spectrum (independent photons: weak scaling,
-no collective on the data path); rank 0 prints one JSON line.
+no collective on the data path); with --scaling strong the ranks split the photons of
+one spectrum by photon-id ranges and sum their int64 counts with one all-reduce (NCCL)
+per step, which gives the single-rank counts bit for bit.  Rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -81,6 +83,9 @@ def parse():
     ap.add_argument("--stacks", choices=["on", "off"], default="on",
                     help="time the uneven multilayer-stack batch (graph-captured, "
                          "autotuned) with both walks")
+    ap.add_argument("--scaling", choices=["weak", "strong"], default="weak",
+                    help="under torchrun: a spectrum per rank (weak), or one spectrum split "
+                         "across the ranks by photon ranges (strong)")
     ap.add_argument("--fast-steps", type=int, default=5,
                     help="steps of the paint layer timed again with the fast (SFU) walk")
     ap.add_argument("--legs", choices=["on", "off"], default="on",
@@ -230,20 +235,31 @@ def run_fos(args):
     stream = torch.cuda.current_stream()
     l2 = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step(seed, flags=fos.FOS_ASYNC, ev=None, src=d, mc_flags=0):
+    strong = args.scaling == "strong" and world > 1
+    if strong:
+        # this rank's photon-id range of every wavelength of the one spectrum
+        from paper_2409_00165_gb300 import shard
+        pf, pn = shard.photon_ranges(np.full(n_wl, m["photons_per_item"], np.int64), rank, world)
+        pf, pn = torch.as_tensor(pf, device=dev), torch.as_tensor(pn, device=dev)
+
+    def step(seed, flags=fos.FOS_ASYNC, ev=None, src=d, mc_flags=0, whole=False):
         fos.check(fos.fos_mie_properties(src["wl"], src["nm_re"], src["nm_im"], src["sg"],
                                          src["np_re"], src["np_im"], src["radius"],
                                          src["vol_frac"], mu_s, mu_a, g,
                                          flags=flags & fos.FOS_ASYNC),
                   "fos_mie_properties")
+        split = strong and not whole
         b = fos.make_batch(1, n_wl, 1, mu_s, mu_a, g, src["nm_re"], src["thickness"],
                            photons_per_item=m["photons_per_item"], seed=seed,
-                           item_id_base=rank * n_wl)
+                           item_id_base=0 if strong else rank * n_wl,
+                           photon_first=pf if split else None, n_photons=pn if split else None)
         if ev is not None:
             ev[0].record(stream)
         fos.check(fos.fos_mc_spectrum(b, counts, None, 0, flags | mc_flags), "fos_mc_spectrum")
         if ev is not None:
             ev[1].record(stream)
+        if split:
+            shard.allreduce_counts(counts)   # exact int64 sum over the ranks (NCCL)
         fos.check(fos.fos_solar_weighted(1, src["wl"], src["G"], counts, solar,
                                          flags=flags & fos.FOS_ASYNC), "fos_solar_weighted")
         return b
@@ -292,9 +308,20 @@ def run_fos(args):
         ms_total, coll_all, phot_all = mx[0].item(), sm[1].item(), sm[2].item()
     else:
         coll_all, phot_all = float(coll), float(photons)
+    if strong:   # every rank holds the summed counts of the one spectrum
+        coll_all, phot_all = float(coll), float(photons)
     secs = ms_total / 1e3
     value = coll_all / secs
-    spectra_per_s = world * K / secs
+    spectra_per_s = (1 if strong else world) * K / secs
+    strong_check = None
+    if strong:
+        # the last step's summed counts against one rank running the whole spectrum
+        if rank == 0:
+            last = per_step_counts[K - 1].clone()
+            step(2000 + K - 1, flags=0, whole=True)
+            strong_check = bool(torch.equal(last, counts))
+            assert strong_check, "sharded counts differ from the single-rank run"
+        dist.barrier()
 
     # e2e: the same step from pinned host buffers, copies and the count read-back timed
     e2e = None
@@ -407,13 +434,16 @@ def run_fos(args):
                 sys.stderr.write(f"{name} worst rows: {json.dumps(worst)}\n")
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=K, warmup=args.warmup,
-        ms_per_step=ms_total / K, higher_is_better=True, scaling="weak", vs_baseline=None,
+        ms_per_step=ms_total / K, higher_is_better=True,
+        scaling="strong" if strong else "weak", vs_baseline=None,
         dtype="f32", data="synthetic",
         config=dict(workload=WORKLOAD, photons_per_step=n_wl * m["photons_per_item"],
                     wavelengths=n_wl, l2="flushed before every step by a 512 MiB write "
                     "inside the timed region", tuning=dict(block=tuning[0], ppt=tuning[1]),
                     precision="Mie f64, walk f32 (exact walk), tallies int64",
-                    parallelism=f"replicas x{world}"),
+                    parallelism=(f"photon ranges x{world}, int64 all-reduce" if strong
+                                 else f"replicas x{world}")),
+        strong_scaling_bit_identical=strong_check,
         spectra_per_s=spectra_per_s, photons_per_s=phot_all / secs,
         photon_steps_per_photon=coll / max(photons, 1),
         e2e=e2e, roofline=roof, cpu_baseline=cpu, clocks=clocks,
@@ -472,7 +502,7 @@ def run_fast_walk(args, step, counts, stream, l2, sm_count, clocks, tail_fn):
     per-block times."""
     import torch
     from paper_2409_00165_gb300 import fos
-    step(1500, flags=fos.FOS_AUTOTUNE, mc_flags=fos.FOS_FAST_WALK)
+    step(1500, flags=0 if args.no_autotune else fos.FOS_AUTOTUNE, mc_flags=fos.FOS_FAST_WALK)
     step(1501, mc_flags=fos.FOS_FAST_WALK)
     torch.cuda.synchronize()
     K = args.fast_steps

@@ -282,8 +282,9 @@ fos_status fos_mc_autotune(const fos_mc_batch* batch, unsigned flags, void* stre
 /* Per-block timing of the last walk launched with FOS_RECORD_TIMES on the current device
  * (diagnostic of the persistent grid's load balance): *n_blocks = its grid size (0 if
  * none); start_end_ns (host int64 [2 * capacity]) receives each block's start and end
- * in ns of the GPU's global timer.  capacity < grid size is FOS_ERR_INVALID_ARG.  Call
- * after the walk has finished. */
+ * in ns of the GPU's global timer; start_end_ns = NULL only queries *n_blocks.  A
+ * capacity below the grid size is FOS_ERR_INVALID_ARG.  Call after the walk has
+ * finished. */
 fos_status fos_mc_walk_times(long long* start_end_ns, int capacity, int* n_blocks);
 
 /* --------------------------------------------------------------------------------

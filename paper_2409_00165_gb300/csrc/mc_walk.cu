@@ -636,7 +636,7 @@ fos_status fos_mc_walk_times(long long* start_end_ns, int capacity, int* n_block
         n = mc::g_state.times_blocks[ws->device];
     }
     *n_blocks = n;
-    if (n == 0 || !ws->walk_times) return FOS_OK;
+    if (n == 0 || !ws->walk_times || !start_end_ns) return FOS_OK;   // size query
     if (capacity < n) return FOS_ERR_INVALID_ARG;
     FOS_CUDA_TRY(cudaMemcpy(start_end_ns, ws->walk_times, (size_t)n * 2 * sizeof(long long),
                             cudaMemcpyDeviceToHost));

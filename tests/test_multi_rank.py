@@ -32,14 +32,28 @@ def _batch():
                 n_photons=np.array([3001, 17, 2500, 0, 999], np.int64), seed=77)
 
 
-def _worker(rank, world, port, fail_rank, q):
+def _paint_batch():
+    """The strong-scaling split of the benchmark: one paint-layer spectrum (here 12
+    wavelengths x 3000 photons) whose photon ids are split across the ranks."""
+    import oracle
+    from paper_2409_00165_gb300 import workloads as W
+    m = W.paint_layer(n_wl=12, photons=3000, seed=5)
+    p = oracle.mie_properties(m["wl"], m["nm"], m["species_group"], m["n_p"], m["radius"],
+                              m["vol_frac"])
+    return dict(n_stacks=1, n_wl=12, max_layers=1, mu_s=p["mu_s"].reshape(-1),
+                mu_a=p["mu_a"].reshape(-1), g=p["g"].reshape(-1),
+                n_layer=m["nm"].real.reshape(-1), thickness=m["thickness"],
+                n_photons=np.full(12, 3000, np.int64), seed=m["seed"])
+
+
+def _worker(rank, world, port, fail_rank, q, which="stacks"):
     import oracle
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world,
                             timeout=datetime.timedelta(seconds=10))
     try:
-        b = _batch()
+        b = _batch() if which == "stacks" else _paint_batch()
         first, count = shard.photon_ranges(b["n_photons"], rank, world)
         bb = dict(b, photon_first=first, n_photons=count)
         c = torch.as_tensor(oracle.mc_run(bb, fp32=True))
@@ -56,11 +70,12 @@ def _worker(rank, world, port, fail_rank, q):
             pass
 
 
-def _run(world, fail_rank=-1):
+def _run(world, fail_rank=-1, which="stacks"):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    ps = [ctx.Process(target=_worker, args=(r, world, port, fail_rank, q)) for r in range(world)]
+    ps = [ctx.Process(target=_worker, args=(r, world, port, fail_rank, q, which))
+          for r in range(world)]
     for p in ps:
         p.start()
     out = [q.get(timeout=120) for _ in range(world)]
@@ -87,6 +102,17 @@ def test_two_gloo_ranks_sum_to_the_single_run(orc):
     assert [r[1] for r in res] == ["ok", "ok"]
     for _, _, c in res:
         assert np.array_equal(c, single)
+
+
+def test_two_gloo_ranks_split_one_paint_layer_spectrum(orc):
+    """bench.py --scaling strong: the ranks' photon ranges of one spectrum, summed by
+    all_reduce, equal the single-rank spectrum bit for bit."""
+    single = orc.mc_run(_paint_batch(), fp32=True)
+    res = _run(2, which="paint")
+    assert [r[1] for r in res] == ["ok", "ok"]
+    for _, _, c in res:
+        assert np.array_equal(c, single)
+    assert np.all(single[:, :4].sum(axis=1) == 3000)
 
 
 def test_failed_rank_is_reported_not_hung():
