@@ -394,7 +394,8 @@ fos_status fos_mask_to_rows(const unsigned char* mask, long long n, int* rows, l
  * written to loss_out (device float) if non-NULL; it is summed with atomics, so its last
  * bits may differ between runs (the parameter update does not).  If grad_out (device float
  * [fos_surrogate_param_count()]) is non-NULL the gradient is written there and the
- * parameters are NOT updated (diagnostic).  Synchronous unless FOS_ASYNC.
+ * parameters are NOT updated (diagnostic); otherwise the member's step count kept in
+ * the model (see fos_surrogate_fit) is set to step + 1.  Synchronous unless FOS_ASYNC.
  * The library keeps one activation workspace per member slot (member mod 4): steps of
  * members in different slots may run concurrently on different streams (with
  * FOS_ASYNC); steps of members in the same slot must be ordered (one stream). */
@@ -403,6 +404,26 @@ fos_status fos_surrogate_train_step(void* model, int member, const float* featur
                                     const int* batch_rows, unsigned long long seed, int step,
                                     float lr, float* loss_out, float* grad_out,
                                     unsigned flags, void* stream);
+
+/* n_steps Adam steps of every member 0..n_members-1 with no host work per step (the
+ * training loop of the surrogate; the same arithmetic as fos_surrogate_train_step).  Each
+ * member continues from its own step count g, kept in the model buffer (0 after
+ * fos_surrogate_init / fos_surrogate_load, saved with the buffer): step g draws its batch
+ * from a hash of (seed, member, g), uses Adam's t = g + 1 and the cosine learning rate
+ * lr_min + (lr_max - lr_min)(1 + cos(pi min(g - schedule_origin, schedule_total) /
+ * schedule_total))/2 (g - schedule_origin clamped at 0).  One step of the whole ensemble
+ * is captured once into a CUDA graph (members of different slots, member mod 4, on
+ * parallel branches; the step counts, learning rate and bias corrections live on the
+ * device) and the graph is launched n_steps times on `stream`.
+ *   loss_out: device float [n_members] or NULL: each member's loss of its last step.
+ * Errors of the device work are reported like FOS_ASYNC calls (fos_sync_status); without
+ * FOS_ASYNC the call waits for the stream and returns that status itself.  Batch as for
+ * fos_surrogate_train_step; flags: 0 or FOS_ASYNC. */
+fos_status fos_surrogate_fit(void* model, int n_members, const float* features,
+                             const float* targets, long long n_rows, int batch,
+                             unsigned long long seed, int n_steps, float lr_max, float lr_min,
+                             int schedule_origin, int schedule_total, float* loss_out,
+                             unsigned flags, void* stream);
 
 /* Ensemble prediction with members 0..n_members-1 (1..16): rat [n_rows*3] = mean of the
  * members' (R, A, T); spread [n_rows] (or NULL) = max over R, A, T of (max - min across

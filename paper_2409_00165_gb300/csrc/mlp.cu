@@ -963,11 +963,44 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {   // a 32-bit integer ha
 // Training batch: rows given, or drawn uniformly (with replacement) by hashing (seed,
 // step, slot);
 // standardised features -> X0 [B][64] and X0^T [64][B] (pads stay 0); targets -> Y.
+// Step schedule of one member's training step, computed on the device from the member's
+// step counter (graph-captured training, where the host does not see each step).
+struct SchedOut {
+    unsigned step;        // the member's global step g (Adam's t = g + 1)
+    float lr, c1, c2;     // learning rate; 1 - b1^t, 1 - b2^t
+};
+
+// Cosine schedule lr_min + (lr_max - lr_min)(1 + cos(pi min(g - origin, total) / total))/2
+// and Adam's bias corrections at t = g + 1, from the member's device step counter, which
+// then advances.
+__global__ void sched_kernel(int* step_ctr, SchedOut* out, float lr_max, float lr_min,
+                             int origin, int total) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int g = *step_ctr;
+    double gs = (double)max(g - origin, 0);
+    if (gs > (double)total) gs = (double)total;
+    const double lr = (double)lr_min + 0.5 * ((double)lr_max - (double)lr_min) *
+                                           (1.0 + cos(M_PI * gs / (double)total));
+    const double t = (double)g + 1.0;
+    SchedOut o;
+    o.step = (unsigned)g;
+    o.lr = (float)lr;
+    o.c1 = (float)(1.0 - pow(0.9, t));
+    o.c2 = (float)(1.0 - pow(0.999, t));
+    *out = o;
+    *step_ctr = g + 1;
+}
+
+__global__ void set_step_kernel(int* step_ctr, int value) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *step_ctr = value;
+}
+
 __global__ void gather_kernel(const float* feat, const float* targets, long long n_rows, int B,
                               unsigned seed, unsigned step, const int* rows, const float* stats,
-                              bf16* X0, bf16* X0T, float* Y) {
+                              bf16* X0, bf16* X0T, float* Y, const SchedOut* sched) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
+    if (sched) step = sched->step;
     long long src;
     if (rows) {
         src = rows[b];
@@ -1033,11 +1066,17 @@ struct AdamArgs {
     const float* bpart[N_LAYERS];  // per-split column sums of G_l [COLSUM_SPLITS][real out]
     int splits;
     float lr, b1, b2, eps, c1, c2;  // c1 = 1 - b1^t, c2 = 1 - b2^t
+    const SchedOut* sched;          // non-NULL: lr, c1, c2 from the device schedule
 };
 
 // Adam (Kingma & Ba) on every real parameter, then the bf16 copies W (and W^T for
 // layers >= 1).  Padding stays zero.
 __global__ void adam_kernel(AdamArgs A, long long P) {
+    if (A.sched) {
+        A.lr = A.sched->lr;
+        A.c1 = A.sched->c1;
+        A.c2 = A.sched->c2;
+    }
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
          idx += (long long)gridDim.x * blockDim.x) {
         int l = 0;
@@ -1286,6 +1325,7 @@ struct TrainWs {
     size_t bytes = 0;
     bf16 *X0, *X0T, *H[4], *HT[4], *G4, *G4T, *dZ[4], *dZT[4];
     float *Z[4], *P, *Y, *part[N_LAYERS], *colpart[N_LAYERS], *loss;
+    SchedOut* sched;
 };
 // One training workspace per device and member slot (member mod TRAIN_SLOTS), so that
 // the steps of up to TRAIN_SLOTS members can run concurrently on separate streams.
@@ -1293,9 +1333,10 @@ constexpr int TRAIN_SLOTS = 4;
 static_assert(TRAIN_SLOTS + 1 <= ST_REGIONS, "a status region per training slot");
 static TrainWs g_tws[64][TRAIN_SLOTS];
 
-static fos_status ensure_train_ws(int dev, int slot, int B) {
+static fos_status ensure_train_ws(int dev, int slot, int B, Workspace* ws = nullptr) {
     TrainWs& w = g_tws[dev][slot];
     if (w.mem && w.B == B) return FOS_OK;
+    if (ws) ws->generation++;   // captured training graphs hold the old buffers
     if (w.mem) {
         FOS_CUDA_TRY(cudaDeviceSynchronize());
         cudaFree(w.mem);
@@ -1327,6 +1368,7 @@ static fos_status ensure_train_ws(int dev, int slot, int B) {
         add((void**)&w.colpart[l], (size_t)COLSUM_SPLITS * real_out(l) * 4);
     }
     add((void**)&w.loss, 16);
+    add((void**)&w.sched, sizeof(SchedOut));
     for (auto& it : items) o = al(o + it.bytes);
     void* mem = nullptr;
     cudaError_t e = cudaMalloc(&mem, o);
@@ -1371,16 +1413,18 @@ static GemmArgs gargs(unsigned* status) {
 }
 
 // Forward + backward + Adam for one member on one batch (all on stream s).
+// One Adam step of one member on stream s.  sched = NULL: step and lr as given; else the
+// step, lr and bias corrections come from the device schedule (graph-captured training).
 static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, const float* feat,
                              const float* targets, long long n_rows, int B, unsigned seed,
                              unsigned step, const int* rows, float lr, float* grad_out,
-                             cudaStream_t s) {
+                             cudaStream_t s, const SchedOut* sched = nullptr) {
     TrainWs& w = g_tws[ws->device][slot];
     unsigned* status = ws->status + ST_WORDS * (1 + slot);   // this slot's status region
     const int splits = w.splits;
     FOS_CUDA_TRY(cudaMemsetAsync(w.loss, 0, 4, s));
     gather_kernel<<<(B + 255) / 256, 256, 0, s>>>(feat, targets, n_rows, B, seed, step, rows,
-                                                  mp.stats, w.X0, w.X0T, w.Y);
+                                                  mp.stats, w.X0, w.X0T, w.Y, sched);
     FOS_CUDA_TRY(cudaGetLastError());
     const float* bias[N_LAYERS];
     const bf16* wb[N_LAYERS];
@@ -1467,8 +1511,112 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
     const double t = (double)step + 1.0;
     a.c1 = (float)(1.0 - pow(0.9, t));
     a.c2 = (float)(1.0 - pow(0.999, t));
+    a.sched = sched;
     adam_kernel<<<(unsigned)((LAY.P + 255) / 256), 256, 0, s>>>(a, LAY.P);
     return from_cuda(cudaGetLastError());
+}
+
+// ----------------------------------------------------------------------- graph training
+// Many steps of every member with no host work per step: one ensemble step (for each
+// member: its schedule from its device step counter, the Adam step of train_step, its
+// loss, the status of its slot folded into the accumulated word) is captured once into a
+// CUDA graph, the members of different slots on parallel branches, and the graph is
+// launched once per step.
+struct FitKey {
+    void* model;
+    int n_members, B, origin, total, device;
+    const float *feat, *targets;
+    long long n_rows;
+    unsigned long long seed;
+    float lr_max, lr_min;
+    float* loss_out;
+    unsigned long long generation;
+    bool operator==(const FitKey& o) const { return std::memcmp(this, &o, sizeof(*this)) == 0; }
+};
+struct FitGraph {
+    FitKey key;
+    cudaGraphExec_t exec = nullptr;
+};
+struct FitDev {
+    bool ready = false;
+    cudaStream_t slot_stream[TRAIN_SLOTS] = {};
+    cudaEvent_t fork = nullptr, join[TRAIN_SLOTS] = {};
+    std::vector<FitGraph> graphs;
+};
+static FitDev g_fit[64];
+
+static fos_status fit_resources(int dev) {
+    FitDev& f = g_fit[dev];
+    if (f.ready) return FOS_OK;
+    for (int i = 0; i < TRAIN_SLOTS; ++i) {
+        FOS_CUDA_TRY(cudaStreamCreateWithFlags(&f.slot_stream[i], cudaStreamNonBlocking));
+        FOS_CUDA_TRY(cudaEventCreateWithFlags(&f.join[i], cudaEventDisableTiming));
+    }
+    FOS_CUDA_TRY(cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming));
+    f.ready = true;
+    return FOS_OK;
+}
+
+// Enqueues one ensemble step on the capture stream cs (forked to the slot streams).
+static fos_status enqueue_fit_step(Workspace* ws, const FitKey& k, cudaStream_t cs) {
+    FitDev& f = g_fit[ws->device];
+    const int slots = k.n_members < TRAIN_SLOTS ? k.n_members : TRAIN_SLOTS;
+    FOS_CUDA_TRY(cudaEventRecord(f.fork, cs));
+    for (int i = 0; i < slots; ++i) FOS_CUDA_TRY(cudaStreamWaitEvent(f.slot_stream[i], f.fork, 0));
+    for (int m = 0; m < k.n_members; ++m) {
+        const int slot = m % TRAIN_SLOTS;
+        cudaStream_t s = f.slot_stream[slot];
+        TrainWs& w = g_tws[ws->device][slot];
+        const int region = 1 + slot;
+        FOS_CUDA_TRY(cudaMemsetAsync(ws->status + ST_WORDS * region + ST_CALL, 0,
+                                     sizeof(unsigned), s));
+        MemberPtrs mp = member(k.model, m);
+        sched_kernel<<<1, 32, 0, s>>>(mp.step, w.sched, k.lr_max, k.lr_min, k.origin, k.total);
+        FOS_CUDA_TRY(cudaGetLastError());
+        const unsigned seed = (unsigned)(k.seed ^ (k.seed >> 32)) ^ (unsigned)(m * 0x9E3779B9u);
+        fos_status st = train_step(ws, slot, mp, k.feat, k.targets, k.n_rows, k.B, seed, 0,
+                                   nullptr, 1.0f, nullptr, s, w.sched);
+        if (st != FOS_OK) return st;
+        if (k.loss_out)
+            FOS_CUDA_TRY(cudaMemcpyAsync(k.loss_out + m, w.loss, sizeof(float),
+                                         cudaMemcpyDeviceToDevice, s));
+        st = accumulate_async_status(ws, s, region);
+        if (st != FOS_OK) return st;
+    }
+    for (int i = 0; i < slots; ++i) {
+        FOS_CUDA_TRY(cudaEventRecord(f.join[i], f.slot_stream[i]));
+        FOS_CUDA_TRY(cudaStreamWaitEvent(cs, f.join[i], 0));
+    }
+    return FOS_OK;
+}
+
+static fos_status fit_graph(Workspace* ws, const FitKey& k, cudaGraphExec_t* out) {
+    FitDev& f = g_fit[ws->device];
+    for (auto& g : f.graphs)
+        if (g.key == k) {
+            *out = g.exec;
+            return FOS_OK;
+        }
+    cudaGraph_t graph = nullptr;
+    FOS_CUDA_TRY(cudaStreamBeginCapture(ws->side, cudaStreamCaptureModeThreadLocal));
+    fos_status st = enqueue_fit_step(ws, k, ws->side);
+    cudaError_t ce = cudaStreamEndCapture(ws->side, &graph);
+    if (st != FOS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    FOS_CUDA_TRY(ce);
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    FOS_CUDA_TRY(ce);
+    if (f.graphs.size() >= 8) {
+        cudaGraphExecDestroy(f.graphs.front().exec);
+        f.graphs.erase(f.graphs.begin());
+    }
+    f.graphs.push_back(FitGraph{k, exec});
+    *out = exec;
+    return FOS_OK;
 }
 
 // Inference workspace: rows per chunk.
@@ -1676,7 +1824,7 @@ fos_status fos_surrogate_train_step(void* model, int member, const float* featur
     fos_status st = mlp::prep(&ws);
     if (st != FOS_OK) return st;
     const int slot = member % mlp::TRAIN_SLOTS;
-    st = mlp::ensure_train_ws(ws->device, slot, batch);
+    st = mlp::ensure_train_ws(ws->device, slot, batch, ws);
     if (st != FOS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int region = 1 + slot;   // concurrent slots keep separate call words
@@ -1690,7 +1838,65 @@ fos_status fos_surrogate_train_step(void* model, int member, const float* featur
         mlp::TrainWs& w = mlp::g_tws[ws->device][slot];
         FOS_CUDA_TRY(cudaMemcpyAsync(loss_out, w.loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
     }
+    if (!grad_out) {   // the member's step count in the model (read by fos_surrogate_fit)
+        mlp::set_step_kernel<<<1, 32, 0, s>>>(mp.step, step + 1);
+        FOS_CUDA_TRY(cudaGetLastError());
+    }
     return finish_call(ws, s, flags, region);
+}
+
+fos_status fos_surrogate_fit(void* model, int n_members, const float* features,
+                             const float* targets, long long n_rows, int batch,
+                             unsigned long long seed, int n_steps, float lr_max, float lr_min,
+                             int schedule_origin, int schedule_total, float* loss_out,
+                             unsigned flags, void* stream) {
+    NvtxRange nvtx("fos_surrogate_fit");
+    if (!model || n_members < 1 || !features || !targets || n_rows < 1 || n_steps < 0)
+        return FOS_ERR_INVALID_ARG;
+    if (batch < 256 || batch % 256 != 0 || batch > 65536) return FOS_ERR_INVALID_ARG;
+    if (!(lr_max > 0.f) || !(lr_min >= 0.f) || schedule_total < 1 || schedule_origin < 0)
+        return FOS_ERR_INVALID_ARG;
+    if (flags & ~(unsigned)FOS_ASYNC) return FOS_ERR_INVALID_ARG;
+    Workspace* ws = nullptr;
+    fos_status st = mlp::prep(&ws);
+    if (st != FOS_OK) return st;
+    const int slots = n_members < mlp::TRAIN_SLOTS ? n_members : mlp::TRAIN_SLOTS;
+    for (int i = 0; i < slots; ++i) {
+        st = mlp::ensure_train_ws(ws->device, i, batch, ws);
+        if (st != FOS_OK) return st;
+    }
+    st = mlp::fit_resources(ws->device);
+    if (st != FOS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_steps > 0) {
+        mlp::FitKey k;
+        std::memset(&k, 0, sizeof(k));
+        k.model = model;
+        k.n_members = n_members;
+        k.B = batch;
+        k.origin = schedule_origin;
+        k.total = schedule_total;
+        k.device = ws->device;
+        k.feat = features;
+        k.targets = targets;
+        k.n_rows = n_rows;
+        k.seed = seed;
+        k.lr_max = lr_max;
+        k.lr_min = lr_min;
+        k.loss_out = loss_out;
+        k.generation = ws->generation;
+        cudaGraphExec_t exec = nullptr;
+        st = mlp::fit_graph(ws, k, &exec);
+        if (st != FOS_OK) return st;
+        for (int i = 0; i < n_steps; ++i) FOS_CUDA_TRY(cudaGraphLaunch(exec, s));
+    }
+    if (flags & FOS_ASYNC) return FOS_OK;
+    st = wait_stream(s, default_timeout_ms());
+    if (st != FOS_OK) return st;
+    unsigned bits = 0;
+    FOS_CUDA_TRY(cudaMemcpy(&bits, ws->status + ST_ASYNC, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    FOS_CUDA_TRY(cudaMemset(ws->status + ST_ASYNC, 0, sizeof(unsigned)));
+    return status_from_bits(bits);
 }
 
 fos_status fos_surrogate_predict(void* model, int n_members, const float* features,

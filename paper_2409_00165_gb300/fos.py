@@ -401,6 +401,22 @@ def fos_mask_to_rows(mask, rows, count, stream=None) -> int:
         _dev(count, torch.int64, "count"), _stream(stream))
 
 
+def fos_surrogate_fit(model, n_members, features, targets, batch, seed, n_steps, lr_max,
+                      lr_min, schedule_origin, schedule_total, loss_out=None, flags=0,
+                      stream=None) -> int:
+    f32 = torch.float32
+    n_rows = features.numel() // 9
+    return _sfn("fos_surrogate_fit",
+                [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                 ctypes.c_longlong, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int,
+                 ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                 ctypes.c_uint, ctypes.c_void_p])(
+        _dev(model, torch.uint8, "model"), int(n_members), _dev(features, f32, "features"),
+        _dev(targets, f32, "targets"), n_rows, int(batch), int(seed) & 0xFFFFFFFFFFFFFFFF,
+        int(n_steps), float(lr_max), float(lr_min), int(schedule_origin), int(schedule_total),
+        _dev(loss_out, f32, "loss_out", True), int(flags), _stream(stream))
+
+
 def fos_surrogate_train_step(model, member, features, targets, batch, seed, step, lr,
                              batch_rows=None, loss_out=None, grad_out=None, flags=0,
                              stream=None) -> int:

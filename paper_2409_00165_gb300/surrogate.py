@@ -124,6 +124,9 @@ class Surrogate:
         members = list(range(self.n_members) if members is None else members)
         total = schedule_steps or steps
         dev = features.device
+        if members == list(range(self.n_members)) and len(set(self.steps_done)) == 1:
+            return self._fit_graph(features, targets, steps, batch, lr, lr_min, log_every,
+                                   0 if schedule_steps else self.steps_done[0], total)
         # members in different workspace slots (member mod 4) step concurrently, one
         # stream per slot; a member's own steps stay in order on its slot's stream
         streams = {k % 4: torch.cuda.Stream(device=dev) for k in members}
@@ -148,6 +151,32 @@ class Surrogate:
             cur_stream.wait_stream(st)
         torch.cuda.synchronize(dev)
         fos.check(fos.fos_sync_status(), "training")
+        return hist
+
+    def _fit_graph(self, features, targets, steps, batch, lr, lr_min, log_every, origin, total):
+        """All members together, one graph launch per step (fos_surrogate_fit); the loss is
+        read back at the logging steps only."""
+        dev = features.device
+        loss = torch.zeros(self.n_members, dtype=torch.float32, device=dev)
+        hist = {k: [] for k in range(self.n_members)}
+        marks = sorted({t for t in range(steps) if log_every and (t % log_every == 0
+                                                                  or t == steps - 1)})
+        done = 0
+        for t in marks + [steps - 1]:
+            n = t + 1 - done
+            if n <= 0:
+                continue
+            fos.check(fos.fos_surrogate_fit(self.model, self.n_members, features, targets,
+                                            batch, self.seed, n, lr, lr_min, origin, total,
+                                            loss_out=loss, flags=fos.FOS_ASYNC), "fit")
+            done += n
+            if t in marks:
+                vals = loss.cpu().tolist()
+                for k in range(self.n_members):
+                    hist[k].append((t, vals[k]))
+        torch.cuda.synchronize(dev)
+        fos.check(fos.fos_sync_status(), "training")
+        self.steps_done = [s + steps for s in self.steps_done]
         return hist
 
     def save(self, path: str):
