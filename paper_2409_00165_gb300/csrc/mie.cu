@@ -236,6 +236,15 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
     const cx q = n_m / n_p, qi = n_p / n_m;
     Sums S{0.0, 0.0, 0.0, 0.0};
     cx a_prev = mk(0.0, 0.0), b_prev = mk(0.0, 0.0);
+    // Early end of the sums.  Past n_w = |x| + 4.05 |x|^(1/3) + 2 (Wiscombe's count for the
+    // host argument) psi_n(x) falls and xi_n(x) grows super-exponentially, and the terms
+    // (2n + 1)(|a_n| + |b_n|) fall faster than geometrically (their ratio tends to
+    // (|x| / (2n + 3))^2 < 1/4 there), so once two successive terms are below 2^-60 of the
+    // partial sums, everything after them (the rest of Eqs. 11-12, and Eq. 15 with its
+    // a_{n+1}) is below 2^-60 of the sums too.  The downward recurrences still start above
+    // the n_max of Eq. 12's criterion, so every order used is as accurate as before.
+    const int n_w = (int)ceil(ax + 4.05 * cbrt(ax) + 2.0);
+    int small = 0;
     for (int n = 1; n <= nt; ++n) {
         const double dn = (double)n;
         const cx c = (double)(2 * n - 1) * xi_, nx = dn * xi_;
@@ -256,6 +265,13 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
         div_pair(mul_sub(qa, psi_n, psi_0), mul_sub(qa, xi_n, xi_0), mul_sub(qb, psi_n, psi_0),
                  mul_sub(qb, xi_n, xi_0), an, bn);
         accumulate(S, n, nmax, an, bn, a_prev, b_prev);
+        if (n > n_w) {
+            const double t = (2.0 * dn + 1.0) *
+                             (fabs(an.re) + fabs(an.im) + fabs(bn.re) + fabs(bn.im));
+            const double ref = fabs(S.ext_re) + fabs(S.ext_im) + S.sca;
+            small = (t < 0x1p-60 * ref) ? small + 1 : 0;
+            if (small >= 2) break;
+        }
         a_prev = an;
         b_prev = bn;
         psi_m1 = psi_0;
