@@ -47,10 +47,22 @@ __device__ __forceinline__ cx div_smith(cx a, cx b) {
 __device__ __forceinline__ int exponent_field(double v) {
     return (__double2hiint(v) >> 20) & 0x7ff;
 }
+// 1/v for v of moderate exponent (the callers check the range): the SFU's approximate
+// FP64 reciprocal refined by two Newton-Raphson steps r <- r + r (1 - v r), each of which
+// squares the relative error, so the result is within an ulp or two of 1/v with 4 FP64
+// fused multiply-adds in place of a correctly rounded division.
+__device__ __forceinline__ double rcp_nr(double v) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(v));
+    double e = fma(-v, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-v, r, 1.0);
+    return fma(r, e, r);
+}
 __device__ __forceinline__ cx operator/(cx a, cx b) {
     const int e = max(exponent_field(b.re), exponent_field(b.im));
     if (e > 1023 + 490 || e < 1023 - 490) return div_smith(a, b);
-    const double inv = 1.0 / (b.re * b.re + b.im * b.im);
+    const double inv = rcp_nr(b.re * b.re + b.im * b.im);
     return cx{(a.re * b.re + a.im * b.im) * inv, (a.im * b.re - a.re * b.im) * inv};
 }
 // 1/b = conj(b) / |b|^2 (the quotient above with a = 1, without its products by 0).
@@ -74,7 +86,7 @@ __device__ __forceinline__ void div_pair(cx na, cx da, cx nb, cx db, cx& qa, cx&
         return;
     }
     const double pa = da.re * da.re + da.im * da.im, pb = db.re * db.re + db.im * db.im;
-    const double inv = 1.0 / (pa * pb);
+    const double inv = rcp_nr(pa * pb);
     const double ia = pb * inv, ib = pa * inv;
     qa = cx{(na.re * da.re + na.im * da.im) * ia, (na.im * da.re - na.re * da.im) * ia};
     qb = cx{(nb.re * db.re + nb.im * db.im) * ib, (nb.im * db.re - nb.re * db.im) * ib};
@@ -134,20 +146,21 @@ __device__ __forceinline__ void flag(unsigned* st, unsigned bit, long long idx) 
 }
 
 // Downward recurrence D_{n-1} = n/z - 1/(D_n + n/z) from D_{nstart} = 0; D_n stored for
-// nlow <= n <= nt at col[(n-1) T] (orders below nlow are not needed by the caller).
+// nlow <= n <= nt at col[(n - nbase) T] (orders below nlow are not needed by the caller;
+// nbase = 1 stores order n at row n - 1).
 __device__ __forceinline__ void downward_D(cx z, int nstart, int nt, double2* col, long long T,
-                                           int nlow = 1) {
+                                           int nlow = 1, int nbase = 1) {
     const cx zi = crcp(z);
     cx D = mk(0.0, 0.0);
     for (int n = nstart; n >= nlow; --n) {
-        if (n <= nt) col[(long long)(n - 1) * T] = make_double2(D.re, D.im);
+        if (n <= nt) col[(long long)(n - nbase) * T] = make_double2(D.re, D.im);
         const cx nz = (double)n * zi;
         const cx w = D + nz;   // D_{n-1} = nz - conj(w) / |w|^2
         const int e = max(exponent_field(w.re), exponent_field(w.im));
         if (e > 1023 + 490 || e < 1023 - 490) {
             D = nz - div_smith(mk(1.0, 0.0), w);
         } else {
-            const double inv = 1.0 / (w.re * w.re + w.im * w.im);
+            const double inv = rcp_nr(w.re * w.re + w.im * w.im);
             D = mk(fma(-w.re, inv, nz.re), fma(w.im, inv, nz.im));
         }
     }
@@ -172,6 +185,15 @@ struct Eq15Weights {
     }
 };
 __constant__ Eq15Weights g_eq15 = Eq15Weights();
+// The weights of order m, from the table below FOS_MIE_MAX_TERMS and computed above it
+// (large spheres only).
+__device__ __forceinline__ double eq15_c1(int m) {
+    return m < FOS_MIE_MAX_TERMS ? g_eq15.c1[m] : (double)m * ((double)m + 2.0) / ((double)m + 1.0);
+}
+__device__ __forceinline__ double eq15_c2(int m) {
+    return m < FOS_MIE_MAX_TERMS ? g_eq15.c2[m]
+                                 : (2.0 * (double)m + 1.0) / ((double)m * ((double)m + 1.0));
+}
 
 // Accumulates Eqs. 11, 12 and the numerator of 15 for order n given a_n, b_n and the
 // previous order's coefficients.
@@ -189,7 +211,7 @@ __device__ __forceinline__ void accumulate(Sums& S, int n, int nmax, cx an, cx b
         const double t1 = a_prev.re * an.re + a_prev.im * an.im + b_prev.re * bn.re +
                           b_prev.im * bn.im;              // Re(a_m a_n^* + b_m b_n^*)
         const double t2 = a_prev.re * b_prev.re + a_prev.im * b_prev.im;   // Re(a_m b_m^*)
-        S.g += g_eq15.c1[n - 1] * t1 + g_eq15.c2[n - 1] * t2;
+        S.g += eq15_c1(n - 1) * t1 + eq15_c2(n - 1) * t2;
     }
 }
 
@@ -211,7 +233,10 @@ __device__ __forceinline__ void efficiencies(const Sums& S, double lam, double r
 // a_n = (q D_n(y) psi_n - psi_n') / (q D_n(y) xi_n - xi_n'), q = n_m / n_p, and b_n the
 // same with 1/q; with the derivatives from the recurrence this is
 // a_n = ((q D_n(y) + n/x) psi_n - psi_{n-1}) / ((q D_n(y) + n/x) xi_n - xi_{n-1}).
-// Returns false when n_max + 16 exceeds the scratch.
+// The scratch holds FOS_MIE_MAX_TERMS orders per column: larger spheres are summed in
+// chunks of that many orders, each chunk's D_n taken from a downward recurrence started at
+// the same N* (so every order has the accuracy of one recurrence from N*), which
+// repeats the downward work once per chunk.  Always returns true.
 __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY, double2* colX,
                             long long T, double* qe, double* qs, double* gg) {
     const double k = 2.0 * M_PI * r / lam;
@@ -221,13 +246,10 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
     const int nmax = (int)ceil(2.0 + ay + 4.3 * cbrt(ay));
     const int nt = nmax + 1;          // a_{n+1}, b_{n+1} for Eq. 15
     const int nstart = nt + 16;
-    if (nstart > FOS_MIE_MAX_TERMS) return false;
     const cx xi_ = crcp(x);
-    downward_D(y, nstart, nt, colY, T);
     // orders n <= n_up (n <= |x|) take psi_n(x) from the upward recurrence; integer
     // comparisons keep the per-order test off the FP64 pipe
     const int n_up = (int)fmin(floor(ax), (double)nstart);
-    downward_D(x, nstart, nt, colX, T, n_up + 1);
     cx psi_m1 = ccos(x), psi_0 = csin(x);
     const double eb = exp(-x.im);
     cx xi_m1 = mk(eb * cos(x.re), eb * sin(x.re));        // e^{ix}
@@ -245,20 +267,25 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
     // the n_max of Eq. 12's criterion, so every order used is as accurate as before.
     const int n_w = (int)ceil(ax + 4.05 * cbrt(ax) + 2.0);
     int small = 0;
-    for (int n = 1; n <= nt; ++n) {
+    bool done = false;
+    for (int c0 = 1; c0 <= nt && !done; c0 += FOS_MIE_MAX_TERMS) {
+    const int c1 = min(nt, c0 + FOS_MIE_MAX_TERMS - 1);
+    downward_D(y, nstart, c1, colY, T, c0, c0);
+    if (c1 > n_up) downward_D(x, nstart, c1, colX, T, max(c0, n_up + 1), c0);
+    for (int n = c0; n <= c1; ++n) {
         const double dn = (double)n;
         const cx c = (double)(2 * n - 1) * xi_, nx = dn * xi_;
         cx psi_n;
         if (n <= n_up) {
             psi_n = mul_sub(c, psi_0, psi_m1);
         } else {
-            const double2 d = colX[(long long)(n - 1) * T];
+            const double2 d = colX[(long long)(n - c0) * T];
             psi_n = psi_0 / (mk(d.x, d.y) + nx);
         }
         const cx xi_n = mul_sub(c, xi_0, xi_m1);
         // with psi_n' = psi_{n-1} - (n/x) psi_n (and the same for xi_n), q D psi_n - psi_n'
         // = (q D + n/x) psi_n - psi_{n-1}
-        const double2 dy = colY[(long long)(n - 1) * T];
+        const double2 dy = colY[(long long)(n - c0) * T];
         const cx Dy = mk(dy.x, dy.y);
         const cx qa = mul_add(q, Dy, nx), qb = mul_add(qi, Dy, nx);
         cx an, bn;   // Eqs. 2 and 3
@@ -270,7 +297,10 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
                              (fabs(an.re) + fabs(an.im) + fabs(bn.re) + fabs(bn.im));
             const double ref = fabs(S.ext_re) + fabs(S.ext_im) + S.sca;
             small = (t < 0x1p-60 * ref) ? small + 1 : 0;
-            if (small >= 2) break;
+            if (small >= 2) {
+                done = true;
+                break;
+            }
         }
         a_prev = an;
         b_prev = bn;
@@ -278,6 +308,7 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
         psi_0 = psi_n;
         xi_m1 = xi_0;
         xi_0 = xi_n;
+    }
     }
     efficiencies(S, lam, r, n_m, inv_nm2, qe, qs, gg);
     return true;

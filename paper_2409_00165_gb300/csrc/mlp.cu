@@ -149,9 +149,9 @@ static MemberPtrs member(void* model, int k) {
 
 // ----------------------------------------------------------------------- GEMM kernel
 enum Mode {
-    FWD_HIDDEN = 0,    // Z = acc + b (fp32), H = GELU(Z) (bf16) and H^T
+    FWD_HIDDEN = 0,    // Z = acc + b; H = GELU(Z) (bf16) and H^T; GELU'(Z) (bf16)
     FWD_OUT = 2,       // softmax(acc + b) over 3 columns -> P; CE gradient G, G^T; loss
-    BWD_HIDDEN = 4,    // dZ = acc * GELU'(Z_prev) -> dZ (bf16), dZ^T
+    BWD_HIDDEN = 4,    // dZ = acc * GELU'(Z_prev) (stored by FWD_HIDDEN) -> dZ (bf16), dZ^T
     DW_PARTIAL = 5,    // partial[split] = acc (fp32)
 };
 
@@ -165,8 +165,10 @@ struct GemmArgs {
     int ldh;
     bf16* out_t;           // H^T | G^T | dZ^T  [N][ldt]
     int ldt;
-    const float* aux;      // Z_prev [M][ld_aux] (BWD_HIDDEN) | targets [M][3] (FWD_OUT)
+    const float* aux;      // targets [M][3] (FWD_OUT)
     int ld_aux;
+    bf16* out_g;           // GELU'(Z) [M][ldh] (FWD_HIDDEN)
+    const bf16* aux_g;     // GELU'(Z_prev) [M][ld_aux] (BWD_HIDDEN)
     float* loss_sum;
     float inv_batch;
     unsigned* status;
@@ -183,17 +185,15 @@ __device__ __forceinline__ float tanh_fast(float x) {
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ float gelu_f(float z) {
-    const float z2 = z * z;
-    const float t = tanh_fast(z * fmaf(0.0356774081f, z2, 0.7978845608f));
-    const float hz = 0.5f * z;
-    return fmaf(hz, t, hz);
-}
-__device__ __forceinline__ float gelu_grad_f(float z) {
+// GELU and its derivative from one tanh: d/dz [z/2 (1 + t)] = (1 + t)/2 + z/2 (1 - t^2) du/dz
+// with t = tanh(u), u = sqrt(2/pi) (z + 0.044715 z^3).
+__device__ __forceinline__ void gelu_and_grad(float z, float& gel, float& grad) {
     const float z2 = z * z;
     const float t = tanh_fast(z * fmaf(0.0356774081f, z2, 0.7978845608f));
     const float dudz = fmaf(0.1070322243f, z2, 0.7978845608f);   // d/dz of the tanh argument
-    return fmaf(0.5f, 1.0f + t, 0.5f * z * (1.0f - t * t) * dudz);
+    const float hz = 0.5f * z;
+    gel = fmaf(hz, t, hz);
+    grad = fmaf(0.5f, 1.0f + t, hz * (1.0f - t * t) * dudz);
 }
 
 template <int NT>
@@ -361,21 +361,24 @@ __global__ void __launch_bounds__(128, 1)
             }
             __align__(16) bf16 hb[16];
             if (MODE == BWD_HIDDEN) {
-                const float* zp = args.aux + (long long)m * args.ld_aux + n;
+                __align__(16) bf16 gp[16];
+                const uint4* gs = reinterpret_cast<const uint4*>(args.aux_g + (long long)m * args.ld_aux + n);
+                reinterpret_cast<uint4*>(gp)[0] = gs[0];
+                reinterpret_cast<uint4*>(gp)[1] = gs[1];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) hb[i] = __float2bfloat16(v[i] * gelu_grad_f(zp[i]));
+                for (int i = 0; i < 16; ++i) hb[i] = __float2bfloat16(v[i] * __bfloat162float(gp[i]));
             } else {
-                float z[16];
+                __align__(16) bf16 gd[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) z[i] = v[i] + args.bias[n + i];
-                if (MODE == FWD_HIDDEN) {
-                    float* zd = args.out_f + (long long)m * args.ldf + n;
-#pragma unroll
-                    for (int i = 0; i < 16; i += 4)
-                        *reinterpret_cast<float4*>(zd + i) = make_float4(z[i], z[i + 1], z[i + 2], z[i + 3]);
+                for (int i = 0; i < 16; ++i) {
+                    float gel, grad;
+                    gelu_and_grad(v[i] + args.bias[n + i], gel, grad);
+                    hb[i] = __float2bfloat16(gel);
+                    gd[i] = __float2bfloat16(grad);
                 }
-#pragma unroll
-                for (int i = 0; i < 16; ++i) hb[i] = __float2bfloat16(gelu_f(z[i]));
+                uint4* gdst = reinterpret_cast<uint4*>(args.out_g + (long long)m * args.ldh + n);
+                gdst[0] = reinterpret_cast<const uint4*>(gd)[0];
+                gdst[1] = reinterpret_cast<const uint4*>(gd)[1];
             }
             uint4* hd = reinterpret_cast<uint4*>(args.out_h + (long long)m * args.ldh + n);
             hd[0] = reinterpret_cast<const uint4*>(hb)[0];
@@ -970,37 +973,48 @@ struct SchedOut {
     float lr, c1, c2;     // learning rate; 1 - b1^t, 1 - b2^t
 };
 
+// Device schedule of graph-captured training: the member's step counter, where the
+// schedule of the step goes, and the schedule's parameters.
+struct DevSched {
+    int* step_ctr;
+    SchedOut* out;
+    float lr_max, lr_min;
+    int origin, total;
+};
+
 // Cosine schedule lr_min + (lr_max - lr_min)(1 + cos(pi min(g - origin, total) / total))/2
-// and Adam's bias corrections at t = g + 1, from the member's device step counter, which
-// then advances.
-__global__ void sched_kernel(int* step_ctr, SchedOut* out, float lr_max, float lr_min,
-                             int origin, int total) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int g = *step_ctr;
-    double gs = (double)max(g - origin, 0);
-    if (gs > (double)total) gs = (double)total;
-    const double lr = (double)lr_min + 0.5 * ((double)lr_max - (double)lr_min) *
-                                           (1.0 + cos(M_PI * gs / (double)total));
+// and Adam's bias corrections at t = g + 1, from the member's step counter g.
+__device__ __forceinline__ SchedOut schedule_of(const DevSched& d, int g) {
+    double gs = (double)max(g - d.origin, 0);
+    if (gs > (double)d.total) gs = (double)d.total;
+    const double lr = (double)d.lr_min + 0.5 * ((double)d.lr_max - (double)d.lr_min) *
+                                             (1.0 + cos(M_PI * gs / (double)d.total));
     const double t = (double)g + 1.0;
     SchedOut o;
     o.step = (unsigned)g;
     o.lr = (float)lr;
     o.c1 = (float)(1.0 - pow(0.9, t));
     o.c2 = (float)(1.0 - pow(0.999, t));
-    *out = o;
-    *step_ctr = g + 1;
+    return o;
 }
 
 __global__ void set_step_kernel(int* step_ctr, int value) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *step_ctr = value;
 }
 
+// With a device schedule (ds.step_ctr non-NULL) the step is the member's step counter, and
+// thread 0 also writes the step's schedule for Adam (the counter advances in the bias
+// gradient kernel, after every thread here has read it).
 __global__ void gather_kernel(const float* feat, const float* targets, long long n_rows, int B,
                               unsigned seed, unsigned step, const int* rows, const float* stats,
-                              bf16* X0, bf16* X0T, float* Y, const SchedOut* sched) {
+                              bf16* X0, bf16* X0T, float* Y, DevSched ds) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ds.step_ctr) {
+        const int g = *ds.step_ctr;
+        step = (unsigned)g;
+        if (b == 0) *ds.out = schedule_of(ds, g);
+    }
     if (b >= B) return;
-    if (sched) step = sched->step;
     long long src;
     if (rows) {
         src = rows[b];
@@ -1030,9 +1044,12 @@ struct ColsumArgs {
     int ld[N_LAYERS];
     float* part[N_LAYERS];
     int rows;
+    int* step_ctr;   // device schedule: advanced here (NULL: none)
 };
 __global__ void colsum_layers_kernel(ColsumArgs A) {
     __shared__ float ph[4][64];
+    if (A.step_ctr && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
+        *A.step_ctr += 1;
     const int l = blockIdx.z;
     const int ncols = real_out(l), rows = A.rows, ld = A.ld[l];
     if ((int)blockIdx.x * 64 >= ncols) return;   // the whole block: no column of this layer
@@ -1324,7 +1341,8 @@ struct TrainWs {
     void* mem = nullptr;
     size_t bytes = 0;
     bf16 *X0, *X0T, *H[4], *HT[4], *G4, *G4T, *dZ[4], *dZT[4];
-    float *Z[4], *P, *Y, *part[N_LAYERS], *colpart[N_LAYERS], *loss;
+    bf16* Gp[4];   // GELU'(Z_l) of the hidden layers
+    float *P, *Y, *part[N_LAYERS], *colpart[N_LAYERS], *loss;
     SchedOut* sched;
 };
 // One training workspace per device and member slot (member mod TRAIN_SLOTS), so that
@@ -1342,7 +1360,9 @@ static fos_status ensure_train_ws(int dev, int slot, int B, Workspace* ws = null
         cudaFree(w.mem);
         w.mem = nullptr;
     }
-    const int splits = B / 256 > 0 ? (B / 256 < 32 ? B / 256 : 32) : 1;
+    // split-K of the weight gradients: K = B / splits rows each (>= 512 for B >= 4096),
+    // fewer partials for Adam to read
+    const int splits = B >= 8192 ? 16 : (B / 256 > 0 ? (B / 256 < 16 ? B / 256 : 16) : 1);
     size_t o = 0;
     auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
     struct Item { void** p; size_t bytes; };
@@ -1351,7 +1371,7 @@ static fos_status ensure_train_ws(int dev, int slot, int B, Workspace* ws = null
     add((void**)&w.X0, (size_t)B * IN_PAD * 2);
     add((void**)&w.X0T, (size_t)IN_PAD * B * 2);
     for (int l = 0; l < 4; ++l) {
-        add((void**)&w.Z[l], (size_t)B * HID * 4);
+        add((void**)&w.Gp[l], (size_t)B * HID * 2);
         add((void**)&w.H[l], (size_t)B * HID * 2);
         add((void**)&w.HT[l], (size_t)HID * B * 2);
     }
@@ -1418,13 +1438,16 @@ static GemmArgs gargs(unsigned* status) {
 static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, const float* feat,
                              const float* targets, long long n_rows, int B, unsigned seed,
                              unsigned step, const int* rows, float lr, float* grad_out,
-                             cudaStream_t s, const SchedOut* sched = nullptr) {
+                             cudaStream_t s, const DevSched* ds = nullptr) {
     TrainWs& w = g_tws[ws->device][slot];
     unsigned* status = ws->status + ST_WORDS * (1 + slot);   // this slot's status region
     const int splits = w.splits;
+    DevSched dsv;
+    std::memset(&dsv, 0, sizeof(dsv));
+    if (ds) dsv = *ds;
     FOS_CUDA_TRY(cudaMemsetAsync(w.loss, 0, 4, s));
     gather_kernel<<<(B + 255) / 256, 256, 0, s>>>(feat, targets, n_rows, B, seed, step, rows,
-                                                  mp.stats, w.X0, w.X0T, w.Y, sched);
+                                                  mp.stats, w.X0, w.X0T, w.Y, dsv);
     FOS_CUDA_TRY(cudaGetLastError());
     const float* bias[N_LAYERS];
     const bf16* wb[N_LAYERS];
@@ -1441,7 +1464,7 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
         Operand Bm{wb[l], HID, lay_in(l), lay_in(l)};
         GemmArgs g = gargs(status);
         g.M = B; g.N = HID; g.bias = bias[l];
-        g.out_f = w.Z[l]; g.ldf = HID; g.out_h = w.H[l]; g.ldh = HID; g.out_t = w.HT[l]; g.ldt = B;
+        g.out_g = w.Gp[l]; g.out_h = w.H[l]; g.ldh = HID; g.out_t = w.HT[l]; g.ldt = B;
         st = gemm<128, FWD_HIDDEN>(A, Bm, 1, g, s);
         if (st != FOS_OK) return st;
     }
@@ -1459,6 +1482,7 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
     int gcols = OUT_PAD;
     ColsumArgs ca;
     ca.rows = B;
+    ca.step_ctr = dsv.step_ctr;
     for (int l = 4; l >= 0; --l) {
         // the bias gradient's column sums wait for one launch after the loop
         ca.G[l] = Gcur;
@@ -1482,7 +1506,7 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
             Operand A{Gcur, B, lay_out(l), gcols};
             Operand Bm{wt[l], HID, lay_out(l), lay_out(l)};
             GemmArgs g = gargs(status);
-            g.M = B; g.N = HID; g.aux = w.Z[l - 1]; g.ld_aux = HID;
+            g.M = B; g.N = HID; g.aux_g = w.Gp[l - 1]; g.ld_aux = HID;
             g.out_h = dz; g.ldh = HID; g.out_t = dzt; g.ldt = B;
             st = gemm<128, BWD_HIDDEN>(A, Bm, 1, g, s);
             if (st != FOS_OK) return st;
@@ -1511,7 +1535,7 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
     const double t = (double)step + 1.0;
     a.c1 = (float)(1.0 - pow(0.9, t));
     a.c2 = (float)(1.0 - pow(0.999, t));
-    a.sched = sched;
+    a.sched = dsv.out;
     adam_kernel<<<(unsigned)((LAY.P + 255) / 256), 256, 0, s>>>(a, LAY.P);
     return from_cuda(cudaGetLastError());
 }
@@ -1571,11 +1595,10 @@ static fos_status enqueue_fit_step(Workspace* ws, const FitKey& k, cudaStream_t 
         FOS_CUDA_TRY(cudaMemsetAsync(ws->status + ST_WORDS * region + ST_CALL, 0,
                                      sizeof(unsigned), s));
         MemberPtrs mp = member(k.model, m);
-        sched_kernel<<<1, 32, 0, s>>>(mp.step, w.sched, k.lr_max, k.lr_min, k.origin, k.total);
-        FOS_CUDA_TRY(cudaGetLastError());
+        const DevSched ds{mp.step, w.sched, k.lr_max, k.lr_min, k.origin, k.total};
         const unsigned seed = (unsigned)(k.seed ^ (k.seed >> 32)) ^ (unsigned)(m * 0x9E3779B9u);
         fos_status st = train_step(ws, slot, mp, k.feat, k.targets, k.n_rows, k.B, seed, 0,
-                                   nullptr, 1.0f, nullptr, s, w.sched);
+                                   nullptr, 1.0f, nullptr, s, &ds);
         if (st != FOS_OK) return st;
         if (k.loss_out)
             FOS_CUDA_TRY(cudaMemcpyAsync(k.loss_out + m, w.loss, sizeof(float),

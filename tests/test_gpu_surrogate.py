@@ -16,19 +16,25 @@ torch = pytest.importorskip("torch")
 
 
 def test_surrogate_gains_over_monte_carlo():
-    f, y, info = S.training_set(n_designs=4000, wl_per_block=24, blocks=10, photons=10000,
-                                seed=11)
+    """4 members trained on 96,000 Monte Carlo rows at 3e4 photons; the sweep's ensemble
+    spread threshold is the 0.01 target, so the rows the ensemble is unsure about go to
+    Monte Carlo.  Every audited row (against Monte Carlo at 1e5 photons, whose own noise
+    is up to about 0.002) is within 0.01 in R, A and T, and so are the worst 64 audited
+    rows against Monte Carlo at 1e6 photons."""
+    f, y, info = S.training_set(n_designs=4000, wl_per_block=24, blocks=10, photons=30000,
+                                seed=11, log_share=0.5)
     assert info["rows"] == f.shape[0] == 96000
     assert torch.all(torch.abs(y.sum(dim=1) - 1) < 1e-5)
-    sur = S.Surrogate(2, S.Surrogate.stats_of(f), seed=3)
-    hist = sur.fit(f, y, steps=2500, batch=8192, lr=2e-3, log_every=500)
+    sur = S.Surrogate(4, S.Surrogate.stats_of(f), seed=3)
+    hist = sur.fit(f, y, steps=4000, batch=8192, lr=2e-3, log_every=500)
     for k, h in hist.items():
         assert h[-1][1] < 0.7 * h[0][1]
-    r = S.sweep(sur, n_designs=2000, n_wl=300, seed=12, threshold=0.02, audit_frac=0.01)
+    r = S.sweep(sur, n_designs=2000, n_wl=300, seed=12, threshold=0.01, audit_frac=0.01)
     a = r["audit"]
     assert a["rows"] == 6000
-    assert max(a["mae"]) < 0.01, a
-    assert max(a["max"]) < 0.08, a
+    assert max(a["mae"]) < 0.003, a
+    assert max(a["max"]) <= 0.01, a
+    assert max(a["refined"]["max"]) <= 0.01, a
     # the surrogate sweep (incl. Mie, features, fallback Monte Carlo) beats plain GPU Monte
     # Carlo at 1e5 photons per wavelength by well over an order of magnitude
     assert r["speedup_vs_mc"] > 50, r
