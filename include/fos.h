@@ -79,7 +79,9 @@ enum {
 
 #define FOS_MAX_LAYERS   8     /* layers per stack                                     */
 #define FOS_NCOUNT       6     /* counts per item: R, A, T, runaway, collisions, interface events */
-#define FOS_MIE_MAX_TERMS 512  /* Mie: highest order n_max + 16 the kernel supports    */
+#define FOS_MIE_MAX_TERMS 512  /* Mie: orders the scratch holds per chunk; homogeneous
+                                  spheres of any size are summed in chunks of this many
+                                  orders; core-shell spheres need n_max + 16 <= this    */
 
 const char* fos_status_string(fos_status s);
 int fos_api_version(void);
@@ -116,8 +118,10 @@ fos_status fos_sync_status(void* stream, int timeout_ms);
  *   vol_frac      [n_species]            volume fraction in [0,1); per-group sum < 1
  *   mu_s, mu_a, g [n_groups*n_wl]        outputs (overwritten)
  *   q_ext, q_sca, g_species [n_species*n_wl]  optional outputs (NULL to skip)
- * Errors: FOS_ERR_INVALID_ARG (sizes, NULL, bad values), FOS_ERR_OUT_OF_RANGE (some
- * n_max + 16 > FOS_MIE_MAX_TERMS; outputs then undefined), FOS_ERR_CUDA.
+ * The sums end early once two successive terms past |x| + 4.05 |x|^(1/3) + 2 fall below
+ * 2^-60 of the partial sums (the rest is smaller still); spheres of any size are
+ * computed (their orders in chunks of FOS_MIE_MAX_TERMS).
+ * Errors: FOS_ERR_INVALID_ARG (sizes, NULL, bad values), FOS_ERR_CUDA.
  * ------------------------------------------------------------------------------ */
 fos_status fos_mie_properties(int n_wl, const double* wl,
                               int n_groups, const double* nm_re, const double* nm_im,

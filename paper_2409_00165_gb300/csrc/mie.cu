@@ -269,46 +269,46 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
     int small = 0;
     bool done = false;
     for (int c0 = 1; c0 <= nt && !done; c0 += FOS_MIE_MAX_TERMS) {
-    const int c1 = min(nt, c0 + FOS_MIE_MAX_TERMS - 1);
-    downward_D(y, nstart, c1, colY, T, c0, c0);
-    if (c1 > n_up) downward_D(x, nstart, c1, colX, T, max(c0, n_up + 1), c0);
-    for (int n = c0; n <= c1; ++n) {
-        const double dn = (double)n;
-        const cx c = (double)(2 * n - 1) * xi_, nx = dn * xi_;
-        cx psi_n;
-        if (n <= n_up) {
-            psi_n = mul_sub(c, psi_0, psi_m1);
-        } else {
-            const double2 d = colX[(long long)(n - c0) * T];
-            psi_n = psi_0 / (mk(d.x, d.y) + nx);
-        }
-        const cx xi_n = mul_sub(c, xi_0, xi_m1);
-        // with psi_n' = psi_{n-1} - (n/x) psi_n (and the same for xi_n), q D psi_n - psi_n'
-        // = (q D + n/x) psi_n - psi_{n-1}
-        const double2 dy = colY[(long long)(n - c0) * T];
-        const cx Dy = mk(dy.x, dy.y);
-        const cx qa = mul_add(q, Dy, nx), qb = mul_add(qi, Dy, nx);
-        cx an, bn;   // Eqs. 2 and 3
-        div_pair(mul_sub(qa, psi_n, psi_0), mul_sub(qa, xi_n, xi_0), mul_sub(qb, psi_n, psi_0),
-                 mul_sub(qb, xi_n, xi_0), an, bn);
-        accumulate(S, n, nmax, an, bn, a_prev, b_prev);
-        if (n > n_w) {
-            const double t = (2.0 * dn + 1.0) *
-                             (fabs(an.re) + fabs(an.im) + fabs(bn.re) + fabs(bn.im));
-            const double ref = fabs(S.ext_re) + fabs(S.ext_im) + S.sca;
-            small = (t < 0x1p-60 * ref) ? small + 1 : 0;
-            if (small >= 2) {
-                done = true;
-                break;
+        const int c1 = min(nt, c0 + FOS_MIE_MAX_TERMS - 1);
+        downward_D(y, nstart, c1, colY, T, c0, c0);
+        if (c1 > n_up) downward_D(x, nstart, c1, colX, T, max(c0, n_up + 1), c0);
+        for (int n = c0; n <= c1; ++n) {
+            const double dn = (double)n;
+            const cx c = (double)(2 * n - 1) * xi_, nx = dn * xi_;
+            cx psi_n;
+            if (n <= n_up) {
+                psi_n = mul_sub(c, psi_0, psi_m1);
+            } else {
+                const double2 d = colX[(long long)(n - c0) * T];
+                psi_n = psi_0 / (mk(d.x, d.y) + nx);
             }
+            const cx xi_n = mul_sub(c, xi_0, xi_m1);
+            // with psi_n' = psi_{n-1} - (n/x) psi_n (and the same for xi_n), q D psi_n - psi_n'
+            // = (q D + n/x) psi_n - psi_{n-1}
+            const double2 dy = colY[(long long)(n - c0) * T];
+            const cx Dy = mk(dy.x, dy.y);
+            const cx qa = mul_add(q, Dy, nx), qb = mul_add(qi, Dy, nx);
+            cx an, bn;   // Eqs. 2 and 3
+            div_pair(mul_sub(qa, psi_n, psi_0), mul_sub(qa, xi_n, xi_0), mul_sub(qb, psi_n, psi_0),
+                     mul_sub(qb, xi_n, xi_0), an, bn);
+            accumulate(S, n, nmax, an, bn, a_prev, b_prev);
+            if (n > n_w) {
+                const double t = (2.0 * dn + 1.0) *
+                                 (fabs(an.re) + fabs(an.im) + fabs(bn.re) + fabs(bn.im));
+                const double ref = fabs(S.ext_re) + fabs(S.ext_im) + S.sca;
+                small = (t < 0x1p-60 * ref) ? small + 1 : 0;
+                if (small >= 2) {
+                    done = true;
+                    break;
+                }
+            }
+            a_prev = an;
+            b_prev = bn;
+            psi_m1 = psi_0;
+            psi_0 = psi_n;
+            xi_m1 = xi_0;
+            xi_0 = xi_n;
         }
-        a_prev = an;
-        b_prev = bn;
-        psi_m1 = psi_0;
-        psi_0 = psi_n;
-        xi_m1 = xi_0;
-        xi_0 = xi_n;
-    }
     }
     efficiencies(S, lam, r, n_m, inv_nm2, qe, qs, gg);
     return true;

@@ -59,15 +59,34 @@ def test_edge_sizes_and_indices(orc):
 
 
 def test_host_at_zero_of_psi0(orc):
-    """x = 240 pi (r = 60, lambda = 0.5, n_m = 1): psi_0(x) = sin x = 0."""
-    m = dict(wl=np.array([0.5]), nm=np.array([[1.0 + 0j]]), n_groups=1,
-             species_group=np.array([0], np.int32), n_p=np.array([[1.5 + 0.01j]]),
-             radius=np.array([60.0]), vol_frac=np.array([0.1]))
-    with pytest.raises(fos.FosError):
-        gpu_mie(m)   # n_max + 16 > FOS_MIE_MAX_TERMS: reported, not computed
-    m["radius"] = np.array([10.0])  # x = 40 pi: sin x = 0 again, n_max = 215 in range
+    """x = 240 pi (r = 60, lambda = 0.5, n_m = 1): psi_0(x) = sin x = 0, and n_max = 1178,
+    summed in three chunks of the scratch's 512 orders; x = 40 pi (r = 10): one chunk."""
+    for r in (60.0, 10.0):
+        m = dict(wl=np.array([0.5]), nm=np.array([[1.0 + 0j]]), n_groups=1,
+                 species_group=np.array([0], np.int32), n_p=np.array([[1.5 + 0.01j]]),
+                 radius=np.array([r]), vol_frac=np.array([0.1]))
+        g, o = gpu_mie(m), _oracle(orc, m)
+        for k in ("q_ext", "q_sca", "g_species"):
+            ok = "g_sp" if k == "g_species" else k
+            assert _close(g[k], o[ok], rtol=1e-9), (r, k)
+
+
+def test_large_spheres_any_size(orc):
+    """Spheres whose n_max exceeds the scratch (FOS_MIE_MAX_TERMS orders per chunk): the
+    paint-layer particle at r = 20 um (n_max 680) and r = 60 um (1945) over the wavelength
+    grid's ends, absorbing and not, in the paint matrix."""
+    wl = np.array([0.3, 0.5, 2.5])
+    radius = np.array([20.0, 60.0])
+    n_p = np.array([[2.5 + 0.5j, 2.6 + 1e-4j, 2.508 + 1e-4j]] * 2)
+    nm = np.array([[1.48 + 3e-6j, 1.48 + 5e-6j, 1.48 + 2.5e-5j]])
+    m = dict(wl=wl, nm=nm, n_groups=1, species_group=np.array([0, 0], np.int32), n_p=n_p,
+             radius=radius, vol_frac=np.array([0.05, 0.05]))
     g, o = gpu_mie(m), _oracle(orc, m)
-    assert _close(g["q_ext"], o["q_ext"], rtol=1e-9)
+    for k in ("q_ext", "q_sca", "g_species"):
+        ok = "g_sp" if k == "g_species" else k
+        assert _close(g[k], o[ok], rtol=1e-9), k
+    for k in ("mu_s", "mu_a", "g"):
+        assert _close(g[k], o[k], rtol=1e-9), k
 
 
 def test_invalid_and_injected():
