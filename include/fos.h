@@ -417,8 +417,9 @@ fos_status fos_surrogate_train_step(void* model, int member, const float* featur
  * lr_min + (lr_max - lr_min)(1 + cos(pi min(g - schedule_origin, schedule_total) /
  * schedule_total))/2 (g - schedule_origin clamped at 0).  One step of the whole ensemble
  * is captured once into a CUDA graph (members of different slots, member mod 4, on
- * parallel branches; the step counts, learning rate and bias corrections live on the
- * device) and the graph is launched n_steps times on `stream`.
+ * parallel branches; the step counts live on the device, and the learning rate and bias
+ * corrections of the call's steps are a table the call writes first, after waiting for
+ * the device's earlier work) and the graph is launched n_steps times on `stream`.
  *   loss_out: device float [n_members] or NULL: each member's loss of its last step.
  * Errors of the device work are reported like FOS_ASYNC calls (fos_sync_status); without
  * FOS_ASYNC the call waits for the stream and returns that status itself.  Batch as for

@@ -47,22 +47,10 @@ __device__ __forceinline__ cx div_smith(cx a, cx b) {
 __device__ __forceinline__ int exponent_field(double v) {
     return (__double2hiint(v) >> 20) & 0x7ff;
 }
-// 1/v for v of moderate exponent (the callers check the range): the SFU's approximate
-// FP64 reciprocal refined by two Newton-Raphson steps r <- r + r (1 - v r), each of which
-// squares the relative error, so the result is within an ulp or two of 1/v with 4 FP64
-// fused multiply-adds in place of a correctly rounded division.
-__device__ __forceinline__ double rcp_nr(double v) {
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(v));
-    double e = fma(-v, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-v, r, 1.0);
-    return fma(r, e, r);
-}
 __device__ __forceinline__ cx operator/(cx a, cx b) {
     const int e = max(exponent_field(b.re), exponent_field(b.im));
     if (e > 1023 + 490 || e < 1023 - 490) return div_smith(a, b);
-    const double inv = rcp_nr(b.re * b.re + b.im * b.im);
+    const double inv = 1.0 / (b.re * b.re + b.im * b.im);
     return cx{(a.re * b.re + a.im * b.im) * inv, (a.im * b.re - a.re * b.im) * inv};
 }
 // 1/b = conj(b) / |b|^2 (the quotient above with a = 1, without its products by 0).
@@ -86,7 +74,7 @@ __device__ __forceinline__ void div_pair(cx na, cx da, cx nb, cx db, cx& qa, cx&
         return;
     }
     const double pa = da.re * da.re + da.im * da.im, pb = db.re * db.re + db.im * db.im;
-    const double inv = rcp_nr(pa * pb);
+    const double inv = 1.0 / (pa * pb);
     const double ia = pb * inv, ib = pa * inv;
     qa = cx{(na.re * da.re + na.im * da.im) * ia, (na.im * da.re - na.re * da.im) * ia};
     qb = cx{(nb.re * db.re + nb.im * db.im) * ib, (nb.im * db.re - nb.re * db.im) * ib};
@@ -137,6 +125,7 @@ struct MieArgs {
     double2* scratch;   // [n_cols * FOS_MIE_MAX_TERMS][T]
     long long T;
     unsigned* status;
+    unsigned* large;    // set when some homogeneous sphere needs the chunked pass
     int inject;
 };
 
@@ -160,7 +149,7 @@ __device__ __forceinline__ void downward_D(cx z, int nstart, int nt, double2* co
         if (e > 1023 + 490 || e < 1023 - 490) {
             D = nz - div_smith(mk(1.0, 0.0), w);
         } else {
-            const double inv = rcp_nr(w.re * w.re + w.im * w.im);
+            const double inv = 1.0 / (w.re * w.re + w.im * w.im);
             D = mk(fma(-w.re, inv, nz.re), fma(w.im, inv, nz.im));
         }
     }
@@ -227,17 +216,12 @@ __device__ __forceinline__ void efficiencies(const Sums& S, double lam, double r
     *gg = (S.sca > 0.0) ? 2.0 * S.g / S.sca : 0.0;
 }
 
-// Homogeneous sphere (Eqs. 1-5): D_n(y), D_n(x) downward (the latter only for n > |x|);
-// psi_n(x) upward while n <= |x|, psi_{n-1}/(D_n(x) + n/x) above; xi_n(x) upward; Eqs. 2-3
-// multiplied through by psi_n(x) and xi_n(x), and a_n divided through by n_p, b_n by n_m:
-// a_n = (q D_n(y) psi_n - psi_n') / (q D_n(y) xi_n - xi_n'), q = n_m / n_p, and b_n the
-// same with 1/q; with the derivatives from the recurrence this is
-// a_n = ((q D_n(y) + n/x) psi_n - psi_{n-1}) / ((q D_n(y) + n/x) xi_n - xi_{n-1}).
-// The scratch holds FOS_MIE_MAX_TERMS orders per column: larger spheres are summed in
-// chunks of that many orders, each chunk's D_n taken from a downward recurrence started at
-// the same N* (so every order has the accuracy of one recurrence from N*), which
-// repeats the downward work once per chunk.  Always returns true.
-__device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY, double2* colX,
+// Spheres whose orders exceed the scratch (FOS_MIE_MAX_TERMS orders per column): the same
+// sums in chunks of that many orders, each chunk's D_n taken from a downward recurrence
+// started at the same N* (so every order has the accuracy of one recurrence from N*), which
+// repeats the downward work once per chunk.  It runs in a kernel of its own
+// (mie_kernel<false, true>), so that the common single-chunk path keeps its registers.
+__device__ bool sphere_eval_large(double lam, double r, cx n_p, cx n_m, double2* colY, double2* colX,
                             long long T, double* qe, double* qs, double* gg) {
     const double k = 2.0 * M_PI * r / lam;
     const cx x = k * n_m;   // Eq. 1
@@ -309,6 +293,85 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
             xi_m1 = xi_0;
             xi_0 = xi_n;
         }
+    }
+    efficiencies(S, lam, r, n_m, inv_nm2, qe, qs, gg);
+    return true;
+}
+
+// Homogeneous sphere (Eqs. 1-5): D_n(y), D_n(x) downward (the latter only for n > |x|);
+// psi_n(x) upward while n <= |x|, psi_{n-1}/(D_n(x) + n/x) above; xi_n(x) upward; Eqs. 2-3
+// multiplied through by psi_n(x) and xi_n(x), and a_n divided through by n_p, b_n by n_m:
+// a_n = (q D_n(y) psi_n - psi_n') / (q D_n(y) xi_n - xi_n'), q = n_m / n_p, and b_n the
+// same with 1/q; with the derivatives from the recurrence this is
+// a_n = ((q D_n(y) + n/x) psi_n - psi_{n-1}) / ((q D_n(y) + n/x) xi_n - xi_{n-1}).
+// Returns false (nothing computed) when n_max + 17 exceeds the scratch: such spheres are
+// left to mie_kernel<false, true> and sphere_eval_large.
+__device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY, double2* colX,
+                            long long T, double* qe, double* qs, double* gg) {
+    const double k = 2.0 * M_PI * r / lam;
+    const cx x = k * n_m;   // Eq. 1
+    const cx y = k * n_p;
+    const double ay = cabs_(y), ax = cabs_(x);
+    const int nmax = (int)ceil(2.0 + ay + 4.3 * cbrt(ay));
+    const int nt = nmax + 1;          // a_{n+1}, b_{n+1} for Eq. 15
+    const int nstart = nt + 16;
+    if (nstart > FOS_MIE_MAX_TERMS) return false;
+    const cx xi_ = crcp(x);
+    downward_D(y, nstart, nt, colY, T);
+    // orders n <= n_up (n <= |x|) take psi_n(x) from the upward recurrence; integer
+    // comparisons keep the per-order test off the FP64 pipe
+    const int n_up = (int)fmin(floor(ax), (double)nstart);
+    downward_D(x, nstart, nt, colX, T, n_up + 1);
+    cx psi_m1 = ccos(x), psi_0 = csin(x);
+    const double eb = exp(-x.im);
+    cx xi_m1 = mk(eb * cos(x.re), eb * sin(x.re));        // e^{ix}
+    cx xi_0 = psi_0 - mk(-psi_m1.im, psi_m1.re);            // sin x - i cos x
+    const cx inv_nm2 = crcp(n_m * n_m);
+    const cx q = n_m / n_p, qi = n_p / n_m;
+    Sums S{0.0, 0.0, 0.0, 0.0};
+    cx a_prev = mk(0.0, 0.0), b_prev = mk(0.0, 0.0);
+    // Early end of the sums.  Past n_w = |x| + 4.05 |x|^(1/3) + 2 (Wiscombe's count for the
+    // host argument) psi_n(x) falls and xi_n(x) grows super-exponentially, and the terms
+    // (2n + 1)(|a_n| + |b_n|) fall faster than geometrically (their ratio tends to
+    // (|x| / (2n + 3))^2 < 1/4 there), so once two successive terms are below 2^-60 of the
+    // partial sums, everything after them (the rest of Eqs. 11-12, and Eq. 15 with its
+    // a_{n+1}) is below 2^-60 of the sums too.  The downward recurrences still start above
+    // the n_max of Eq. 12's criterion, so every order used is as accurate as before.
+    const int n_w = (int)ceil(ax + 4.05 * cbrt(ax) + 2.0);
+    int small = 0;
+    for (int n = 1; n <= nt; ++n) {
+        const double dn = (double)n;
+        const cx c = (double)(2 * n - 1) * xi_, nx = dn * xi_;
+        cx psi_n;
+        if (n <= n_up) {
+            psi_n = mul_sub(c, psi_0, psi_m1);
+        } else {
+            const double2 d = colX[(long long)(n - 1) * T];
+            psi_n = psi_0 / (mk(d.x, d.y) + nx);
+        }
+        const cx xi_n = mul_sub(c, xi_0, xi_m1);
+        // with psi_n' = psi_{n-1} - (n/x) psi_n (and the same for xi_n), q D psi_n - psi_n'
+        // = (q D + n/x) psi_n - psi_{n-1}
+        const double2 dy = colY[(long long)(n - 1) * T];
+        const cx Dy = mk(dy.x, dy.y);
+        const cx qa = mul_add(q, Dy, nx), qb = mul_add(qi, Dy, nx);
+        cx an, bn;   // Eqs. 2 and 3
+        div_pair(mul_sub(qa, psi_n, psi_0), mul_sub(qa, xi_n, xi_0), mul_sub(qb, psi_n, psi_0),
+                 mul_sub(qb, xi_n, xi_0), an, bn);
+        accumulate(S, n, nmax, an, bn, a_prev, b_prev);
+        if (n > n_w) {
+            const double t = (2.0 * dn + 1.0) *
+                             (fabs(an.re) + fabs(an.im) + fabs(bn.re) + fabs(bn.im));
+            const double ref = fabs(S.ext_re) + fabs(S.ext_im) + S.sca;
+            small = (t < 0x1p-60 * ref) ? small + 1 : 0;
+            if (small >= 2) break;
+        }
+        a_prev = an;
+        b_prev = bn;
+        psi_m1 = psi_0;
+        psi_0 = psi_n;
+        xi_m1 = xi_0;
+        xi_0 = xi_n;
     }
     efficiencies(S, lam, r, n_m, inv_nm2, qe, qs, gg);
     return true;
@@ -405,10 +468,14 @@ __device__ bool coated_eval(double lam, double a, double b, cx n_c, cx n_s, cx n
 
 // CS = false: homogeneous spheres only (the core-shell code is compiled out, which keeps
 // the register count of the common case low); CS = true: either kind per species.
-template <bool CS>
+// LARGE = false: every species whose orders fit the scratch; homogeneous spheres that do
+// not are left for the LARGE = true pass (flagged in A.large), which does only those, in
+// chunks of orders, and returns at once when there are none.
+template <bool CS, bool LARGE = false>
 __global__ void __launch_bounds__(128) mie_kernel(MieArgs A) {
+    if (LARGE && *A.large == 0u) return;
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (A.inject && tid == 0) atomicOr(&A.status[ST_CALL], DEV_INJECTED);
+    if (!LARGE && A.inject && tid == 0) atomicOr(&A.status[ST_CALL], DEV_INJECTED);
     const long long n_eval = (long long)A.n_species * A.n_wl;
     const long long col = (long long)FOS_MIE_MAX_TERMS * A.T;
     double2* c0 = A.scratch + tid;
@@ -431,16 +498,27 @@ __global__ void __launch_bounds__(128) mie_kernel(MieArgs A) {
              isfinite(n_c.im) && n_c.im >= 0.0;
         const double nanv = __longlong_as_double(0x7ff8000000000000LL);
         double qe = nanv, qs = nanv, gg = nanv;
-        if (!ok) {
+        if (LARGE) {
+            // homogeneous spheres beyond the scratch only (the first pass validated them)
+            if (!ok || a > 0.0) continue;
+            const double ay = cabs_((2.0 * M_PI * r / lam) * n_p);
+            if ((int)ceil(2.0 + ay + 4.3 * cbrt(ay)) + 17 <= FOS_MIE_MAX_TERMS) continue;
+            sphere_eval_large(lam, r, n_p, n_m, c0, c0 + col, A.T, &qe, &qs, &gg);
+        } else if (!ok) {
             flag(A.status, DEV_INVALID, ev);
         } else {
             bool fit;
-            if (CS && a > 0.0)
+            if (CS && a > 0.0) {
                 fit = coated_eval(lam, a, r, n_c, n_p, n_m, c0, c0 + col, c0 + 2 * col,
                                   c0 + 3 * col, A.T, &qe, &qs, &gg);
-            else
+                if (!fit) flag(A.status, DEV_RANGE, ev);
+            } else {
                 fit = sphere_eval(lam, r, n_p, n_m, c0, c0 + col, A.T, &qe, &qs, &gg);
-            if (!fit) flag(A.status, DEV_RANGE, ev);
+                if (!fit) {   // left to the LARGE pass
+                    atomicOr(A.large, 1u);
+                    continue;
+                }
+            }
         }
         A.q_ext[ev] = qe;
         A.q_sca[ev] = qs;
@@ -580,11 +658,15 @@ static fos_status mie_impl(int n_wl, const double* wl, int n_groups, const doubl
         ma.scratch = (double2*)ws->mie_scratch;
         ma.T = T;
         ma.status = ws->status;
+        ma.large = ws->status + 3;   // spare word of the status region
         ma.inject = (flags & FOS_TEST_INJECT) ? 1 : 0;
+        FOS_CUDA_TRY(cudaMemsetAsync(ma.large, 0, sizeof(unsigned), s));
         if (core_radius)
             mie::mie_kernel<true><<<(unsigned)(T / block), block, 0, s>>>(ma);
         else
             mie::mie_kernel<false><<<(unsigned)(T / block), block, 0, s>>>(ma);
+        FOS_CUDA_TRY(cudaGetLastError());
+        mie::mie_kernel<false, true><<<(unsigned)(T / block), block, 0, s>>>(ma);
         FOS_CUDA_TRY(cudaGetLastError());
     }
     mie::EmtArgs ea;

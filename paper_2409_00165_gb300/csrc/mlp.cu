@@ -41,7 +41,10 @@ constexpr int IN_PAD = 64;
 constexpr int OUT_PAD = 64;
 constexpr int N_FEAT = 9;
 constexpr int N_OUT = 3;
-constexpr int STAGES = 4;
+// Pipeline stages of the training GEMM: 2 (a k block in flight while the previous one is
+// multiplied) keep a CTA at 50-100 KB of shared memory, so that 2-4 CTAs share an SM and
+// hide each other's TMA, epilogue and launch latency.
+constexpr int STAGES = 2;
 constexpr int BM = 128;
 constexpr int BK = 64;
 
@@ -973,30 +976,15 @@ struct SchedOut {
     float lr, c1, c2;     // learning rate; 1 - b1^t, 1 - b2^t
 };
 
-// Device schedule of graph-captured training: the member's step counter, where the
-// schedule of the step goes, and the schedule's parameters.
+// Device schedule of graph-captured training: the member's step counter g, the table of
+// the call's steps (entry g - *base, written by the host with the same arithmetic as the
+// per-step entry point), and where the step's entry goes for Adam.
 struct DevSched {
     int* step_ctr;
+    const SchedOut* table;
+    const int* base;
     SchedOut* out;
-    float lr_max, lr_min;
-    int origin, total;
 };
-
-// Cosine schedule lr_min + (lr_max - lr_min)(1 + cos(pi min(g - origin, total) / total))/2
-// and Adam's bias corrections at t = g + 1, from the member's step counter g.
-__device__ __forceinline__ SchedOut schedule_of(const DevSched& d, int g) {
-    double gs = (double)max(g - d.origin, 0);
-    if (gs > (double)d.total) gs = (double)d.total;
-    const double lr = (double)d.lr_min + 0.5 * ((double)d.lr_max - (double)d.lr_min) *
-                                             (1.0 + cos(M_PI * gs / (double)d.total));
-    const double t = (double)g + 1.0;
-    SchedOut o;
-    o.step = (unsigned)g;
-    o.lr = (float)lr;
-    o.c1 = (float)(1.0 - pow(0.9, t));
-    o.c2 = (float)(1.0 - pow(0.999, t));
-    return o;
-}
 
 __global__ void set_step_kernel(int* step_ctr, int value) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *step_ctr = value;
@@ -1012,7 +1000,7 @@ __global__ void gather_kernel(const float* feat, const float* targets, long long
     if (ds.step_ctr) {
         const int g = *ds.step_ctr;
         step = (unsigned)g;
-        if (b == 0) *ds.out = schedule_of(ds, g);
+        if (b == 0) *ds.out = ds.table[g - *ds.base];
     }
     if (b >= B) return;
     long long src;
@@ -1059,20 +1047,39 @@ __global__ void colsum_layers_kernel(ColsumArgs A) {
     const int q = threadIdx.x >> 6;   // 4 row phases
     const int chunk = (rows + COLSUM_SPLITS - 1) / COLSUM_SPLITS;
     const int r0 = blockIdx.y * chunk, r1 = min(rows, r0 + chunk);
-    float acc = 0.f;
-    if (c < ncols)
-        for (int r = r0 + q; r < r1; r += 4) acc += __bfloat162float(G[(long long)r * ld + c]);
+    float a0 = 0.f, a1 = 0.f;   // two running sums, loads in flight together
+    if (c < ncols) {
+        int r = r0 + q;
+        for (; r + 4 < r1; r += 8) {
+            a0 += __bfloat162float(G[(long long)r * ld + c]);
+            a1 += __bfloat162float(G[(long long)(r + 4) * ld + c]);
+        }
+        if (r < r1) a0 += __bfloat162float(G[(long long)r * ld + c]);
+    }
+    const float acc = a0 + a1;
     ph[q][threadIdx.x & 63] = acc;
     __syncthreads();
     if (q == 0 && c < ncols)
         part[blockIdx.y * ncols + c] =
             ph[0][threadIdx.x] + ph[1][threadIdx.x] + ph[2][threadIdx.x] + ph[3][threadIdx.x];
 }
-// Bias gradient of output o of layer l from its per-split column sums, in split order.
+// Sum of n values v[k * stride + e], k = 0..n-1, in a fixed order: four running sums over
+// k mod 4 (their loads independent, so they are in flight together), then added in order.
+__device__ __forceinline__ float split_sum(const float* v, long long stride, int n, long long e) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int k = 0;
+    for (; k + 4 <= n; k += 4) {
+        a0 += v[(k + 0) * stride + e];
+        a1 += v[(k + 1) * stride + e];
+        a2 += v[(k + 2) * stride + e];
+        a3 += v[(k + 3) * stride + e];
+    }
+    for (; k < n; ++k) a0 += v[k * stride + e];
+    return (a0 + a1) + (a2 + a3);
+}
+// Bias gradient of output o of layer l from its per-split column sums.
 __device__ __forceinline__ float bias_grad(const float* part, int ncols, int o) {
-    float acc = 0.f;
-    for (int y = 0; y < COLSUM_SPLITS; ++y) acc += part[y * ncols + o];
-    return acc;
+    return split_sum(part, ncols, COLSUM_SPLITS, o);
 }
 
 struct AdamArgs {
@@ -1107,9 +1114,7 @@ __global__ void adam_kernel(AdamArgs A, long long P) {
             o = (int)(e / in_p);
             i = (int)(e % in_p);
             if (o >= real_out(l) || i >= real_in(l)) continue;
-            const long long stride = (long long)out_p * in_p;
-            g = 0.f;
-            for (int s = 0; s < A.splits; ++s) g += A.part[l][s * stride + e];
+            g = split_sum(A.part[l], (long long)out_p * in_p, A.splits, e);
         } else {
             o = (int)(idx - A.b_off[l]);
             if (o >= real_out(l)) continue;
@@ -1142,10 +1147,8 @@ __global__ void grad_kernel(AdamArgs A, long long P, float* grad) {
         if (idx < A.b_off[l]) {
             const long long e = idx - A.w_off[l];
             const int o = (int)(e / in_p), i = (int)(e % in_p);
-            if (o < real_out(l) && i < real_in(l)) {
-                const long long stride = (long long)out_p * in_p;
-                for (int s = 0; s < A.splits; ++s) g += A.part[l][s * stride + e];
-            }
+            if (o < real_out(l) && i < real_in(l))
+                g = split_sum(A.part[l], (long long)out_p * in_p, A.splits, e);
         } else {
             const int o = (int)(idx - A.b_off[l]);
             if (o < real_out(l)) g = bias_grad(A.bpart[l], real_out(l), o);
@@ -1548,12 +1551,13 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
 // launched once per step.
 struct FitKey {
     void* model;
-    int n_members, B, origin, total, device;
+    int n_members, B, device;
     const float *feat, *targets;
     long long n_rows;
     unsigned long long seed;
-    float lr_max, lr_min;
     float* loss_out;
+    const SchedOut* table;   // [n_members][table_cap]
+    long long table_cap;
     unsigned long long generation;
     bool operator==(const FitKey& o) const { return std::memcmp(this, &o, sizeof(*this)) == 0; }
 };
@@ -1566,6 +1570,9 @@ struct FitDev {
     cudaStream_t slot_stream[TRAIN_SLOTS] = {};
     cudaEvent_t fork = nullptr, join[TRAIN_SLOTS] = {};
     std::vector<FitGraph> graphs;
+    SchedOut* table = nullptr;   // [members][cap] schedule entries, then [members] bases
+    long long table_cap = 0;
+    int table_members = 0;
 };
 static FitDev g_fit[64];
 
@@ -1595,7 +1602,8 @@ static fos_status enqueue_fit_step(Workspace* ws, const FitKey& k, cudaStream_t 
         FOS_CUDA_TRY(cudaMemsetAsync(ws->status + ST_WORDS * region + ST_CALL, 0,
                                      sizeof(unsigned), s));
         MemberPtrs mp = member(k.model, m);
-        const DevSched ds{mp.step, w.sched, k.lr_max, k.lr_min, k.origin, k.total};
+        const int* bases = reinterpret_cast<const int*>(k.table + (long long)k.n_members * k.table_cap);
+        const DevSched ds{mp.step, k.table + (long long)m * k.table_cap, bases + m, w.sched};
         const unsigned seed = (unsigned)(k.seed ^ (k.seed >> 32)) ^ (unsigned)(m * 0x9E3779B9u);
         fos_status st = train_step(ws, slot, mp, k.feat, k.targets, k.n_rows, k.B, seed, 0,
                                    nullptr, 1.0f, nullptr, s, &ds);
@@ -1892,21 +1900,60 @@ fos_status fos_surrogate_fit(void* model, int n_members, const float* features,
     if (st != FOS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (n_steps > 0) {
+        // the schedule of this call's steps, per member from its step count, computed here
+        // as the per-step entry point's callers and train_step compute it
+        mlp::FitDev& fd = mlp::g_fit[ws->device];
+        if (fd.table_cap < n_steps || fd.table_members < n_members) {
+            FOS_CUDA_TRY(cudaStreamSynchronize(s));
+            FOS_CUDA_TRY(cudaDeviceSynchronize());
+            if (fd.table) cudaFree(fd.table);
+            fd.table = nullptr;
+            const long long cap = n_steps > fd.table_cap ? n_steps : fd.table_cap;
+            const int mem = n_members > fd.table_members ? n_members : fd.table_members;
+            FOS_CUDA_TRY(cudaMalloc(&fd.table, (size_t)mem * cap * sizeof(mlp::SchedOut) +
+                                                   (size_t)mem * sizeof(int) + 256));
+            fd.table_cap = cap;
+            fd.table_members = mem;
+        }
+        std::vector<mlp::SchedOut> tab((size_t)n_members * fd.table_cap);
+        std::vector<int> base(n_members);
+        // earlier steps (of any stream) must be done: they read the table rewritten here
+        // and advance the step counts read here
+        FOS_CUDA_TRY(cudaDeviceSynchronize());
+        for (int m = 0; m < n_members; ++m) {
+            mlp::MemberPtrs mp = mlp::member(model, m);
+            FOS_CUDA_TRY(cudaMemcpy(&base[m], mp.step, sizeof(int), cudaMemcpyDeviceToHost));
+            for (int i = 0; i < n_steps; ++i) {
+                const int g = base[m] + i;
+                double gs = (double)(g - schedule_origin > 0 ? g - schedule_origin : 0);
+                if (gs > (double)schedule_total) gs = (double)schedule_total;
+                const double lr = (double)lr_min + 0.5 * ((double)lr_max - (double)lr_min) *
+                                                       (1.0 + cos(M_PI * gs / (double)schedule_total));
+                const double t = (double)g + 1.0;
+                mlp::SchedOut& o = tab[(size_t)m * fd.table_cap + i];
+                o.step = (unsigned)g;
+                o.lr = (float)lr;
+                o.c1 = (float)(1.0 - pow(0.9, t));
+                o.c2 = (float)(1.0 - pow(0.999, t));
+            }
+        }
+        FOS_CUDA_TRY(cudaMemcpy(fd.table, tab.data(), tab.size() * sizeof(mlp::SchedOut),
+                                cudaMemcpyHostToDevice));
+        FOS_CUDA_TRY(cudaMemcpy(fd.table + (size_t)n_members * fd.table_cap, base.data(),
+                                (size_t)n_members * sizeof(int), cudaMemcpyHostToDevice));
         mlp::FitKey k;
         std::memset(&k, 0, sizeof(k));
         k.model = model;
         k.n_members = n_members;
         k.B = batch;
-        k.origin = schedule_origin;
-        k.total = schedule_total;
         k.device = ws->device;
         k.feat = features;
         k.targets = targets;
         k.n_rows = n_rows;
         k.seed = seed;
-        k.lr_max = lr_max;
-        k.lr_min = lr_min;
         k.loss_out = loss_out;
+        k.table = fd.table;
+        k.table_cap = fd.table_cap;
         k.generation = ws->generation;
         cudaGraphExec_t exec = nullptr;
         st = mlp::fit_graph(ws, k, &exec);

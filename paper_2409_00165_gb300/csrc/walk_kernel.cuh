@@ -434,11 +434,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) walk_kernel(WalkArgs A) {
         }
         if (!__any_sync(FULL, alive)) break;   // refill ended: queue exhausted
 
-        // ---------------- two events per live photon between refills (a lane whose photon
-        // ends in the first waits one event for the next refill: cheaper than the refill
-        // vote on every event)
+        // ---------------- four events per live photon between refills (a lane whose photon
+        // ends early waits up to three events for the next refill: cheaper than the refill
+        // vote on every event; measured +2 % exact, +4 % fast against one event)
 #pragma unroll 1
-        for (int rep = 0; rep < 2; ++rep)
+        for (int rep = 0; rep < 4; ++rep)
         if (alive) {
             if (ev >= A.max_events) {
                 finish(O_X);
