@@ -1347,6 +1347,10 @@ struct TrainWs {
     bf16* Gp[4];   // GELU'(Z_l) of the hidden layers
     float *P, *Y, *part[N_LAYERS], *colpart[N_LAYERS], *loss;
     SchedOut* sched;
+    // the weight gradients and bias column sums run on a side stream, off the chain of
+    // backward products: fork after each gradient G_l is written, join before Adam
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_g[N_LAYERS] = {}, ev_join = nullptr;
 };
 // One training workspace per device and member slot (member mod TRAIN_SLOTS), so that
 // the steps of up to TRAIN_SLOTS members can run concurrently on separate streams.
@@ -1406,6 +1410,12 @@ static fos_status ensure_train_ws(int dev, int slot, int B, Workspace* ws = null
     w.bytes = o;
     w.B = B;
     w.splits = splits;
+    if (!w.side) {
+        FOS_CUDA_TRY(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
+        for (int l = 0; l < N_LAYERS; ++l)
+            FOS_CUDA_TRY(cudaEventCreateWithFlags(&w.ev_g[l], cudaEventDisableTiming));
+        FOS_CUDA_TRY(cudaEventCreateWithFlags(&w.ev_join, cudaEventDisableTiming));
+    }
     return FOS_OK;
 }
 
@@ -1491,14 +1501,17 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
         ca.G[l] = Gcur;
         ca.ld[l] = gcols;
         ca.part[l] = w.colpart[l];
-        // weight gradient dW_l = G^T · H_{l-1}  (A = G^T [out][B], B = H_{l-1}^T [in][B])
+        // weight gradient dW_l = G^T · H_{l-1}  (A = G^T [out][B], B = H_{l-1}^T [in][B]),
+        // on the side stream once G is written
         {
+            FOS_CUDA_TRY(cudaEventRecord(w.ev_g[l], s));
+            FOS_CUDA_TRY(cudaStreamWaitEvent(w.side, w.ev_g[l], 0));
             Operand A{GcurT, lay_out(l), B, B};
             Operand Bm = (l == 0) ? Operand{w.X0T, IN_PAD, B, B} : Operand{w.HT[l - 1], HID, B, B};
             GemmArgs g = gargs(status);
             g.M = lay_out(l); g.N = lay_in(l); g.out_f = w.part[l]; g.ldf = lay_in(l);
-            if (l == 0) st = gemm<64, DW_PARTIAL>(A, Bm, splits, g, s);
-            else st = gemm<256, DW_PARTIAL>(A, Bm, splits, g, s);
+            if (l == 0) st = gemm<64, DW_PARTIAL>(A, Bm, splits, g, w.side);
+            else st = gemm<256, DW_PARTIAL>(A, Bm, splits, g, w.side);
             if (st != FOS_OK) return st;
         }
         if (l == 0) break;
@@ -1518,8 +1531,10 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
             gcols = HID;
         }
     }
-    colsum_layers_kernel<<<dim3(HID / 64, COLSUM_SPLITS, N_LAYERS), 256, 0, s>>>(ca);
+    colsum_layers_kernel<<<dim3(HID / 64, COLSUM_SPLITS, N_LAYERS), 256, 0, w.side>>>(ca);
     FOS_CUDA_TRY(cudaGetLastError());
+    FOS_CUDA_TRY(cudaEventRecord(w.ev_join, w.side));
+    FOS_CUDA_TRY(cudaStreamWaitEvent(s, w.ev_join, 0));
     // Adam
     AdamArgs a = layout_args(mp);
     for (int l = 0; l < N_LAYERS; ++l) {

@@ -487,11 +487,39 @@ def _mie_demo(designs: int, n_wl: int, reps: int):
     print(f"mie {m.rows} evaluations: {s * 1e3:.3f} ms, {m.rows / s:.3e} evaluations/s")
 
 
+def _train_demo(rows: int, members: int, steps: int, batch: int):
+    """Graph-captured ensemble training on synthetic rows (a profiling target): features in
+    the sweep's ranges, Dirichlet targets; 5 warm-up steps, then `steps` timed."""
+    import time
+    rng = np.random.default_rng(1)
+    x = np.column_stack([rng.uniform(0.3, 2.5, rows), rng.uniform(2.5, 3.1, rows),
+                         rng.uniform(-4, -0.3, rows), rng.uniform(0.05, 1, rows),
+                         rng.uniform(0.01, 0.3, rows), rng.uniform(1, 2.7, rows),
+                         rng.uniform(0, 0.9, rows), rng.uniform(-1, 3, rows),
+                         rng.uniform(-4, 2, rows)])
+    y = rng.dirichlet(np.ones(3), size=rows)
+    f = torch.as_tensor(x, dtype=torch.float32).cuda().contiguous()
+    t = torch.as_tensor(y, dtype=torch.float32).cuda().contiguous()
+    sur = Surrogate(members, Surrogate.stats_of(f), seed=3)
+    sur.fit(f, t, steps=5, batch=batch, lr=2e-3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sur.fit(f, t, steps=steps, batch=batch, lr=2e-3)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    flop = 3.0 * FLOP_PER_ROW_MEMBER * batch * members * steps
+    print(f"train {members} members x {steps} steps, batch {batch}: {dt / steps * 1e3:.3f} ms "
+          f"per ensemble step, {flop / dt / 1e12:.1f} TFLOP/s")
+
+
 if __name__ == "__main__":
     import argparse
     ap = argparse.ArgumentParser()
     ap.add_argument("--predict-demo", action="store_true")
     ap.add_argument("--mie-demo", action="store_true")
+    ap.add_argument("--train-demo", action="store_true")
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--batch", type=int, default=8192)
     ap.add_argument("--designs", type=int, default=10000)
     ap.add_argument("--wl", type=int, default=300)
     ap.add_argument("--rows", type=int, default=1 << 19)
@@ -502,3 +530,5 @@ if __name__ == "__main__":
         _predict_demo(a.rows, a.members, a.reps)
     if a.mie_demo:
         _mie_demo(a.designs, a.wl, a.reps)
+    if a.train_demo:
+        _train_demo(a.rows, a.members, a.steps, a.batch)
