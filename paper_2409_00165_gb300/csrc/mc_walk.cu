@@ -110,6 +110,15 @@ __global__ void pack_kernel(PackArgs A) {
     const double na = b.n_above ? b.n_above[it] : 1.0;
     const double nb = b.n_below ? b.n_below[it] : 1.0;
     if (!finite_pos(na) || !finite_pos(nb)) ok = false;
+    // index quotients of each layer's faces (the walk's Fresnel step at boundary events)
+    for (int j = 0; j < nl; ++j) {
+        float4* lc = &A.t.layC[(long long)r * b.max_layers + j];
+        const float nj = A.t.layA[(long long)r * b.max_layers + j].w;
+        const float n_up = (j == 0) ? (float)na : A.t.layA[(long long)r * b.max_layers + j - 1].w;
+        const float n_dn = (j == nl - 1) ? (float)nb : A.t.layA[(long long)r * b.max_layers + j + 1].w;
+        lc->z = nj / n_up;
+        lc->w = nj / n_dn;
+    }
     float rsub = -1.0f;
     if (b.substrate_R) {
         const double v = b.substrate_R[it];

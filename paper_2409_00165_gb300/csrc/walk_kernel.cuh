@@ -47,7 +47,9 @@ struct Tables {
     float4* edge;     // {entry mu_z (refraction cosine), cos incidence, k below, 0}
     float4* layA;     // [row*max_layers + j] {mu_t, absorption threshold (uint bits), g, n}
     float4* layB;     // [row*max_layers + j] {d, 1-g^2, 1+g^2, 1-g}
-    float4* layC;     // [row*max_layers + j] {1/mu_t, 1/(2g), 0, 0}
+    float4* layC;     // [row*max_layers + j] {1/mu_t, 1/(2g), n_j / n above, n_j / n below}
+                      //  (the index ratios of the layer's top and bottom faces, the same
+                      //  IEEE quotients the Fresnel step would form)
     long long* prefix;  // [n_run + 1] exclusive prefix of work units
 };
 
@@ -198,6 +200,27 @@ __device__ __forceinline__ float fresnel(float ni, float nt, float ci, float& ct
     const float rs = (a - b) / (a + b);
     const float c = ni * ct, d = nt * ci;
     const float rp = (c - d) / (c + d);
+    return (rs * rs + rp * rp) * 0.5f;
+}
+
+// The same at a layer face whose quotient ratio = ni / nt is precomputed (the walk's
+// boundary events); FAST: approximate square root and divisions.
+template <bool FAST>
+__device__ __forceinline__ float fresnel_face(float ni, float nt, float ratio, float ci,
+                                              float& ct, bool& tir) {
+    const float r2 = ratio * ratio;
+    const float st2 = r2 * fmaf(-ci, ci, 1.0f);
+    if (st2 >= 1.0f) {
+        tir = true;
+        ct = 0.0f;
+        return 1.0f;
+    }
+    tir = false;
+    ct = FAST ? sqrt_sfu(1.0f - st2) : sqrtf(1.0f - st2);
+    const float a = ni * ci, b = nt * ct;
+    const float rs = FAST ? __fdividef(a - b, a + b) : (a - b) / (a + b);
+    const float c = ni * ct, d = nt * ci;
+    const float rp = FAST ? __fdividef(c - d, c + d) : (c - d) / (c + d);
     return (rs * rs + rp * rp) * 0.5f;
 }
 
@@ -509,7 +532,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) walk_kernel(WalkArgs A) {
                 } else {
                     float ct;
                     bool tir;
-                    const float Rf = fresnel(ni, nt, fabsf(mu), ct, tir);
+                    const float2 rat = *reinterpret_cast<const float2*>(
+                        &A.t.layC[(long long)row * A.max_layers + j].z);
+                    const float Rf = fresnel_face<FAST>(ni, nt, down ? rat.y : rat.x, fabsf(mu),
+                                                        ct, tir);
                     if (tir) {
                         transmit = false;
                     } else {
