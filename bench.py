@@ -139,11 +139,18 @@ def cpu_baseline(m, seconds: float):
     per_photon = t0 / max(p0, 1)
     n = int(max(64 * cores, min(m["photons_per_item"], seconds / max(per_photon, 1e-9) / 8)))
     coll, phot, dt = oracle_sample(m, props, n, cores, wl_idx)
+    # the same oracle on one core, on a smaller sample of the same 8 wavelengths
+    per_photon_1 = dt / max(phot, 1) * cores      # one core, from the threaded run
+    n1 = int(max(64, min(n, seconds / 3.0 / max(per_photon_1, 1e-9) / 8)))
+    c1, p1, t1 = oracle_sample(m, props, n1, 1, wl_idx)
     return dict(value=coll / dt, unit=UNIT, cores=cores, kind="oracle",
                 sample=f"8 of 400 wavelengths (evenly spaced) x {n} photons each, FP32-mirror "
                        f"oracle walk, {cores} host threads sharing photon ranges; "
                        f"{coll} photon-steps in {dt:.1f} s",
-                photons_per_s=phot / dt)
+                photons_per_s=phot / dt,
+                single_core=dict(value=c1 / t1, unit=UNIT, cores=1,
+                                 sample=f"the same 8 wavelengths x {n1} photons on one thread; "
+                                        f"{c1} photon-steps in {t1:.1f} s"))
 
 
 # ------------------------------------------------------------------------ clocks
