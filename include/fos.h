@@ -298,9 +298,13 @@ fos_status fos_mc_walk_times(long long* start_end_ns, int capacity, int* n_block
  * fos_walk_math_f32: for u[i] in (0,1): neg_log[i] = -ln u, cos2pi[i] = cos(2 pi u),
  *   as the walk evaluates them (device float arrays [n]; either output may be NULL).
  * fos_walk_math_fast_f32: the same as the fast walk (FOS_FAST_WALK) evaluates them.
+ * fos_philox4x32_10_curand: the same outputs as fos_philox4x32_10, computed by cuRAND's
+ *   device Philox4x32-10 (a library routine), an independent check of the walk's generator.
  * ------------------------------------------------------------------------------ */
 fos_status fos_philox4x32_10(const unsigned* ctr, unsigned k0, unsigned k1, unsigned* out,
                              long long n, void* stream);
+fos_status fos_philox4x32_10_curand(const unsigned* ctr, unsigned k0, unsigned k1,
+                                    unsigned* out, long long n, void* stream);
 fos_status fos_walk_math_f32(const float* u, float* neg_log, float* cos2pi, long long n,
                              void* stream);
 fos_status fos_walk_math_fast_f32(const float* u, float* neg_log, float* cos2pi, long long n,

@@ -9,6 +9,8 @@
 #include <mutex>
 #include <vector>
 
+#include <curand_philox4x32_x.h>
+
 #include "walk_kernel.cuh"
 
 namespace fos {
@@ -210,6 +212,15 @@ __global__ void philox_fill_kernel(const uint4* ctr, unsigned k0, unsigned k1, u
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         out[i] = philox(ctr[i], k0, k1);
+}
+
+// The same generator as computed by cuRAND's device Philox4x32-10 (a library routine,
+// called, for the parity tests).
+__global__ void philox_curand_kernel(const uint4* ctr, unsigned k0, unsigned k1, uint4* out,
+                                     long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = curand_Philox4x32_10(ctr[i], make_uint2(k0, k1));
 }
 
 __global__ void walk_math_kernel(const float* u, float* nl, float* cs, long long n) {
@@ -661,6 +672,19 @@ fos_status fos_philox4x32_10(const unsigned* ctr, unsigned k0, unsigned k1, unsi
     if (blocks > 65535) blocks = 65535;
     mc::philox_fill_kernel<<<(unsigned)blocks, 256, 0, s>>>((const uint4*)ctr, k0, k1,
                                                             (uint4*)out, n);
+    FOS_CUDA_TRY(cudaGetLastError());
+    return from_cuda(cudaStreamSynchronize(s));
+}
+
+fos_status fos_philox4x32_10_curand(const unsigned* ctr, unsigned k0, unsigned k1,
+                                    unsigned* out, long long n, void* stream) {
+    if (n < 0 || (n > 0 && (!ctr || !out))) return FOS_ERR_INVALID_ARG;
+    if (n == 0) return FOS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    mc::philox_curand_kernel<<<(unsigned)blocks, 256, 0, s>>>((const uint4*)ctr, k0, k1,
+                                                              (uint4*)out, n);
     FOS_CUDA_TRY(cudaGetLastError());
     return from_cuda(cudaStreamSynchronize(s));
 }

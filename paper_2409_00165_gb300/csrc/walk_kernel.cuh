@@ -78,6 +78,20 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Checked build (FOS_CHECKED, `build(checked=True)`): every table index the walk forms is
+// tested; a bad one sets DEV_RANGE with the check's code (0xF0000000 | code) in the
+// status word's index field, and the access is skipped.  No trap, no assert.  The
+// default build compiles the checks out.
+__device__ __noinline__ void walk_bad(unsigned* status, unsigned code) {
+    atomicOr(&status[ST_CALL], DEV_RANGE);
+    atomicMin(&status[ST_INDEX], 0xF0000000u | code);
+}
+#ifdef FOS_CHECKED
+#define FOS_WALK_OK(cond, code) ((cond) ? true : (walk_bad(A.status, (code)), false))
+#else
+#define FOS_WALK_OK(cond, code) true
+#endif
+
 __device__ __forceinline__ uint4 philox_rk(uint4 c, const RoundKeys& rk) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -283,7 +297,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ void warp_flush(bool want, int tag, unsigned c0, unsigned c1,
                                            unsigned c2, unsigned c3,
                                            unsigned long long c4, unsigned long long c5,
-                                           unsigned long long* counts, unsigned* status) {
+                                           unsigned long long* counts, unsigned* status,
+                                           int n_run) {
     const int lane = threadIdx.x & 31;
     unsigned m = __ballot_sync(FULL, want);
     while (m) {
@@ -301,7 +316,13 @@ __device__ __forceinline__ void warp_flush(bool want, int tag, unsigned c0, unsi
             s4 += __shfl_xor_sync(FULL, s4, off);
             s5 += __shfl_xor_sync(FULL, s5, off);
         }
+#ifdef FOS_CHECKED
+        if (lane == leader && (t < 0 || t >= n_run)) walk_bad(status, 6);
+        if (lane == leader && t >= 0 && t < n_run) {
+#else
+        (void)n_run;
         if (lane == leader) {
+#endif
             unsigned long long* c = counts + (long long)t * FOS_NCOUNT;
             if (s0) atomicAdd(c + 0, (unsigned long long)s0);
             if (s1) atomicAdd(c + 1, (unsigned long long)s1);
@@ -352,6 +373,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) walk_kernel(WalkArgs A) {
     unsigned long long cC = 0, cI = 0;
 
     auto load_layer = [&](int jj) {
+        if (!FOS_WALK_OK(jj >= 0 && jj < nl && nl <= A.max_layers && row >= 0 && row < A.n_run, 4))
+            return;
         const long long li = (long long)row * A.max_layers + jj;
         const float4 a = A.t.layA[li];
         const float4 b = A.t.layB[li];
@@ -370,7 +393,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) walk_kernel(WalkArgs A) {
         const unsigned long long coll = (unsigned long long)e + (out == O_A ? 1ull : 0ull);
         cC += coll;
         cI += (unsigned long long)ev - coll;
-        if (A.photon_log) {
+        if (A.photon_log && FOS_WALK_OK((long long)(p - p_first) < A.log_stride, 5)) {
             unsigned long long rec = (coll << 2) | (unsigned long long)out;
             if (rec > 0x7fffffffull) rec = 0x7fffffffull;
             A.photon_log[(long long)row * A.log_stride + (p - p_first)] = (int)rec;
@@ -400,12 +423,16 @@ __global__ void __launch_bounds__(BLOCK, MINB) walk_kernel(WalkArgs A) {
                 }
                 uidx = __shfl_sync(FULL, uidx, 0);
                 r = __shfl_sync(FULL, r, 0);
-                if ((long long)uidx >= total_units) {
+                if ((long long)uidx >= total_units || !FOS_WALK_OK(r >= 0 && r < A.n_run, 1)) {
                     exhausted = true;
                     break;
                 }
                 const unsigned q = (unsigned)(uidx - (unsigned long long)A.t.prefix[r]);
                 const unsigned n_eff = scaled_count((unsigned)A.t.info[r].z, A.scale);
+                if (!FOS_WALK_OK((unsigned long long)q * A.unit < (unsigned long long)n_eff, 2)) {
+                    exhausted = true;
+                    break;
+                }
                 u_row = r;
                 u_next = q * A.unit;
                 u_end = (unsigned)min((unsigned long long)u_next + A.unit,
@@ -417,7 +444,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) walk_kernel(WalkArgs A) {
             const bool mine = ((need >> lane) & 1u) && rank < avail;
             const unsigned taken = __ballot_sync(FULL, mine);
             const bool switching = mine && tag >= 0 && tag != u_row;
-            warp_flush(switching, tag, cR, cA, cT, cX, cC, cI, A.counts, A.status);
+            warp_flush(switching, tag, cR, cA, cT, cX, cC, cI, A.counts, A.status, A.n_run);
             if (mine) {
                 if (tag != u_row) {
                     tag = u_row;
@@ -559,7 +586,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) walk_kernel(WalkArgs A) {
         }
     }
     const bool have = tag >= 0 && (cR | cA | cT | cX) != 0u;
-    warp_flush(have, tag, cR, cA, cT, cX, cC, cI, A.counts, A.status);
+    warp_flush(have, tag, cR, cA, cT, cX, cC, cI, A.counts, A.status, A.n_run);
     if (A.cta_times) {
         __syncthreads();
         if (threadIdx.x == 0) A.cta_times[2 * blockIdx.x + 1] = global_ns();

@@ -67,8 +67,13 @@ class FosBatch(ctypes.Structure):
     ]
 
 
+def _checked() -> bool:
+    """FOS_CHECKED=1 selects the checked build (in-kernel index checks in the walk)."""
+    return os.environ.get("FOS_CHECKED", "") == "1"
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if _checked() else _build.LIB
 
 
 def lib():
@@ -76,7 +81,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(checked=_checked())
             if not os.path.exists(path):
                 raise RuntimeError("libfos.so is missing: the CUDA path cannot run")
             L = ctypes.CDLL(path)
@@ -293,11 +298,13 @@ def fos_sync_status(stream=None, timeout_ms: int = 0) -> int:
 
 
 # --------------------------------------------------------------------------- diagnostics
-def fos_philox4x32_10(ctr, k0: int, k1: int, out, stream=None) -> int:
+def fos_philox4x32_10(ctr, k0: int, k1: int, out, stream=None, curand: bool = False) -> int:
     n = ctr.numel() // 4
-    return lib().fos_philox4x32_10(_dev(ctr, torch.int32, "ctr"), int(k0) & 0xFFFFFFFF,
-                                   int(k1) & 0xFFFFFFFF, _dev(out, torch.int32, "out"), n,
-                                   _stream(stream))
+    fn = (_sfn("fos_philox4x32_10_curand", [ctypes.c_void_p, ctypes.c_uint, ctypes.c_uint,
+                                            ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p])
+          if curand else lib().fos_philox4x32_10)
+    return fn(_dev(ctr, torch.int32, "ctr"), int(k0) & 0xFFFFFFFF, int(k1) & 0xFFFFFFFF,
+              _dev(out, torch.int32, "out"), n, _stream(stream))
 
 
 def fos_walk_math_f32(u, neg_log=None, cos2pi=None, stream=None, fast: bool = False) -> int:

@@ -50,6 +50,10 @@ def test_philox_bit_exact(orc):
     got = out.cpu().numpy().view(np.uint32)
     for i in range(0, 4096, 97):
         assert np.array_equal(got[i], orc.philox4x32_10(ctr[i], key))
+    # cuRAND's device Philox4x32-10 on the same counters and key (a library routine)
+    ref = torch.zeros_like(t_ctr)
+    fos.check(fos.fos_philox4x32_10(t_ctr, key[0], key[1], ref, curand=True), "curand philox")
+    assert torch.equal(ref, out)
     # known-answer vector
     z = torch.zeros((1, 4), dtype=torch.int32, device="cuda")
     o = torch.zeros_like(z)
