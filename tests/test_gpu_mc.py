@@ -194,7 +194,10 @@ def test_empty_and_zero_photons():
 def test_invalid_values_are_reported():
     for bad in (dict(mu_s=np.array([np.nan])), dict(mu_a=np.array([-1.0])),
                 dict(g=np.array([1.0])), dict(thickness=np.array([0.0])),
-                dict(n_layer=np.array([-1.5])), dict(substrate_R=np.array([1.5]))):
+                dict(n_layer=np.array([-1.5])), dict(substrate_R=np.array([1.5])),
+                # photon ids are 32-bit: a count of 2^32 (or first + count > 2^32) is refused
+                dict(n_photons=np.array([2 ** 32], np.int64)),
+                dict(photon_first=np.array([2 ** 32 - 50], np.int64))):
         b = _slab([1.0], [0.1], [0.5], [1.5], [0.5], 100)
         b.update(bad)
         c, st = gpu_mc(b, allow=(fos.FOS_ERR_INVALID_ARG,))
