@@ -5,15 +5,23 @@
 // (R, A, T).  BF16 weights and activations on the tensor cores, FP32 accumulation,
 // FP32 master weights and Adam state.
 //
-// Inference runs in one fused persistent kernel (infer_kernel, below).  Every matrix
-// product of training runs in gemm_kernel: a 128 x NT output
-// tile per CTA; K-major BF16 operands are staged by TMA (128-byte swizzle) through a
-// 4-stage mbarrier ring; one thread issues tcgen05.mma (M=128, N=NT, K=16) into FP32
-// accumulators in tensor memory; the 4 warps read the accumulators back with tcgen05.ld
-// and apply the fused epilogue of the layer (bias + GELU, softmax + cross-entropy
-// gradient, GELU derivative, or a split-K weight-gradient partial).  Transposed copies of
-// activations and gradients written by the epilogues make every product "A times B^T"
-// with both operands K-major.
+// Inference runs in one fused persistent kernel (infer_kernel): per 128-row tile the
+// activations stay in tensor memory from the features to the softmax.  Training runs the
+// same way: train_kernel takes a (member, 128-row tile) of the batch through the forward
+// pass, the softmax cross-entropy gradient and the backward pass down to the output
+// gradient of layer 0, with every activation and gradient on chip; it writes to global
+// memory only what the weight gradients need (each layer's input and output gradient) and
+// GELU'(Z), which it reads back itself.  Those arrays are "chunk-major", X[c/8][row][c%8]:
+// one 16-byte store per thread and 8 columns, 512 contiguous bytes per warp, and each
+// 8-row x 8-column block a 128-byte core matrix of the tensor cores' MN-major operand
+// layout.  dw_kernel then forms every weight gradient dW_l = dZ_l^T H_{l-1} as a split-K
+// tcgen05 product over the batch with both operands MN-major (TMA copies of the chunk-
+// major arrays), and the bias gradients as the same product with a column of ones.  Adam
+// sums the split partials in a fixed order and rewrites the BF16 weight images.
+//
+// gemm_kernel is a plain C = A B^T product (K-major BF16 operands staged by TMA with
+// 128-byte swizzle through an mbarrier ring, FP32 accumulators in tensor memory), kept
+// as a diagnostic entry point.
 //
 // Padded shapes (zero padding, never updated): layer 0 is 256 x 64 (9 real inputs),
 // layers 1-3 are 256 x 256, layer 4 is 64 x 256 (3 real outputs).
@@ -57,24 +65,23 @@ __host__ __device__ constexpr int real_in(int l) { return l == 0 ? N_FEAT : HID;
 // Per member (all offsets in elements of the named type, from the member base):
 //   theta  fp32 [P]  : W_0 | b_0 | W_1 | b_1 | ... | W_4 | b_4  (W_l row-major [out][in])
 //   adam_m fp32 [P], adam_v fp32 [P]
-//   wb     bf16      : W_l in bf16, [out][in] per layer (forward B operands)
-//   wt     bf16      : W_l^T in bf16, [in][out] for l = 1..4 (backward B operands)
+//   wg     bf16      : W_l^T (l = 4, 3, 2, 1) as shared-memory images for the backward
+//                      pass of train_kernel (see wg_index)
 //   stats  fp32 [64] : mean[16] | std[16] | lo[16] | hi[16] of the raw features
 //   step   int32 [4]
-//   wi     bf16      : the weights as shared-memory images for the fused inference
-//                      kernel (see img_index), one contiguous block per pipeline stage
+//   wi     bf16      : the weights as shared-memory images for the forward passes of the
+//                      fused kernels (see img_index), one contiguous block per pipeline stage
 struct Layout {
     long long w_off[N_LAYERS], b_off[N_LAYERS], P;
-    long long wb_off[N_LAYERS], wt_off[N_LAYERS], n_wb, n_wt;
-    size_t theta_b, m_b, v_b, wb_b, wt_b, stats_b, step_b, wi_b, bytes;
+    size_t theta_b, m_b, v_b, wg_b, stats_b, step_b, wi_b, bytes;
 };
 
-// Weight image: the B operands of the fused inference kernel, already in the 128-byte-
-// swizzled K-major layout a stage of shared memory holds, so that one untiled bulk copy
-// fills a stage (32 KB).  Layer 0 is one stage: all 256 output rows x 64 inputs (9 real).
-// Layers 1-3 are four stages each, (output half h, input pair j) in the order 2h + j:
-// 128 output rows x inputs 128 j .. +127, as two k blocks of 128 x 64 (16 KB).  Layer 4
-// keeps its first 16 output rows (3 real) as 4 blocks of 16 x 64 (2 KB), one per k
+// Weight image: the B operands of the fused kernels' forward pass, already in the
+// 128-byte-swizzled K-major layout a stage of shared memory holds, so that one untiled
+// bulk copy fills a stage (32 KB).  Layer 0 is one stage: all 256 output rows x 64 inputs
+// (9 real).  Layers 1-3 are four stages each, (output half h, input pair j) in the order
+// 2h + j: 128 output rows x inputs 128 j .. +127, as two k blocks of 128 x 64 (16 KB).
+// Layer 4 keeps its first 16 output rows (3 real) as 4 blocks of 16 x 64 (2 KB), one per k
 // block, copied as one stage.
 constexpr long long IMG_BLK = 256 * 64;          // elements of a 32 KB stage
 constexpr long long IMG_HALF_KB = 128 * 64;      // elements of a 16 KB k block of a half
@@ -85,44 +92,59 @@ __host__ __device__ constexpr long long img_off(int l) {
 constexpr long long IMG_ELEMS = 13 * IMG_BLK + 4 * IMG_L4_BLK;
 constexpr int IMG_ROWS_L4 = 16;
 
-// Element index in the image of weight (l, o, i), or -1 when the image leaves it out.
-// Row n of a block starts at n * 64 elements; its 16-byte chunk j (inputs 8j..8j+7 of
-// the k block) sits at chunk position j ^ (n mod 8).
+// Position of element (n, c) of a 64-column k block in the 128-byte swizzle: row n starts
+// at n * 64 elements; its 16-byte chunk j (columns 8j..8j+7) sits at chunk j ^ (n mod 8).
+__host__ __device__ constexpr long long swz64(int n, int c) {
+    return (long long)n * 64 + ((((c >> 3) ^ (n & 7)) << 3) | (c & 7));
+}
+
+// Element index in the forward image of weight (l, o, i), or -1 when the image leaves it
+// out.
 __host__ __device__ inline long long img_index(int l, int o, int i) {
     const int kb = i >> 6, c = i & 63;
-    const long long swz = (((c >> 3) ^ (o & 7)) << 3) | (c & 7);
     if (l == 4) {
         if (o >= IMG_ROWS_L4) return -1;
-        return img_off(l) + (long long)kb * IMG_L4_BLK + o * 64 + swz;
+        return img_off(l) + (long long)kb * IMG_L4_BLK + swz64(o, c);
     }
-    if (l == 0) return img_off(l) + o * 64 + swz;
+    if (l == 0) return img_off(l) + swz64(o, c);
     return img_off(l) + (long long)((o >> 7) * 2 + (kb >> 1)) * IMG_BLK +
-           (long long)(kb & 1) * IMG_HALF_KB + (o & 127) * 64 + swz;
+           (long long)(kb & 1) * IMG_HALF_KB + swz64(o & 127, c);
+}
+
+// Backward image: the B operands of the backward pass, which multiplies an output
+// gradient dZ_l [rows][out] by W_l, i.e. by B = W_l^T [in][out] (row n = input i, k =
+// output o).  13 stages of 32 KB in the order the backward pass uses them: W_4^T (256
+// rows x 64 k, the 3 real outputs in k 0-2; the pass multiplies K = 16 of them), then
+// W_3^T, W_2^T, W_1^T as four stages each, (input half h, output pair j) as in the
+// forward image.  Layer 0 has no backward product (no gradient for the features).
+constexpr long long WG_ELEMS = 13 * IMG_BLK;
+__host__ __device__ constexpr long long wg_off(int l) {
+    return l == 4 ? 0 : (1 + 4 * (3 - l)) * IMG_BLK;
+}
+__host__ __device__ inline long long wg_index(int l, int o, int i) {
+    if (l == 0) return -1;
+    if (l == 4) return o < 64 ? wg_off(4) + swz64(i, o) : -1;
+    const int kb = o >> 6, c = o & 63;
+    return wg_off(l) + (long long)((i >> 7) * 2 + (kb >> 1)) * IMG_BLK +
+           (long long)(kb & 1) * IMG_HALF_KB + swz64(i & 127, c);
 }
 
 static Layout make_layout() {
     Layout L;
-    long long p = 0, q = 0, t = 0;
+    long long p = 0;
     for (int l = 0; l < N_LAYERS; ++l) {
         L.w_off[l] = p;
         p += (long long)lay_out(l) * lay_in(l);
         L.b_off[l] = p;
         p += lay_out(l);
-        L.wb_off[l] = q;
-        q += (long long)lay_out(l) * lay_in(l);
-        L.wt_off[l] = t;
-        if (l > 0) t += (long long)lay_out(l) * lay_in(l);
     }
     L.P = p;
-    L.n_wb = q;
-    L.n_wt = t;
     auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
     size_t o = 0;
     L.theta_b = o; o = al(o + (size_t)p * 4);
     L.m_b = o;     o = al(o + (size_t)p * 4);
     L.v_b = o;     o = al(o + (size_t)p * 4);
-    L.wb_b = o;    o = al(o + (size_t)q * 2);
-    L.wt_b = o;    o = al(o + (size_t)t * 2);
+    L.wg_b = o;    o = al(o + (size_t)WG_ELEMS * 2);
     L.stats_b = o; o = al(o + 64 * 4);
     L.step_b = o;  o = al(o + 16);
     L.wi_b = o;    o = al(o + (size_t)IMG_ELEMS * 2);
@@ -133,7 +155,7 @@ static const Layout LAY = make_layout();
 
 struct MemberPtrs {
     float *theta, *m, *v, *stats;
-    bf16 *wb, *wt, *wi;
+    bf16 *wg, *wi;
     int* step;
 };
 static MemberPtrs member(void* model, int k) {
@@ -142,8 +164,7 @@ static MemberPtrs member(void* model, int k) {
     p.theta = (float*)(base + LAY.theta_b);
     p.m = (float*)(base + LAY.m_b);
     p.v = (float*)(base + LAY.v_b);
-    p.wb = (bf16*)(base + LAY.wb_b);
-    p.wt = (bf16*)(base + LAY.wt_b);
+    p.wg = (bf16*)(base + LAY.wg_b);
     p.stats = (float*)(base + LAY.stats_b);
     p.step = (int*)(base + LAY.step_b);
     p.wi = (bf16*)(base + LAY.wi_b);
@@ -151,31 +172,14 @@ static MemberPtrs member(void* model, int k) {
 }
 
 // ----------------------------------------------------------------------- GEMM kernel
-enum Mode {
-    FWD_HIDDEN = 0,    // Z = acc + b; H = GELU(Z) (bf16) and H^T; GELU'(Z) (bf16)
-    FWD_OUT = 2,       // softmax(acc + b) over 3 columns -> P; CE gradient G, G^T; loss
-    BWD_HIDDEN = 4,    // dZ = acc * GELU'(Z_prev) (stored by FWD_HIDDEN) -> dZ (bf16), dZ^T
-    DW_PARTIAL = 5,    // partial[split] = acc (fp32)
-};
-
+// C[split] = A B^T over one K range per split: a 128 x NT output tile per CTA, FP32
+// partials [split][M][ldf].
 struct GemmArgs {
     int M, N;              // output rows / columns (unpadded extents to store)
     int k_per_split;       // multiple of BK
-    const float* bias;     // [N]
-    float* out_f;          // Z [M][ldf] | P [M][4] | partial [split][M][ldf]
+    float* out_f;          // partial [split][M][ldf]
     int ldf;
-    bf16* out_h;           // H | G | dZ  [M][ldh]
-    int ldh;
-    bf16* out_t;           // H^T | G^T | dZ^T  [N][ldt]
-    int ldt;
-    const float* aux;      // targets [M][3] (FWD_OUT)
-    int ld_aux;
-    bf16* out_g;           // GELU'(Z) [M][ldh] (FWD_HIDDEN)
-    const bf16* aux_g;     // GELU'(Z_prev) [M][ld_aux] (BWD_HIDDEN)
-    float* loss_sum;
-    float inv_batch;
     unsigned* status;
-    int a_rows_box;        // rows of the A box (128, or fewer when A has fewer rows)
     unsigned tx_bytes;     // bytes one stage receives from the two TMA loads
     long long wait_limit;  // cycles an mbarrier wait may take before the kernel gives up
     int test_stall;        // test only: the producer never issues the load of chunk 0
@@ -188,16 +192,6 @@ __device__ __forceinline__ float tanh_fast(float x) {
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-// GELU and its derivative from one tanh: d/dz [z/2 (1 + t)] = (1 + t)/2 + z/2 (1 - t^2) du/dz
-// with t = tanh(u), u = sqrt(2/pi) (z + 0.044715 z^3).
-__device__ __forceinline__ void gelu_and_grad(float z, float& gel, float& grad) {
-    const float z2 = z * z;
-    const float t = tanh_fast(z * fmaf(0.0356774081f, z2, 0.7978845608f));
-    const float dudz = fmaf(0.1070322243f, z2, 0.7978845608f);   // d/dz of the tanh argument
-    const float hz = 0.5f * z;
-    gel = fmaf(hz, t, hz);
-    grad = fmaf(0.5f, 1.0f + t, hz * (1.0f - t * t) * dudz);
-}
 
 template <int NT>
 struct Smem {
@@ -209,7 +203,7 @@ struct Smem {
     static constexpr int ALLOC = TOTAL + 1024;   // slack for 1024-byte alignment
 };
 
-template <int NT, int MODE>
+template <int NT>
 __global__ void __launch_bounds__(128, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 GemmArgs args) {
@@ -308,87 +302,17 @@ __global__ void __launch_bounds__(128, 1)
     const bool row_ok = m < args.M && done_ok;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     float v[16];
-    if (MODE == FWD_OUT) {
-        tmem_ld16(trow, v);
-        float li = 0.f;
-        if (row_ok) {
-            float lg[N_OUT], p[N_OUT];
-            float mx = -3.0e38f;
-#pragma unroll
-            for (int c = 0; c < N_OUT; ++c) {
-                lg[c] = v[c] + args.bias[c];
-                mx = fmaxf(mx, lg[c]);
-            }
-            float sum = 0.f;
-#pragma unroll
-            for (int c = 0; c < N_OUT; ++c) {
-                p[c] = expf(lg[c] - mx);
-                sum += p[c];
-            }
-            const float inv = 1.0f / sum;
-#pragma unroll
-            for (int c = 0; c < N_OUT; ++c) p[c] *= inv;
-            *reinterpret_cast<float4*>(args.out_f + (long long)m * 4) =
-                make_float4(p[0], p[1], p[2], 0.f);
-            if (MODE == FWD_OUT) {
-#pragma unroll
-                for (int c = 0; c < N_OUT; ++c) {
-                    const float y = args.aux[(long long)m * 3 + c];
-                    li -= y * logf(fmaxf(p[c], 1e-30f));
-                    const bf16 gb = __float2bfloat16((p[c] - y) * args.inv_batch);
-                    args.out_h[(long long)m * args.ldh + c] = gb;
-                    args.out_t[(long long)c * args.ldt + m] = gb;
-                }
-            }
-        }
-        if (MODE == FWD_OUT) {   // batch-mean loss: warp sum, one atomic per warp
-            li *= args.inv_batch;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) li += __shfl_xor_sync(0xffffffffu, li, off);
-            if (lane == 0 && li != 0.f) atomicAdd(args.loss_sum, li);
-        }
-    } else {
 #pragma unroll 1
-        for (int c0 = 0; c0 < NT; c0 += 16) {
-            __syncwarp();
-            tmem_ld16(trow + c0, v);
-            const int n = n0 + c0;
-            if (!row_ok || n >= args.N) continue;
-            if (MODE == DW_PARTIAL) {
-                float* dst = args.out_f + (long long)blockIdx.z * args.M * args.ldf +
-                             (long long)m * args.ldf + n;
+    for (int c0 = 0; c0 < NT; c0 += 16) {
+        __syncwarp();
+        tmem_ld16(trow + c0, v);
+        const int n = n0 + c0;
+        if (!row_ok || n >= args.N) continue;
+        float* dst = args.out_f + (long long)blockIdx.z * args.M * args.ldf +
+                     (long long)m * args.ldf + n;
 #pragma unroll
-                for (int i = 0; i < 16; i += 4)
-                    *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-                continue;
-            }
-            __align__(16) bf16 hb[16];
-            if (MODE == BWD_HIDDEN) {
-                __align__(16) bf16 gp[16];
-                const uint4* gs = reinterpret_cast<const uint4*>(args.aux_g + (long long)m * args.ld_aux + n);
-                reinterpret_cast<uint4*>(gp)[0] = gs[0];
-                reinterpret_cast<uint4*>(gp)[1] = gs[1];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) hb[i] = __float2bfloat16(v[i] * __bfloat162float(gp[i]));
-            } else {
-                __align__(16) bf16 gd[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    float gel, grad;
-                    gelu_and_grad(v[i] + args.bias[n + i], gel, grad);
-                    hb[i] = __float2bfloat16(gel);
-                    gd[i] = __float2bfloat16(grad);
-                }
-                uint4* gdst = reinterpret_cast<uint4*>(args.out_g + (long long)m * args.ldh + n);
-                gdst[0] = reinterpret_cast<const uint4*>(gd)[0];
-                gdst[1] = reinterpret_cast<const uint4*>(gd)[1];
-            }
-            uint4* hd = reinterpret_cast<uint4*>(args.out_h + (long long)m * args.ldh + n);
-            hd[0] = reinterpret_cast<const uint4*>(hb)[0];
-            hd[1] = reinterpret_cast<const uint4*>(hb)[1];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) args.out_t[(long long)(n + i) * args.ldt + m] = hb[i];
-        }
+        for (int i = 0; i < 16; i += 4)
+            *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
     }
     tc_fence_before();
     __syncthreads();
@@ -857,6 +781,679 @@ __global__ void __launch_bounds__(FI_THREADS, 1) infer_kernel(InferArgs A) {
     if (warp == 0) tmem_dealloc(tmem, FI_TMEM_COLS);
 }
 
+// Step schedule of one member's training step (graph-captured training, where the host
+// does not see each step): the member's global step g (Adam's t = g + 1), the learning
+// rate and Adam's bias corrections 1 - b1^t, 1 - b2^t.
+struct SchedOut {
+    unsigned step;
+    float lr, c1, c2;
+};
+
+// ----------------------------------------------------------------- fused training
+// The products of one Adam step for 128-row tiles of every member's batch in one
+// persistent kernel, with infer_kernel's roles, tensor-memory plan and weight ring.  A
+// work item is (member k, tile t).  Its layer sequence s = 0..8 reads activation buffer
+// s mod 2 and writes the next layer's input into the other:
+//   s = 0..3  hidden layer s forward: Z = X W_s^T + b_s; H_s = GELU(Z) is the next
+//             input; H_s and GELU'(Z) go to global memory (chunk-major);
+//   s = 4     output layer: P = softmax(X W_4^T + b_4); the batch-mean cross-entropy
+//             -sum y log P into the member's loss; its gradient G = (P - y) / B (3 real
+//             columns of 16) is the next input and goes to global memory, with its
+//             column sums per tile and warp (the bias gradient of layer 4);
+//   s = 5..8  backward through layer j + 1, j = 8 - s: dZ_j = (G_{j+1} W_{j+1}) *
+//             GELU'(Z_j), where G_4 = G and G_{j+1} = dZ_{j+1} is the previous output;
+//             dZ_j goes to global memory and, except for j = 0, is the next input.
+// s = 0 and 5 multiply K = 16 (the features; the output gradient) by a 256 x 64 stage,
+// s = 4 gives N = 16 outputs, the others are 256 x 256 products in four stages, as in
+// infer_kernel.  The weight ring carries the forward image (14 items) and then the
+// backward image (13 items) of the item's member.  The batch rows are drawn in the
+// kernel: the caller's rows, or a hash of (seed, step, row) scaled to the data set.
+constexpr int FT_ITEMS = FI_ITEMS + 13;   // ring items per work item
+
+struct TrainArgs {
+    const float* feat;            // raw features [n_rows][9]
+    const float* targets;         // [n_rows][3]
+    long long n_rows;
+    const int* rows;              // the batch's rows [B] (one member), or NULL: hashed
+    int B, n_tiles, n_members;
+    unsigned seed, seed_mul;      // member k draws with seed ^ (k * seed_mul)
+    unsigned step;                // the draw's step without a device schedule
+    const uint8_t* model;
+    size_t member_bytes, theta_b, stats_b, wi_b, wg_b, step_b;
+    long long b_off[N_LAYERS];
+    // device schedule (graph-captured training): member k's step is its step counter,
+    // and table[k * table_cap + step - table_base[k]] is copied to the member's slot
+    int dev_step;
+    const SchedOut* table;
+    long long table_cap;
+    const int* table_base;
+    // workspace: member k's arrays at ws + k * region_bytes (byte offsets below)
+    uint8_t* ws;
+    size_t region_bytes;
+    size_t x0_b, h_b[4], g4_b, dz_b[4], gp_b[4], bp4_b, sched_b;
+    float* loss;                  // [n_members], zeroed by the caller
+    unsigned* status;
+    long long wait_limit;
+    int test_stall;               // test only: the first weight copy is never issued
+};
+
+// GELU (tanh form) and its derivative for two columns, from hz = z/2 = acc/2 + bias/2:
+// GELU = hz (1 + t), t = tanh(u), u = hz (2 c0 + 8 c1 hz^2); d GELU / dz = (1 + t)/2 +
+// hz (1 - t^2) (c0 + 12 c1 hz^2), with c0 = sqrt(2/pi), c1 = 0.044715 c0.  Both as packed
+// BF16 pairs.
+__device__ __forceinline__ void gelu_grad_half2(float acc0, float acc1, float hb0, float hb1,
+                                                uint32_t& gel, uint32_t& grad) {
+    const float2 hz = fma2(make_float2(0.5f, 0.5f), make_float2(acc0, acc1), make_float2(hb0, hb1));
+    const float2 h2 = mul2(hz, hz);
+    const float2 u = mul2(hz, fma2(make_float2(0.2854192648f, 0.2854192648f), h2,
+                                   make_float2(1.5957691216f, 1.5957691216f)));
+    const float2 t = make_float2(tanh_fast(u.x), tanh_fast(u.y));
+    const float2 g = fma2(hz, t, hz);
+    gel = pack_bf16(g.x, g.y);
+    const float2 du = fma2(make_float2(0.4281288972f, 0.4281288972f), h2,
+                           make_float2(0.7978845608f, 0.7978845608f));
+    const float2 om = fma2(make_float2(-t.x, -t.y), t, make_float2(1.0f, 1.0f));
+    const float2 half1 = fma2(make_float2(0.5f, 0.5f), t, make_float2(0.5f, 0.5f));
+    const float2 d = fma2(mul2(hz, om), du, half1);
+    grad = pack_bf16(d.x, d.y);
+}
+
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {   // a 32-bit integer hash (murmur3 finaliser)
+    x ^= x >> 16; x *= 0x85ebca6bu; x ^= x >> 13; x *= 0xc2b2ae35u; x ^= x >> 16;
+    return x;
+}
+
+// Data-set row of batch row b at a step: drawn uniformly (with replacement) by hashing
+// (seed, step, b).
+__device__ __forceinline__ long long draw_row(unsigned seed, unsigned step, int b, long long n_rows) {
+    const uint32_t h = mix32(mix32(seed ^ 0x9E3779B9u) ^ mix32(step * 0x85ebca6bu + (uint32_t)b));
+    return (long long)(((unsigned long long)h * (unsigned long long)n_rows) >> 32);
+}
+
+__global__ void __launch_bounds__(FI_THREADS, 1) train_kernel(TrainArgs A) {
+    extern __shared__ __align__(1024) uint8_t ft_smem[];
+    const uint32_t base = smem_u32(ft_smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t ring = base;
+    float* par = reinterpret_cast<float*>(ft_smem + FI_STAGES * FI_SLOT);
+    const uint32_t bars = ring + FI_STAGES * FI_SLOT + FI_PAR_BYTES;
+    const uint32_t bar_full = bars, bar_empty = bars + 8 * FI_STAGES;
+    const uint32_t bar_acc = bars + 16 * FI_STAGES;   // 2: output half h accumulated
+    const uint32_t bar_a = bar_acc + 16;              // 2: input k blocks 2h, 2h+1 written
+    const uint32_t bar_p = bar_a + 16;                // parameter staging done
+    const uint32_t tslot = bar_p + 8;
+    uint8_t* bars_g = ft_smem + FI_STAGES * FI_SLOT + FI_PAR_BYTES;
+    volatile uint32_t* tslot_ptr = reinterpret_cast<volatile uint32_t*>(bars_g + 8 * FI_NBARS);
+    volatile int& abort_flag = *reinterpret_cast<volatile int*>(bars_g + 8 * FI_NBARS + 4);
+
+    if ((base & 1023u) != 0u) {   // the swizzled stages need 1024-byte alignment
+        if (threadIdx.x == 0) atomicOr(&A.status[ST_CALL], DEV_RANGE);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < FI_STAGES; ++i) {
+            mbar_init(bar_full + 8 * i, 1);
+            mbar_init(bar_empty + 8 * i, 1);
+        }
+        for (int h = 0; h < 2; ++h) {
+            mbar_init(bar_acc + 8 * h, 1);
+            mbar_init(bar_a + 8 * h, 32 * FI_EPI_WARPS);
+        }
+        mbar_init(bar_p, 32 * FI_EPI_WARPS);
+        abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncwarp();
+    if (warp == 0) tmem_alloc(tslot, FI_TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot_ptr;
+
+    const long long n_items = (long long)A.n_members * A.n_tiles;
+    const long long my_items =
+        n_items > blockIdx.x ? (n_items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp == FI_EPI_WARPS) {
+        // ------------------------------------------------------------ bulk copies
+        if (lane == 0) {
+            const long long total = my_items * FT_ITEMS;
+            long long issued = 0, it = blockIdx.x;
+            int slot = 0, q = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (; issued < total && ok && !abort_flag; ++issued) {
+                if (issued >= FI_STAGES &&
+                    !mbar_wait_sleep(bar_empty + 8 * slot, phase ^ 1u, A.wait_limit)) {
+                    ok = false;
+                    break;
+                }
+                const int k = (int)(it / A.n_tiles);
+                const uint8_t* mb = A.model + (size_t)k * A.member_bytes;
+                const uint8_t* src;
+                uint32_t bytes;
+                if (q < FI_ITEMS) {
+                    int layer, blk;
+                    long long off;
+                    fi_item(q, layer, blk, off, bytes);
+                    src = mb + A.wi_b + (size_t)off * 2;
+                } else {
+                    src = mb + A.wg_b + (size_t)(q - FI_ITEMS) * IMG_BLK * 2;
+                    bytes = FI_SLOT;
+                }
+                if (!(A.test_stall && issued == 0)) {
+                    mbar_arrive_expect_tx(bar_full + 8 * slot, bytes);
+                    bulk_load(ring + slot * FI_SLOT, src, bytes, bar_full + 8 * slot);
+                }
+                if (++slot == FI_STAGES) {
+                    slot = 0;
+                    phase ^= 1u;
+                }
+                if (++q == FT_ITEMS) {
+                    q = 0;
+                    it += gridDim.x;
+                }
+            }
+            if (!ok) {
+                atomicOr(&A.status[ST_CALL], DEV_TIMEOUT);
+                abort_flag = 1;
+            }
+            // the last copy of each slot has landed before the CTA exits
+            const long long first = issued > FI_STAGES ? issued - FI_STAGES : 0;
+            for (long long g = first; g < issued; ++g) {
+                if (A.test_stall && g == 0) continue;   // never issued
+                mbar_wait(bar_full + 8 * (int)(g % FI_STAGES), (uint32_t)(g / FI_STAGES) & 1u,
+                          1000000000LL);
+            }
+        }
+        __syncwarp();
+    } else if (warp == FI_EPI_WARPS + 1) {
+        // ------------------------------------------------------------ MMAs
+        if (lane == 0) {
+            int slot = 0;
+            uint32_t phase = 0, pa = 0;
+            long long consumed = 0;
+            bool ok = true;
+            const uint64_t dring = desc_sw128(ring);
+            constexpr uint32_t ID128 = idesc_bf16(128, 128), ID16 = idesc_bf16(128, 16);
+            auto take = [&](int& s) {
+                if (!mbar_wait(bar_full + 8 * slot, phase, A.wait_limit)) return false;
+                s = slot;
+                ++consumed;
+                if (++slot == FI_STAGES) {
+                    slot = 0;
+                    phase ^= 1u;
+                }
+                return true;
+            };
+            auto wait_a = [&](int h) {
+                if (!mbar_wait_sleep(bar_a + 8 * h, pa, A.wait_limit) || abort_flag) return false;
+                tc_fence_after();
+                return true;
+            };
+            auto bdesc = [&](int s) { return dring + (uint64_t)(s * (FI_SLOT >> 4)); };
+            for (long long i = 0; i < my_items && ok; ++i) {
+                for (int s = 0; s < 9 && ok; ++s) {
+                    const uint32_t ta = tmem + FI_ABUF + (uint32_t)((s & 1) * 128);
+                    int st = 0;
+                    if (s == 0 || s == 5) {
+                        // K = 16 (the features; the output gradient) x 256 outputs: half h
+                        // of the stage's 256 rows starts 16 KB into it
+                        if (!(ok = take(st))) break;
+                        ok = wait_a(0) && wait_a(1);
+                        if (ok)
+                            for (int h = 0; h < 2; ++h) {
+                                mma_bf16_ts(tmem + FI_ACC + (uint32_t)(h * 128), ta,
+                                            bdesc(st) + (uint64_t)(h * (16384 >> 4)), ID128, 0u);
+                                mma_commit(bar_acc + 8 * h);
+                            }
+                        mma_commit(bar_empty + 8 * st);
+                    } else if (s == 4) {
+                        // the 16 padded output columns (3 real), four 2 KB k blocks
+                        if (!(ok = take(st))) break;
+                        for (int kb = 0; kb < 4 && ok; ++kb) {
+                            if ((kb & 1) == 0 && !(ok = wait_a(kb >> 1))) break;
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                mma_bf16_ts(tmem + FI_ACC, ta + (uint32_t)(kb * 32 + kk * 8),
+                                            bdesc(st) + (uint64_t)(kb * ((int)IMG_L4_BLK * 2 >> 4) + 2 * kk),
+                                            ID16, (kb > 0 || kk > 0) ? 1u : 0u);
+                        }
+                        mma_commit(bar_empty + 8 * st);
+                        if (ok)
+                            for (int h = 0; h < 2; ++h) mma_commit(bar_acc + 8 * h);
+                    } else {
+                        // stage (h, j): output rows 128 h .. +127 x k blocks 2j, 2j + 1
+                        for (int h = 0; h < 2 && ok; ++h) {
+                            for (int j = 0; j < 2 && ok; ++j) {
+                                if (!(ok = take(st))) break;
+                                if (h == 0 && !(ok = wait_a(j))) {
+                                    mma_commit(bar_empty + 8 * st);
+                                    break;
+                                }
+#pragma unroll
+                                for (int x = 0; x < 2; ++x) {
+                                    const int kb = 2 * j + x;
+#pragma unroll
+                                    for (int kk = 0; kk < 4; ++kk)
+                                        mma_bf16_ts(tmem + FI_ACC + (uint32_t)(h * 128),
+                                                    ta + (uint32_t)(kb * 32 + kk * 8),
+                                                    bdesc(st) + (uint64_t)(x * (16384 >> 4) + 2 * kk),
+                                                    ID128, (kb > 0 || kk > 0) ? 1u : 0u);
+                                }
+                                mma_commit(bar_empty + 8 * st);
+                            }
+                            if (ok) mma_commit(bar_acc + 8 * h);
+                        }
+                    }
+                    pa ^= 1u;
+                }
+            }
+            if (!ok) {
+                atomicOr(&A.status[ST_CALL], DEV_TIMEOUT);
+                abort_flag = 1;
+            }
+            // every MMA has finished before the CTA exits (commits complete in order)
+            if (consumed > 0) {
+                const long long g = consumed - 1;
+                mbar_wait(bar_empty + 8 * (int)(g % FI_STAGES), (uint32_t)(g / FI_STAGES) & 1u,
+                          1000000000LL);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ epilogue warps
+        const int lq = warp & 3, cg = warp >> 2;            // TMEM lane quarter, column group
+        const int r = lq * 32 + lane;                       // tile row = TMEM lane
+        const uint32_t trow = tmem + ((uint32_t)(lq * 32) << 16);
+        const bool lead = cg == 0;                          // builds X0, the output layer
+        const int et = threadIdx.x;                         // 0 .. 32 * FI_EPI_WARPS - 1
+        const long long Bp = (long long)A.n_tiles * 128;
+        const float inv_b = 1.0f / (float)A.B;
+        uint32_t pp = 0, pacc = 0;
+        bool ok = true;
+        if (A.dev_step && et == 0) {   // the schedule entry of each member's step, for Adam
+            for (int k = 0; k < A.n_members; ++k) {
+                const int g = *reinterpret_cast<const int*>(A.model + (size_t)k * A.member_bytes +
+                                                            A.step_b);
+                *reinterpret_cast<SchedOut*>(A.ws + (size_t)k * A.region_bytes + A.sched_b) =
+                    A.table[(long long)k * A.table_cap + (g - A.table_base[k])];
+            }
+        }
+        long long n_staged = 0;
+        for (long long it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+            const int k = (int)(it / A.n_tiles);
+            const int t = (int)(it - (long long)k * A.n_tiles);
+            const uint8_t* mb = A.model + (size_t)k * A.member_bytes;
+            uint8_t* reg = A.ws + (size_t)k * A.region_bytes;
+            const long long row = (long long)t * 128 + r;   // batch row (B is a multiple of 128)
+            // 16-byte block (chunk, this row) of a chunk-major array at byte offset off
+            auto cm = [&](size_t off, int chunk) {
+                return reinterpret_cast<uint4*>(reg + off + ((size_t)chunk * Bp + row) * 16);
+            };
+            // member k's biases (hidden layers halved, for the GELU in z/2) and feature
+            // statistics into parameter slot n_staged mod 2: every epilogue thread has
+            // passed the staging barrier of the item in between, so none still reads it
+            float* pk_par = par + (n_staged & 1) * FI_PAR_FLOATS;
+            {
+                const float* th = reinterpret_cast<const float*>(mb + A.theta_b);
+                const float* stt = reinterpret_cast<const float*>(mb + A.stats_b);
+                for (int i = et; i < FI_PAR_FLOATS; i += 32 * FI_EPI_WARPS) {
+                    float v;
+                    if (i < N_LAYERS * 256) {
+                        const int l = i >> 8, c = i & 255;
+                        v = (c < real_out(l)) ? __ldg(th + A.b_off[l] + c) : 0.f;
+                        if (l < 4) v *= 0.5f;
+                    } else {
+                        v = __ldg(stt + (i - N_LAYERS * 256));   // mean[16] | std[16]
+                    }
+                    pk_par[i] = v;
+                }
+                mbar_arrive(bar_p);
+                if (!__all_sync(0xffffffffu, mbar_wait_sleep(bar_p, pp, A.wait_limit))) ok = false;
+                pp ^= 1u;
+                ++n_staged;
+            }
+            if (!ok) break;
+            float y[N_OUT] = {0.f, 0.f, 0.f};
+            if (lead) {   // layer-0 input: standardised features in k 0-8, zeros to 15
+                const unsigned step =
+                    A.dev_step ? (unsigned)*reinterpret_cast<const int*>(mb + A.step_b) : A.step;
+                const long long src = A.rows ? (long long)A.rows[row]
+                                             : draw_row(A.seed ^ ((unsigned)k * A.seed_mul), step,
+                                                        (int)row, A.n_rows);
+                const float* st = pk_par + N_LAYERS * 256;
+                float z[N_FEAT];
+#pragma unroll
+                for (int f = 0; f < N_FEAT; ++f) z[f] = (A.feat[src * N_FEAT + f] - st[f]) / st[16 + f];
+#pragma unroll
+                for (int c = 0; c < N_OUT; ++c) y[c] = A.targets[src * 3 + c];
+                const uint32_t pk[8] = {pack_bf16(z[0], z[1]), pack_bf16(z[2], z[3]),
+                                        pack_bf16(z[4], z[5]), pack_bf16(z[6], z[7]),
+                                        pack_bf16(z[8], 0.f), 0u, 0u, 0u};
+                tmem_st8(trow + FI_ABUF, pk);
+                *cm(A.x0_b, 0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *cm(A.x0_b, 1) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                tmem_wait_st();
+            }
+            tc_fence_before();
+            mbar_arrive(bar_a);
+            mbar_arrive(bar_a + 8);
+            for (int s = 0; s < 9 && ok; ++s) {
+                // every thread waits for both halves of every layer (a parity wait that fell
+                // two phases behind its barrier would return at once); a wait's outcome is
+                // made uniform over the warp, whose TMEM accesses and shuffles are collective
+                const uint32_t dst = trow + FI_ABUF + (uint32_t)(((s + 1) & 1) * 128);
+                if (s < 4) {
+                    const float* bias = pk_par + s * 256;
+                    for (int h = 0; h < 2; ++h) {
+                        if (!__all_sync(0xffffffffu, mbar_wait_sleep(bar_acc + 8 * h, pacc, A.wait_limit))) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        uint32_t v[32];
+                        tmem_ld32_async(trow + FI_ACC + (uint32_t)(h * 128 + cg * 32), v);
+                        tmem_wait_ld(v);
+#pragma unroll
+                        for (int c16 = 0; c16 < 32; c16 += 16) {
+                            const float* b = bias + h * 128 + cg * 32 + c16;
+                            uint32_t pk[8], gk[8];
+#pragma unroll
+                            for (int i = 0; i < 16; i += 4) {
+                                const float4 b4 = *reinterpret_cast<const float4*>(b + i);
+                                gelu_grad_half2(__uint_as_float(v[c16 + i]), __uint_as_float(v[c16 + i + 1]),
+                                                b4.x, b4.y, pk[i / 2], gk[i / 2]);
+                                gelu_grad_half2(__uint_as_float(v[c16 + i + 2]),
+                                                __uint_as_float(v[c16 + i + 3]), b4.z, b4.w,
+                                                pk[i / 2 + 1], gk[i / 2 + 1]);
+                            }
+                            tmem_st8(dst + (uint32_t)(h * 64 + cg * 16 + c16 / 2), pk);
+                            const int ch = (h * 128 + cg * 32 + c16) >> 3;
+                            *cm(A.h_b[s], ch) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                            *cm(A.h_b[s], ch + 1) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                            *cm(A.gp_b[s], ch) = make_uint4(gk[0], gk[1], gk[2], gk[3]);
+                            *cm(A.gp_b[s], ch + 1) = make_uint4(gk[4], gk[5], gk[6], gk[7]);
+                        }
+                        tmem_wait_st();
+                        tc_fence_before();
+                        mbar_arrive(bar_a + 8 * h);
+                    }
+                } else if (s == 4) {
+                    for (int h = 0; h < 2; ++h)
+                        if (!__all_sync(0xffffffffu, mbar_wait_sleep(bar_acc + 8 * h, pacc, A.wait_limit)))
+                            ok = false;
+                    if (ok && lead) {
+                        tc_fence_after();
+                        float v[16];
+                        tmem_ld16(trow + FI_ACC, v);
+                        const float* b4 = pk_par + 4 * 256;
+                        float lg[N_OUT], mx = -3.0e38f;
+#pragma unroll
+                        for (int c = 0; c < N_OUT; ++c) {
+                            lg[c] = v[c] + b4[c];
+                            mx = fmaxf(mx, lg[c]);
+                        }
+                        float p[N_OUT], sum = 0.f;
+#pragma unroll
+                        for (int c = 0; c < N_OUT; ++c) {
+                            p[c] = expf(lg[c] - mx);
+                            sum += p[c];
+                        }
+                        const float inv = 1.0f / sum;
+                        float li = 0.f, gq[N_OUT];
+#pragma unroll
+                        for (int c = 0; c < N_OUT; ++c) {
+                            p[c] *= inv;
+                            li -= y[c] * logf(fmaxf(p[c], 1e-30f));
+                            // the gradient as the products will see it (BF16)
+                            gq[c] = __bfloat162float(__float2bfloat16((p[c] - y[c]) * inv_b));
+                        }
+                        const uint32_t pk[8] = {pack_bf16(gq[0], gq[1]), pack_bf16(gq[2], 0.f),
+                                                0u, 0u, 0u, 0u, 0u, 0u};
+                        tmem_st8(dst, pk);
+                        *cm(A.g4_b, 0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        *cm(A.g4_b, 1) = make_uint4(0u, 0u, 0u, 0u);
+                        // per-warp sums: the bias gradient of layer 4 (column sums of G over
+                        // the warp's 32 rows) and the loss
+                        li *= inv_b;
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) {
+                            li += __shfl_xor_sync(0xffffffffu, li, off);
+#pragma unroll
+                            for (int c = 0; c < N_OUT; ++c) gq[c] += __shfl_xor_sync(0xffffffffu, gq[c], off);
+                        }
+                        if (lane == 0) {
+                            float* bp = reinterpret_cast<float*>(reg + A.bp4_b) + ((long long)t * 4 + lq) * 4;
+                            *reinterpret_cast<float4*>(bp) = make_float4(gq[0], gq[1], gq[2], 0.f);
+                            if (li != 0.f) atomicAdd(A.loss + k, li);
+                        }
+                        tmem_wait_st();
+                    }
+                    tc_fence_before();
+                    mbar_arrive(bar_a);
+                    mbar_arrive(bar_a + 8);
+                } else {
+                    const int j = 8 - s;   // this step's output gradient dZ_j
+                    for (int h = 0; h < 2; ++h) {
+                        const int ch = (h * 128 + cg * 32) >> 3;   // this thread's 4 chunks
+                        uint4 gp[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) gp[q] = *cm(A.gp_b[j], ch + q);
+                        if (!__all_sync(0xffffffffu, mbar_wait_sleep(bar_acc + 8 * h, pacc, A.wait_limit))) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        uint32_t v[32];
+                        tmem_ld32_async(trow + FI_ACC + (uint32_t)(h * 128 + cg * 32), v);
+                        tmem_wait_ld(v);
+#pragma unroll
+                        for (int c16 = 0; c16 < 32; c16 += 16) {
+                            uint32_t pk[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const uint4 g4 = gp[c16 / 8 + e / 4];
+                                const uint32_t w = (e & 3) == 0 ? g4.x : (e & 3) == 1 ? g4.y
+                                                 : (e & 3) == 2 ? g4.z : g4.w;
+                                const float2 d = mul2(make_float2(__uint_as_float(v[c16 + 2 * e]),
+                                                                  __uint_as_float(v[c16 + 2 * e + 1])),
+                                                      make_float2(__uint_as_float(w << 16),
+                                                                  __uint_as_float(w & 0xffff0000u)));
+                                pk[e] = pack_bf16(d.x, d.y);
+                            }
+                            if (s < 8) tmem_st8(dst + (uint32_t)(h * 64 + cg * 16 + c16 / 2), pk);
+                            *cm(A.dz_b[j], ch + c16 / 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                            *cm(A.dz_b[j], ch + c16 / 8 + 1) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                        }
+                        if (s < 8) {
+                            tmem_wait_st();
+                            tc_fence_before();
+                            mbar_arrive(bar_a + 8 * h);
+                        }
+                    }
+                }
+                pacc ^= 1u;
+            }
+            if (abort_flag) ok = false;
+        }
+        if (!ok) atomicOr(&A.status[ST_CALL], DEV_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, FI_TMEM_COLS);
+}
+
+// ----------------------------------------------------------------- weight gradients
+// Split-K partials of the weight gradients, C[split][m][n] = sum over the split's batch
+// rows b of A[b][m] B[b][n], where A and B are train_kernel's chunk-major arrays: dW_l =
+// dZ_l^T H_{l-1} (H_{-1} = the features) for l = 0..3, and dW_4^T = H_3^T G.  Both
+// operands are MN-major without swizzle: a core matrix is 8 batch rows x 8 columns (16
+// bytes per row), core matrices consecutive in b lie 128 bytes apart (the descriptor's
+// leading byte offset) and those consecutive in m or n DW_BK * 16 bytes apart (its stride
+// byte offset); a 4-D TMA box {8 columns, DW_BK rows, column groups, member} lands in
+// shared memory in exactly that order.  A CTA computes the 128 x NT tile (m tile, column
+// block) of one (member, layer, split); with a bias partial, the CTAs of column block 0
+// also form sum_b A[b][m] (the bias gradient) as the product with a K-major tile whose
+// row 0 is ones, in 16 more accumulator columns.
+constexpr int DW_BK = 64;
+constexpr int DW_STAGES = 3;
+constexpr int DW_LAYS = 3;
+
+struct DwArgs {
+    int n_lay;                  // layers in this launch; blockIdx.y = member * n_lay + lay
+    int k_per_split;            // multiple of DW_BK; blockIdx.z = split
+    uint8_t* ws;                // member k's region at ws + k * region_bytes
+    size_t region_bytes;
+    size_t part_b[DW_LAYS];     // partial [split][256][part_ld] FP32 (byte offset in the region)
+    int part_ld[DW_LAYS];
+    size_t bias_b[DW_LAYS];     // bias partial [split][256] FP32, or 0: none
+    unsigned* status;
+    long long wait_limit;
+};
+struct DwMaps {
+    CUtensorMap a[DW_LAYS], b[DW_LAYS];
+};
+
+template <int NT>
+struct DwSmem {
+    static constexpr int A_BYTES = 128 * DW_BK * 2;
+    static constexpr int B_BYTES = NT * DW_BK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;     // a multiple of 1024
+    static constexpr int ONES_OFF = DW_STAGES * STAGE;  // 1024-aligned (128-byte swizzle)
+    static constexpr int BAR_OFF = ONES_OFF + 16 * 128;
+    static constexpr int TOTAL = BAR_OFF + (2 * DW_STAGES + 1) * 8 + 16;
+    static constexpr int ALLOC = TOTAL + 1024;          // slack for 1024-byte alignment
+    static constexpr uint32_t TCOLS = NT + 16 <= 32 ? 32 : (NT + 16 <= 64 ? 64 : (NT + 16 <= 128 ? 128 : 256));
+};
+
+template <int NT>
+__global__ void __launch_bounds__(128, 1)
+    dw_kernel(const __grid_constant__ DwMaps maps, const __grid_constant__ DwArgs args) {
+    using S = DwSmem<NT>;
+    static_assert(S::STAGE % 1024 == 0 && NT + 16 <= 256, "stage alignment, tensor memory");
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - raw);
+    const uint32_t ones = base + S::ONES_OFF;
+    const uint32_t bar_full = base + S::BAR_OFF;
+    const uint32_t bar_empty = bar_full + DW_STAGES * 8;
+    const uint32_t bar_done = bar_empty + DW_STAGES * 8;
+    const uint32_t tslot = bar_done + 8;
+    volatile uint32_t* tslot_ptr = (volatile uint32_t*)(gbase + S::BAR_OFF + (2 * DW_STAGES + 1) * 8);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = blockIdx.x & 1, nb = blockIdx.x >> 1;
+    const int lay = blockIdx.y % args.n_lay, k = blockIdx.y / args.n_lay;
+    const int split = blockIdx.z;
+    const int k0 = split * args.k_per_split, n_k = args.k_per_split / DW_BK;
+    const bool bias = args.bias_b[lay] != 0 && nb == 0;
+    const CUtensorMap* ta = &maps.a[lay];
+    const CUtensorMap* tb = &maps.b[lay];
+    constexpr uint32_t ID_W = idesc_bf16_major(128, NT, true, true);
+    constexpr uint32_t ID_B = idesc_bf16_major(128, 16, true, false);
+
+    {   // the ones tile: row 0 of a K-major 16 x 64 BF16 tile is 1.0 (0x3F80), the rest 0
+        uint32_t* o = reinterpret_cast<uint32_t*>(gbase + S::ONES_OFF);
+        for (int i = threadIdx.x; i < 16 * 64 / 2; i += blockDim.x) o[i] = i < 32 ? 0x3F803F80u : 0u;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the MMAs
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < DW_STAGES; ++s) {
+            mbar_init(bar_full + 8 * s, 1);
+            mbar_init(bar_empty + 8 * s, 1);
+        }
+        mbar_init(bar_done, 1);
+        fence_barrier_init();
+        tma_prefetch_desc(ta);
+        tma_prefetch_desc(tb);
+    }
+    __syncwarp();
+    if (warp == 0) tmem_alloc(tslot, S::TCOLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot_ptr;
+
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        int last_issued = -1, consumed = 0;
+        auto load = [&](int j) {
+            const int s = j % DW_STAGES;
+            const uint32_t a_s = base + s * S::STAGE, b_s = a_s + S::A_BYTES;
+            last_issued = j;
+            mbar_arrive_expect_tx(bar_full + 8 * s, (uint32_t)S::STAGE);
+            tma_load_4d(a_s, ta, bar_full + 8 * s, 0, k0 + j * DW_BK, mt * 16, k);
+            tma_load_4d(b_s, tb, bar_full + 8 * s, 0, k0 + j * DW_BK, nb * (NT / 8), k);
+        };
+        for (int j = 0; j < n_k && j < DW_STAGES; ++j) load(j);
+        for (int j = 0; j < n_k; ++j) {
+            const int s = j % DW_STAGES;
+            const uint32_t ph = (uint32_t)(j / DW_STAGES) & 1u;
+            if (!mbar_wait(bar_full + 8 * s, ph, args.wait_limit)) {
+                ok = false;
+                break;
+            }
+            consumed++;
+            tc_fence_after();
+            const uint32_t a_s = base + s * S::STAGE, b_s = a_s + S::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < DW_BK / 16; ++kk) {   // 16 batch rows = 2 core matrices = 256 B
+                const uint64_t da = desc_mn_plain(a_s + kk * 256, 128, DW_BK * 16);
+                const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
+                mma_bf16(tmem, da, desc_mn_plain(b_s + kk * 256, 128, DW_BK * 16), ID_W, acc);
+                if (bias) mma_bf16(tmem + NT, da, desc_sw128(ones + kk * 32), ID_B, acc);
+            }
+            mma_commit(bar_empty + 8 * s);
+            if (j + DW_STAGES < n_k) {
+                if (!mbar_wait(bar_empty + 8 * s, ph, args.wait_limit)) {
+                    ok = false;
+                    break;
+                }
+                load(j + DW_STAGES);
+            }
+        }
+        mma_commit(bar_done);
+        if (!ok) {
+            // let every load that was issued land before the CTA can exit
+            for (int j = consumed; j <= last_issued; ++j)
+                mbar_wait(bar_full + 8 * (j % DW_STAGES), (uint32_t)(j / DW_STAGES) & 1u,
+                          1000000000LL);
+            atomicOr(&args.status[ST_CALL], DEV_TIMEOUT);
+        }
+    }
+    __syncwarp();
+    const bool done_ok = __all_sync(0xffffffffu, mbar_wait(bar_done, 0, args.wait_limit));
+    tc_fence_after();
+    if (!done_ok && lane == 0) atomicOr(&args.status[ST_CALL], DEV_TIMEOUT);
+
+    const int r = warp * 32 + lane;
+    const int m = mt * 128 + r;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    uint8_t* reg = args.ws + (size_t)k * args.region_bytes;
+    const int ld = args.part_ld[lay];
+    if (done_ok) {
+        float* out = reinterpret_cast<float*>(reg + args.part_b[lay]) +
+                     ((long long)split * 256 + m) * ld + nb * NT;
+        float v[16];
+#pragma unroll 1
+        for (int c0 = 0; c0 < NT; c0 += 16) {
+            tmem_ld16(trow + c0, v);
+#pragma unroll
+            for (int i = 0; i < 16; i += 4)
+                *reinterpret_cast<float4*>(out + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        }
+        if (bias) {
+            tmem_ld16(trow + NT, v);
+            reinterpret_cast<float*>(reg + args.bias_b[lay])[(long long)split * 256 + m] = v[0];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, S::TCOLS);
+}
+
 // ----------------------------------------------------------------------- small kernels
 // Raw features of row (d, w): wavelength, n_p, log10 k_p, radius, volume fraction,
 // log10 thickness, g, log10(mu_s d + 1e-6), log10(mu_a d + 1e-6).
@@ -961,108 +1558,31 @@ __global__ void mask_rows_kernel(const unsigned char* mask, long long n, int* ro
     if (on) rows[base + wsum[warp] + __popc(bal & ((1u << lane) - 1u))] = (int)i;
 }
 
-__device__ __forceinline__ uint32_t mix32(uint32_t x) {   // a 32-bit integer hash (murmur3 finaliser)
-    x ^= x >> 16; x *= 0x85ebca6bu; x ^= x >> 13; x *= 0xc2b2ae35u; x ^= x >> 16;
-    return x;
-}
-
-// Training batch: rows given, or drawn uniformly (with replacement) by hashing (seed,
-// step, slot);
-// standardised features -> X0 [B][64] and X0^T [64][B] (pads stay 0); targets -> Y.
-// Step schedule of one member's training step, computed on the device from the member's
-// step counter (graph-captured training, where the host does not see each step).
-struct SchedOut {
-    unsigned step;        // the member's global step g (Adam's t = g + 1)
-    float lr, c1, c2;     // learning rate; 1 - b1^t, 1 - b2^t
+// Offsets of each layer's weights and biases in theta (floats).
+struct ParamOffsets {
+    long long w_off[N_LAYERS], b_off[N_LAYERS];
 };
 
-// Device schedule of graph-captured training: the member's step counter g, the table of
-// the call's steps (entry g - *base, written by the host with the same arithmetic as the
-// per-step entry point), and where the step's entry goes for Adam.
-struct DevSched {
-    int* step_ctr;
-    const SchedOut* table;
-    const int* base;
-    SchedOut* out;
-};
-
-__global__ void set_step_kernel(int* step_ctr, int value) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) *step_ctr = value;
+// Layer l and the weight (o, i) or bias o that parameter idx of theta is; false for
+// padding (never updated, always 0).
+__device__ __forceinline__ bool param_locate(const ParamOffsets& po, long long idx, int& l,
+                                             int& o, int& i, bool& is_w) {
+    l = 0;
+    while (l + 1 < N_LAYERS && idx >= po.w_off[l + 1]) ++l;
+    if (idx < po.b_off[l]) {
+        const long long e = idx - po.w_off[l];
+        const int sh = l == 0 ? 6 : 8;   // log2 of the padded input width (64 or 256)
+        o = (int)(e >> sh);
+        i = (int)(e & ((1 << sh) - 1));
+        is_w = true;
+        return o < real_out(l) && i < real_in(l);
+    }
+    o = (int)(idx - po.b_off[l]);
+    i = 0;
+    is_w = false;
+    return o < real_out(l);
 }
 
-// With a device schedule (ds.step_ctr non-NULL) the step is the member's step counter, and
-// thread 0 also writes the step's schedule for Adam (the counter advances in the bias
-// gradient kernel, after every thread here has read it).
-__global__ void gather_kernel(const float* feat, const float* targets, long long n_rows, int B,
-                              unsigned seed, unsigned step, const int* rows, const float* stats,
-                              bf16* X0, bf16* X0T, float* Y, DevSched ds) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ds.step_ctr) {
-        const int g = *ds.step_ctr;
-        step = (unsigned)g;
-        if (b == 0) *ds.out = ds.table[g - *ds.base];
-    }
-    if (b >= B) return;
-    long long src;
-    if (rows) {
-        src = rows[b];
-    } else {
-        const uint32_t h = mix32(mix32(seed ^ 0x9E3779B9u) ^ mix32(step * 0x85ebca6bu + (uint32_t)b));
-        src = (long long)(((unsigned long long)h * (unsigned long long)n_rows) >> 32);
-    }
-    for (int f = 0; f < N_FEAT; ++f) {
-        const float x = (feat[src * N_FEAT + f] - stats[f]) / stats[16 + f];
-        const bf16 xb = __float2bfloat16(x);
-        X0[(long long)b * IN_PAD + f] = xb;
-        X0T[(long long)f * B + b] = xb;
-    }
-    for (int c = 0; c < N_OUT; ++c) Y[(long long)b * 3 + c] = targets[src * 3 + c];
-}
-
-// Column sums of a bf16 [rows][ld] matrix (bias gradients), in two deterministic
-// passes.  Pass 1: block (x, y) sums rows y*chunk .. +chunk of columns 64x .. +63 (4 row
-// phases, then a fixed combine) into part[y][c].  Pass 2 sums the COLSUM_SPLITS partials
-// of each column in order.
-constexpr int COLSUM_SPLITS = 64;
-// Bias gradients of all layers in one launch (blockIdx.z = layer): per-split column sums
-// part[l][split][c] of layer l's output gradient G_l [rows][ld]; Adam adds the splits in
-// a fixed order, so the result does not depend on scheduling.
-struct ColsumArgs {
-    const bf16* G[N_LAYERS];
-    int ld[N_LAYERS];
-    float* part[N_LAYERS];
-    int rows;
-    int* step_ctr;   // device schedule: advanced here (NULL: none)
-};
-__global__ void colsum_layers_kernel(ColsumArgs A) {
-    __shared__ float ph[4][64];
-    if (A.step_ctr && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
-        *A.step_ctr += 1;
-    const int l = blockIdx.z;
-    const int ncols = real_out(l), rows = A.rows, ld = A.ld[l];
-    if ((int)blockIdx.x * 64 >= ncols) return;   // the whole block: no column of this layer
-    const bf16* G = A.G[l];
-    float* part = A.part[l];
-    const int c = blockIdx.x * 64 + (threadIdx.x & 63);
-    const int q = threadIdx.x >> 6;   // 4 row phases
-    const int chunk = (rows + COLSUM_SPLITS - 1) / COLSUM_SPLITS;
-    const int r0 = blockIdx.y * chunk, r1 = min(rows, r0 + chunk);
-    float a0 = 0.f, a1 = 0.f;   // two running sums, loads in flight together
-    if (c < ncols) {
-        int r = r0 + q;
-        for (; r + 4 < r1; r += 8) {
-            a0 += __bfloat162float(G[(long long)r * ld + c]);
-            a1 += __bfloat162float(G[(long long)(r + 4) * ld + c]);
-        }
-        if (r < r1) a0 += __bfloat162float(G[(long long)r * ld + c]);
-    }
-    const float acc = a0 + a1;
-    ph[q][threadIdx.x & 63] = acc;
-    __syncthreads();
-    if (q == 0 && c < ncols)
-        part[blockIdx.y * ncols + c] =
-            ph[0][threadIdx.x] + ph[1][threadIdx.x] + ph[2][threadIdx.x] + ph[3][threadIdx.x];
-}
 // Sum of n values v[k * stride + e], k = 0..n-1, in a fixed order: four running sums over
 // k mod 4 (their loads independent, so they are in flight together), then added in order.
 __device__ __forceinline__ float split_sum(const float* v, long long stride, int n, long long e) {
@@ -1077,156 +1597,141 @@ __device__ __forceinline__ float split_sum(const float* v, long long stride, int
     for (; k < n; ++k) a0 += v[k * stride + e];
     return (a0 + a1) + (a2 + a3);
 }
-// Bias gradient of output o of layer l from its per-split column sums.
-__device__ __forceinline__ float bias_grad(const float* part, int ncols, int o) {
-    return split_sum(part, ncols, COLSUM_SPLITS, o);
-}
 
 struct AdamArgs {
-    float *theta, *m, *v;
-    bf16 *wb, *wt, *wi;
-    long long w_off[N_LAYERS], b_off[N_LAYERS], wb_off[N_LAYERS], wt_off[N_LAYERS];
-    const float* part[N_LAYERS];   // split-K partials of dW_l [splits][out][in]
-    const float* bpart[N_LAYERS];  // per-split column sums of G_l [COLSUM_SPLITS][real out]
+    ParamOffsets po;
+    uint8_t* model;                 // member k = blockIdx.y at model + k * member_bytes
+    size_t member_bytes, theta_b, m_b, v_b, wi_b, wg_b, step_b;
+    const uint8_t* ws;              // member k's training arrays at ws + k * region_bytes
+    size_t region_bytes;
+    size_t part_b[N_LAYERS];        // dW_l split partials [split][rows][ld]; l = 4 transposed
+    int part_ld[N_LAYERS];
+    long long part_plane[N_LAYERS]; // floats per split
     int splits;
+    size_t bias_b[N_LAYERS];        // bias partials: bias_n[l] partials bias_ld[l] floats apart
+    int bias_n[N_LAYERS], bias_ld[N_LAYERS];
     float lr, b1, b2, eps, c1, c2;  // c1 = 1 - b1^t, c2 = 1 - b2^t
-    const SchedOut* sched;          // non-NULL: lr, c1, c2 from the device schedule
+    int dev_sched;                  // lr, c1, c2 from the member's schedule slot; step += 1
+    size_t sched_b;
+    int host_step;                  // without a device schedule: the step count becomes this + 1
 };
 
-// Adam (Kingma & Ba) on every real parameter, then the bf16 copies W (and W^T for
-// layers >= 1).  Padding stays zero.
-__global__ void adam_kernel(AdamArgs A, long long P) {
-    if (A.sched) {
-        A.lr = A.sched->lr;
-        A.c1 = A.sched->c1;
-        A.c2 = A.sched->c2;
+// Gradient of weight (o, i) or bias o of layer l from the member's partials, each summed
+// in a fixed order (so the result does not depend on scheduling).
+__device__ __forceinline__ float param_grad(const AdamArgs& A, const uint8_t* reg, int l, int o,
+                                            int i, bool is_w) {
+    if (is_w) {
+        const float* part = reinterpret_cast<const float*>(reg + A.part_b[l]);
+        const long long e = (l == 4) ? (long long)i * A.part_ld[l] + o : (long long)o * A.part_ld[l] + i;
+        return split_sum(part, A.part_plane[l], A.splits, e);
     }
+    const float* bp = reinterpret_cast<const float*>(reg + A.bias_b[l]);
+    return split_sum(bp, A.bias_ld[l], A.bias_n[l], o);
+}
+
+// Adam (Kingma & Ba) on every real parameter of member blockIdx.y, then its BF16 weight
+// images (forward and backward); the member's step count advances.  Padding stays zero.
+__global__ void adam_kernel(AdamArgs A, long long P) {
+    const int k = blockIdx.y;
+    uint8_t* mb = A.model + (size_t)k * A.member_bytes;
+    const uint8_t* reg = A.ws + (size_t)k * A.region_bytes;
+    float lr = A.lr, c1 = A.c1, c2 = A.c2;
+    if (A.dev_sched) {
+        const SchedOut* so = reinterpret_cast<const SchedOut*>(reg + A.sched_b);
+        lr = so->lr;
+        c1 = so->c1;
+        c2 = so->c2;
+    }
+    float* theta = reinterpret_cast<float*>(mb + A.theta_b);
+    float* am = reinterpret_cast<float*>(mb + A.m_b);
+    float* av = reinterpret_cast<float*>(mb + A.v_b);
+    bf16* wi = reinterpret_cast<bf16*>(mb + A.wi_b);
+    bf16* wg = reinterpret_cast<bf16*>(mb + A.wg_b);
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
          idx += (long long)gridDim.x * blockDim.x) {
-        int l = 0;
-        while (l + 1 < N_LAYERS && idx >= A.w_off[l + 1]) ++l;
-        const int in_p = lay_in(l), out_p = lay_out(l);
-        float g;
-        long long e = -1;
-        int o, i = 0;
-        if (idx < A.b_off[l]) {
-            e = idx - A.w_off[l];
-            o = (int)(e / in_p);
-            i = (int)(e % in_p);
-            if (o >= real_out(l) || i >= real_in(l)) continue;
-            g = split_sum(A.part[l], (long long)out_p * in_p, A.splits, e);
-        } else {
-            o = (int)(idx - A.b_off[l]);
-            if (o >= real_out(l)) continue;
-            g = bias_grad(A.bpart[l], real_out(l), o);
-        }
-        const float mm = A.b1 * A.m[idx] + (1.f - A.b1) * g;
-        const float vv = A.b2 * A.v[idx] + (1.f - A.b2) * g * g;
-        A.m[idx] = mm;
-        A.v[idx] = vv;
-        const float th = A.theta[idx] - A.lr * (mm / A.c1) / (sqrtf(vv / A.c2) + A.eps);
-        A.theta[idx] = th;
-        if (e >= 0) {
+        int l, o, i;
+        bool is_w;
+        if (!param_locate(A.po, idx, l, o, i, is_w)) continue;
+        const float g = param_grad(A, reg, l, o, i, is_w);
+        const float mm = A.b1 * am[idx] + (1.f - A.b1) * g;
+        const float vv = A.b2 * av[idx] + (1.f - A.b2) * g * g;
+        am[idx] = mm;
+        av[idx] = vv;
+        const float th = theta[idx] - lr * (mm / c1) / (sqrtf(vv / c2) + A.eps);
+        theta[idx] = th;
+        if (is_w) {
             const bf16 tb = __float2bfloat16(th);
-            A.wb[A.wb_off[l] + e] = tb;
-            if (l > 0) A.wt[A.wt_off[l] + (long long)i * out_p + o] = tb;
             const long long ii = img_index(l, o, i);
-            if (ii >= 0) A.wi[ii] = tb;
+            if (ii >= 0) wi[ii] = tb;
+            const long long gi = wg_index(l, o, i);
+            if (gi >= 0) wg[gi] = tb;
         }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int* st = reinterpret_cast<int*>(mb + A.step_b);
+        *st = A.dev_sched ? *st + 1 : A.host_step + 1;
     }
 }
 
-// The gradient vector in the layout of theta (padding 0): what adam_kernel consumes.
+// The gradient vector of member 0 in the layout of theta (padding 0): what adam_kernel
+// consumes.
 __global__ void grad_kernel(AdamArgs A, long long P, float* grad) {
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
          idx += (long long)gridDim.x * blockDim.x) {
-        int l = 0;
-        while (l + 1 < N_LAYERS && idx >= A.w_off[l + 1]) ++l;
-        const int in_p = lay_in(l), out_p = lay_out(l);
-        float g = 0.f;
-        if (idx < A.b_off[l]) {
-            const long long e = idx - A.w_off[l];
-            const int o = (int)(e / in_p), i = (int)(e % in_p);
-            if (o < real_out(l) && i < real_in(l))
-                g = split_sum(A.part[l], (long long)out_p * in_p, A.splits, e);
-        } else {
-            const int o = (int)(idx - A.b_off[l]);
-            if (o < real_out(l)) g = bias_grad(A.bpart[l], real_out(l), o);
-        }
-        grad[idx] = g;
+        int l, o, i;
+        bool is_w;
+        grad[idx] = param_locate(A.po, idx, l, o, i, is_w) ? param_grad(A, A.ws, l, o, i, is_w) : 0.f;
     }
 }
 
+// Weight (l, o, i) = th into the BF16 images of a member (forward and backward).
+__device__ __forceinline__ void write_images(bf16* wi, bf16* wg, int l, int o, int i, float th) {
+    const bf16 tb = __float2bfloat16(th);
+    const long long ii = img_index(l, o, i);
+    if (ii >= 0) wi[ii] = tb;
+    const long long gi = wg_index(l, o, i);
+    if (gi >= 0) wg[gi] = tb;
+}
+
 // He-uniform initial weights (hash of seed, member, index -> uniform), zero biases,
-// zero Adam state, bf16 copies, step 0.
-__global__ void init_kernel(float* theta, float* m, float* v, bf16* wb, bf16* wt, bf16* wi,
-                            int* step, unsigned seed, unsigned member, AdamArgs lay,
-                            long long P) {
+// zero Adam state, BF16 images, step 0.
+__global__ void init_kernel(float* theta, float* m, float* v, bf16* wi, bf16* wg, int* step,
+                            unsigned seed, unsigned member, ParamOffsets po, long long P) {
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
          idx += (long long)gridDim.x * blockDim.x) {
-        int l = 0;
-        while (l + 1 < N_LAYERS && idx >= lay.w_off[l + 1]) ++l;
-        const int in_p = lay_in(l), out_p = lay_out(l);
+        int l, o, i;
+        bool is_w;
+        const bool real = param_locate(po, idx, l, o, i, is_w);
         float th = 0.f;
-        long long e = -1;
-        int o = 0, i = 0;
-        if (idx < lay.b_off[l]) {
-            e = idx - lay.w_off[l];
-            o = (int)(e / in_p);
-            i = (int)(e % in_p);
-            if (o < real_out(l) && i < real_in(l)) {
-                const uint32_t h = mix32(mix32(seed) ^ mix32(member * 0x27d4eb2du + 0x165667b1u) ^
-                                         mix32((uint32_t)idx));
-                const float u = ((float)(h >> 8) + 0.5f) * 0x1p-24f;   // (0,1)
-                const float lim = sqrtf(6.0f / (float)real_in(l));
-                th = (2.f * u - 1.f) * lim;
-            }
+        if (real && is_w) {
+            const uint32_t h = mix32(mix32(seed) ^ mix32(member * 0x27d4eb2du + 0x165667b1u) ^
+                                     mix32((uint32_t)idx));
+            const float u = ((float)(h >> 8) + 0.5f) * 0x1p-24f;   // (0,1)
+            const float lim = sqrtf(6.0f / (float)real_in(l));
+            th = (2.f * u - 1.f) * lim;
         }
         theta[idx] = th;
         m[idx] = 0.f;
         v[idx] = 0.f;
-        if (e >= 0) {
-            const bf16 tb = __float2bfloat16(th);
-            wb[lay.wb_off[l] + e] = tb;
-            if (l > 0) wt[lay.wt_off[l] + (long long)i * out_p + o] = tb;
-            const long long ii = img_index(l, o, i);
-            if (ii >= 0) wi[ii] = tb;
-        }
+        if (is_w) write_images(wi, wg, l, o, i, th);
         if (idx == 0) step[0] = 0;
     }
 }
 
 // Parameters given by the caller (device theta in the padded layout): entries outside
-// the real rows and columns are stored as 0; Adam state and step are reset and the bf16
-// copies rebuilt.
-__global__ void load_kernel(const float* src, float* theta, float* m, float* v, bf16* wb,
-                            bf16* wt, bf16* wi, int* step, AdamArgs lay, long long P) {
+// the real rows and columns are stored as 0; Adam state and step are reset and the BF16
+// images rebuilt.
+__global__ void load_kernel(const float* src, float* theta, float* m, float* v, bf16* wi,
+                            bf16* wg, int* step, ParamOffsets po, long long P) {
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
          idx += (long long)gridDim.x * blockDim.x) {
-        int l = 0;
-        while (l + 1 < N_LAYERS && idx >= lay.w_off[l + 1]) ++l;
-        const int in_p = lay_in(l), out_p = lay_out(l);
-        float th = 0.f;
-        long long e = -1;
-        int o = 0, i = 0;
-        if (idx < lay.b_off[l]) {
-            e = idx - lay.w_off[l];
-            o = (int)(e / in_p);
-            i = (int)(e % in_p);
-            if (o < real_out(l) && i < real_in(l)) th = src[idx];
-        } else if ((int)(idx - lay.b_off[l]) < real_out(l)) {
-            th = src[idx];
-        }
+        int l, o, i;
+        bool is_w;
+        const float th = param_locate(po, idx, l, o, i, is_w) ? src[idx] : 0.f;
         theta[idx] = th;
         m[idx] = 0.f;
         v[idx] = 0.f;
-        if (e >= 0) {
-            const bf16 tb = __float2bfloat16(th);
-            wb[lay.wb_off[l] + e] = tb;
-            if (l > 0) wt[lay.wt_off[l] + (long long)i * out_p + o] = tb;
-            const long long ii = img_index(l, o, i);
-            if (ii >= 0) wi[ii] = tb;
-        }
+        if (is_w) write_images(wi, wg, l, o, i, th);
         if (idx == 0) step[0] = 0;
     }
 }
@@ -1309,15 +1814,14 @@ struct Operand {
     long long rows, cols, ld;   // cols = K extent (multiple of 64)
 };
 
-template <int NT, int MODE>
+template <int NT>
 static fos_status gemm(const Operand& A, const Operand& B, int splits, GemmArgs g,
                        cudaStream_t s) {
     static bool attr_set[64] = {false};
     int dev = 0;
     FOS_CUDA_TRY(cudaGetDevice(&dev));
     if (!attr_set[dev]) {
-        FOS_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel<NT, MODE>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+        FOS_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           Smem<NT>::ALLOC));
         attr_set[dev] = true;
     }
@@ -1330,111 +1834,117 @@ static fos_status gemm(const Operand& A, const Operand& B, int splits, GemmArgs 
     st = make_map(&tb, B.ptr, B.rows, B.cols, B.ld, NT);
     if (st != FOS_OK) return st;
     g.k_per_split = (int)(A.cols / splits);
-    g.a_rows_box = a_box;
     g.tx_bytes = (unsigned)(a_box * BK * 2 + NT * BK * 2);
     dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + NT - 1) / NT), (unsigned)splits);
-    gemm_kernel<NT, MODE><<<grid, 128, Smem<NT>::ALLOC, s>>>(ta, tb, g);
+    gemm_kernel<NT><<<grid, 128, Smem<NT>::ALLOC, s>>>(ta, tb, g);
     return from_cuda(cudaGetLastError());
 }
 
-// Training workspace for batch B (library-owned, per device).
-struct TrainWs {
-    int B = 0;
-    int splits = 0;
-    void* mem = nullptr;
-    size_t bytes = 0;
-    bf16 *X0, *X0T, *H[4], *HT[4], *G4, *G4T, *dZ[4], *dZT[4];
-    bf16* Gp[4];   // GELU'(Z_l) of the hidden layers
-    float *P, *Y, *part[N_LAYERS], *colpart[N_LAYERS], *loss;
-    SchedOut* sched;
-    // the weight gradients and bias column sums run on a side stream, off the chain of
-    // backward products: fork after each gradient G_l is written, join before Adam
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_g[N_LAYERS] = {}, ev_join = nullptr;
-};
-// One training workspace per device and member slot (member mod TRAIN_SLOTS), so that
-// the steps of up to TRAIN_SLOTS members can run concurrently on separate streams.
+// 4-D map of a chunk-major BF16 array X[c/8][row][c%8] at byte offset `off` of every member
+// region: dims {8 columns, Bp rows, chunks, members}, box {8, DW_BK, box_chunks, 1}, no
+// swizzle (the MN-major operand layout of dw_kernel).
+static fos_status make_cm_map(CUtensorMap* map, const uint8_t* ws, size_t off, long long Bp,
+                              int chunks, int members, size_t region, int box_chunks) {
+    const uint8_t* ptr = ws + off;
+    if (((uintptr_t)ptr & 15u) != 0 || region % 16 != 0) return FOS_ERR_INVALID_ARG;
+    cuuint64_t dims[4] = {8, (cuuint64_t)Bp, (cuuint64_t)chunks, (cuuint64_t)members};
+    cuuint64_t strides[3] = {16, (cuuint64_t)Bp * 16, (cuuint64_t)region};
+    cuuint32_t box[4] = {8, (cuuint32_t)DW_BK, (cuuint32_t)box_chunks, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint8_t*>(ptr), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? FOS_OK : FOS_ERR_CUDA;
+}
+
+// Training workspace (library-owned, per device), in member regions of region_bytes: a
+// per-step call for member m uses region m mod TRAIN_SLOTS (so that the steps of up to
+// TRAIN_SLOTS members can run concurrently on separate streams), graph-captured training
+// region k for member k.  A region holds train_kernel's chunk-major arrays (the features
+// X0 and output gradient G: 2 chunks; H_l, dZ_l, GELU'(Z_l): 32 chunks), the split-K
+// partials of the weight and bias gradients, the layer-4 bias partials per tile and warp,
+// and the schedule slot; the members' losses sit in one array after the regions.
 constexpr int TRAIN_SLOTS = 4;
 static_assert(TRAIN_SLOTS + 1 <= ST_REGIONS, "a status region per training slot");
-static TrainWs g_tws[64][TRAIN_SLOTS];
+struct TrainWs {
+    int B = 0, splits = 0, regions = 0;
+    uint8_t* mem = nullptr;
+    size_t region_bytes = 0;
+    float* loss = nullptr;   // [regions]
+    size_t x0_b, h_b[4], g4_b, dz_b[4], gp_b[4], part_b[N_LAYERS], bias_b[4], bp4_b, sched_b;
+    // the weight gradients of layers 0 and 4 run on a side stream beside those of 1-3
+    cudaStream_t side[TRAIN_SLOTS] = {};
+    cudaEvent_t ev_fork[TRAIN_SLOTS] = {}, ev_join[TRAIN_SLOTS] = {};
+};
+static TrainWs g_tws[64];
 
-static fos_status ensure_train_ws(int dev, int slot, int B, Workspace* ws = nullptr) {
-    TrainWs& w = g_tws[dev][slot];
-    if (w.mem && w.B == B) return FOS_OK;
-    if (ws) ws->generation++;   // captured training graphs hold the old buffers
+// Split-K count of the weight gradients: at most 8, each split at least 1024 batch rows
+// (or 1 split), and dividing the batch's 64-row blocks.
+static int dw_splits(int B) {
+    int s = 8;
+    while (s > 1 && ((B / 64) % s != 0 || B / s < 1024)) s >>= 1;
+    return s;
+}
+
+static fos_status ensure_train_ws(int dev, int B, int regions, Workspace* ws) {
+    TrainWs& w = g_tws[dev];
+    if (w.mem && w.B == B && w.regions >= regions) return FOS_OK;
+    if (regions < TRAIN_SLOTS) regions = TRAIN_SLOTS;
+    if (w.mem && w.B == B && regions < w.regions) regions = w.regions;
+    ws->generation++;   // captured training graphs hold the old buffers
     if (w.mem) {
         FOS_CUDA_TRY(cudaDeviceSynchronize());
         cudaFree(w.mem);
         w.mem = nullptr;
     }
-    // split-K of the weight gradients: K = B / splits rows each (>= 512 for B >= 4096),
-    // fewer partials for Adam to read
-    const int splits = B >= 8192 ? 16 : (B / 256 > 0 ? (B / 256 < 16 ? B / 256 : 16) : 1);
-    size_t o = 0;
+    const int splits = dw_splits(B);
+    const size_t Bp = (size_t)B;
     auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
-    struct Item { void** p; size_t bytes; };
-    std::vector<Item> items;
-    auto add = [&](void** p, size_t bytes) { items.push_back({p, bytes}); };
-    add((void**)&w.X0, (size_t)B * IN_PAD * 2);
-    add((void**)&w.X0T, (size_t)IN_PAD * B * 2);
-    for (int l = 0; l < 4; ++l) {
-        add((void**)&w.Gp[l], (size_t)B * HID * 2);
-        add((void**)&w.H[l], (size_t)B * HID * 2);
-        add((void**)&w.HT[l], (size_t)HID * B * 2);
-    }
-    add((void**)&w.P, (size_t)B * 4 * 4);
-    add((void**)&w.Y, (size_t)B * 3 * 4);
-    add((void**)&w.G4, (size_t)B * OUT_PAD * 2);
-    add((void**)&w.G4T, (size_t)OUT_PAD * B * 2);
-    for (int k = 0; k < 4; ++k) {   // the output gradient of hidden layer k
-        add((void**)&w.dZ[k], (size_t)B * HID * 2);
-        add((void**)&w.dZT[k], (size_t)HID * B * 2);
-    }
-    for (int l = 0; l < N_LAYERS; ++l) {
-        add((void**)&w.part[l], (size_t)splits * lay_out(l) * lay_in(l) * 4);
-        add((void**)&w.colpart[l], (size_t)COLSUM_SPLITS * real_out(l) * 4);
-    }
-    add((void**)&w.loss, 16);
-    add((void**)&w.sched, sizeof(SchedOut));
-    for (auto& it : items) o = al(o + it.bytes);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = al(o + bytes);
+        return at;
+    };
+    w.x0_b = take(2 * Bp * 16);
+    for (int l = 0; l < 4; ++l) w.h_b[l] = take(32 * Bp * 16);
+    w.g4_b = take(2 * Bp * 16);
+    for (int l = 0; l < 4; ++l) w.dz_b[l] = take(32 * Bp * 16);
+    for (int l = 0; l < 4; ++l) w.gp_b[l] = take(32 * Bp * 16);
+    for (int l = 0; l < N_LAYERS; ++l)
+        w.part_b[l] = take((size_t)splits * 256 * ((l == 0 || l == 4) ? 16 : 256) * 4);
+    for (int l = 0; l < 4; ++l) w.bias_b[l] = take((size_t)splits * 256 * 4);
+    w.bp4_b = take((Bp / 128) * 4 * 4 * 4);
+    w.sched_b = take(sizeof(SchedOut));
+    w.region_bytes = o;
+    const size_t total = o * (size_t)regions + al((size_t)regions * 4);
     void* mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, o);
+    cudaError_t e = cudaMalloc(&mem, total);
     if (e != cudaSuccess) return from_cuda(e);
-    FOS_CUDA_TRY(cudaMemset(mem, 0, o));   // padding columns stay zero for good
-    size_t q = 0;
-    for (auto& it : items) {
-        *it.p = (char*)mem + q;
-        q = al(q + it.bytes);
-    }
-    w.mem = mem;
-    w.bytes = o;
+    FOS_CUDA_TRY(cudaMemset(mem, 0, total));
+    w.mem = (uint8_t*)mem;
+    w.loss = (float*)(w.mem + o * (size_t)regions);
     w.B = B;
     w.splits = splits;
-    if (!w.side) {
-        FOS_CUDA_TRY(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
-        for (int l = 0; l < N_LAYERS; ++l)
-            FOS_CUDA_TRY(cudaEventCreateWithFlags(&w.ev_g[l], cudaEventDisableTiming));
-        FOS_CUDA_TRY(cudaEventCreateWithFlags(&w.ev_join, cudaEventDisableTiming));
+    w.regions = regions;
+    if (!w.side[0]) {
+        for (int i = 0; i < TRAIN_SLOTS; ++i) {
+            FOS_CUDA_TRY(cudaStreamCreateWithFlags(&w.side[i], cudaStreamNonBlocking));
+            FOS_CUDA_TRY(cudaEventCreateWithFlags(&w.ev_fork[i], cudaEventDisableTiming));
+            FOS_CUDA_TRY(cudaEventCreateWithFlags(&w.ev_join[i], cudaEventDisableTiming));
+        }
     }
     return FOS_OK;
 }
 
-static AdamArgs layout_args(const MemberPtrs& mp) {
-    AdamArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.theta = mp.theta;
-    a.m = mp.m;
-    a.v = mp.v;
-    a.wb = mp.wb;
-    a.wt = mp.wt;
-    a.wi = mp.wi;
+static ParamOffsets param_offsets() {
+    ParamOffsets po;
     for (int l = 0; l < N_LAYERS; ++l) {
-        a.w_off[l] = LAY.w_off[l];
-        a.b_off[l] = LAY.b_off[l];
-        a.wb_off[l] = LAY.wb_off[l];
-        a.wt_off[l] = LAY.wt_off[l];
+        po.w_off[l] = LAY.w_off[l];
+        po.b_off[l] = LAY.b_off[l];
     }
-    return a;
+    return po;
 }
 
 static GemmArgs gargs(unsigned* status) {
@@ -1445,105 +1955,165 @@ static GemmArgs gargs(unsigned* status) {
     return g;
 }
 
-// Forward + backward + Adam for one member on one batch (all on stream s).
-// One Adam step of one member on stream s.  sched = NULL: step and lr as given; else the
-// step, lr and bias corrections come from the device schedule (graph-captured training).
-static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, const float* feat,
-                             const float* targets, long long n_rows, int B, unsigned seed,
-                             unsigned step, const int* rows, float lr, float* grad_out,
-                             cudaStream_t s, const DevSched* ds = nullptr) {
-    TrainWs& w = g_tws[ws->device][slot];
-    unsigned* status = ws->status + ST_WORDS * (1 + slot);   // this slot's status region
-    const int splits = w.splits;
-    DevSched dsv;
-    std::memset(&dsv, 0, sizeof(dsv));
-    if (ds) dsv = *ds;
-    FOS_CUDA_TRY(cudaMemsetAsync(w.loss, 0, 4, s));
-    gather_kernel<<<(B + 255) / 256, 256, 0, s>>>(feat, targets, n_rows, B, seed, step, rows,
-                                                  mp.stats, w.X0, w.X0T, w.Y, dsv);
-    FOS_CUDA_TRY(cudaGetLastError());
-    const float* bias[N_LAYERS];
-    const bf16* wb[N_LAYERS];
-    const bf16* wt[N_LAYERS];
-    for (int l = 0; l < N_LAYERS; ++l) {
-        bias[l] = mp.theta + LAY.b_off[l];
-        wb[l] = mp.wb + LAY.wb_off[l];
-        wt[l] = mp.wt + LAY.wt_off[l];
+// Device schedule of graph-captured training: member k's entries at table[k * cap + i],
+// its first step at base[k].
+struct DevSched {
+    const SchedOut* table;
+    long long cap;
+    const int* base;
+};
+
+// One Adam step of n_members consecutive members (model at their first member) whose
+// workspace regions start at region0, on stream s: train_kernel, the weight gradients
+// (layers 1-3 on s, layers 0 and 4 on the slot's side stream), then Adam, or with
+// grad_out the gradient of one member.  Without a device schedule the step, learning rate
+// and bias corrections are the given ones.
+static fos_status train_step(Workspace* ws, int slot, uint8_t* model, int n_members, int region0,
+                             const float* feat, const float* targets, long long n_rows, int B,
+                             unsigned seed, unsigned seed_mul, unsigned step, const int* rows,
+                             float lr, float* grad_out, unsigned* status, cudaStream_t s,
+                             const DevSched* ds = nullptr) {
+    static bool attr_set[64] = {};
+    if (!attr_set[ws->device]) {
+        FOS_CUDA_TRY(cudaFuncSetAttribute(train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          FI_SMEM));
+        FOS_CUDA_TRY(cudaFuncSetAttribute(dw_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          DwSmem<128>::ALLOC));
+        FOS_CUDA_TRY(cudaFuncSetAttribute(dw_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          DwSmem<16>::ALLOC));
+        attr_set[ws->device] = true;
     }
-    fos_status st;
-    // forward
+    TrainWs& w = g_tws[ws->device];
+    uint8_t* reg0 = w.mem + (size_t)region0 * w.region_bytes;
+    const int n_tiles = B / 128;
+    FOS_CUDA_TRY(cudaMemsetAsync(w.loss + region0, 0, (size_t)n_members * sizeof(float), s));
+
+    TrainArgs ta;
+    std::memset(&ta, 0, sizeof(ta));
+    ta.feat = feat;
+    ta.targets = targets;
+    ta.n_rows = n_rows;
+    ta.rows = rows;
+    ta.B = B;
+    ta.n_tiles = n_tiles;
+    ta.n_members = n_members;
+    ta.seed = seed;
+    ta.seed_mul = seed_mul;
+    ta.step = step;
+    ta.model = model;
+    ta.member_bytes = LAY.bytes;
+    ta.theta_b = LAY.theta_b;
+    ta.stats_b = LAY.stats_b;
+    ta.wi_b = LAY.wi_b;
+    ta.wg_b = LAY.wg_b;
+    ta.step_b = LAY.step_b;
+    for (int l = 0; l < N_LAYERS; ++l) ta.b_off[l] = LAY.b_off[l];
+    if (ds) {
+        ta.dev_step = 1;
+        ta.table = ds->table;
+        ta.table_cap = ds->cap;
+        ta.table_base = ds->base;
+    }
+    ta.ws = reg0;
+    ta.region_bytes = w.region_bytes;
+    ta.x0_b = w.x0_b;
+    ta.g4_b = w.g4_b;
     for (int l = 0; l < 4; ++l) {
-        Operand A = (l == 0) ? Operand{w.X0, B, IN_PAD, IN_PAD} : Operand{w.H[l - 1], B, HID, HID};
-        Operand Bm{wb[l], HID, lay_in(l), lay_in(l)};
-        GemmArgs g = gargs(status);
-        g.M = B; g.N = HID; g.bias = bias[l];
-        g.out_g = w.Gp[l]; g.out_h = w.H[l]; g.ldh = HID; g.out_t = w.HT[l]; g.ldt = B;
-        st = gemm<128, FWD_HIDDEN>(A, Bm, 1, g, s);
-        if (st != FOS_OK) return st;
+        ta.h_b[l] = w.h_b[l];
+        ta.dz_b[l] = w.dz_b[l];
+        ta.gp_b[l] = w.gp_b[l];
     }
-    {
-        GemmArgs g = gargs(status);
-        g.M = B; g.N = OUT_PAD; g.bias = bias[4];
-        g.out_f = w.P; g.out_h = w.G4; g.ldh = OUT_PAD; g.out_t = w.G4T; g.ldt = B;
-        g.aux = w.Y; g.loss_sum = w.loss; g.inv_batch = 1.0f / (float)B;
-        st = gemm<64, FWD_OUT>(Operand{w.H[3], B, HID, HID}, Operand{wb[4], OUT_PAD, HID, HID}, 1, g, s);
-        if (st != FOS_OK) return st;
-    }
-    // backward: layer 4 gradients, then down through the hidden layers
-    const bf16* Gcur = w.G4;
-    const bf16* GcurT = w.G4T;
-    int gcols = OUT_PAD;
-    ColsumArgs ca;
-    ca.rows = B;
-    ca.step_ctr = dsv.step_ctr;
-    for (int l = 4; l >= 0; --l) {
-        // the bias gradient's column sums wait for one launch after the loop
-        ca.G[l] = Gcur;
-        ca.ld[l] = gcols;
-        ca.part[l] = w.colpart[l];
-        // weight gradient dW_l = G^T · H_{l-1}  (A = G^T [out][B], B = H_{l-1}^T [in][B]),
-        // on the side stream once G is written
-        {
-            FOS_CUDA_TRY(cudaEventRecord(w.ev_g[l], s));
-            FOS_CUDA_TRY(cudaStreamWaitEvent(w.side, w.ev_g[l], 0));
-            Operand A{GcurT, lay_out(l), B, B};
-            Operand Bm = (l == 0) ? Operand{w.X0T, IN_PAD, B, B} : Operand{w.HT[l - 1], HID, B, B};
-            GemmArgs g = gargs(status);
-            g.M = lay_out(l); g.N = lay_in(l); g.out_f = w.part[l]; g.ldf = lay_in(l);
-            if (l == 0) st = gemm<64, DW_PARTIAL>(A, Bm, splits, g, w.side);
-            else st = gemm<256, DW_PARTIAL>(A, Bm, splits, g, w.side);
-            if (st != FOS_OK) return st;
-        }
-        if (l == 0) break;
-        // dZ_{l-1} = (G · W_l) * GELU'(Z_{l-1})  (A = G [B][out], B = W_l^T [in][out])
-        {
-            bf16* dz = w.dZ[l - 1];
-            bf16* dzt = w.dZT[l - 1];
-            Operand A{Gcur, B, lay_out(l), gcols};
-            Operand Bm{wt[l], HID, lay_out(l), lay_out(l)};
-            GemmArgs g = gargs(status);
-            g.M = B; g.N = HID; g.aux_g = w.Gp[l - 1]; g.ld_aux = HID;
-            g.out_h = dz; g.ldh = HID; g.out_t = dzt; g.ldt = B;
-            st = gemm<128, BWD_HIDDEN>(A, Bm, 1, g, s);
-            if (st != FOS_OK) return st;
-            Gcur = dz;
-            GcurT = dzt;
-            gcols = HID;
-        }
-    }
-    colsum_layers_kernel<<<dim3(HID / 64, COLSUM_SPLITS, N_LAYERS), 256, 0, w.side>>>(ca);
+    ta.bp4_b = w.bp4_b;
+    ta.sched_b = w.sched_b;
+    ta.loss = w.loss + region0;
+    ta.status = status;
+    ta.wait_limit = 4000000000LL;   // ~2 s at 2 GHz
+    const long long items = (long long)n_members * n_tiles;
+    const long long grid = items < ws->num_sms ? items : ws->num_sms;
+    train_kernel<<<(unsigned)grid, FI_THREADS, FI_SMEM, s>>>(ta);
     FOS_CUDA_TRY(cudaGetLastError());
-    FOS_CUDA_TRY(cudaEventRecord(w.ev_join, w.side));
-    FOS_CUDA_TRY(cudaStreamWaitEvent(s, w.ev_join, 0));
-    // Adam
-    AdamArgs a = layout_args(mp);
+
+    // weight gradients
+    const int splits = w.splits;
+    DwArgs da;
+    std::memset(&da, 0, sizeof(da));
+    da.k_per_split = B / splits;
+    da.ws = reg0;
+    da.region_bytes = w.region_bytes;
+    da.status = status;
+    da.wait_limit = 4000000000LL;
+    {   // layers 0 and 4 (16 columns) on the side stream
+        DwMaps mp;
+        std::memset(&mp, 0, sizeof(mp));
+        fos_status st = make_cm_map(&mp.a[0], reg0, w.dz_b[0], B, 32, n_members, w.region_bytes, 16);
+        if (st == FOS_OK) st = make_cm_map(&mp.b[0], reg0, w.x0_b, B, 2, n_members, w.region_bytes, 2);
+        if (st == FOS_OK) st = make_cm_map(&mp.a[1], reg0, w.h_b[3], B, 32, n_members, w.region_bytes, 16);
+        if (st == FOS_OK) st = make_cm_map(&mp.b[1], reg0, w.g4_b, B, 2, n_members, w.region_bytes, 2);
+        if (st != FOS_OK) return st;
+        DwArgs d = da;
+        d.n_lay = 2;
+        d.part_b[0] = w.part_b[0];
+        d.part_ld[0] = 16;
+        d.bias_b[0] = w.bias_b[0];
+        d.part_b[1] = w.part_b[4];
+        d.part_ld[1] = 16;
+        d.bias_b[1] = 0;
+        FOS_CUDA_TRY(cudaEventRecord(w.ev_fork[slot], s));
+        FOS_CUDA_TRY(cudaStreamWaitEvent(w.side[slot], w.ev_fork[slot], 0));
+        dw_kernel<16><<<dim3(2, 2 * n_members, splits), 128, DwSmem<16>::ALLOC, w.side[slot]>>>(mp, d);
+        FOS_CUDA_TRY(cudaGetLastError());
+        FOS_CUDA_TRY(cudaEventRecord(w.ev_join[slot], w.side[slot]));
+    }
+    {   // layers 1-3: dW_l = dZ_l^T H_{l-1}, two column blocks of 128
+        DwMaps mp;
+        std::memset(&mp, 0, sizeof(mp));
+        DwArgs d = da;
+        d.n_lay = 3;
+        for (int l = 1; l <= 3; ++l) {
+            fos_status st = make_cm_map(&mp.a[l - 1], reg0, w.dz_b[l], B, 32, n_members, w.region_bytes, 16);
+            if (st == FOS_OK)
+                st = make_cm_map(&mp.b[l - 1], reg0, w.h_b[l - 1], B, 32, n_members, w.region_bytes, 16);
+            if (st != FOS_OK) return st;
+            d.part_b[l - 1] = w.part_b[l];
+            d.part_ld[l - 1] = 256;
+            d.bias_b[l - 1] = w.bias_b[l];
+        }
+        dw_kernel<128><<<dim3(4, 3 * n_members, splits), 128, DwSmem<128>::ALLOC, s>>>(mp, d);
+        FOS_CUDA_TRY(cudaGetLastError());
+    }
+    FOS_CUDA_TRY(cudaStreamWaitEvent(s, w.ev_join[slot], 0));
+
+    AdamArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.po = param_offsets();
+    a.model = model;
+    a.member_bytes = LAY.bytes;
+    a.theta_b = LAY.theta_b;
+    a.m_b = LAY.m_b;
+    a.v_b = LAY.v_b;
+    a.wi_b = LAY.wi_b;
+    a.wg_b = LAY.wg_b;
+    a.step_b = LAY.step_b;
+    a.ws = reg0;
+    a.region_bytes = w.region_bytes;
     for (int l = 0; l < N_LAYERS; ++l) {
-        a.part[l] = w.part[l];
-        a.bpart[l] = w.colpart[l];
+        a.part_b[l] = w.part_b[l];
+        a.part_ld[l] = (l == 0 || l == 4) ? 16 : 256;
+        a.part_plane[l] = 256LL * a.part_ld[l];
+        if (l < 4) {
+            a.bias_b[l] = w.bias_b[l];
+            a.bias_n[l] = splits;
+            a.bias_ld[l] = 256;
+        } else {
+            a.bias_b[l] = w.bp4_b;
+            a.bias_n[l] = n_tiles * 4;
+            a.bias_ld[l] = 4;
+        }
     }
     a.splits = splits;
+    const unsigned pblocks = (unsigned)((LAY.P + 255) / 256);
     if (grad_out) {   // diagnostic: export the gradient instead of updating
-        grad_kernel<<<(unsigned)((LAY.P + 255) / 256), 256, 0, s>>>(a, LAY.P, grad_out);
+        grad_kernel<<<pblocks, 256, 0, s>>>(a, LAY.P, grad_out);
         return from_cuda(cudaGetLastError());
     }
     a.lr = lr;
@@ -1553,17 +2123,18 @@ static fos_status train_step(Workspace* ws, int slot, const MemberPtrs& mp, cons
     const double t = (double)step + 1.0;
     a.c1 = (float)(1.0 - pow(0.9, t));
     a.c2 = (float)(1.0 - pow(0.999, t));
-    a.sched = dsv.out;
-    adam_kernel<<<(unsigned)((LAY.P + 255) / 256), 256, 0, s>>>(a, LAY.P);
+    a.dev_sched = ds ? 1 : 0;
+    a.sched_b = w.sched_b;
+    a.host_step = (int)step;
+    adam_kernel<<<dim3(pblocks, (unsigned)n_members), 256, 0, s>>>(a, LAY.P);
     return from_cuda(cudaGetLastError());
 }
 
 // ----------------------------------------------------------------------- graph training
-// Many steps of every member with no host work per step: one ensemble step (for each
-// member: its schedule from its device step counter, the Adam step of train_step, its
-// loss, the status of its slot folded into the accumulated word) is captured once into a
-// CUDA graph, the members of different slots on parallel branches, and the graph is
-// launched once per step.
+// Many steps of every member with no host work per step: one ensemble step (every
+// member's schedule entry from its device step counter, train_step over all members, the
+// losses, the status folded into the accumulated word) is captured once into a CUDA graph,
+// and the graph is launched once per step.
 struct FitKey {
     void* model;
     int n_members, B, device;
@@ -1581,9 +2152,6 @@ struct FitGraph {
     cudaGraphExec_t exec = nullptr;
 };
 struct FitDev {
-    bool ready = false;
-    cudaStream_t slot_stream[TRAIN_SLOTS] = {};
-    cudaEvent_t fork = nullptr, join[TRAIN_SLOTS] = {};
     std::vector<FitGraph> graphs;
     SchedOut* table = nullptr;   // [members][cap] schedule entries, then [members] bases
     long long table_cap = 0;
@@ -1591,49 +2159,23 @@ struct FitDev {
 };
 static FitDev g_fit[64];
 
-static fos_status fit_resources(int dev) {
-    FitDev& f = g_fit[dev];
-    if (f.ready) return FOS_OK;
-    for (int i = 0; i < TRAIN_SLOTS; ++i) {
-        FOS_CUDA_TRY(cudaStreamCreateWithFlags(&f.slot_stream[i], cudaStreamNonBlocking));
-        FOS_CUDA_TRY(cudaEventCreateWithFlags(&f.join[i], cudaEventDisableTiming));
-    }
-    FOS_CUDA_TRY(cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming));
-    f.ready = true;
-    return FOS_OK;
-}
-
-// Enqueues one ensemble step on the capture stream cs (forked to the slot streams).
+// Enqueues one ensemble step on stream cs (status region 1).
 static fos_status enqueue_fit_step(Workspace* ws, const FitKey& k, cudaStream_t cs) {
-    FitDev& f = g_fit[ws->device];
-    const int slots = k.n_members < TRAIN_SLOTS ? k.n_members : TRAIN_SLOTS;
-    FOS_CUDA_TRY(cudaEventRecord(f.fork, cs));
-    for (int i = 0; i < slots; ++i) FOS_CUDA_TRY(cudaStreamWaitEvent(f.slot_stream[i], f.fork, 0));
-    for (int m = 0; m < k.n_members; ++m) {
-        const int slot = m % TRAIN_SLOTS;
-        cudaStream_t s = f.slot_stream[slot];
-        TrainWs& w = g_tws[ws->device][slot];
-        const int region = 1 + slot;
-        FOS_CUDA_TRY(cudaMemsetAsync(ws->status + ST_WORDS * region + ST_CALL, 0,
-                                     sizeof(unsigned), s));
-        MemberPtrs mp = member(k.model, m);
-        const int* bases = reinterpret_cast<const int*>(k.table + (long long)k.n_members * k.table_cap);
-        const DevSched ds{mp.step, k.table + (long long)m * k.table_cap, bases + m, w.sched};
-        const unsigned seed = (unsigned)(k.seed ^ (k.seed >> 32)) ^ (unsigned)(m * 0x9E3779B9u);
-        fos_status st = train_step(ws, slot, mp, k.feat, k.targets, k.n_rows, k.B, seed, 0,
-                                   nullptr, 1.0f, nullptr, s, &ds);
-        if (st != FOS_OK) return st;
-        if (k.loss_out)
-            FOS_CUDA_TRY(cudaMemcpyAsync(k.loss_out + m, w.loss, sizeof(float),
-                                         cudaMemcpyDeviceToDevice, s));
-        st = accumulate_async_status(ws, s, region);
-        if (st != FOS_OK) return st;
-    }
-    for (int i = 0; i < slots; ++i) {
-        FOS_CUDA_TRY(cudaEventRecord(f.join[i], f.slot_stream[i]));
-        FOS_CUDA_TRY(cudaStreamWaitEvent(cs, f.join[i], 0));
-    }
-    return FOS_OK;
+    TrainWs& w = g_tws[ws->device];
+    const int region = 1;
+    unsigned* status = ws->status + ST_WORDS * region;
+    FOS_CUDA_TRY(cudaMemsetAsync(status + ST_CALL, 0, sizeof(unsigned), cs));
+    const int* bases = reinterpret_cast<const int*>(k.table + (long long)k.n_members * k.table_cap);
+    const DevSched ds{k.table, k.table_cap, bases};
+    const unsigned seed = (unsigned)(k.seed ^ (k.seed >> 32));
+    fos_status st = train_step(ws, 0, (uint8_t*)k.model, k.n_members, 0, k.feat, k.targets,
+                               k.n_rows, k.B, seed, 0x9E3779B9u, 0, nullptr, 1.0f, nullptr, status,
+                               cs, &ds);
+    if (st != FOS_OK) return st;
+    if (k.loss_out)
+        FOS_CUDA_TRY(cudaMemcpyAsync(k.loss_out, w.loss, (size_t)k.n_members * sizeof(float),
+                                     cudaMemcpyDeviceToDevice, cs));
+    return accumulate_async_status(ws, cs, region);
 }
 
 static fos_status fit_graph(Workspace* ws, const FitKey& k, cudaGraphExec_t* out) {
@@ -1740,11 +2282,10 @@ fos_status fos_surrogate_init(void* model, int n_members, unsigned long long see
     cudaStream_t s = (cudaStream_t)stream;
     for (int k = 0; k < n_members; ++k) {
         mlp::MemberPtrs mp = mlp::member(model, k);
-        mlp::AdamArgs lay = mlp::layout_args(mp);
         FOS_CUDA_TRY(cudaMemsetAsync((char*)model + (size_t)k * mlp::LAY.bytes, 0, mlp::LAY.bytes, s));
         mlp::init_kernel<<<(unsigned)((mlp::LAY.P + 255) / 256), 256, 0, s>>>(
-            mp.theta, mp.m, mp.v, mp.wb, mp.wt, mp.wi, mp.step, (unsigned)(seed ^ (seed >> 32)),
-            (unsigned)k, lay, mlp::LAY.P);
+            mp.theta, mp.m, mp.v, mp.wi, mp.wg, mp.step, (unsigned)(seed ^ (seed >> 32)),
+            (unsigned)k, mlp::param_offsets(), mlp::LAY.P);
         FOS_CUDA_TRY(cudaGetLastError());
         FOS_CUDA_TRY(cudaMemcpyAsync(mp.stats, feat_stats, 64 * sizeof(float),
                                      cudaMemcpyHostToDevice, s));
@@ -1764,11 +2305,10 @@ fos_status fos_surrogate_load(void* model, int member, const float* theta,
     if (st != FOS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     mlp::MemberPtrs mp = mlp::member(model, member);
-    mlp::AdamArgs lay = mlp::layout_args(mp);
     FOS_CUDA_TRY(cudaMemsetAsync((char*)model + (size_t)member * mlp::LAY.bytes, 0,
                                  mlp::LAY.bytes, s));
     mlp::load_kernel<<<(unsigned)((mlp::LAY.P + 255) / 256), 256, 0, s>>>(
-        theta, mp.theta, mp.m, mp.v, mp.wb, mp.wt, mp.wi, mp.step, lay, mlp::LAY.P);
+        theta, mp.theta, mp.m, mp.v, mp.wi, mp.wg, mp.step, mlp::param_offsets(), mlp::LAY.P);
     FOS_CUDA_TRY(cudaGetLastError());
     FOS_CUDA_TRY(cudaMemcpyAsync(mp.stats, feat_stats, 64 * sizeof(float),
                                  cudaMemcpyHostToDevice, s));
@@ -1870,24 +2410,20 @@ fos_status fos_surrogate_train_step(void* model, int member, const float* featur
     fos_status st = mlp::prep(&ws);
     if (st != FOS_OK) return st;
     const int slot = member % mlp::TRAIN_SLOTS;
-    st = mlp::ensure_train_ws(ws->device, slot, batch, ws);
+    st = mlp::ensure_train_ws(ws->device, batch, mlp::TRAIN_SLOTS, ws);
     if (st != FOS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int region = 1 + slot;   // concurrent slots keep separate call words
-    FOS_CUDA_TRY(cudaMemsetAsync(ws->status + ST_WORDS * region + ST_CALL, 0, sizeof(unsigned), s));
-    mlp::MemberPtrs mp = mlp::member(model, member);
-    st = mlp::train_step(ws, slot, mp, features, targets, n_rows, batch,
-                         (unsigned)(seed ^ (seed >> 32)) ^ (unsigned)(member * 0x9E3779B9u),
-                         (unsigned)step, batch_rows, lr, grad_out, s);
+    unsigned* status = ws->status + ST_WORDS * region;
+    FOS_CUDA_TRY(cudaMemsetAsync(status + ST_CALL, 0, sizeof(unsigned), s));
+    st = mlp::train_step(ws, slot, (uint8_t*)model + (size_t)member * mlp::LAY.bytes, 1, slot,
+                         features, targets, n_rows, batch,
+                         (unsigned)(seed ^ (seed >> 32)) ^ (unsigned)(member * 0x9E3779B9u), 0u,
+                         (unsigned)step, batch_rows, lr, grad_out, status, s);
     if (st != FOS_OK) return st;
-    if (loss_out) {
-        mlp::TrainWs& w = mlp::g_tws[ws->device][slot];
-        FOS_CUDA_TRY(cudaMemcpyAsync(loss_out, w.loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
-    }
-    if (!grad_out) {   // the member's step count in the model (read by fos_surrogate_fit)
-        mlp::set_step_kernel<<<1, 32, 0, s>>>(mp.step, step + 1);
-        FOS_CUDA_TRY(cudaGetLastError());
-    }
+    if (loss_out)
+        FOS_CUDA_TRY(cudaMemcpyAsync(loss_out, mlp::g_tws[ws->device].loss + slot, sizeof(float),
+                                     cudaMemcpyDeviceToDevice, s));
     return finish_call(ws, s, flags, region);
 }
 
@@ -1906,12 +2442,7 @@ fos_status fos_surrogate_fit(void* model, int n_members, const float* features,
     Workspace* ws = nullptr;
     fos_status st = mlp::prep(&ws);
     if (st != FOS_OK) return st;
-    const int slots = n_members < mlp::TRAIN_SLOTS ? n_members : mlp::TRAIN_SLOTS;
-    for (int i = 0; i < slots; ++i) {
-        st = mlp::ensure_train_ws(ws->device, i, batch, ws);
-        if (st != FOS_OK) return st;
-    }
-    st = mlp::fit_resources(ws->device);
+    st = mlp::ensure_train_ws(ws->device, batch, n_members, ws);
     if (st != FOS_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (n_steps > 0) {
@@ -2025,8 +2556,8 @@ fos_status fos_gemm_bf16(const void* A, const void* B, float* C, int M, int N, i
         g.wait_limit = 2000000LL;
     }
     mlp::Operand a{(const mlp::bf16*)A, M, K, K}, b{(const mlp::bf16*)B, N, K, K};
-    if (N % 256 == 0) st = mlp::gemm<256, mlp::DW_PARTIAL>(a, b, splits, g, s);
-    else st = mlp::gemm<64, mlp::DW_PARTIAL>(a, b, splits, g, s);
+    if (N % 256 == 0) st = mlp::gemm<256>(a, b, splits, g, s);
+    else st = mlp::gemm<64>(a, b, splits, g, s);
     if (st != FOS_OK) return st;
     return finish_call(ws, s, flags & FOS_ASYNC);
 }

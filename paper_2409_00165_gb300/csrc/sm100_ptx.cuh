@@ -87,6 +87,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
         : "memory");
 }
+// 4-D tiled load (coordinates innermost first).
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y, int z, int w) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z), "r"(w)
+        : "memory");
+}
 // Untiled bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16),
 // completing `bytes` of transaction on the mbarrier.
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
@@ -218,12 +227,33 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t smem_addr) {
     return d;
 }
 
+// Shared-memory matrix descriptor of an MN-major BF16 operand without swizzle: core
+// matrices of 8 rows along K x 16 bytes (8 consecutive M or N elements), 128 bytes each;
+// `k_step` bytes between core matrices adjacent in K (the leading byte offset) and
+// `mn_step` bytes between core matrices adjacent in M or N (the stride byte offset),
+// descriptor version 1, swizzle mode 0.
+__device__ __forceinline__ uint64_t desc_mn_plain(uint32_t smem_addr, uint32_t k_step,
+                                                  uint32_t mn_step) {
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((k_step >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((mn_step >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
 // Instruction descriptor of tcgen05.mma.kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 (bits 17-22),
 // M >> 4 (bits 24-28).
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
+}
+
+// The same with the operands' major modes: bit 15 set for an MN-major A, bit 16 for an
+// MN-major B.
+__host__ __device__ constexpr uint32_t idesc_bf16_major(int M, int N, bool a_mn, bool b_mn) {
+    return idesc_bf16(M, N) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16);
 }
 
 }  // namespace sm100
