@@ -11,13 +11,14 @@
 // pass, the softmax cross-entropy gradient and the backward pass down to the output
 // gradient of layer 0, with every activation and gradient on chip; it writes to global
 // memory only what the weight gradients need (each layer's input and output gradient) and
-// GELU'(Z), which it reads back itself.  Those arrays are "chunk-major", X[c/8][row][c%8]:
-// one 16-byte store per thread and 8 columns, 512 contiguous bytes per warp, and each
-// 8-row x 8-column block a 128-byte core matrix of the tensor cores' MN-major operand
-// layout.  dw_kernel then forms every weight gradient dW_l = dZ_l^T H_{l-1} as a split-K
-// tcgen05 product over the batch with both operands MN-major (TMA copies of the chunk-
-// major arrays), and the bias gradients as the same product with a column of ones.  Adam
-// sums the split partials in a fixed order and rewrites the BF16 weight images.
+// GELU'(Z), which it reads back itself.  Those arrays are row-blocked and chunk-major,
+// X[row/64][c/8][row%64][c%8]: one 16-byte store per thread and 8 columns, 512 contiguous
+// bytes per warp; each 8-row x 8-column block is a 128-byte core matrix of the tensor
+// cores' MN-major operand layout, and the 64 rows x 128 columns a product stage needs are
+// 16 contiguous KB.  dw_kernel then forms every weight gradient dW_l = dZ_l^T H_{l-1} as a
+// split-K tcgen05 product over the batch with both operands MN-major (one bulk copy per
+// operand and stage), and the bias gradients as the same product with a column of ones.
+// Adam sums the split partials in a fixed order and rewrites the BF16 weight images.
 //
 // gemm_kernel is a plain C = A B^T product (K-major BF16 operands staged by TMA with
 // 128-byte swizzle through an mbarrier ring, FP32 accumulators in tensor memory), kept
@@ -65,20 +66,18 @@ __host__ __device__ constexpr int real_in(int l) { return l == 0 ? N_FEAT : HID;
 // Per member (all offsets in elements of the named type, from the member base):
 //   theta  fp32 [P]  : W_0 | b_0 | W_1 | b_1 | ... | W_4 | b_4  (W_l row-major [out][in])
 //   adam_m fp32 [P], adam_v fp32 [P]
-//   wg     bf16      : W_l^T (l = 4, 3, 2, 1) as shared-memory images for the backward
-//                      pass of train_kernel (see wg_index)
 //   stats  fp32 [64] : mean[16] | std[16] | lo[16] | hi[16] of the raw features
 //   step   int32 [4]
-//   wi     bf16      : the weights as shared-memory images for the forward passes of the
-//                      fused kernels (see img_index), one contiguous block per pipeline stage
+//   wi     bf16      : the weights as shared-memory images for the fused kernels (see
+//                      img_index), one contiguous block per pipeline stage
 struct Layout {
     long long w_off[N_LAYERS], b_off[N_LAYERS], P;
-    size_t theta_b, m_b, v_b, wg_b, stats_b, step_b, wi_b, bytes;
+    size_t theta_b, m_b, v_b, stats_b, step_b, wi_b, bytes;
 };
 
-// Weight image: the B operands of the fused kernels' forward pass, already in the
-// 128-byte-swizzled K-major layout a stage of shared memory holds, so that one untiled
-// bulk copy fills a stage (32 KB).  Layer 0 is one stage: all 256 output rows x 64 inputs
+// Weight image: the B operands of the fused kernels, already in the 128-byte-swizzled
+// K-major layout a stage of shared memory holds, so that one untiled bulk copy fills a
+// stage (32 KB).  Layer 0 is one stage: all 256 output rows x 64 inputs
 // (9 real).  Layers 1-3 are four stages each, (output half h, input pair j) in the order
 // 2h + j: 128 output rows x inputs 128 j .. +127, as two k blocks of 128 x 64 (16 KB).
 // Layer 4 keeps its first 16 output rows (3 real) as 4 blocks of 16 x 64 (2 KB), one per k
@@ -98,8 +97,12 @@ __host__ __device__ constexpr long long swz64(int n, int c) {
     return (long long)n * 64 + ((((c >> 3) ^ (n & 7)) << 3) | (c & 7));
 }
 
-// Element index in the forward image of weight (l, o, i), or -1 when the image leaves it
-// out.
+// The backward pass multiplies an output gradient dZ_l [rows][out] by W_l: its B operand
+// is W_l^T [in][out] with K = out, and the image, whose rows are outputs and whose 128-byte
+// rows hold 64 consecutive inputs, is exactly that operand in the MN-major 128-byte-
+// swizzled layout (8-row groups 1024 bytes apart along K, 64-input blocks along N).
+//
+// Element index in the image of weight (l, o, i), or -1 when the image leaves it out.
 __host__ __device__ inline long long img_index(int l, int o, int i) {
     const int kb = i >> 6, c = i & 63;
     if (l == 4) {
@@ -109,24 +112,6 @@ __host__ __device__ inline long long img_index(int l, int o, int i) {
     if (l == 0) return img_off(l) + swz64(o, c);
     return img_off(l) + (long long)((o >> 7) * 2 + (kb >> 1)) * IMG_BLK +
            (long long)(kb & 1) * IMG_HALF_KB + swz64(o & 127, c);
-}
-
-// Backward image: the B operands of the backward pass, which multiplies an output
-// gradient dZ_l [rows][out] by W_l, i.e. by B = W_l^T [in][out] (row n = input i, k =
-// output o).  13 stages of 32 KB in the order the backward pass uses them: W_4^T (256
-// rows x 64 k, the 3 real outputs in k 0-2; the pass multiplies K = 16 of them), then
-// W_3^T, W_2^T, W_1^T as four stages each, (input half h, output pair j) as in the
-// forward image.  Layer 0 has no backward product (no gradient for the features).
-constexpr long long WG_ELEMS = 13 * IMG_BLK;
-__host__ __device__ constexpr long long wg_off(int l) {
-    return l == 4 ? 0 : (1 + 4 * (3 - l)) * IMG_BLK;
-}
-__host__ __device__ inline long long wg_index(int l, int o, int i) {
-    if (l == 0) return -1;
-    if (l == 4) return o < 64 ? wg_off(4) + swz64(i, o) : -1;
-    const int kb = o >> 6, c = o & 63;
-    return wg_off(l) + (long long)((i >> 7) * 2 + (kb >> 1)) * IMG_BLK +
-           (long long)(kb & 1) * IMG_HALF_KB + swz64(i & 127, c);
 }
 
 static Layout make_layout() {
@@ -144,7 +129,6 @@ static Layout make_layout() {
     L.theta_b = o; o = al(o + (size_t)p * 4);
     L.m_b = o;     o = al(o + (size_t)p * 4);
     L.v_b = o;     o = al(o + (size_t)p * 4);
-    L.wg_b = o;    o = al(o + (size_t)WG_ELEMS * 2);
     L.stats_b = o; o = al(o + 64 * 4);
     L.step_b = o;  o = al(o + 16);
     L.wi_b = o;    o = al(o + (size_t)IMG_ELEMS * 2);
@@ -155,7 +139,7 @@ static const Layout LAY = make_layout();
 
 struct MemberPtrs {
     float *theta, *m, *v, *stats;
-    bf16 *wg, *wi;
+    bf16* wi;
     int* step;
 };
 static MemberPtrs member(void* model, int k) {
@@ -164,7 +148,6 @@ static MemberPtrs member(void* model, int k) {
     p.theta = (float*)(base + LAY.theta_b);
     p.m = (float*)(base + LAY.m_b);
     p.v = (float*)(base + LAY.v_b);
-    p.wg = (bf16*)(base + LAY.wg_b);
     p.stats = (float*)(base + LAY.stats_b);
     p.step = (int*)(base + LAY.step_b);
     p.wi = (bf16*)(base + LAY.wi_b);
@@ -809,6 +792,22 @@ struct SchedOut {
 // backward image (13 items) of the item's member.  The batch rows are drawn in the
 // kernel: the caller's rows, or a hash of (seed, step, row) scaled to the data set.
 constexpr int FT_ITEMS = FI_ITEMS + 13;   // ring items per work item
+// Raw feature rows of the next work item (9 features and 3 targets per row), staged in
+// shared memory while the current item runs its backward pass: two buffers after the
+// barriers.
+constexpr int FT_ROW_FLOATS = 12;
+constexpr int FT_XBUF_BYTES = 128 * FT_ROW_FLOATS * 4;
+constexpr int FT_XBUF_OFF = (FI_SMEM + 32 + 15) & ~15;   // after 4 more barriers
+constexpr int FT_SMEM = FT_XBUF_OFF + 2 * FT_XBUF_BYTES;
+static_assert(FT_SMEM <= 227 * 1024, "shared memory of the fused training kernel");
+// Roles: infer_kernel's 16 epilogue warps, copy warp and MMA warp, and a staging warp
+// that stages each work item's parameters and rows ahead of it.  19 warps keep the
+// register cap of 18 (five warps on a sub-partition: 96 registers a thread).
+constexpr int FT_STAGE_WARP = FI_EPI_WARPS + 2;
+constexpr int FT_THREADS = 32 * (FI_EPI_WARPS + 3);
+// The staged-item barriers (full and empty per buffer) follow infer_kernel's shared
+// memory, whose barrier area ends with the tensor-memory slot and the abort flag.
+static_assert(FI_BAR_BYTES >= 8 * FI_NBARS + 8, "tmem slot and abort flag after the barriers");
 
 struct TrainArgs {
     const float* feat;            // raw features [n_rows][9]
@@ -819,7 +818,7 @@ struct TrainArgs {
     unsigned seed, seed_mul;      // member k draws with seed ^ (k * seed_mul)
     unsigned step;                // the draw's step without a device schedule
     const uint8_t* model;
-    size_t member_bytes, theta_b, stats_b, wi_b, wg_b, step_b;
+    size_t member_bytes, theta_b, stats_b, wi_b, step_b;
     long long b_off[N_LAYERS];
     // device schedule (graph-captured training): member k's step is its step counter,
     // and table[k * table_cap + step - table_base[k]] is copied to the member's slot
@@ -870,7 +869,7 @@ __device__ __forceinline__ long long draw_row(unsigned seed, unsigned step, int 
     return (long long)(((unsigned long long)h * (unsigned long long)n_rows) >> 32);
 }
 
-__global__ void __launch_bounds__(FI_THREADS, 1) train_kernel(TrainArgs A) {
+__global__ void __launch_bounds__(FT_THREADS, 1) train_kernel(TrainArgs A) {
     extern __shared__ __align__(1024) uint8_t ft_smem[];
     const uint32_t base = smem_u32(ft_smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -885,6 +884,9 @@ __global__ void __launch_bounds__(FI_THREADS, 1) train_kernel(TrainArgs A) {
     uint8_t* bars_g = ft_smem + FI_STAGES * FI_SLOT + FI_PAR_BYTES;
     volatile uint32_t* tslot_ptr = reinterpret_cast<volatile uint32_t*>(bars_g + 8 * FI_NBARS);
     volatile int& abort_flag = *reinterpret_cast<volatile int*>(bars_g + 8 * FI_NBARS + 4);
+    const uint32_t bar_sf = base + FI_SMEM;     // 2: staged item in buffer b (32 arrivals)
+    const uint32_t bar_se = bar_sf + 16;        // 2: buffer b read (one arrival per epilogue warp)
+    float* xbuf = reinterpret_cast<float*>(ft_smem + FT_XBUF_OFF);
 
     if ((base & 1023u) != 0u) {   // the swizzled stages need 1024-byte alignment
         if (threadIdx.x == 0) atomicOr(&A.status[ST_CALL], DEV_RANGE);
@@ -900,6 +902,10 @@ __global__ void __launch_bounds__(FI_THREADS, 1) train_kernel(TrainArgs A) {
             mbar_init(bar_a + 8 * h, 32 * FI_EPI_WARPS);
         }
         mbar_init(bar_p, 32 * FI_EPI_WARPS);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bar_sf + 8 * b, 32);
+            mbar_init(bar_se + 8 * b, FI_EPI_WARPS);
+        }
         abort_flag = 0;
         fence_barrier_init();
     }
@@ -938,8 +944,19 @@ __global__ void __launch_bounds__(FI_THREADS, 1) train_kernel(TrainArgs A) {
                     fi_item(q, layer, blk, off, bytes);
                     src = mb + A.wi_b + (size_t)off * 2;
                 } else {
-                    src = mb + A.wg_b + (size_t)(q - FI_ITEMS) * IMG_BLK * 2;
-                    bytes = FI_SLOT;
+                    // backward: layer 4 whole (8 KB), then layers 3, 2, 1, four stages each
+                    // in the order (output rows 0-127, inputs 0-127), (128-255, 0-127),
+                    // (0-127, 128-255), (128-255, 128-255): input half h of the product
+                    // takes the two stages that hold inputs 128 h .. +127
+                    const int qb = q - FI_ITEMS;
+                    if (qb == 0) {
+                        src = mb + A.wi_b + (size_t)img_off(4) * 2;
+                        bytes = (uint32_t)(4 * IMG_L4_BLK * 2);
+                    } else {
+                        const int l = 3 - (qb - 1) / 4, p = (qb - 1) & 3;
+                        src = mb + A.wi_b + (size_t)(img_off(l) + (long long)((p >> 1) | ((p & 1) << 1)) * IMG_BLK) * 2;
+                        bytes = FI_SLOT;
+                    }
                 }
                 if (!(A.test_stall && issued == 0)) {
                     mbar_arrive_expect_tx(bar_full + 8 * slot, bytes);
@@ -976,6 +993,7 @@ __global__ void __launch_bounds__(FI_THREADS, 1) train_kernel(TrainArgs A) {
             bool ok = true;
             const uint64_t dring = desc_sw128(ring);
             constexpr uint32_t ID128 = idesc_bf16(128, 128), ID16 = idesc_bf16(128, 16);
+            constexpr uint32_t ID128_BMN = idesc_bf16_major(128, 128, false, true);
             auto take = [&](int& s) {
                 if (!mbar_wait(bar_full + 8 * slot, phase, A.wait_limit)) return false;
                 s = slot;
@@ -996,9 +1014,9 @@ __global__ void __launch_bounds__(FI_THREADS, 1) train_kernel(TrainArgs A) {
                 for (int s = 0; s < 9 && ok; ++s) {
                     const uint32_t ta = tmem + FI_ABUF + (uint32_t)((s & 1) * 128);
                     int st = 0;
-                    if (s == 0 || s == 5) {
-                        // K = 16 (the features; the output gradient) x 256 outputs: half h
-                        // of the stage's 256 rows starts 16 KB into it
+                    if (s == 0) {
+                        // K = 16 (the features) x 256 outputs: half h of the stage's 256 rows
+                        // starts 16 KB into it
                         if (!(ok = take(st))) break;
                         ok = wait_a(0) && wait_a(1);
                         if (ok)
@@ -1022,6 +1040,42 @@ __global__ void __launch_bounds__(FI_THREADS, 1) train_kernel(TrainArgs A) {
                         mma_commit(bar_empty + 8 * st);
                         if (ok)
                             for (int h = 0; h < 2; ++h) mma_commit(bar_acc + 8 * h);
+                    } else if (s == 5) {
+                        // G (K = 16 outputs) x W_4 -> 256 inputs: the layer-4 stage read
+                        // MN-major, input half h = its 2 KB blocks 2h, 2h + 1 (8-output-row
+                        // groups 1 KB apart, 64-input blocks 2 KB apart)
+                        if (!(ok = take(st))) break;
+                        ok = wait_a(0) && wait_a(1);
+                        if (ok)
+                            for (int h = 0; h < 2; ++h) {
+                                mma_bf16_ts(tmem + FI_ACC + (uint32_t)(h * 128), ta,
+                                            desc_sw128_mn(ring + st * FI_SLOT + h * 4096, 2048, 1024),
+                                            ID128_BMN, 0u);
+                                mma_commit(bar_acc + 8 * h);
+                            }
+                        mma_commit(bar_empty + 8 * st);
+                    } else if (s > 5) {
+                        // dZ (K = 256 outputs) x W_l -> 256 inputs, input half h from the
+                        // stages (outputs 128 g .. +127, inputs 128 h .. +127), g = 0, 1,
+                        // read MN-major: 16 output rows (2048 bytes) per MMA, the two 64-input
+                        // k blocks of the stage 16 KB apart
+                        for (int h = 0; h < 2 && ok; ++h) {
+                            for (int g = 0; g < 2 && ok; ++g) {
+                                if (!(ok = take(st))) break;
+                                if (h == 0 && !(ok = wait_a(g))) {
+                                    mma_commit(bar_empty + 8 * st);
+                                    break;
+                                }
+#pragma unroll
+                                for (int kk = 0; kk < 8; ++kk)
+                                    mma_bf16_ts(tmem + FI_ACC + (uint32_t)(h * 128),
+                                                ta + (uint32_t)(g * 64 + kk * 8),
+                                                desc_sw128_mn(ring + st * FI_SLOT + kk * 2048, 16384, 1024),
+                                                ID128_BMN, (g > 0 || kk > 0) ? 1u : 0u);
+                                mma_commit(bar_empty + 8 * st);
+                            }
+                            if (ok) mma_commit(bar_acc + 8 * h);
+                        }
                     } else {
                         // stage (h, j): output rows 128 h .. +127 x k blocks 2j, 2j + 1
                         for (int h = 0; h < 2 && ok; ++h) {
@@ -1061,79 +1115,131 @@ __global__ void __launch_bounds__(FI_THREADS, 1) train_kernel(TrainArgs A) {
             }
         }
         __syncwarp();
+    } else if (warp == FT_STAGE_WARP) {
+        // ------------------------------------------------------------ staging
+        // Work item n into buffer n mod 2 once the epilogue warps have read the item two
+        // before it: member k's biases (hidden layers halved, for the GELU in z/2) and
+        // feature statistics into parameter slot b, the raw features and targets of the
+        // item's 128 rows into row buffer b.
+        bool ok = true;
+        long long n = 0;
+        for (long long it = blockIdx.x; it < n_items && ok && !abort_flag; it += gridDim.x, ++n) {
+            const int b = (int)(n & 1);
+            if (n >= 2 && !__all_sync(0xffffffffu, mbar_wait_sleep(bar_se + 8 * b,
+                                                                    (uint32_t)((n - 2) >> 1) & 1u,
+                                                                    A.wait_limit))) {
+                ok = false;
+                break;
+            }
+            const int kn = (int)(it / A.n_tiles);
+            const int tn = (int)(it - (long long)kn * A.n_tiles);
+            const uint8_t* mbn = A.model + (size_t)kn * A.member_bytes;
+            const float* th = reinterpret_cast<const float*>(mbn + A.theta_b);
+            const float* stt = reinterpret_cast<const float*>(mbn + A.stats_b);
+            float* dst = par + b * FI_PAR_FLOATS;
+            {   // all 41 loads of a lane in flight together, then the stores
+                static_assert(FI_PAR_FLOATS % 32 == 0, "parameter staging: whole lanes");
+                float v[FI_PAR_FLOATS / 32];
+#pragma unroll
+                for (int q = 0; q < FI_PAR_FLOATS / 32; ++q) {
+                    const int i = q * 32 + lane;
+                    v[q] = 0.f;
+                    if (i < N_LAYERS * 256) {
+                        const int l = i >> 8, c = i & 255;
+                        if (c < real_out(l)) v[q] = __ldg(th + A.b_off[l] + c) * (l < 4 ? 0.5f : 1.0f);
+                    } else {
+                        v[q] = __ldg(stt + (i - N_LAYERS * 256));   // mean[16] | std[16]
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < FI_PAR_FLOATS / 32; ++q) dst[q * 32 + lane] = v[q];
+            }
+            {   // rows q * 32 + lane: the 48 loads of a lane in flight together
+                const unsigned stepn =
+                    A.dev_step ? (unsigned)*reinterpret_cast<const int*>(mbn + A.step_b) : A.step;
+                long long src[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const long long rown = (long long)tn * 128 + q * 32 + lane;
+                    src[q] = A.rows ? (long long)A.rows[rown]
+                                    : draw_row(A.seed ^ ((unsigned)kn * A.seed_mul), stepn, (int)rown,
+                                               A.n_rows);
+                }
+                float xv[4][FT_ROW_FLOATS];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                    for (int f = 0; f < N_FEAT; ++f) xv[q][f] = A.feat[src[q] * N_FEAT + f];
+#pragma unroll
+                    for (int c = 0; c < N_OUT; ++c) xv[q][N_FEAT + c] = A.targets[src[q] * 3 + c];
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float* xr = xbuf + (b * 128 + q * 32 + lane) * FT_ROW_FLOATS;
+#pragma unroll
+                    for (int c = 0; c < FT_ROW_FLOATS; c += 4)
+                        *reinterpret_cast<float4*>(xr + c) =
+                            make_float4(xv[q][c], xv[q][c + 1], xv[q][c + 2], xv[q][c + 3]);
+                }
+            }
+            mbar_arrive(bar_sf + 8 * b);
+            if (n == 0 && A.dev_step && blockIdx.x == 0) {
+                // the schedule entry of each member's step, for Adam
+                for (int km = lane; km < A.n_members; km += 32) {
+                    const int g = *reinterpret_cast<const int*>(A.model + (size_t)km * A.member_bytes +
+                                                                A.step_b);
+                    *reinterpret_cast<SchedOut*>(A.ws + (size_t)km * A.region_bytes + A.sched_b) =
+                        A.table[(long long)km * A.table_cap + (g - A.table_base[km])];
+                }
+            }
+        }
+        if (!ok) {
+            atomicOr(&A.status[ST_CALL], DEV_TIMEOUT);
+            abort_flag = 1;
+        }
     } else {
         // ------------------------------------------------------------ epilogue warps
         const int lq = warp & 3, cg = warp >> 2;            // TMEM lane quarter, column group
         const int r = lq * 32 + lane;                       // tile row = TMEM lane
         const uint32_t trow = tmem + ((uint32_t)(lq * 32) << 16);
         const bool lead = cg == 0;                          // builds X0, the output layer
-        const int et = threadIdx.x;                         // 0 .. 32 * FI_EPI_WARPS - 1
-        const long long Bp = (long long)A.n_tiles * 128;
         const float inv_b = 1.0f / (float)A.B;
-        uint32_t pp = 0, pacc = 0;
+        uint32_t pacc = 0;
         bool ok = true;
-        if (A.dev_step && et == 0) {   // the schedule entry of each member's step, for Adam
-            for (int k = 0; k < A.n_members; ++k) {
-                const int g = *reinterpret_cast<const int*>(A.model + (size_t)k * A.member_bytes +
-                                                            A.step_b);
-                *reinterpret_cast<SchedOut*>(A.ws + (size_t)k * A.region_bytes + A.sched_b) =
-                    A.table[(long long)k * A.table_cap + (g - A.table_base[k])];
-            }
-        }
-        long long n_staged = 0;
-        for (long long it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+        long long n_done = 0;
+        for (long long it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++n_done) {
             const int k = (int)(it / A.n_tiles);
             const int t = (int)(it - (long long)k * A.n_tiles);
-            const uint8_t* mb = A.model + (size_t)k * A.member_bytes;
             uint8_t* reg = A.ws + (size_t)k * A.region_bytes;
             const long long row = (long long)t * 128 + r;   // batch row (B is a multiple of 128)
-            // 16-byte block (chunk, this row) of a chunk-major array at byte offset off
-            auto cm = [&](size_t off, int chunk) {
-                return reinterpret_cast<uint4*>(reg + off + ((size_t)chunk * Bp + row) * 16);
+            // 16-byte block (chunk, this row) of a row-blocked chunk-major array of nc
+            // chunks at byte offset off
+            auto cm = [&](size_t off, int nc, int chunk) {
+                return reinterpret_cast<uint4*>(
+                    reg + off + (((size_t)(row >> 6) * nc + chunk) * 64 + (row & 63)) * 16);
             };
-            // member k's biases (hidden layers halved, for the GELU in z/2) and feature
-            // statistics into parameter slot n_staged mod 2: every epilogue thread has
-            // passed the staging barrier of the item in between, so none still reads it
-            float* pk_par = par + (n_staged & 1) * FI_PAR_FLOATS;
-            {
-                const float* th = reinterpret_cast<const float*>(mb + A.theta_b);
-                const float* stt = reinterpret_cast<const float*>(mb + A.stats_b);
-                for (int i = et; i < FI_PAR_FLOATS; i += 32 * FI_EPI_WARPS) {
-                    float v;
-                    if (i < N_LAYERS * 256) {
-                        const int l = i >> 8, c = i & 255;
-                        v = (c < real_out(l)) ? __ldg(th + A.b_off[l] + c) : 0.f;
-                        if (l < 4) v *= 0.5f;
-                    } else {
-                        v = __ldg(stt + (i - N_LAYERS * 256));   // mean[16] | std[16]
-                    }
-                    pk_par[i] = v;
-                }
-                mbar_arrive(bar_p);
-                if (!__all_sync(0xffffffffu, mbar_wait_sleep(bar_p, pp, A.wait_limit))) ok = false;
-                pp ^= 1u;
-                ++n_staged;
+            const int slot = (int)(n_done & 1);
+            const float* pk_par = par + slot * FI_PAR_FLOATS;
+            if (!__all_sync(0xffffffffu, mbar_wait_sleep(bar_sf + 8 * slot, (uint32_t)(n_done >> 1) & 1u,
+                                                         A.wait_limit))) {
+                ok = false;
+                break;
             }
-            if (!ok) break;
             float y[N_OUT] = {0.f, 0.f, 0.f};
             if (lead) {   // layer-0 input: standardised features in k 0-8, zeros to 15
-                const unsigned step =
-                    A.dev_step ? (unsigned)*reinterpret_cast<const int*>(mb + A.step_b) : A.step;
-                const long long src = A.rows ? (long long)A.rows[row]
-                                             : draw_row(A.seed ^ ((unsigned)k * A.seed_mul), step,
-                                                        (int)row, A.n_rows);
                 const float* st = pk_par + N_LAYERS * 256;
+                const float* xr = xbuf + (slot * 128 + r) * FT_ROW_FLOATS;
                 float z[N_FEAT];
 #pragma unroll
-                for (int f = 0; f < N_FEAT; ++f) z[f] = (A.feat[src * N_FEAT + f] - st[f]) / st[16 + f];
+                for (int f = 0; f < N_FEAT; ++f) z[f] = (xr[f] - st[f]) / st[16 + f];
 #pragma unroll
-                for (int c = 0; c < N_OUT; ++c) y[c] = A.targets[src * 3 + c];
+                for (int c = 0; c < N_OUT; ++c) y[c] = xr[N_FEAT + c];
                 const uint32_t pk[8] = {pack_bf16(z[0], z[1]), pack_bf16(z[2], z[3]),
                                         pack_bf16(z[4], z[5]), pack_bf16(z[6], z[7]),
                                         pack_bf16(z[8], 0.f), 0u, 0u, 0u};
                 tmem_st8(trow + FI_ABUF, pk);
-                *cm(A.x0_b, 0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                *cm(A.x0_b, 1) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                *cm(A.x0_b, 2, 0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *cm(A.x0_b, 2, 1) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                 tmem_wait_st();
             }
             tc_fence_before();
@@ -1170,10 +1276,10 @@ __global__ void __launch_bounds__(FI_THREADS, 1) train_kernel(TrainArgs A) {
                             }
                             tmem_st8(dst + (uint32_t)(h * 64 + cg * 16 + c16 / 2), pk);
                             const int ch = (h * 128 + cg * 32 + c16) >> 3;
-                            *cm(A.h_b[s], ch) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                            *cm(A.h_b[s], ch + 1) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                            *cm(A.gp_b[s], ch) = make_uint4(gk[0], gk[1], gk[2], gk[3]);
-                            *cm(A.gp_b[s], ch + 1) = make_uint4(gk[4], gk[5], gk[6], gk[7]);
+                            *cm(A.h_b[s], 32, ch) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                            *cm(A.h_b[s], 32, ch + 1) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                            *cm(A.gp_b[s], 32, ch) = make_uint4(gk[0], gk[1], gk[2], gk[3]);
+                            *cm(A.gp_b[s], 32, ch + 1) = make_uint4(gk[4], gk[5], gk[6], gk[7]);
                         }
                         tmem_wait_st();
                         tc_fence_before();
@@ -1212,8 +1318,8 @@ __global__ void __launch_bounds__(FI_THREADS, 1) train_kernel(TrainArgs A) {
                         const uint32_t pk[8] = {pack_bf16(gq[0], gq[1]), pack_bf16(gq[2], 0.f),
                                                 0u, 0u, 0u, 0u, 0u, 0u};
                         tmem_st8(dst, pk);
-                        *cm(A.g4_b, 0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                        *cm(A.g4_b, 1) = make_uint4(0u, 0u, 0u, 0u);
+                        *cm(A.g4_b, 2, 0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        *cm(A.g4_b, 2, 1) = make_uint4(0u, 0u, 0u, 0u);
                         // per-warp sums: the bias gradient of layer 4 (column sums of G over
                         // the warp's 32 rows) and the loss
                         li *= inv_b;
@@ -1233,13 +1339,16 @@ __global__ void __launch_bounds__(FI_THREADS, 1) train_kernel(TrainArgs A) {
                     tc_fence_before();
                     mbar_arrive(bar_a);
                     mbar_arrive(bar_a + 8);
+                    // this item's parameters and rows are no longer read: buffer free
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar_se + 8 * slot);
                 } else {
                     const int j = 8 - s;   // this step's output gradient dZ_j
                     for (int h = 0; h < 2; ++h) {
                         const int ch = (h * 128 + cg * 32) >> 3;   // this thread's 4 chunks
                         uint4 gp[4];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) gp[q] = *cm(A.gp_b[j], ch + q);
+                        for (int q = 0; q < 4; ++q) gp[q] = *cm(A.gp_b[j], 32, ch + q);
                         if (!__all_sync(0xffffffffu, mbar_wait_sleep(bar_acc + 8 * h, pacc, A.wait_limit))) {
                             ok = false;
                             break;
@@ -1263,8 +1372,16 @@ __global__ void __launch_bounds__(FI_THREADS, 1) train_kernel(TrainArgs A) {
                                 pk[e] = pack_bf16(d.x, d.y);
                             }
                             if (s < 8) tmem_st8(dst + (uint32_t)(h * 64 + cg * 16 + c16 / 2), pk);
-                            *cm(A.dz_b[j], ch + c16 / 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                            *cm(A.dz_b[j], ch + c16 / 8 + 1) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                            *cm(A.dz_b[j], 32, ch + c16 / 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                            *cm(A.dz_b[j], 32, ch + c16 / 8 + 1) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                        }
+                        // GELU'(Z_j) of these rows and columns is dead: its 16 L2 lines (the
+                        // warp's 4 chunks x 512 bytes) go without a write-back
+                        __syncwarp();
+                        if (lane < 16) {
+                            const long long row0 = row - lane + (lane & 3) * 8;
+                            l2_discard(reg + A.gp_b[j] +
+                                       (((size_t)(row0 >> 6) * 32 + ch + (lane >> 2)) * 64 + (row0 & 63)) * 16);
                         }
                         if (s < 8) {
                             tmem_wait_st();
@@ -1286,16 +1403,16 @@ __global__ void __launch_bounds__(FI_THREADS, 1) train_kernel(TrainArgs A) {
 
 // ----------------------------------------------------------------- weight gradients
 // Split-K partials of the weight gradients, C[split][m][n] = sum over the split's batch
-// rows b of A[b][m] B[b][n], where A and B are train_kernel's chunk-major arrays: dW_l =
-// dZ_l^T H_{l-1} (H_{-1} = the features) for l = 0..3, and dW_4^T = H_3^T G.  Both
-// operands are MN-major without swizzle: a core matrix is 8 batch rows x 8 columns (16
-// bytes per row), core matrices consecutive in b lie 128 bytes apart (the descriptor's
+// rows b of A[b][m] B[b][n], where A and B are train_kernel's row-blocked chunk-major
+// arrays: dW_l = dZ_l^T H_{l-1} (H_{-1} = the features) for l = 0..3, and dW_4^T = H_3^T G.
+// Both operands are MN-major without swizzle: a core matrix is 8 batch rows x 8 columns
+// (16 bytes per row), core matrices consecutive in b lie 128 bytes apart (the descriptor's
 // leading byte offset) and those consecutive in m or n DW_BK * 16 bytes apart (its stride
-// byte offset); a 4-D TMA box {8 columns, DW_BK rows, column groups, member} lands in
-// shared memory in exactly that order.  A CTA computes the 128 x NT tile (m tile, column
-// block) of one (member, layer, split); with a bias partial, the CTAs of column block 0
-// also form sum_b A[b][m] (the bias gradient) as the product with a K-major tile whose
-// row 0 is ones, in 16 more accumulator columns.
+// byte offset), which is the order a 64-row block of the arrays already has: a stage is
+// one bulk copy per operand.  A CTA computes the 128 x NT tile (m tile, column block) of
+// one (member, layer, split); with a bias partial, the CTAs of column block 0 also form
+// sum_b A[b][m] (the bias gradient) as the product with a K-major tile whose row 0 is
+// ones, in 16 more accumulator columns.
 constexpr int DW_BK = 64;
 constexpr int DW_STAGES = 3;
 constexpr int DW_LAYS = 3;
@@ -1303,16 +1420,15 @@ constexpr int DW_LAYS = 3;
 struct DwArgs {
     int n_lay;                  // layers in this launch; blockIdx.y = member * n_lay + lay
     int k_per_split;            // multiple of DW_BK; blockIdx.z = split
-    uint8_t* ws;                // member k's region at ws + k * region_bytes
+    const uint8_t* ws;          // member k's region at ws + k * region_bytes
     size_t region_bytes;
-    size_t part_b[DW_LAYS];     // partial [split][256][part_ld] FP32 (byte offset in the region)
+    size_t a_b[DW_LAYS], b_b[DW_LAYS];  // the operands' arrays (byte offsets in the region)
+    int a_chunks[DW_LAYS], b_chunks[DW_LAYS];
+    size_t part_b[DW_LAYS];     // partial [split][256][part_ld] FP32
     int part_ld[DW_LAYS];
     size_t bias_b[DW_LAYS];     // bias partial [split][256] FP32, or 0: none
     unsigned* status;
     long long wait_limit;
-};
-struct DwMaps {
-    CUtensorMap a[DW_LAYS], b[DW_LAYS];
 };
 
 template <int NT>
@@ -1328,8 +1444,7 @@ struct DwSmem {
 };
 
 template <int NT>
-__global__ void __launch_bounds__(128, 1)
-    dw_kernel(const __grid_constant__ DwMaps maps, const __grid_constant__ DwArgs args) {
+__global__ void __launch_bounds__(128, 1) dw_kernel(const __grid_constant__ DwArgs args) {
     using S = DwSmem<NT>;
     static_assert(S::STAGE % 1024 == 0 && NT + 16 <= 256, "stage alignment, tensor memory");
     extern __shared__ uint8_t smem_raw[];
@@ -1349,8 +1464,10 @@ __global__ void __launch_bounds__(128, 1)
     const int split = blockIdx.z;
     const int k0 = split * args.k_per_split, n_k = args.k_per_split / DW_BK;
     const bool bias = args.bias_b[lay] != 0 && nb == 0;
-    const CUtensorMap* ta = &maps.a[lay];
-    const CUtensorMap* tb = &maps.b[lay];
+    const uint8_t* reg = args.ws + (size_t)k * args.region_bytes;
+    const uint8_t* ga = reg + args.a_b[lay] + (size_t)(mt * 16) * 1024;
+    const uint8_t* gb = reg + args.b_b[lay] + (size_t)(nb * (NT / 8)) * 1024;
+    const size_t a_blk = (size_t)args.a_chunks[lay] * 1024, b_blk = (size_t)args.b_chunks[lay] * 1024;
     constexpr uint32_t ID_W = idesc_bf16_major(128, NT, true, true);
     constexpr uint32_t ID_B = idesc_bf16_major(128, 16, true, false);
 
@@ -1366,8 +1483,6 @@ __global__ void __launch_bounds__(128, 1)
         }
         mbar_init(bar_done, 1);
         fence_barrier_init();
-        tma_prefetch_desc(ta);
-        tma_prefetch_desc(tb);
     }
     __syncwarp();
     if (warp == 0) tmem_alloc(tslot, S::TCOLS);
@@ -1383,9 +1498,10 @@ __global__ void __launch_bounds__(128, 1)
             const int s = j % DW_STAGES;
             const uint32_t a_s = base + s * S::STAGE, b_s = a_s + S::A_BYTES;
             last_issued = j;
+            const size_t rb = (size_t)(k0 / DW_BK + j);   // 64-row block of the batch
             mbar_arrive_expect_tx(bar_full + 8 * s, (uint32_t)S::STAGE);
-            tma_load_4d(a_s, ta, bar_full + 8 * s, 0, k0 + j * DW_BK, mt * 16, k);
-            tma_load_4d(b_s, tb, bar_full + 8 * s, 0, k0 + j * DW_BK, nb * (NT / 8), k);
+            bulk_load(a_s, ga + rb * a_blk, (uint32_t)S::A_BYTES, bar_full + 8 * s);
+            bulk_load(b_s, gb + rb * b_blk, (uint32_t)S::B_BYTES, bar_full + 8 * s);
         };
         for (int j = 0; j < n_k && j < DW_STAGES; ++j) load(j);
         for (int j = 0; j < n_k; ++j) {
@@ -1431,10 +1547,10 @@ __global__ void __launch_bounds__(128, 1)
     const int r = warp * 32 + lane;
     const int m = mt * 128 + r;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    uint8_t* reg = args.ws + (size_t)k * args.region_bytes;
+    uint8_t* wreg = const_cast<uint8_t*>(reg);
     const int ld = args.part_ld[lay];
     if (done_ok) {
-        float* out = reinterpret_cast<float*>(reg + args.part_b[lay]) +
+        float* out = reinterpret_cast<float*>(wreg + args.part_b[lay]) +
                      ((long long)split * 256 + m) * ld + nb * NT;
         float v[16];
 #pragma unroll 1
@@ -1446,7 +1562,7 @@ __global__ void __launch_bounds__(128, 1)
         }
         if (bias) {
             tmem_ld16(trow + NT, v);
-            reinterpret_cast<float*>(reg + args.bias_b[lay])[(long long)split * 256 + m] = v[0];
+            reinterpret_cast<float*>(wreg + args.bias_b[lay])[(long long)split * 256 + m] = v[0];
         }
     }
     tc_fence_before();
@@ -1601,7 +1717,7 @@ __device__ __forceinline__ float split_sum(const float* v, long long stride, int
 struct AdamArgs {
     ParamOffsets po;
     uint8_t* model;                 // member k = blockIdx.y at model + k * member_bytes
-    size_t member_bytes, theta_b, m_b, v_b, wi_b, wg_b, step_b;
+    size_t member_bytes, theta_b, m_b, v_b, wi_b, step_b;
     const uint8_t* ws;              // member k's training arrays at ws + k * region_bytes
     size_t region_bytes;
     size_t part_b[N_LAYERS];        // dW_l split partials [split][rows][ld]; l = 4 transposed
@@ -1629,8 +1745,34 @@ __device__ __forceinline__ float param_grad(const AdamArgs& A, const uint8_t* re
     return split_sum(bp, A.bias_ld[l], A.bias_n[l], o);
 }
 
-// Adam (Kingma & Ba) on every real parameter of member blockIdx.y, then its BF16 weight
-// images (forward and backward); the member's step count advances.  Padding stays zero.
+// Weight (l, o, i) = th into the BF16 weight image of a member.
+__device__ __forceinline__ void write_image(bf16* wi, int l, int o, int i, float th) {
+    const long long ii = img_index(l, o, i);
+    if (ii >= 0) wi[ii] = __float2bfloat16(th);
+}
+
+// The same sum for four consecutive elements e .. e + 3 (e and stride multiples of 4).
+__device__ __forceinline__ float4 split_sum4(const float* v, long long stride, int n, long long e) {
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a, d = a;
+    auto add = [](float4& x, const float4 y) {
+        x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w;
+    };
+    int k = 0;
+    for (; k + 4 <= n; k += 4) {
+        add(a, *reinterpret_cast<const float4*>(v + (k + 0) * stride + e));
+        add(b, *reinterpret_cast<const float4*>(v + (k + 1) * stride + e));
+        add(c, *reinterpret_cast<const float4*>(v + (k + 2) * stride + e));
+        add(d, *reinterpret_cast<const float4*>(v + (k + 3) * stride + e));
+    }
+    for (; k < n; ++k) add(a, *reinterpret_cast<const float4*>(v + k * stride + e));
+    return make_float4((a.x + b.x) + (c.x + d.x), (a.y + b.y) + (c.y + d.y),
+                       (a.z + b.z) + (c.z + d.z), (a.w + b.w) + (c.w + d.w));
+}
+
+// Adam (Kingma & Ba) on every real parameter of member blockIdx.y, four consecutive
+// parameters per thread (one weight row or the biases of a layer: every layer's block
+// of theta and every row are multiples of 4 long), then its BF16 weight image; the
+// member's step count advances.  Padding stays zero.
 __global__ void adam_kernel(AdamArgs A, long long P) {
     const int k = blockIdx.y;
     uint8_t* mb = A.model + (size_t)k * A.member_bytes;
@@ -1646,26 +1788,46 @@ __global__ void adam_kernel(AdamArgs A, long long P) {
     float* am = reinterpret_cast<float*>(mb + A.m_b);
     float* av = reinterpret_cast<float*>(mb + A.v_b);
     bf16* wi = reinterpret_cast<bf16*>(mb + A.wi_b);
-    bf16* wg = reinterpret_cast<bf16*>(mb + A.wg_b);
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
-         idx += (long long)gridDim.x * blockDim.x) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < P / 4;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long idx = q * 4;
         int l, o, i;
         bool is_w;
-        if (!param_locate(A.po, idx, l, o, i, is_w)) continue;
-        const float g = param_grad(A, reg, l, o, i, is_w);
-        const float mm = A.b1 * am[idx] + (1.f - A.b1) * g;
-        const float vv = A.b2 * av[idx] + (1.f - A.b2) * g * g;
-        am[idx] = mm;
-        av[idx] = vv;
-        const float th = theta[idx] - lr * (mm / c1) / (sqrtf(vv / c2) + A.eps);
-        theta[idx] = th;
-        if (is_w) {
-            const bf16 tb = __float2bfloat16(th);
-            const long long ii = img_index(l, o, i);
-            if (ii >= 0) wi[ii] = tb;
-            const long long gi = wg_index(l, o, i);
-            if (gi >= 0) wg[gi] = tb;
+        param_locate(A.po, idx, l, o, i, is_w);
+        // the four parameters: weights (o, i .. i + 3) or biases o .. o + 3 of layer l
+        const int n_real = is_w ? (o < real_out(l) ? min(4, max(0, real_in(l) - i)) : 0)
+                                : min(4, max(0, real_out(l) - o));
+        if (n_real == 0) continue;
+        float g[4];
+        if (n_real == 4 && l != 4) {
+            const float4 g4 = is_w ? split_sum4(reinterpret_cast<const float*>(reg + A.part_b[l]),
+                                                A.part_plane[l], A.splits,
+                                                (long long)o * A.part_ld[l] + i)
+                                   : split_sum4(reinterpret_cast<const float*>(reg + A.bias_b[l]),
+                                                A.bias_ld[l], A.bias_n[l], o);
+            g[0] = g4.x; g[1] = g4.y; g[2] = g4.z; g[3] = g4.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                g[e] = e < n_real ? param_grad(A, reg, l, is_w ? o : o + e, is_w ? i + e : 0, is_w) : 0.f;
         }
+        const float4 m0 = *reinterpret_cast<const float4*>(am + idx);
+        const float4 v0 = *reinterpret_cast<const float4*>(av + idx);
+        const float4 t0 = *reinterpret_cast<const float4*>(theta + idx);
+        float mm[4] = {m0.x, m0.y, m0.z, m0.w}, vv[4] = {v0.x, v0.y, v0.z, v0.w};
+        float th[4] = {t0.x, t0.y, t0.z, t0.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (e >= n_real) continue;   // padding: stays 0
+            mm[e] = A.b1 * mm[e] + (1.f - A.b1) * g[e];
+            vv[e] = A.b2 * vv[e] + (1.f - A.b2) * g[e] * g[e];
+            th[e] = th[e] - lr * (mm[e] / c1) / (sqrtf(vv[e] / c2) + A.eps);
+        }
+        *reinterpret_cast<float4*>(am + idx) = make_float4(mm[0], mm[1], mm[2], mm[3]);
+        *reinterpret_cast<float4*>(av + idx) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+        *reinterpret_cast<float4*>(theta + idx) = make_float4(th[0], th[1], th[2], th[3]);
+        if (is_w)
+            for (int e = 0; e < n_real; ++e) write_image(wi, l, o, i + e, th[e]);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         int* st = reinterpret_cast<int*>(mb + A.step_b);
@@ -1684,18 +1846,9 @@ __global__ void grad_kernel(AdamArgs A, long long P, float* grad) {
     }
 }
 
-// Weight (l, o, i) = th into the BF16 images of a member (forward and backward).
-__device__ __forceinline__ void write_images(bf16* wi, bf16* wg, int l, int o, int i, float th) {
-    const bf16 tb = __float2bfloat16(th);
-    const long long ii = img_index(l, o, i);
-    if (ii >= 0) wi[ii] = tb;
-    const long long gi = wg_index(l, o, i);
-    if (gi >= 0) wg[gi] = tb;
-}
-
 // He-uniform initial weights (hash of seed, member, index -> uniform), zero biases,
-// zero Adam state, BF16 images, step 0.
-__global__ void init_kernel(float* theta, float* m, float* v, bf16* wi, bf16* wg, int* step,
+// zero Adam state, BF16 weight image, step 0.
+__global__ void init_kernel(float* theta, float* m, float* v, bf16* wi, int* step,
                             unsigned seed, unsigned member, ParamOffsets po, long long P) {
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -1713,16 +1866,16 @@ __global__ void init_kernel(float* theta, float* m, float* v, bf16* wi, bf16* wg
         theta[idx] = th;
         m[idx] = 0.f;
         v[idx] = 0.f;
-        if (is_w) write_images(wi, wg, l, o, i, th);
+        if (is_w) write_image(wi, l, o, i, th);
         if (idx == 0) step[0] = 0;
     }
 }
 
 // Parameters given by the caller (device theta in the padded layout): entries outside
 // the real rows and columns are stored as 0; Adam state and step are reset and the BF16
-// images rebuilt.
+// weight image rebuilt.
 __global__ void load_kernel(const float* src, float* theta, float* m, float* v, bf16* wi,
-                            bf16* wg, int* step, ParamOffsets po, long long P) {
+                            int* step, ParamOffsets po, long long P) {
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < P;
          idx += (long long)gridDim.x * blockDim.x) {
         int l, o, i;
@@ -1731,7 +1884,7 @@ __global__ void load_kernel(const float* src, float* theta, float* m, float* v, 
         theta[idx] = th;
         m[idx] = 0.f;
         v[idx] = 0.f;
-        if (is_w) write_images(wi, wg, l, o, i, th);
+        if (is_w) write_image(wi, l, o, i, th);
         if (idx == 0) step[0] = 0;
     }
 }
@@ -1838,24 +1991,6 @@ static fos_status gemm(const Operand& A, const Operand& B, int splits, GemmArgs 
     dim3 grid((unsigned)((g.M + BM - 1) / BM), (unsigned)((g.N + NT - 1) / NT), (unsigned)splits);
     gemm_kernel<NT><<<grid, 128, Smem<NT>::ALLOC, s>>>(ta, tb, g);
     return from_cuda(cudaGetLastError());
-}
-
-// 4-D map of a chunk-major BF16 array X[c/8][row][c%8] at byte offset `off` of every member
-// region: dims {8 columns, Bp rows, chunks, members}, box {8, DW_BK, box_chunks, 1}, no
-// swizzle (the MN-major operand layout of dw_kernel).
-static fos_status make_cm_map(CUtensorMap* map, const uint8_t* ws, size_t off, long long Bp,
-                              int chunks, int members, size_t region, int box_chunks) {
-    const uint8_t* ptr = ws + off;
-    if (((uintptr_t)ptr & 15u) != 0 || region % 16 != 0) return FOS_ERR_INVALID_ARG;
-    cuuint64_t dims[4] = {8, (cuuint64_t)Bp, (cuuint64_t)chunks, (cuuint64_t)members};
-    cuuint64_t strides[3] = {16, (cuuint64_t)Bp * 16, (cuuint64_t)region};
-    cuuint32_t box[4] = {8, (cuuint32_t)DW_BK, (cuuint32_t)box_chunks, 1};
-    cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint8_t*>(ptr), dims,
-                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? FOS_OK : FOS_ERR_CUDA;
 }
 
 // Training workspace (library-owned, per device), in member regions of region_bytes: a
@@ -1976,7 +2111,7 @@ static fos_status train_step(Workspace* ws, int slot, uint8_t* model, int n_memb
     static bool attr_set[64] = {};
     if (!attr_set[ws->device]) {
         FOS_CUDA_TRY(cudaFuncSetAttribute(train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          FI_SMEM));
+                                          FT_SMEM));
         FOS_CUDA_TRY(cudaFuncSetAttribute(dw_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           DwSmem<128>::ALLOC));
         FOS_CUDA_TRY(cudaFuncSetAttribute(dw_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2005,7 +2140,6 @@ static fos_status train_step(Workspace* ws, int slot, uint8_t* model, int n_memb
     ta.theta_b = LAY.theta_b;
     ta.stats_b = LAY.stats_b;
     ta.wi_b = LAY.wi_b;
-    ta.wg_b = LAY.wg_b;
     ta.step_b = LAY.step_b;
     for (int l = 0; l < N_LAYERS; ++l) ta.b_off[l] = LAY.b_off[l];
     if (ds) {
@@ -2030,7 +2164,7 @@ static fos_status train_step(Workspace* ws, int slot, uint8_t* model, int n_memb
     ta.wait_limit = 4000000000LL;   // ~2 s at 2 GHz
     const long long items = (long long)n_members * n_tiles;
     const long long grid = items < ws->num_sms ? items : ws->num_sms;
-    train_kernel<<<(unsigned)grid, FI_THREADS, FI_SMEM, s>>>(ta);
+    train_kernel<<<(unsigned)grid, FT_THREADS, FT_SMEM, s>>>(ta);
     FOS_CUDA_TRY(cudaGetLastError());
 
     // weight gradients
@@ -2043,42 +2177,41 @@ static fos_status train_step(Workspace* ws, int slot, uint8_t* model, int n_memb
     da.status = status;
     da.wait_limit = 4000000000LL;
     {   // layers 0 and 4 (16 columns) on the side stream
-        DwMaps mp;
-        std::memset(&mp, 0, sizeof(mp));
-        fos_status st = make_cm_map(&mp.a[0], reg0, w.dz_b[0], B, 32, n_members, w.region_bytes, 16);
-        if (st == FOS_OK) st = make_cm_map(&mp.b[0], reg0, w.x0_b, B, 2, n_members, w.region_bytes, 2);
-        if (st == FOS_OK) st = make_cm_map(&mp.a[1], reg0, w.h_b[3], B, 32, n_members, w.region_bytes, 16);
-        if (st == FOS_OK) st = make_cm_map(&mp.b[1], reg0, w.g4_b, B, 2, n_members, w.region_bytes, 2);
-        if (st != FOS_OK) return st;
         DwArgs d = da;
         d.n_lay = 2;
+        d.a_b[0] = w.dz_b[0];
+        d.a_chunks[0] = 32;
+        d.b_b[0] = w.x0_b;
+        d.b_chunks[0] = 2;
         d.part_b[0] = w.part_b[0];
         d.part_ld[0] = 16;
         d.bias_b[0] = w.bias_b[0];
+        d.a_b[1] = w.h_b[3];
+        d.a_chunks[1] = 32;
+        d.b_b[1] = w.g4_b;
+        d.b_chunks[1] = 2;
         d.part_b[1] = w.part_b[4];
         d.part_ld[1] = 16;
         d.bias_b[1] = 0;
         FOS_CUDA_TRY(cudaEventRecord(w.ev_fork[slot], s));
         FOS_CUDA_TRY(cudaStreamWaitEvent(w.side[slot], w.ev_fork[slot], 0));
-        dw_kernel<16><<<dim3(2, 2 * n_members, splits), 128, DwSmem<16>::ALLOC, w.side[slot]>>>(mp, d);
+        dw_kernel<16><<<dim3(2, 2 * n_members, splits), 128, DwSmem<16>::ALLOC, w.side[slot]>>>(d);
         FOS_CUDA_TRY(cudaGetLastError());
         FOS_CUDA_TRY(cudaEventRecord(w.ev_join[slot], w.side[slot]));
     }
     {   // layers 1-3: dW_l = dZ_l^T H_{l-1}, two column blocks of 128
-        DwMaps mp;
-        std::memset(&mp, 0, sizeof(mp));
         DwArgs d = da;
         d.n_lay = 3;
         for (int l = 1; l <= 3; ++l) {
-            fos_status st = make_cm_map(&mp.a[l - 1], reg0, w.dz_b[l], B, 32, n_members, w.region_bytes, 16);
-            if (st == FOS_OK)
-                st = make_cm_map(&mp.b[l - 1], reg0, w.h_b[l - 1], B, 32, n_members, w.region_bytes, 16);
-            if (st != FOS_OK) return st;
+            d.a_b[l - 1] = w.dz_b[l];
+            d.a_chunks[l - 1] = 32;
+            d.b_b[l - 1] = w.h_b[l - 1];
+            d.b_chunks[l - 1] = 32;
             d.part_b[l - 1] = w.part_b[l];
             d.part_ld[l - 1] = 256;
             d.bias_b[l - 1] = w.bias_b[l];
         }
-        dw_kernel<128><<<dim3(4, 3 * n_members, splits), 128, DwSmem<128>::ALLOC, s>>>(mp, d);
+        dw_kernel<128><<<dim3(4, 3 * n_members, splits), 128, DwSmem<128>::ALLOC, s>>>(d);
         FOS_CUDA_TRY(cudaGetLastError());
     }
     FOS_CUDA_TRY(cudaStreamWaitEvent(s, w.ev_join[slot], 0));
@@ -2092,7 +2225,6 @@ static fos_status train_step(Workspace* ws, int slot, uint8_t* model, int n_memb
     a.m_b = LAY.m_b;
     a.v_b = LAY.v_b;
     a.wi_b = LAY.wi_b;
-    a.wg_b = LAY.wg_b;
     a.step_b = LAY.step_b;
     a.ws = reg0;
     a.region_bytes = w.region_bytes;
@@ -2112,6 +2244,7 @@ static fos_status train_step(Workspace* ws, int slot, uint8_t* model, int n_memb
     }
     a.splits = splits;
     const unsigned pblocks = (unsigned)((LAY.P + 255) / 256);
+    const unsigned qblocks = (unsigned)((LAY.P / 4 + 255) / 256);
     if (grad_out) {   // diagnostic: export the gradient instead of updating
         grad_kernel<<<pblocks, 256, 0, s>>>(a, LAY.P, grad_out);
         return from_cuda(cudaGetLastError());
@@ -2126,7 +2259,7 @@ static fos_status train_step(Workspace* ws, int slot, uint8_t* model, int n_memb
     a.dev_sched = ds ? 1 : 0;
     a.sched_b = w.sched_b;
     a.host_step = (int)step;
-    adam_kernel<<<dim3(pblocks, (unsigned)n_members), 256, 0, s>>>(a, LAY.P);
+    adam_kernel<<<dim3(qblocks, (unsigned)n_members), 256, 0, s>>>(a, LAY.P);
     return from_cuda(cudaGetLastError());
 }
 
@@ -2284,7 +2417,7 @@ fos_status fos_surrogate_init(void* model, int n_members, unsigned long long see
         mlp::MemberPtrs mp = mlp::member(model, k);
         FOS_CUDA_TRY(cudaMemsetAsync((char*)model + (size_t)k * mlp::LAY.bytes, 0, mlp::LAY.bytes, s));
         mlp::init_kernel<<<(unsigned)((mlp::LAY.P + 255) / 256), 256, 0, s>>>(
-            mp.theta, mp.m, mp.v, mp.wi, mp.wg, mp.step, (unsigned)(seed ^ (seed >> 32)),
+            mp.theta, mp.m, mp.v, mp.wi, mp.step, (unsigned)(seed ^ (seed >> 32)),
             (unsigned)k, mlp::param_offsets(), mlp::LAY.P);
         FOS_CUDA_TRY(cudaGetLastError());
         FOS_CUDA_TRY(cudaMemcpyAsync(mp.stats, feat_stats, 64 * sizeof(float),
@@ -2308,7 +2441,7 @@ fos_status fos_surrogate_load(void* model, int member, const float* theta,
     FOS_CUDA_TRY(cudaMemsetAsync((char*)model + (size_t)member * mlp::LAY.bytes, 0,
                                  mlp::LAY.bytes, s));
     mlp::load_kernel<<<(unsigned)((mlp::LAY.P + 255) / 256), 256, 0, s>>>(
-        theta, mp.theta, mp.m, mp.v, mp.wi, mp.wg, mp.step, mlp::param_offsets(), mlp::LAY.P);
+        theta, mp.theta, mp.m, mp.v, mp.wi, mp.step, mlp::param_offsets(), mlp::LAY.P);
     FOS_CUDA_TRY(cudaGetLastError());
     FOS_CUDA_TRY(cudaMemcpyAsync(mp.stats, feat_stats, 64 * sizeof(float),
                                  cudaMemcpyHostToDevice, s));

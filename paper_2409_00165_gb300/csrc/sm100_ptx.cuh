@@ -87,14 +87,10 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
         : "memory");
 }
-// 4-D tiled load (coordinates innermost first).
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
-                                            int x, int y, int z, int w) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z), "r"(w)
-        : "memory");
+// Drops the 128-byte L2 line at p (128-byte aligned) without writing it back: for data
+// that is dead (its later reads would return unspecified values).
+__device__ __forceinline__ void l2_discard(const void* p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(p)) : "memory");
 }
 // Untiled bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16),
 // completing `bytes` of transaction on the mbarrier.
@@ -239,6 +235,21 @@ __device__ __forceinline__ uint64_t desc_mn_plain(uint32_t smem_addr, uint32_t k
     d |= (uint64_t)((k_step >> 4) & 0x3FFFu) << 16;
     d |= (uint64_t)((mn_step >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Shared-memory matrix descriptor of an MN-major, 128-byte-swizzled BF16 operand: 128-byte
+// rows of 64 consecutive M or N elements, one row per K, 8-row swizzle atoms (1024-byte
+// aligned); `mn_step` bytes between 64-element blocks along M or N (the leading byte
+// offset) and `k_step` bytes between 8-row groups along K (the stride byte offset).
+__device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t smem_addr, uint32_t mn_step,
+                                                  uint32_t k_step) {
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((mn_step >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((k_step >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 
