@@ -5,10 +5,11 @@
 //   (sphere_eval) and core-shell spheres (coated_eval, supplement Eqs. S1-S9).  The logarithmic
 //   derivative D_n(z) = psi_n'(z)/psi_n(z) of psi_n(z) = z j_n(z) (A_n of Eq. 4) comes
 //   from the downward recurrence D_{n-1} = n/z - 1/(D_n + n/z) started at
-//   N* = n_max + 17 with D = 0, for the particle argument y and the host argument x.
-//   The values are kept in a scratch laid out [order][thread] so that a warp's
-//   accesses coalesce.  An upward sweep then builds psi_n(x) (upward recurrence
-//   while n <= |x|, psi_{n-1}/(D_n(x) + n/x) above) and xi_n(x) = x h^(1)_n(x)
+//   N* = n_max + 17 with D = 0, for the particle argument y (and, for |x| < 1.5, the
+//   host argument x).  The values are kept in a scratch laid out [order][thread] so
+//   that a warp's accesses coalesce.  An upward sweep then builds psi_n(x) (upward
+//   recurrence; for |x| < 1.5 only while n <= |x|, psi_{n-1}/(D_n(x) + n/x) above)
+//   and xi_n(x) = x h^(1)_n(x)
 //   (upward recurrence), forms a_n, b_n of Eqs. 2-3 multiplied through by psi_n(x)
 //   and xi_n(x) (well conditioned at zeros of psi_n(x)), and accumulates the sums of
 //   Eqs. 11, 12 and 15.
@@ -99,22 +100,65 @@ __device__ __forceinline__ cx ccos(cx z) {
 }
 
 // Geometric term of Eq. 10 with alpha = 4 pi r k_m / lambda.  Below alpha = 0.5 the
-// bracket cancels, so its Taylor series 2 sum_{k>=2} (k-1)/k! alpha^(k-2) is used
-// (19 terms: the next one is < 1e-18 at alpha = 0.5).
-__device__ __forceinline__ double gamma_term(double a) {
-    if (a < 0.5) {
-        double sum = 0.0, pw = 1.0, fact = 2.0;   // i = 0: 2 * 1 / 2!
+// bracket cancels, so its Taylor series 2 sum_{k>=2} (k-1)/k! alpha^(k-2) is used, by
+// Horner's rule over a table of its coefficients: 19 terms (the next one is < 1e-18 at
+// alpha = 0.5), or 6 below alpha = 2^-10 (the next one is < 1e-21 there).
+struct GammaSeries {
+    double c[19];   // c[i] = 2 (i + 1) / (i + 2)!
+    constexpr GammaSeries() : c() {
+        double fact = 2.0;
         for (int i = 0; i < 19; ++i) {
-            if (i > 0) {
-                pw *= a;
-                fact *= (double)(i + 2);
-            }
-            sum += 2.0 * (double)(i + 1) / fact * pw;
+            if (i > 0) fact *= (double)(i + 2);
+            c[i] = 2.0 * (double)(i + 1) / fact;
         }
-        return sum;
+    }
+};
+__constant__ GammaSeries g_gamma = GammaSeries();
+__device__ __forceinline__ double gamma_term(double a) {
+    if (a < 0x1p-10) {
+        double p = g_gamma.c[5];
+#pragma unroll
+        for (int i = 4; i >= 0; --i) p = fma(p, a, g_gamma.c[i]);
+        return p;
+    }
+    if (a < 0.5) {
+        double p = g_gamma.c[18];
+#pragma unroll
+        for (int i = 17; i >= 0; --i) p = fma(p, a, g_gamma.c[i]);
+        return p;
     }
     return 2.0 * (1.0 + (a - 1.0) * exp(a)) / (a * a);
 }
+
+// psi_{-1}(x) = cos x, psi_0(x) = sin x and xi_{-1}(x) = e^{ix} for x = a + ib, with the
+// hyperbolic functions of b from one expm1: E = e^b, cosh b = (E + 1/E)/2,
+// sinh b = (e^b - 1)(1 + 1/E)/2 (no cancellation for small b), e^{-b} = 1/E.
+__device__ __forceinline__ void start_values(cx x, cx& psi_m1, cx& psi_0, cx& xi_m1) {
+    double sa, ca;
+    sincos(x.re, &sa, &ca);
+    const double em1 = expm1(x.im);
+    const double ie = 1.0 / (1.0 + em1);
+    const double ch = 0.5 * (1.0 + em1 + ie), sh = 0.5 * em1 * (1.0 + ie);
+    psi_m1 = mk(ca * ch, -sa * sh);
+    psi_0 = mk(sa * ch, ca * sh);
+    xi_m1 = mk(ie * ca, ie * sa);
+}
+
+// psi_n(x) comes from its upward recurrence at every order when |x| >= this (as in Bohren
+// and Huffman's BHMIE and Wiscombe's Mie algorithm).  Above n = |x| the recurrence's
+// rounding errors grow like the increasing solution chi_n, so psi_n carries an absolute
+// error of about n eps |chi_n|; that moves a_n and b_n by about n eps, which against sums of
+// size x^2 Q / 2 stays far below 1e-10 once x is not small.  For smaller |x| (the Rayleigh
+// regime, where Q can be tiny) psi_n above |x| is psi_{n-1} / (D_n(x) + n/x) with D_n(x)
+// from its downward recurrence.
+// With psi_n from the upward recurrence the computed terms do not fall below that error
+// past |x|, so the sums cannot end by the size of their terms; they end at Wiscombe's count
+// n_w = |x| + 4.05 |x|^(1/3) + 2 plus PSI_UPWARD_EXTRA orders at the latest.  The exact
+// terms past n_w fall by about (|x| / (2n + 3))^2 < 1/4 per order, so those after it are
+// below 2^-60 of the sums, and chi_n, which grows super-exponentially past |x|, stays far
+// from overflow there.
+constexpr double PSI_UPWARD_MIN_X = 1.5;
+constexpr int PSI_UPWARD_EXTRA = 16;
 
 struct MieArgs {
     int n_wl, n_groups, n_species;
@@ -209,10 +253,10 @@ __device__ __forceinline__ void efficiencies(const Sums& S, double lam, double r
                                              cx inv_nm2, double* qe, double* qs, double* gg) {
     const double alpha = 4.0 * M_PI * r * n_m.im / lam;
     const double gam = gamma_term(alpha);
-    const double area = M_PI * r * r;
+    const double scale = lam * lam / (2.0 * M_PI * M_PI * r * r);   // lambda^2 / (2 pi area)
     const double ext = S.ext_re * inv_nm2.re - S.ext_im * inv_nm2.im;   // Re(sum / n_m^2)
-    *qe = lam * lam / (2.0 * M_PI) * ext / area;
-    *qs = lam * lam * exp(-alpha) / (2.0 * M_PI * gam * norm2(n_m)) * S.sca / area;
+    *qe = scale * ext;
+    *qs = scale * exp(-alpha) * S.sca / (gam * norm2(n_m));
     *gg = (S.sca > 0.0) ? 2.0 * S.g / S.sca : 0.0;
 }
 
@@ -231,12 +275,12 @@ __device__ bool sphere_eval_large(double lam, double r, cx n_p, cx n_m, double2*
     const int nt = nmax + 1;          // a_{n+1}, b_{n+1} for Eq. 15
     const int nstart = nt + 16;
     const cx xi_ = crcp(x);
-    // orders n <= n_up (n <= |x|) take psi_n(x) from the upward recurrence; integer
-    // comparisons keep the per-order test off the FP64 pipe
-    const int n_up = (int)fmin(floor(ax), (double)nstart);
-    cx psi_m1 = ccos(x), psi_0 = csin(x);
-    const double eb = exp(-x.im);
-    cx xi_m1 = mk(eb * cos(x.re), eb * sin(x.re));        // e^{ix}
+    // orders n <= n_up (n <= |x|, or all when |x| >= PSI_UPWARD_MIN_X) take psi_n(x) from
+    // the upward recurrence; integer comparisons keep the per-order test off the FP64 pipe
+    const bool up_all = ax >= PSI_UPWARD_MIN_X;
+    const int n_up = up_all ? nt : (int)fmin(floor(ax), (double)nstart);
+    cx psi_m1, psi_0, xi_m1;                                // cos x, sin x, e^{ix}
+    start_values(x, psi_m1, psi_0, xi_m1);
     cx xi_0 = psi_0 - mk(-psi_m1.im, psi_m1.re);            // sin x - i cos x
     const cx inv_nm2 = crcp(n_m * n_m);
     const cx q = n_m / n_p, qi = n_p / n_m;
@@ -250,10 +294,11 @@ __device__ bool sphere_eval_large(double lam, double r, cx n_p, cx n_m, double2*
     // a_{n+1}) is below 2^-60 of the sums too.  The downward recurrences still start above
     // the n_max of Eq. 12's criterion, so every order used is as accurate as before.
     const int n_w = (int)ceil(ax + 4.05 * cbrt(ax) + 2.0);
+    const int n_last = up_all ? min(nt, n_w + PSI_UPWARD_EXTRA) : nt;
     int small = 0;
     bool done = false;
-    for (int c0 = 1; c0 <= nt && !done; c0 += FOS_MIE_MAX_TERMS) {
-        const int c1 = min(nt, c0 + FOS_MIE_MAX_TERMS - 1);
+    for (int c0 = 1; c0 <= n_last && !done; c0 += FOS_MIE_MAX_TERMS) {
+        const int c1 = min(n_last, c0 + FOS_MIE_MAX_TERMS - 1);
         downward_D(y, nstart, c1, colY, T, c0, c0);
         if (c1 > n_up) downward_D(x, nstart, c1, colX, T, max(c0, n_up + 1), c0);
         for (int n = c0; n <= c1; ++n) {
@@ -298,8 +343,8 @@ __device__ bool sphere_eval_large(double lam, double r, cx n_p, cx n_m, double2*
     return true;
 }
 
-// Homogeneous sphere (Eqs. 1-5): D_n(y), D_n(x) downward (the latter only for n > |x|);
-// psi_n(x) upward while n <= |x|, psi_{n-1}/(D_n(x) + n/x) above; xi_n(x) upward; Eqs. 2-3
+// Homogeneous sphere (Eqs. 1-5): D_n(y) downward; psi_n(x) upward (for |x| < 1.5 only
+// while n <= |x|, and psi_{n-1}/(D_n(x) + n/x) above, D_n(x) downward); xi_n(x) upward; Eqs. 2-3
 // multiplied through by psi_n(x) and xi_n(x), and a_n divided through by n_p, b_n by n_m:
 // a_n = (q D_n(y) psi_n - psi_n') / (q D_n(y) xi_n - xi_n'), q = n_m / n_p, and b_n the
 // same with 1/q; with the derivatives from the recurrence this is
@@ -318,13 +363,13 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
     if (nstart > FOS_MIE_MAX_TERMS) return false;
     const cx xi_ = crcp(x);
     downward_D(y, nstart, nt, colY, T);
-    // orders n <= n_up (n <= |x|) take psi_n(x) from the upward recurrence; integer
-    // comparisons keep the per-order test off the FP64 pipe
-    const int n_up = (int)fmin(floor(ax), (double)nstart);
-    downward_D(x, nstart, nt, colX, T, n_up + 1);
-    cx psi_m1 = ccos(x), psi_0 = csin(x);
-    const double eb = exp(-x.im);
-    cx xi_m1 = mk(eb * cos(x.re), eb * sin(x.re));        // e^{ix}
+    // orders n <= n_up (n <= |x|, or all when |x| >= PSI_UPWARD_MIN_X) take psi_n(x) from
+    // the upward recurrence; integer comparisons keep the per-order test off the FP64 pipe
+    const bool up_all = ax >= PSI_UPWARD_MIN_X;
+    const int n_up = up_all ? nt : (int)fmin(floor(ax), (double)nstart);
+    if (!up_all) downward_D(x, nstart, nt, colX, T, n_up + 1);
+    cx psi_m1, psi_0, xi_m1;                                // cos x, sin x, e^{ix}
+    start_values(x, psi_m1, psi_0, xi_m1);
     cx xi_0 = psi_0 - mk(-psi_m1.im, psi_m1.re);            // sin x - i cos x
     const cx inv_nm2 = crcp(n_m * n_m);
     const cx q = n_m / n_p, qi = n_p / n_m;
@@ -338,8 +383,9 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
     // a_{n+1}) is below 2^-60 of the sums too.  The downward recurrences still start above
     // the n_max of Eq. 12's criterion, so every order used is as accurate as before.
     const int n_w = (int)ceil(ax + 4.05 * cbrt(ax) + 2.0);
+    const int n_last = up_all ? min(nt, n_w + PSI_UPWARD_EXTRA) : nt;
     int small = 0;
-    for (int n = 1; n <= nt; ++n) {
+    for (int n = 1; n <= n_last; ++n) {
         const double dn = (double)n;
         const cx c = (double)(2 * n - 1) * xi_, nx = dn * xi_;
         cx psi_n;

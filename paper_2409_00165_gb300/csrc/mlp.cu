@@ -1752,19 +1752,34 @@ __device__ __forceinline__ void write_image(bf16* wi, int l, int o, int i, float
 }
 
 // The same sum for four consecutive elements e .. e + 3 (e and stride multiples of 4).
+// With the usual 8 splits every load is issued before the first addition, so that they
+// are all in flight together; the additions keep the general loop's order.
 __device__ __forceinline__ float4 split_sum4(const float* v, long long stride, int n, long long e) {
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a, d = a;
     auto add = [](float4& x, const float4 y) {
         x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w;
     };
-    int k = 0;
-    for (; k + 4 <= n; k += 4) {
-        add(a, *reinterpret_cast<const float4*>(v + (k + 0) * stride + e));
-        add(b, *reinterpret_cast<const float4*>(v + (k + 1) * stride + e));
-        add(c, *reinterpret_cast<const float4*>(v + (k + 2) * stride + e));
-        add(d, *reinterpret_cast<const float4*>(v + (k + 3) * stride + e));
+    if (n == 8) {
+        float4 x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = *reinterpret_cast<const float4*>(v + k * stride + e);
+#pragma unroll
+        for (int k = 0; k < 8; k += 4) {
+            add(a, x[k]);
+            add(b, x[k + 1]);
+            add(c, x[k + 2]);
+            add(d, x[k + 3]);
+        }
+    } else {
+        int k = 0;
+        for (; k + 4 <= n; k += 4) {
+            add(a, *reinterpret_cast<const float4*>(v + (k + 0) * stride + e));
+            add(b, *reinterpret_cast<const float4*>(v + (k + 1) * stride + e));
+            add(c, *reinterpret_cast<const float4*>(v + (k + 2) * stride + e));
+            add(d, *reinterpret_cast<const float4*>(v + (k + 3) * stride + e));
+        }
+        for (; k < n; ++k) add(a, *reinterpret_cast<const float4*>(v + k * stride + e));
     }
-    for (; k < n; ++k) add(a, *reinterpret_cast<const float4*>(v + k * stride + e));
     return make_float4((a.x + b.x) + (c.x + d.x), (a.y + b.y) + (c.y + d.y),
                        (a.z + b.z) + (c.z + d.z), (a.w + b.w) + (c.w + d.w));
 }
@@ -1772,8 +1787,11 @@ __device__ __forceinline__ float4 split_sum4(const float* v, long long stride, i
 // Adam (Kingma & Ba) on every real parameter of member blockIdx.y, four consecutive
 // parameters per thread (one weight row or the biases of a layer: every layer's block
 // of theta and every row are multiples of 4 long), then its BF16 weight image; the
-// member's step count advances.  Padding stays zero.
-__global__ void adam_kernel(AdamArgs A, long long P) {
+// member's step count advances.  Padding stays zero.  The parameters' moments and values
+// are loaded before the gradient partials, so that all of a thread's loads are in flight
+// together; four real weights of a row sit in one 8-byte piece of the image (a 16-byte
+// chunk of 8 inputs, i a multiple of 4), stored at once.
+__global__ void __launch_bounds__(256) adam_kernel(AdamArgs A, long long P) {
     const int k = blockIdx.y;
     uint8_t* mb = A.model + (size_t)k * A.member_bytes;
     const uint8_t* reg = A.ws + (size_t)k * A.region_bytes;
@@ -1798,6 +1816,9 @@ __global__ void adam_kernel(AdamArgs A, long long P) {
         const int n_real = is_w ? (o < real_out(l) ? min(4, max(0, real_in(l) - i)) : 0)
                                 : min(4, max(0, real_out(l) - o));
         if (n_real == 0) continue;
+        const float4 m0 = *reinterpret_cast<const float4*>(am + idx);
+        const float4 v0 = *reinterpret_cast<const float4*>(av + idx);
+        const float4 t0 = *reinterpret_cast<const float4*>(theta + idx);
         float g[4];
         if (n_real == 4 && l != 4) {
             const float4 g4 = is_w ? split_sum4(reinterpret_cast<const float*>(reg + A.part_b[l]),
@@ -1811,9 +1832,6 @@ __global__ void adam_kernel(AdamArgs A, long long P) {
             for (int e = 0; e < 4; ++e)
                 g[e] = e < n_real ? param_grad(A, reg, l, is_w ? o : o + e, is_w ? i + e : 0, is_w) : 0.f;
         }
-        const float4 m0 = *reinterpret_cast<const float4*>(am + idx);
-        const float4 v0 = *reinterpret_cast<const float4*>(av + idx);
-        const float4 t0 = *reinterpret_cast<const float4*>(theta + idx);
         float mm[4] = {m0.x, m0.y, m0.z, m0.w}, vv[4] = {v0.x, v0.y, v0.z, v0.w};
         float th[4] = {t0.x, t0.y, t0.z, t0.w};
 #pragma unroll
@@ -1826,8 +1844,15 @@ __global__ void adam_kernel(AdamArgs A, long long P) {
         *reinterpret_cast<float4*>(am + idx) = make_float4(mm[0], mm[1], mm[2], mm[3]);
         *reinterpret_cast<float4*>(av + idx) = make_float4(vv[0], vv[1], vv[2], vv[3]);
         *reinterpret_cast<float4*>(theta + idx) = make_float4(th[0], th[1], th[2], th[3]);
-        if (is_w)
-            for (int e = 0; e < n_real; ++e) write_image(wi, l, o, i + e, th[e]);
+        if (is_w) {
+            const long long ii = n_real == 4 ? img_index(l, o, i) : -1;
+            if (ii >= 0) {
+                const uint32_t lo = pack_bf16(th[0], th[1]), hi = pack_bf16(th[2], th[3]);
+                *reinterpret_cast<uint2*>(wi + ii) = make_uint2(lo, hi);
+            } else {
+                for (int e = 0; e < n_real; ++e) write_image(wi, l, o, i + e, th[e]);
+            }
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         int* st = reinterpret_cast<int*>(mb + A.step_b);
