@@ -92,6 +92,19 @@ __device__ __forceinline__ cx sub_mul(cx c, cx a, cx b) {
     return cx{fma(-a.re, b.re, fma(a.im, b.im, c.re)), fma(-a.re, b.im, fma(-a.im, b.re, c.im))};
 }
 __device__ __forceinline__ double cabs_(cx a) { return hypot(a.re, a.im); }
+// |z| of a size parameter (far from overflow: no hypot scaling needed).
+__device__ __forceinline__ double size_abs(cx a) { return sqrt(fma(a.re, a.re, a.im * a.im)); }
+// Order counts that only bound a sum or a recurrence: in FP32, off the narrow FP64 pipe.
+// n_max of Eq. 12's criterion, 2 + |y| + 4.3 |y|^(1/3), and Wiscombe's count for the host
+// argument, |x| + 4.05 |x|^(1/3) + 2, rounded up.
+__device__ __forceinline__ int nmax_of(double ay) {
+    const float a = (float)ay;
+    return (int)ceilf(2.0f + a + 4.3f * cbrtf(a));
+}
+__device__ __forceinline__ int wiscombe_of(double ax) {
+    const float a = (float)ax;
+    return (int)ceilf(a + 4.05f * cbrtf(a) + 2.0f);
+}
 __device__ __forceinline__ cx csin(cx z) {
     return cx{sin(z.re) * cosh(z.im), cos(z.re) * sinh(z.im)};
 }
@@ -152,13 +165,17 @@ __device__ __forceinline__ void start_values(cx x, cx& psi_m1, cx& psi_0, cx& xi
 // regime, where Q can be tiny) psi_n above |x| is psi_{n-1} / (D_n(x) + n/x) with D_n(x)
 // from its downward recurrence.
 // With psi_n from the upward recurrence the computed terms do not fall below that error
-// past |x|, so the sums cannot end by the size of their terms; they end at Wiscombe's count
-// n_w = |x| + 4.05 |x|^(1/3) + 2 plus PSI_UPWARD_EXTRA orders at the latest.  The exact
-// terms past n_w fall by about (|x| / (2n + 3))^2 < 1/4 per order, so those after it are
-// below 2^-60 of the sums, and chi_n, which grows super-exponentially past |x|, stays far
-// from overflow there.
+// past |x|, so the sums cannot end by the size of their terms; they end at order
+// |x| + 8 |x|^(1/3) + 8 at the latest.  Past the transition region n ~ |x| the exact terms
+// fall like exp(-(4 sqrt(2) / 3) (n - |x|)^(3/2) / sqrt(|x|)) (the Debye asymptotics of
+// psi_n and chi_n), which puts every term after that order below 2^-60 of the sums
+// (checked against the oracle's coefficients for |x| from 1.5 to 3000, |m| from 0.7 to 4),
+// and chi_n, which grows as fast, stays far from overflow there.
 constexpr double PSI_UPWARD_MIN_X = 1.5;
-constexpr int PSI_UPWARD_EXTRA = 16;
+__device__ __forceinline__ int psi_upward_last(double ax, int nt) {
+    const float a = (float)ax;
+    return min(nt, (int)ceilf(a + 8.0f * cbrtf(a) + 8.0f));
+}
 
 struct MieArgs {
     int n_wl, n_groups, n_species;
@@ -270,8 +287,8 @@ __device__ bool sphere_eval_large(double lam, double r, cx n_p, cx n_m, double2*
     const double k = 2.0 * M_PI * r / lam;
     const cx x = k * n_m;   // Eq. 1
     const cx y = k * n_p;
-    const double ay = cabs_(y), ax = cabs_(x);
-    const int nmax = (int)ceil(2.0 + ay + 4.3 * cbrt(ay));
+    const double ay = size_abs(y), ax = size_abs(x);
+    const int nmax = nmax_of(ay);
     const int nt = nmax + 1;          // a_{n+1}, b_{n+1} for Eq. 15
     const int nstart = nt + 16;
     const cx xi_ = crcp(x);
@@ -293,8 +310,8 @@ __device__ bool sphere_eval_large(double lam, double r, cx n_p, cx n_m, double2*
     // partial sums, everything after them (the rest of Eqs. 11-12, and Eq. 15 with its
     // a_{n+1}) is below 2^-60 of the sums too.  The downward recurrences still start above
     // the n_max of Eq. 12's criterion, so every order used is as accurate as before.
-    const int n_w = (int)ceil(ax + 4.05 * cbrt(ax) + 2.0);
-    const int n_last = up_all ? min(nt, n_w + PSI_UPWARD_EXTRA) : nt;
+    const int n_w = wiscombe_of(ax);
+    const int n_last = up_all ? psi_upward_last(ax, nt) : nt;
     int small = 0;
     bool done = false;
     for (int c0 = 1; c0 <= n_last && !done; c0 += FOS_MIE_MAX_TERMS) {
@@ -356,8 +373,8 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
     const double k = 2.0 * M_PI * r / lam;
     const cx x = k * n_m;   // Eq. 1
     const cx y = k * n_p;
-    const double ay = cabs_(y), ax = cabs_(x);
-    const int nmax = (int)ceil(2.0 + ay + 4.3 * cbrt(ay));
+    const double ay = size_abs(y), ax = size_abs(x);
+    const int nmax = nmax_of(ay);
     const int nt = nmax + 1;          // a_{n+1}, b_{n+1} for Eq. 15
     const int nstart = nt + 16;
     if (nstart > FOS_MIE_MAX_TERMS) return false;
@@ -382,8 +399,8 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
     // partial sums, everything after them (the rest of Eqs. 11-12, and Eq. 15 with its
     // a_{n+1}) is below 2^-60 of the sums too.  The downward recurrences still start above
     // the n_max of Eq. 12's criterion, so every order used is as accurate as before.
-    const int n_w = (int)ceil(ax + 4.05 * cbrt(ax) + 2.0);
-    const int n_last = up_all ? min(nt, n_w + PSI_UPWARD_EXTRA) : nt;
+    const int n_w = wiscombe_of(ax);
+    const int n_last = up_all ? psi_upward_last(ax, nt) : nt;
     int small = 0;
     for (int n = 1; n <= n_last; ++n) {
         const double dn = (double)n;
@@ -547,8 +564,8 @@ __global__ void __launch_bounds__(128) mie_kernel(MieArgs A) {
         if (LARGE) {
             // homogeneous spheres beyond the scratch only (the first pass validated them)
             if (!ok || a > 0.0) continue;
-            const double ay = cabs_((2.0 * M_PI * r / lam) * n_p);
-            if ((int)ceil(2.0 + ay + 4.3 * cbrt(ay)) + 17 <= FOS_MIE_MAX_TERMS) continue;
+            // the same test as sphere_eval's (the same arithmetic)
+            if (nmax_of(size_abs((2.0 * M_PI * r / lam) * n_p)) + 17 <= FOS_MIE_MAX_TERMS) continue;
             sphere_eval_large(lam, r, n_p, n_m, c0, c0 + col, A.T, &qe, &qs, &gg);
         } else if (!ok) {
             flag(A.status, DEV_INVALID, ev);

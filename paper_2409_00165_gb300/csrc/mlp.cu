@@ -1730,6 +1730,10 @@ struct AdamArgs {
     int dev_sched;                  // lr, c1, c2 from the member's schedule slot; step += 1
     size_t sched_b;
     int host_step;                  // without a device schedule: the step count becomes this + 1
+    // graph-captured training: the step's call status word folded into the accumulated
+    // word by the last kernel of the step (NULL: the caller does it)
+    const unsigned* fold_call;
+    unsigned* fold_acc;
 };
 
 // Gradient of weight (o, i) or bias o of layer l from the member's partials, each summed
@@ -1806,8 +1810,29 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs A, long long P) {
     float* am = reinterpret_cast<float*>(mb + A.m_b);
     float* av = reinterpret_cast<float*>(mb + A.v_b);
     bf16* wi = reinterpret_cast<bf16*>(mb + A.wi_b);
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < P / 4;
-         q += (long long)gridDim.x * blockDim.x) {
+    // The output layer's bias gradient is a sum of bias_n[4] per-tile, per-warp partials:
+    // summed by one warp of the block that updates those biases (lane j adds partials j,
+    // j + 32, ... in order, then a shuffle tree, which leaves the same value in every lane),
+    // before the block's parameters, instead of by one thread.
+    __shared__ float g_out[N_OUT];
+    const long long span = (long long)gridDim.x * blockDim.x;
+    if (((A.po.b_off[4] / 4) % span) / blockDim.x == blockIdx.x && threadIdx.x < 32) {
+        const float* bp = reinterpret_cast<const float*>(reg + A.bias_b[4]);
+        float acc[N_OUT] = {};
+#pragma unroll 8
+        for (int j = threadIdx.x; j < A.bias_n[4]; j += 32)
+#pragma unroll
+            for (int c = 0; c < N_OUT; ++c) acc[c] += bp[(long long)j * A.bias_ld[4] + c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int c = 0; c < N_OUT; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int c = 0; c < N_OUT; ++c) g_out[c] = acc[c];
+    }
+    __syncthreads();
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < P / 4; q += span) {
         const long long idx = q * 4;
         int l, o, i;
         bool is_w;
@@ -1827,6 +1852,9 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs A, long long P) {
                                    : split_sum4(reinterpret_cast<const float*>(reg + A.bias_b[l]),
                                                 A.bias_ld[l], A.bias_n[l], o);
             g[0] = g4.x; g[1] = g4.y; g[2] = g4.z; g[3] = g4.w;
+        } else if (l == 4 && !is_w) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) g[e] = e < n_real ? g_out[o + e] : 0.f;
         } else {
 #pragma unroll
             for (int e = 0; e < 4; ++e)
@@ -1857,6 +1885,11 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs A, long long P) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         int* st = reinterpret_cast<int*>(mb + A.step_b);
         *st = A.dev_sched ? *st + 1 : A.host_step + 1;
+        // every other kernel of the step has finished (stream order; Adam sets no status)
+        if (A.fold_acc && k == 0) {
+            const unsigned v = A.fold_call[ST_CALL];
+            if (v) atomicOr(&A.fold_acc[ST_ASYNC], v);
+        }
     }
 }
 
@@ -2132,7 +2165,7 @@ static fos_status train_step(Workspace* ws, int slot, uint8_t* model, int n_memb
                              const float* feat, const float* targets, long long n_rows, int B,
                              unsigned seed, unsigned seed_mul, unsigned step, const int* rows,
                              float lr, float* grad_out, unsigned* status, cudaStream_t s,
-                             const DevSched* ds = nullptr) {
+                             const DevSched* ds = nullptr, bool fold_status = false) {
     static bool attr_set[64] = {};
     if (!attr_set[ws->device]) {
         FOS_CUDA_TRY(cudaFuncSetAttribute(train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2284,6 +2317,10 @@ static fos_status train_step(Workspace* ws, int slot, uint8_t* model, int n_memb
     a.dev_sched = ds ? 1 : 0;
     a.sched_b = w.sched_b;
     a.host_step = (int)step;
+    if (fold_status) {
+        a.fold_call = status;
+        a.fold_acc = ws->status;
+    }
     adam_kernel<<<dim3(qblocks, (unsigned)n_members), 256, 0, s>>>(a, LAY.P);
     return from_cuda(cudaGetLastError());
 }
@@ -2328,12 +2365,12 @@ static fos_status enqueue_fit_step(Workspace* ws, const FitKey& k, cudaStream_t 
     const unsigned seed = (unsigned)(k.seed ^ (k.seed >> 32));
     fos_status st = train_step(ws, 0, (uint8_t*)k.model, k.n_members, 0, k.feat, k.targets,
                                k.n_rows, k.B, seed, 0x9E3779B9u, 0, nullptr, 1.0f, nullptr, status,
-                               cs, &ds);
+                               cs, &ds, true);   // Adam folds the status word
     if (st != FOS_OK) return st;
     if (k.loss_out)
         FOS_CUDA_TRY(cudaMemcpyAsync(k.loss_out, w.loss, (size_t)k.n_members * sizeof(float),
                                      cudaMemcpyDeviceToDevice, cs));
-    return accumulate_async_status(ws, cs, region);
+    return FOS_OK;
 }
 
 static fos_status fit_graph(Workspace* ws, const FitKey& k, cudaGraphExec_t* out) {
