@@ -1703,6 +1703,14 @@ __device__ __forceinline__ bool param_locate(const ParamOffsets& po, long long i
 // k mod 4 (their loads independent, so they are in flight together), then added in order.
 __device__ __forceinline__ float split_sum(const float* v, long long stride, int n, long long e) {
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    if (n == 8) {   // the usual split count: every load issued before the first addition
+        float x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = v[k * stride + e];
+        a0 += x[0]; a1 += x[1]; a2 += x[2]; a3 += x[3];
+        a0 += x[4]; a1 += x[5]; a2 += x[6]; a3 += x[7];
+        return (a0 + a1) + (a2 + a3);
+    }
     int k = 0;
     for (; k + 4 <= n; k += 4) {
         a0 += v[(k + 0) * stride + e];
