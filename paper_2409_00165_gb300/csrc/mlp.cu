@@ -2315,8 +2315,8 @@ static fos_status train_step(Workspace* ws, int slot, uint8_t* model, int n_memb
 // ----------------------------------------------------------------------- graph training
 // Many steps of every member with no host work per step: one ensemble step (every
 // member's schedule entry from its device step counter, train_step over all members, the
-// losses, the status folded into the accumulated word) is captured once into a CUDA graph,
-// and the graph is launched once per step.
+// losses, the status folded into the accumulated word) is captured into CUDA graphs of
+// FIT_REPS steps and of one step, and a call launches as many of each as its steps need.
 struct FitKey {
     void* model;
     int n_members, B, device;
@@ -2327,6 +2327,7 @@ struct FitKey {
     const SchedOut* table;   // [n_members][table_cap]
     long long table_cap;
     unsigned long long generation;
+    long long reps;          // ensemble steps per graph launch
     bool operator==(const FitKey& o) const { return std::memcmp(this, &o, sizeof(*this)) == 0; }
 };
 struct FitGraph {
@@ -2340,6 +2341,7 @@ struct FitDev {
     int table_members = 0;
 };
 static FitDev g_fit[64];
+constexpr int FIT_REPS = 8;
 
 // Enqueues one ensemble step on stream cs (status region 1).
 static fos_status enqueue_fit_step(Workspace* ws, const FitKey& k, cudaStream_t cs) {
@@ -2369,7 +2371,8 @@ static fos_status fit_graph(Workspace* ws, const FitKey& k, cudaGraphExec_t* out
         }
     cudaGraph_t graph = nullptr;
     FOS_CUDA_TRY(cudaStreamBeginCapture(ws->side, cudaStreamCaptureModeThreadLocal));
-    fos_status st = enqueue_fit_step(ws, k, ws->side);
+    fos_status st = FOS_OK;
+    for (long long r = 0; r < k.reps && st == FOS_OK; ++r) st = enqueue_fit_step(ws, k, ws->side);
     cudaError_t ce = cudaStreamEndCapture(ws->side, &graph);
     if (st != FOS_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -2683,10 +2686,16 @@ fos_status fos_surrogate_fit(void* model, int n_members, const float* features,
         k.table = fd.table;
         k.table_cap = fd.table_cap;
         k.generation = ws->generation;
-        cudaGraphExec_t exec = nullptr;
-        st = mlp::fit_graph(ws, k, &exec);
-        if (st != FOS_OK) return st;
-        for (int i = 0; i < n_steps; ++i) FOS_CUDA_TRY(cudaGraphLaunch(exec, s));
+        // graphs of FIT_REPS steps (fewer gaps between graph launches), then single steps
+        for (const long long reps : {(long long)mlp::FIT_REPS, 1LL}) {
+            const long long n = reps > 1 ? n_steps / reps : n_steps % mlp::FIT_REPS;
+            if (n == 0) continue;
+            k.reps = reps;
+            cudaGraphExec_t exec = nullptr;
+            st = mlp::fit_graph(ws, k, &exec);
+            if (st != FOS_OK) return st;
+            for (long long i = 0; i < n; ++i) FOS_CUDA_TRY(cudaGraphLaunch(exec, s));
+        }
     }
     if (flags & FOS_ASYNC) return FOS_OK;
     st = wait_stream(s, default_timeout_ms());
