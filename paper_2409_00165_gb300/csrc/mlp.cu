@@ -815,7 +815,8 @@ struct TrainArgs {
     long long n_rows;
     const int* rows;              // the batch's rows [B] (one member), or NULL: hashed
     int B, n_tiles, n_members;
-    unsigned seed, seed_mul;      // member k draws with seed ^ (k * seed_mul)
+    unsigned seed, seed_mul;      // member k draws with seed ^ ((member0 + k) * seed_mul)
+    int member0;
     unsigned step;                // the draw's step without a device schedule
     const uint8_t* model;
     size_t member_bytes, theta_b, stats_b, wi_b, step_b;
@@ -1162,7 +1163,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) train_kernel(TrainArgs A) {
                 for (int q = 0; q < 4; ++q) {
                     const long long rown = (long long)tn * 128 + q * 32 + lane;
                     src[q] = A.rows ? (long long)A.rows[rown]
-                                    : draw_row(A.seed ^ ((unsigned)kn * A.seed_mul), stepn, (int)rown,
+                                    : draw_row(A.seed ^ ((unsigned)(A.member0 + kn) * A.seed_mul), stepn, (int)rown,
                                                A.n_rows);
                 }
                 float xv[4][FT_ROW_FLOATS];
@@ -2152,7 +2153,8 @@ static fos_status train_step(Workspace* ws, int slot, uint8_t* model, int n_memb
                              const float* feat, const float* targets, long long n_rows, int B,
                              unsigned seed, unsigned seed_mul, unsigned step, const int* rows,
                              float lr, float* grad_out, unsigned* status, cudaStream_t s,
-                             const DevSched* ds = nullptr, bool fold_status = false) {
+                             const DevSched* ds = nullptr, bool fold_status = false,
+                             int member0 = 0) {
     static bool attr_set[64] = {};
     if (!attr_set[ws->device]) {
         FOS_CUDA_TRY(cudaFuncSetAttribute(train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2179,6 +2181,7 @@ static fos_status train_step(Workspace* ws, int slot, uint8_t* model, int n_memb
     ta.n_members = n_members;
     ta.seed = seed;
     ta.seed_mul = seed_mul;
+    ta.member0 = member0;
     ta.step = step;
     ta.model = model;
     ta.member_bytes = LAY.bytes;
@@ -2352,10 +2355,28 @@ static fos_status enqueue_fit_step(Workspace* ws, const FitKey& k, cudaStream_t 
     const int* bases = reinterpret_cast<const int*>(k.table + (long long)k.n_members * k.table_cap);
     const DevSched ds{k.table, k.table_cap, bases};
     const unsigned seed = (unsigned)(k.seed ^ (k.seed >> 32));
-    fos_status st = train_step(ws, 0, (uint8_t*)k.model, k.n_members, 0, k.feat, k.targets,
-                               k.n_rows, k.B, seed, 0x9E3779B9u, 0, nullptr, 1.0f, nullptr, status,
-                               cs, &ds, true);   // Adam folds the status word
+    // The members in two halves on parallel branches, each its own train_kernel, weight
+    // gradients and Adam: the weight gradients and Adam of one half run beside the other
+    // half's last tiles instead of after every member's (the members are independent).
+    const int h = k.n_members >= 2 ? k.n_members / 2 : k.n_members;
+    cudaStream_t s2 = w.side[2];
+    if (h < k.n_members) {
+        FOS_CUDA_TRY(cudaEventRecord(w.ev_fork[2], cs));
+        FOS_CUDA_TRY(cudaStreamWaitEvent(s2, w.ev_fork[2], 0));
+    }
+    fos_status st = train_step(ws, 0, (uint8_t*)k.model, h, 0, k.feat, k.targets, k.n_rows, k.B,
+                               seed, 0x9E3779B9u, 0, nullptr, 1.0f, nullptr, status, cs, &ds,
+                               true);   // Adam folds the status word
     if (st != FOS_OK) return st;
+    if (h < k.n_members) {
+        const DevSched ds2{k.table + (long long)h * k.table_cap, k.table_cap, bases + h};
+        st = train_step(ws, 1, (uint8_t*)k.model + (size_t)h * LAY.bytes, k.n_members - h, h,
+                        k.feat, k.targets, k.n_rows, k.B, seed, 0x9E3779B9u, 0, nullptr, 1.0f,
+                        nullptr, status, s2, &ds2, true, h);
+        if (st != FOS_OK) return st;
+        FOS_CUDA_TRY(cudaEventRecord(w.ev_join[2], s2));
+        FOS_CUDA_TRY(cudaStreamWaitEvent(cs, w.ev_join[2], 0));
+    }
     if (k.loss_out)
         FOS_CUDA_TRY(cudaMemcpyAsync(k.loss_out, w.loss, (size_t)k.n_members * sizeof(float),
                                      cudaMemcpyDeviceToDevice, cs));
