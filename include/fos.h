@@ -419,11 +419,11 @@ fos_status fos_surrogate_train_step(void* model, int member, const float* featur
  * fos_surrogate_init / fos_surrogate_load, saved with the buffer): step g draws its batch
  * from a hash of (seed, member, g), uses Adam's t = g + 1 and the cosine learning rate
  * lr_min + (lr_max - lr_min)(1 + cos(pi min(g - schedule_origin, schedule_total) /
- * schedule_total))/2 (g - schedule_origin clamped at 0).  One step of the whole ensemble
- * is captured once into a CUDA graph (members of different slots, member mod 4, on
- * parallel branches; the step counts live on the device, and the learning rate and bias
- * corrections of the call's steps are a table the call writes first, after waiting for
- * the device's earlier work) and the graph is launched n_steps times on `stream`.
+ * schedule_total))/2 (g - schedule_origin clamped at 0).  Ensemble steps are captured
+ * once into CUDA graphs of 8 steps and of 1 step (each step: the two halves of the
+ * ensemble on parallel branches; the step counts live on the device, and the learning
+ * rate and bias corrections of the call's steps are a table the call writes first, after
+ * waiting for the device's earlier work), launched on `stream` as often as n_steps needs.
  *   loss_out: device float [n_members] or NULL: each member's loss of its last step.
  * Errors of the device work are reported like FOS_ASYNC calls (fos_sync_status); without
  * FOS_ASYNC the call waits for the stream and returns that status itself.  Batch as for

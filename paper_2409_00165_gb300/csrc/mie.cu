@@ -338,7 +338,7 @@ __device__ bool sphere_eval_large(double lam, double r, cx n_p, cx n_m, double2*
             div_pair(mul_sub(qa, psi_n, psi_0), mul_sub(qa, xi_n, xi_0), mul_sub(qb, psi_n, psi_0),
                      mul_sub(qb, xi_n, xi_0), an, bn);
             accumulate(S, n, nmax, an, bn, a_prev, b_prev);
-            if (n > n_w) {
+            if (!up_all && n > n_w) {   // (up_all: the sums end at n_last)
                 const double t = (2.0 * dn + 1.0) *
                                  (fabs(an.re) + fabs(an.im) + fabs(bn.re) + fabs(bn.im));
                 const double ref = fabs(S.ext_re) + fabs(S.ext_im) + S.sca;
@@ -422,7 +422,7 @@ __device__ bool sphere_eval(double lam, double r, cx n_p, cx n_m, double2* colY,
         div_pair(mul_sub(qa, psi_n, psi_0), mul_sub(qa, xi_n, xi_0), mul_sub(qb, psi_n, psi_0),
                  mul_sub(qb, xi_n, xi_0), an, bn);
         accumulate(S, n, nmax, an, bn, a_prev, b_prev);
-        if (n > n_w) {
+        if (!up_all && n > n_w) {   // (up_all: the sums end at n_last)
             const double t = (2.0 * dn + 1.0) *
                              (fabs(an.re) + fabs(an.im) + fabs(bn.re) + fabs(bn.im));
             const double ref = fabs(S.ext_re) + fabs(S.ext_im) + S.sca;
