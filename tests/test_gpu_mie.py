@@ -40,6 +40,31 @@ def test_layer_stacks_all_species(orc):
         assert _close(g[k], o[k]), k
 
 
+def test_host_argument_across_the_upward_psi_switch(orc):
+    """psi_n(x) of the host argument comes from its upward recurrence at every order for
+    |x| >= 1.5 and from D_n(x) above |x| below that: spheres on both sides of the switch
+    and up to |x| = 300 (the chunked pass for large spheres), with particles nearly
+    index-matched (m = 1.01), below the host index, absorbing and strongly absorbing."""
+    wl = np.array([1.0])
+    nm = np.array([[1.48 + 2e-5j]])
+    xs = np.array([1.45, 1.499, 1.5, 1.501, 1.6, 3.0, 10.0, 40.0, 150.0, 300.0])
+    idx = [1.495 + 0j, 1.2 + 0j, 2.5 + 1e-4j, 3.5 + 0.5j]
+    radius = np.repeat(xs / (2 * np.pi * 1.48), len(idx))
+    n_p = np.array([[c] for _ in xs for c in idx])
+    n_sp = radius.size
+    m = dict(wl=wl, nm=nm, n_groups=1, species_group=np.zeros(n_sp, np.int32), n_p=n_p,
+             radius=radius, vol_frac=np.full(n_sp, 0.001))
+    g, o = gpu_mie(m), _oracle(orc, m)
+    # rel 1e-10, and 1e-9 for the spheres of the chunked pass (|x| >= 150), as for the
+    # large spheres below (their sums run over hundreds of orders)
+    rtol = np.where(np.repeat(xs, len(idx)) >= 150, 1e-9, RTOL)[:, None]
+    for k in ("q_ext", "q_sca", "g_species"):
+        ok = "g_sp" if k == "g_species" else k
+        a, b = np.asarray(g[k]), np.asarray(o[ok])
+        rel = np.abs(a - b) / np.abs(b)
+        assert np.all(rel <= rtol), (k, np.argmax(rel / rtol), rel.max())
+
+
 def test_edge_sizes_and_indices(orc):
     rng = np.random.default_rng(11)
     wl = np.array([0.3, 0.31, 0.5, 1.0, 2.5])
