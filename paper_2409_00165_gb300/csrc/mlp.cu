@@ -1792,17 +1792,24 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs A, long long P) {
         c1 = so->c1;
         c2 = so->c2;
     }
+    const float lr_c1 = lr / c1, ic2 = 1.0f / c2;
     float* theta = reinterpret_cast<float*>(mb + A.theta_b);
     float* am = reinterpret_cast<float*>(mb + A.m_b);
     float* av = reinterpret_cast<float*>(mb + A.v_b);
     bf16* wi = reinterpret_cast<bf16*>(mb + A.wi_b);
-    // The output layer's bias gradient is a sum of bias_n[4] per-tile, per-warp partials:
-    // summed by one warp of the block that updates those biases (lane j adds partials j,
-    // j + 32, ... in order, then a shuffle tree, which leaves the same value in every lane),
-    // before the block's parameters, instead of by one thread.
-    __shared__ float g_out[N_OUT];
-    const long long span = (long long)gridDim.x * blockDim.x;
-    if (((A.po.b_off[4] / 4) % span) / blockDim.x == blockIdx.x && threadIdx.x < 32) {
+    // The output layer's biases are updated by an extra last block: their gradient is a sum
+    // of bias_n[4] per-tile, per-warp partials, which its first warp adds (lane j adds
+    // partials j, j + 32, ... in order, then a shuffle tree, which leaves the same value in
+    // every lane), so that no block of the parameter loop waits for that sum.
+    if (blockIdx.x == gridDim.x - 1) {
+        if (threadIdx.x >= 32) return;
+        const long long b4 = A.po.b_off[4];
+        float mo = 0.f, vo = 0.f, to = 0.f;
+        if (threadIdx.x < N_OUT) {
+            mo = am[b4 + threadIdx.x];
+            vo = av[b4 + threadIdx.x];
+            to = theta[b4 + threadIdx.x];
+        }
         const float* bp = reinterpret_cast<const float*>(reg + A.bias_b[4]);
         float acc[N_OUT] = {};
 #pragma unroll 8
@@ -1813,11 +1820,21 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs A, long long P) {
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
             for (int c = 0; c < N_OUT; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
-        if (threadIdx.x == 0)
+        if (threadIdx.x < N_OUT) {
+            float gg = acc[0];
 #pragma unroll
-            for (int c = 0; c < N_OUT; ++c) g_out[c] = acc[c];
+            for (int c = 1; c < N_OUT; ++c)
+                if (threadIdx.x == c) gg = acc[c];
+            mo = A.b1 * mo + (1.f - A.b1) * gg;
+            vo = A.b2 * vo + (1.f - A.b2) * gg * gg;
+            to = to - __fdividef(lr_c1 * mo, sqrtf(vo * ic2) + A.eps);
+            am[b4 + threadIdx.x] = mo;
+            av[b4 + threadIdx.x] = vo;
+            theta[b4 + threadIdx.x] = to;
+        }
+        return;
     }
-    __syncthreads();
+    const long long span = (long long)(gridDim.x - 1) * blockDim.x;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < P / 4; q += span) {
         const long long idx = q * 4;
         int l, o, i;
@@ -1826,7 +1843,7 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs A, long long P) {
         // the four parameters: weights (o, i .. i + 3) or biases o .. o + 3 of layer l
         const int n_real = is_w ? (o < real_out(l) ? min(4, max(0, real_in(l) - i)) : 0)
                                 : min(4, max(0, real_out(l) - o));
-        if (n_real == 0) continue;
+        if (n_real == 0 || (l == 4 && !is_w)) continue;   // output biases: the last block
         const float4 m0 = *reinterpret_cast<const float4*>(am + idx);
         const float4 v0 = *reinterpret_cast<const float4*>(av + idx);
         const float4 t0 = *reinterpret_cast<const float4*>(theta + idx);
@@ -1838,9 +1855,6 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs A, long long P) {
                                    : split_sum4(reinterpret_cast<const float*>(reg + A.bias_b[l]),
                                                 A.bias_ld[l], A.bias_n[l], o);
             g[0] = g4.x; g[1] = g4.y; g[2] = g4.z; g[3] = g4.w;
-        } else if (l == 4 && !is_w) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) g[e] = e < n_real ? g_out[o + e] : 0.f;
         } else {
 #pragma unroll
             for (int e = 0; e < 4; ++e)
@@ -1853,7 +1867,9 @@ __global__ void __launch_bounds__(256) adam_kernel(AdamArgs A, long long P) {
             if (e >= n_real) continue;   // padding: stays 0
             mm[e] = A.b1 * mm[e] + (1.f - A.b1) * g[e];
             vv[e] = A.b2 * vv[e] + (1.f - A.b2) * g[e] * g[e];
-            th[e] = th[e] - lr * (mm[e] / c1) / (sqrtf(vv[e] / c2) + A.eps);
+            // lr m_hat / (sqrt(v_hat) + eps) with the bias corrections as reciprocals and
+            // the quotient by the SFU reciprocal (a few ulp; Adam needs no more)
+            th[e] = th[e] - __fdividef(lr_c1 * mm[e], sqrtf(vv[e] * ic2) + A.eps);
         }
         *reinterpret_cast<float4*>(am + idx) = make_float4(mm[0], mm[1], mm[2], mm[3]);
         *reinterpret_cast<float4*>(av + idx) = make_float4(vv[0], vv[1], vv[2], vv[3]);
@@ -2311,7 +2327,7 @@ static fos_status train_step(Workspace* ws, int slot, uint8_t* model, int n_memb
         a.fold_call = status;
         a.fold_acc = ws->status;
     }
-    adam_kernel<<<dim3(qblocks, (unsigned)n_members), 256, 0, s>>>(a, LAY.P);
+    adam_kernel<<<dim3(qblocks + 1, (unsigned)n_members), 256, 0, s>>>(a, LAY.P);
     return from_cuda(cudaGetLastError());
 }
 
