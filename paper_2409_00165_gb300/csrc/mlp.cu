@@ -1400,6 +1400,9 @@ __global__ void __launch_bounds__(FT_THREADS, 1) train_kernel(TrainArgs A) {
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, FI_TMEM_COLS);
+    // the weight-gradient launch that follows may start (programmatic dependent launch;
+    // it waits in griddepcontrol.wait until this grid has completed)
+    asm volatile("griddepcontrol.launch_dependents;");
 }
 
 // ----------------------------------------------------------------- weight gradients
@@ -1491,6 +1494,9 @@ __global__ void __launch_bounds__(128, 1) dw_kernel(const __grid_constant__ DwAr
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot_ptr;
+    // launched as a programmatic dependent of train_kernel: its outputs are complete and
+    // visible after this (at once without such a launch)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     if (threadIdx.x == 0) {
         bool ok = true;
@@ -2275,8 +2281,18 @@ static fos_status train_step(Workspace* ws, int slot, uint8_t* model, int n_memb
             d.part_ld[l - 1] = 256;
             d.bias_b[l - 1] = w.bias_b[l];
         }
-        dw_kernel<128><<<dim3(4, 3 * n_members, splits), 128, DwSmem<128>::ALLOC, s>>>(d);
-        FOS_CUDA_TRY(cudaGetLastError());
+        // a programmatic dependent of train_kernel: its prologue overlaps that grid's end
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(4, 3 * n_members, splits);
+        cfg.blockDim = dim3(128, 1, 1);
+        cfg.dynamicSmemBytes = DwSmem<128>::ALLOC;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        FOS_CUDA_TRY(cudaLaunchKernelEx(&cfg, dw_kernel<128>, d));
     }
     FOS_CUDA_TRY(cudaStreamWaitEvent(s, w.ev_join[slot], 0));
 
