@@ -341,6 +341,15 @@ __device__ __forceinline__ void warp_flush(bool want, int tag, unsigned c0, unsi
 
 enum { O_R = 0, O_A = 1, O_T = 2, O_X = 3 };
 
+// Events per live photon between the warp's refill votes.  Measured on the benchmark
+// legs (photon-steps/s against 4 events): 8 gives +2.4 % on the 400-wavelength paint
+// layer (228 collisions per photon), +2.4 % on the 64-design stack batch, +2.5 % on the
+// core-shell media, but -7 % on the dilute size-distribution layer (9 collisions per
+// photon), where finished lanes wait longer; 16 gives +3.6 % on the paint layer and -22 %
+// on the dilute layer.  A vote counting the free lanes after every event or every few
+// events measured no faster than 4 on the paint layer.
+constexpr int WALK_EVENTS_PER_REFILL = 8;
+
 // The walk.  BLOCK threads per block and MINB resident blocks per SM bound the
 // registers (28 resident warps at 64-128 threads: 72 registers, which hide the latency
 // of the dependent Philox and float chains better than 24 warps at 80 registers).
@@ -484,11 +493,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) walk_kernel(WalkArgs A) {
         }
         if (!__any_sync(FULL, alive)) break;   // refill ended: queue exhausted
 
-        // ---------------- four events per live photon between refills (a lane whose photon
-        // ends early waits up to three events for the next refill: cheaper than the refill
-        // vote on every event; measured +2 % exact, +4 % fast against one event)
+        // ---------------- WALK_EVENTS_PER_REFILL events per live photon between refills (a
+        // lane whose photon ends early waits for the next refill: cheaper than the refill
+        // vote on every event)
 #pragma unroll 1
-        for (int rep = 0; rep < 4; ++rep)
+        for (int rep = 0; rep < WALK_EVENTS_PER_REFILL; ++rep)
         if (alive) {
             if (ev >= A.max_events) {
                 finish(O_X);
