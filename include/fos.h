@@ -267,7 +267,9 @@ fos_status fos_solar_weighted(int n_stacks, int n_wl, const double* wl, const do
 /* Launch shape of the walk kernel: threads per block (multiple of 32, 32..256; the
  * kernel is compiled for 64, 96, 128 and 256 and a smaller block runs the next larger
  * variant) and photons per thread per work unit (a warp claims 32*ppt photons at a
- * time).  fos_mc_set_tuning(0, 0) returns to autotuned/default shapes (128, 8).
+ * time).  fos_mc_set_tuning(0, 0) returns to autotuned/default shapes (128, 8).  A shape
+ * set here runs with the default refill cadence (8 events per live photon between a
+ * warp's refill votes); autotuned shapes carry the cadence the autotuner chose.
  * fos_mc_get_tuning reports the shape a call with `flags` (FOS_FAST_WALK or 0) would use
  * for this batch shape. */
 fos_status fos_mc_set_tuning(int block, int photons_per_thread);
@@ -275,10 +277,12 @@ fos_status fos_mc_get_tuning(const fos_mc_batch* batch, unsigned flags, int* blo
                              int* photons_per_thread);
 
 /* The launch-shape autotuner: times every (block in 64, 96, 128, 256) x (photons per
- * thread in 4, 8, 16) on a copy of `batch` whose photon budgets are all scaled by one
- * factor (to about 2^26 photons in total, each non-empty item keeping at least one), so
- * the probe keeps the batch's budget distribution, and caches the fastest for batches of
- * this shape and walk (flags: FOS_FAST_WALK or 0).  Writes it to *block, *ppt if
+ * thread in 4, 8, 16) at 8 events per live photon between a warp's refill votes, then 4
+ * and 16 events at the fastest of those, on a copy of `batch` whose photon budgets are all
+ * scaled by one factor (to about 2^26 photons in total, each non-empty item keeping at
+ * least one), so the probe keeps the batch's budget distribution, and caches the fastest
+ * for batches of this shape and walk (flags: FOS_FAST_WALK or 0).  The cadence changes no
+ * result (every photon's walk is a function of its seed, item and id).  Writes it to *block, *ppt if
  * non-NULL.  fos_mc_spectrum with FOS_AUTOTUNE runs it first. */
 fos_status fos_mc_autotune(const fos_mc_batch* batch, unsigned flags, void* stream, int* block,
                            int* photons_per_thread);

@@ -243,6 +243,7 @@ static const void* walk_fn(bool fast, int block) {
 struct Tuning {
     int block = 128;
     int ppt = 8;
+    int epr = WALK_EVENTS_PER_REFILL;   // events per live photon between refill votes
 };
 
 struct GraphKey {
@@ -250,7 +251,7 @@ struct GraphKey {
     long long* counts;
     int* log;
     long long log_stride;
-    int block, ppt, inject, device, fast;
+    int block, ppt, epr, inject, device, fast;
     unsigned long long* times;
     unsigned long long generation;
 };
@@ -369,6 +370,7 @@ static fos_status enqueue_walk(Workspace* ws, const fos_mc_batch* b, long long n
     wa.max_layers = b->max_layers;
     wa.unit = unit;
     wa.scale = scale;
+    wa.events_per_refill = tu.epr;
     {
         unsigned k0 = (unsigned)(b->seed & 0xffffffffull), k1 = (unsigned)(b->seed >> 32);
         for (int r = 0; r < 10; ++r) {
@@ -427,6 +429,7 @@ static fos_status launch(Workspace* ws, const fos_mc_batch* b, long long n_run,
     key.log_stride = log_stride;
     key.block = tu.block;
     key.ppt = tu.ppt;
+    key.epr = tu.epr;
     key.inject = inject;
     key.device = ws->device;
     key.fast = fast ? 1 : 0;
@@ -479,9 +482,10 @@ static fos_status launch(Workspace* ws, const fos_mc_batch* b, long long n_run,
 // so that the probe measures the steady state rather than the tail of its last units.
 constexpr double PROBE_PHOTONS = 67108864.0;   // 2^26
 
-// Times every (block, ppt) candidate on a copy of the batch whose photon budgets are all
-// scaled by one factor (so the probe keeps the batch's budget distribution; rows keep at
-// least one photon), and caches the fastest per batch shape.
+// Times every (block, ppt) candidate, then the other refill cadences at the best of those,
+// on a copy of the batch whose photon budgets are all scaled by one factor (so the probe
+// keeps the batch's budget distribution; rows keep at least one photon), and caches the
+// fastest per batch shape.
 static fos_status autotune(Workspace* ws, const fos_mc_batch* b, long long n_run, bool fast,
                            cudaStream_t s, Tuning* best) {
     const size_t cbytes = (size_t)n_run * FOS_NCOUNT * sizeof(long long);
@@ -514,37 +518,56 @@ static fos_status autotune(Workspace* ws, const fos_mc_batch* b, long long n_run
     float best_ms = 1e30f;
     Tuning bt;
     bool first = true;
+    // the fastest of two or three timed runs of one shape (the very first run is a warm-up)
+    auto probe = [&](const Tuning& tu, float* out_ms) -> fos_status {
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < (first ? 3 : 2); ++rep) {
+            fos_status r = enqueue_pack(ws, b, n_run, ws->tune_counts, nullptr, 0, 0, s);
+            if (r != FOS_OK) return r;
+            cudaEventRecord(e0, s);
+            r = enqueue_walk(ws, b, n_run, ws->tune_counts, nullptr, 0, tu, scale, fast, nullptr, s);
+            if (r != FOS_OK) return r;
+            cudaEventRecord(e1, s);
+            r = wait_stream(s, default_timeout_ms());
+            if (r != FOS_OK) return r;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if ((rep > 0 || !first) && ms < ms_min) ms_min = ms;
+        }
+        first = false;
+        if (verbose)
+            fprintf(stderr, "fos autotune: %s block %d ppt %d events per refill %d: %.3f ms\n",
+                    fast ? "fast" : "exact", tu.block, tu.ppt, tu.epr, ms_min);
+        *out_ms = ms_min;
+        return FOS_OK;
+    };
+    // (block, photons per thread) at the default refill cadence, then the other cadences at
+    // the best of those
     for (int bl : WALK_BLOCKS) {
         for (int pp : ppts) {
             Tuning tu;
             tu.block = bl;
             tu.ppt = pp;
-            float ms_min = 1e30f;
-            for (int rep = 0; rep < (first ? 3 : 2); ++rep) {
-                st = enqueue_pack(ws, b, n_run, ws->tune_counts, nullptr, 0, 0, s);
-                if (st != FOS_OK) break;
-                cudaEventRecord(e0, s);
-                st = enqueue_walk(ws, b, n_run, ws->tune_counts, nullptr, 0, tu, scale, fast,
-                                  nullptr, s);
-                if (st != FOS_OK) break;
-                cudaEventRecord(e1, s);
-                st = wait_stream(s, default_timeout_ms());
-                if (st != FOS_OK) break;
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if ((rep > 0 || !first) && ms < ms_min) ms_min = ms;
-            }
-            first = false;
+            float ms = 0.f;
+            st = probe(tu, &ms);
             if (st != FOS_OK) break;
-            if (verbose)
-                fprintf(stderr, "fos autotune: %s block %d ppt %d: %.3f ms\n",
-                        fast ? "fast" : "exact", bl, pp, ms_min);
-            if (ms_min < best_ms) {
-                best_ms = ms_min;
+            if (ms < best_ms) {
+                best_ms = ms;
                 bt = tu;
             }
         }
         if (st != FOS_OK) break;
+    }
+    for (int epr : WALK_EVENTS_PER_REFILL_ALT) {
+        if (st != FOS_OK) break;
+        Tuning tu = bt;
+        tu.epr = epr;
+        float ms = 0.f;
+        st = probe(tu, &ms);
+        if (st == FOS_OK && ms < best_ms) {
+            best_ms = ms;
+            bt = tu;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

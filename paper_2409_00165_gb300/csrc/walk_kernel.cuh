@@ -67,6 +67,7 @@ struct WalkArgs {
     long long log_stride;
     unsigned* status;
     unsigned long long* cta_times;  // optional [2 * grid]: start, end (ns) of each block
+    int events_per_refill;          // events per live photon between the warp's refill votes
 };
 
 // Photons of a row run by this launch (the scaled count used by the autotuner's probe).
@@ -341,14 +342,16 @@ __device__ __forceinline__ void warp_flush(bool want, int tag, unsigned c0, unsi
 
 enum { O_R = 0, O_A = 1, O_T = 2, O_X = 3 };
 
-// Events per live photon between the warp's refill votes.  Measured on the benchmark
-// legs (photon-steps/s against 4 events): 8 gives +2.4 % on the 400-wavelength paint
-// layer (228 collisions per photon), +2.4 % on the 64-design stack batch, +2.5 % on the
+// Events per live photon between the warp's refill votes (WalkArgs::events_per_refill):
+// the default, and the other values the autotuner tries.  Measured on the benchmark legs
+// (photon-steps/s against 4 events): 8 gives +2.4 % on the 400-wavelength paint layer
+// (228 collisions per photon), +2.4 % on the 64-design stack batch, +2.5 % on the
 // core-shell media, but -7 % on the dilute size-distribution layer (9 collisions per
 // photon), where finished lanes wait longer; 16 gives +3.6 % on the paint layer and -22 %
 // on the dilute layer.  A vote counting the free lanes after every event or every few
 // events measured no faster than 4 on the paint layer.
 constexpr int WALK_EVENTS_PER_REFILL = 8;
+constexpr int WALK_EVENTS_PER_REFILL_ALT[] = {4, 16};
 
 // The walk.  BLOCK threads per block and MINB resident blocks per SM bound the
 // registers (28 resident warps at 64-128 threads: 72 registers, which hide the latency
@@ -493,11 +496,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) walk_kernel(WalkArgs A) {
         }
         if (!__any_sync(FULL, alive)) break;   // refill ended: queue exhausted
 
-        // ---------------- WALK_EVENTS_PER_REFILL events per live photon between refills (a
-        // lane whose photon ends early waits for the next refill: cheaper than the refill
-        // vote on every event)
+        // ---------------- events_per_refill events per live photon between refills (a lane
+        // whose photon ends early waits for the next refill: cheaper than the refill vote
+        // on every event)
 #pragma unroll 1
-        for (int rep = 0; rep < WALK_EVENTS_PER_REFILL; ++rep)
+        for (int rep = 0; rep < A.events_per_refill; ++rep)
         if (alive) {
             if (ev >= A.max_events) {
                 finish(O_X);
