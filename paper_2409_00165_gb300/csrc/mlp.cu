@@ -2077,6 +2077,9 @@ struct TrainWs {
     // the weight gradients of layers 0 and 4 run on a side stream beside those of 1-3
     cudaStream_t side[TRAIN_SLOTS] = {};
     cudaEvent_t ev_fork[TRAIN_SLOTS] = {}, ev_join[TRAIN_SLOTS] = {};
+    // graph-captured training: the branches of the member groups after the first
+    cudaStream_t branch[TRAIN_SLOTS] = {};
+    cudaEvent_t ev_bfork[TRAIN_SLOTS] = {}, ev_bjoin[TRAIN_SLOTS] = {};
 };
 static TrainWs g_tws[64];
 
@@ -2136,6 +2139,9 @@ static fos_status ensure_train_ws(int dev, int B, int regions, Workspace* ws) {
             FOS_CUDA_TRY(cudaStreamCreateWithFlags(&w.side[i], cudaStreamNonBlocking));
             FOS_CUDA_TRY(cudaEventCreateWithFlags(&w.ev_fork[i], cudaEventDisableTiming));
             FOS_CUDA_TRY(cudaEventCreateWithFlags(&w.ev_join[i], cudaEventDisableTiming));
+            FOS_CUDA_TRY(cudaStreamCreateWithFlags(&w.branch[i], cudaStreamNonBlocking));
+            FOS_CUDA_TRY(cudaEventCreateWithFlags(&w.ev_bfork[i], cudaEventDisableTiming));
+            FOS_CUDA_TRY(cudaEventCreateWithFlags(&w.ev_bjoin[i], cudaEventDisableTiming));
         }
     }
     return FOS_OK;
@@ -2377,6 +2383,9 @@ struct FitDev {
 };
 static FitDev g_fit[64];
 constexpr int FIT_REPS = 8;
+// member groups on parallel branches of a step (3 or 4 groups of a 4-member ensemble
+// measured no faster than 2)
+constexpr int FIT_GROUPS = 2;
 
 // Enqueues one ensemble step on stream cs (status region 1).
 static fos_status enqueue_fit_step(Workspace* ws, const FitKey& k, cudaStream_t cs) {
@@ -2385,29 +2394,28 @@ static fos_status enqueue_fit_step(Workspace* ws, const FitKey& k, cudaStream_t 
     unsigned* status = ws->status + ST_WORDS * region;
     FOS_CUDA_TRY(cudaMemsetAsync(status + ST_CALL, 0, sizeof(unsigned), cs));
     const int* bases = reinterpret_cast<const int*>(k.table + (long long)k.n_members * k.table_cap);
-    const DevSched ds{k.table, k.table_cap, bases};
     const unsigned seed = (unsigned)(k.seed ^ (k.seed >> 32));
-    // The members in two halves on parallel branches, each its own train_kernel, weight
-    // gradients and Adam: the weight gradients and Adam of one half run beside the other
-    // half's last tiles instead of after every member's (the members are independent).
-    const int h = k.n_members >= 2 ? k.n_members / 2 : k.n_members;
-    cudaStream_t s2 = w.side[2];
-    if (h < k.n_members) {
-        FOS_CUDA_TRY(cudaEventRecord(w.ev_fork[2], cs));
-        FOS_CUDA_TRY(cudaStreamWaitEvent(s2, w.ev_fork[2], 0));
+    // The members in FIT_GROUPS groups on parallel branches, each its own train_kernel,
+    // weight gradients and Adam: the weight gradients and Adam of one group run beside the
+    // other groups' tiles instead of after every member's (the members are independent).
+    const int G = k.n_members < FIT_GROUPS ? k.n_members : FIT_GROUPS;
+    for (int g = 1; g < G; ++g) {
+        FOS_CUDA_TRY(cudaEventRecord(w.ev_bfork[g], cs));
+        FOS_CUDA_TRY(cudaStreamWaitEvent(w.branch[g], w.ev_bfork[g], 0));
     }
-    fos_status st = train_step(ws, 0, (uint8_t*)k.model, h, 0, k.feat, k.targets, k.n_rows, k.B,
-                               seed, 0x9E3779B9u, 0, nullptr, 1.0f, nullptr, status, cs, &ds,
-                               true);   // Adam folds the status word
-    if (st != FOS_OK) return st;
-    if (h < k.n_members) {
-        const DevSched ds2{k.table + (long long)h * k.table_cap, k.table_cap, bases + h};
-        st = train_step(ws, 1, (uint8_t*)k.model + (size_t)h * LAY.bytes, k.n_members - h, h,
-                        k.feat, k.targets, k.n_rows, k.B, seed, 0x9E3779B9u, 0, nullptr, 1.0f,
-                        nullptr, status, s2, &ds2, true, h);
+    for (int g = 0; g < G; ++g) {
+        const int m0 = g * k.n_members / G, m1 = (g + 1) * k.n_members / G;
+        const DevSched dsg{k.table + (long long)m0 * k.table_cap, k.table_cap, bases + m0};
+        cudaStream_t sg = g == 0 ? cs : w.branch[g];
+        const fos_status st = train_step(ws, g, (uint8_t*)k.model + (size_t)m0 * LAY.bytes,
+                                         m1 - m0, m0, k.feat, k.targets, k.n_rows, k.B, seed,
+                                         0x9E3779B9u, 0, nullptr, 1.0f, nullptr, status, sg, &dsg,
+                                         true, m0);   // Adam folds the status word
         if (st != FOS_OK) return st;
-        FOS_CUDA_TRY(cudaEventRecord(w.ev_join[2], s2));
-        FOS_CUDA_TRY(cudaStreamWaitEvent(cs, w.ev_join[2], 0));
+    }
+    for (int g = 1; g < G; ++g) {
+        FOS_CUDA_TRY(cudaEventRecord(w.ev_bjoin[g], w.branch[g]));
+        FOS_CUDA_TRY(cudaStreamWaitEvent(cs, w.ev_bjoin[g], 0));
     }
     if (k.loss_out)
         FOS_CUDA_TRY(cudaMemcpyAsync(k.loss_out, w.loss, (size_t)k.n_members * sizeof(float),
